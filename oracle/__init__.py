@@ -1,0 +1,186 @@
+"""Double-precision CPU oracle for the HySCO hot path (PyHySCO, arXiv 2403.10706).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the package smoke check and by the
+benchmark's CPU-baseline leg, never by the product path.  It is a ctypes wrapper around
+oracle/hysco_oracle.c, which shares no code with the CUDA library.
+
+All arrays are numpy, C-contiguous.  Images are float32 (the dtype the GPU path receives);
+fields, gradients and vectors are float64.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hysco_oracle.c")
+_LIB = os.path.join(_HERE, "libhysco_oracle.so")
+
+ST_FIELDS = ["J", "D", "S", "P", "gnorm", "gq", "gamma", "pcg_iters", "pcg_relres", "ls_trials"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc (IEEE semantics: no fast-math, no FP contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+class Geom(C.Structure):
+    _fields_ = [("d", C.c_int64 * 3), ("h", C.c_double * 3), ("p", C.c_int32),
+                ("pad_", C.c_int32), ("alpha", C.c_double), ("beta", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("gn_iters", C.c_int32), ("pcg_max_iters", C.c_int32),
+                ("ls_max_iters", C.c_int32), ("precond", C.c_int32), ("init", C.c_int32),
+                ("ot_blur", C.c_int32), ("contract", C.c_int32), ("pad_", C.c_int32),
+                ("pcg_rtol", C.c_double), ("armijo_c1", C.c_double), ("ot_eps", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.orc_eval.restype = C.c_int64
+        _lib.orc_eval.argtypes = [P, P, P, P, C.c_int, P, P, P, P, P, P]
+        _lib.orc_hessvec.argtypes = [P, P, P, P, C.c_int, P, P]
+        _lib.orc_hessdiag.argtypes = [P, P, P, P, C.c_int, P]
+        _lib.orc_precond.argtypes = [P, P, P, P, C.c_int, C.c_int, P, P]
+        _lib.orc_column_block.argtypes = [P, P, P, P, C.c_int, C.c_int64, P, P]
+        _lib.orc_apply_laplacian.argtypes = [P, P, P]
+        _lib.orc_ot_init.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
+        _lib.orc_blur.argtypes = [P, P]
+        _lib.orc_solve.argtypes = [P, P, P, P, P, P]
+        _lib.orc_pcg.argtypes = [P, P, P, P, C.c_int, C.c_int, P, C.c_int, C.c_double, P, P]
+        _lib.orc_phi.argtypes = [C.c_double, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def field_dims(dims, p):
+    fd = list(dims)
+    fd[p] += 1
+    return tuple(fd)
+
+
+class Problem:
+    """Geometry + weights of one correction problem: image dims, spacing (mm), PE axis,
+    alpha (smoothness) and beta (barrier) of Eq. 4."""
+
+    def __init__(self, dims, spacing, pe_dim, alpha, beta):
+        self.dims = tuple(int(x) for x in dims)
+        self.spacing = tuple(float(x) for x in spacing)
+        self.pe_dim = int(pe_dim)
+        self.fdims = field_dims(self.dims, self.pe_dim)
+        self.g = Geom((C.c_int64 * 3)(*self.dims), (C.c_double * 3)(*self.spacing),
+                      self.pe_dim, 0, float(alpha), float(beta))
+
+    def eval(self, Ip, Im, b, contract=True, grad=True, corrected=False, cells=False):
+        """Returns dict(J, D, S, P, infeasible, grad?, Tp?, Tm?, cell_p?, cell_m?)."""
+        Ip, Im, b = _f32(Ip), _f32(Im), _f64(b)
+        terms = np.zeros(4)
+        g = np.zeros(self.fdims) if grad else None
+        Tp = np.zeros(self.dims) if corrected else None
+        Tm = np.zeros(self.dims) if corrected else None
+        cp = np.zeros(self.dims, np.int32) if cells else None
+        cm = np.zeros(self.dims, np.int32) if cells else None
+        bad = lib().orc_eval(C.byref(self.g), _p(Ip), _p(Im), _p(b), int(contract), _p(terms),
+                             _p(g), _p(Tp), _p(Tm), _p(cp), _p(cm))
+        out = dict(J=terms[0], D=terms[1], S=terms[2], P=terms[3], infeasible=int(bad))
+        if grad:
+            out["grad"] = g
+        if corrected:
+            out["Tp"], out["Tm"] = Tp, Tm
+        if cells:
+            out["cell_p"], out["cell_m"] = cp, cm
+        return out
+
+    def hessvec(self, Ip, Im, b, v, contract=True):
+        Hv = np.zeros(self.fdims)
+        lib().orc_hessvec(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                          int(contract), _p(_f64(v)), _p(Hv))
+        return Hv
+
+    def hessdiag(self, Ip, Im, b, contract=True):
+        d = np.zeros(self.fdims)
+        lib().orc_hessdiag(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                           int(contract), _p(d))
+        return d
+
+    def precond(self, Ip, Im, b, r, kind, contract=True):
+        """z = M^{-1} r; kind 0 = Jacobi, 1 = per-column block."""
+        z = np.zeros(self.fdims)
+        lib().orc_precond(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                          int(contract), int(kind), _p(_f64(r)), _p(z))
+        return z
+
+    def column_block(self, Ip, Im, b, col, contract=True):
+        m = self.dims[self.pe_dim]
+        dia, off = np.zeros(m + 1), np.zeros(m)
+        lib().orc_column_block(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                               int(contract), int(col), _p(dia), _p(off))
+        return dia, off
+
+    def laplacian(self, x):
+        y = np.zeros(self.fdims)
+        lib().orc_apply_laplacian(C.byref(self.g), _p(_f64(x)), _p(y))
+        return y
+
+    def ot_init(self, Ip, Im, eps=1e-3, contract=True, blur=True, indices=False):
+        b0 = np.zeros(self.fdims)
+        kp = np.zeros(self.fdims, np.int32) if indices else None
+        km = np.zeros(self.fdims, np.int32) if indices else None
+        lib().orc_ot_init(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), float(eps),
+                          int(contract), int(blur), _p(b0), _p(kp), _p(km))
+        return (b0, kp, km) if indices else b0
+
+    def blur(self, b):
+        b = _f64(b).copy()
+        lib().orc_blur(C.byref(self.g), _p(b))
+        return b
+
+    def pcg(self, Ip, Im, b, rhs, precond=0, max_it=10, rtol=0.1, contract=True):
+        q = np.zeros(self.fdims)
+        rel = np.zeros(1)
+        it = lib().orc_pcg(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                           int(contract), int(precond), _p(_f64(rhs)), int(max_it), float(rtol),
+                           _p(q), _p(rel))
+        return q, it, rel[0]
+
+    def solve(self, Ip, Im, b=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10, precond=0,
+              init=True, ot_blur=True, contract=False, pcg_rtol=0.1, armijo_c1=1e-4,
+              ot_eps=1e-3):
+        """GN-PCG solve; returns (b, status, stats[gn_iters, len(ST_FIELDS)])."""
+        o = Opts(gn_iters, pcg_max_iters, ls_max_iters, precond, int(init), int(ot_blur),
+                 int(contract), 0, pcg_rtol, armijo_c1, ot_eps)
+        bb = np.zeros(self.fdims) if b is None else _f64(b).copy()
+        stats = np.zeros((max(gn_iters, 1), len(ST_FIELDS)))
+        st = lib().orc_solve(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), C.byref(o), _p(bb),
+                             _p(stats))
+        return bb, st, stats[:gn_iters]
+
+
+def phi(z):
+    f, df, d2f = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_phi(float(z), C.byref(f), C.byref(df), C.byref(d2f))
+    return f.value, df.value, d2f.value
