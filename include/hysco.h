@@ -1,0 +1,150 @@
+/*
+ * hysco.h -- C ABI of libhysco, the B300 (sm_103a) implementation of the hot path of the
+ * reversed-gradient-polarity field-map estimation of PyHySCO (Julian & Ruthotto,
+ * arXiv 2403.10706): the objective J(b) = D(b) + alpha S(b) + beta P(b), its gradient, the
+ * Gauss-Newton Hessian-vector product, the Jacobi and per-column block preconditioners, the 1D
+ * optimal-transport initialiser and the GN-PCG solve.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Images are C-contiguous d0 x d1 x d2 arrays (last index fastest) in DEVICE memory, element
+ *    type fixed at hysco_create (float32, bfloat16 or float16).  The phase-encoding (PE) axis is
+ *    pe_dim (0-based; the paper's command line counts from 1).  m = dims[pe_dim].
+ *  - The field map b lives on the e_p-staggered grid (Sec. 2.1, discretisation paragraph): its
+ *    dims are the image dims with dims[pe_dim] replaced by m + 1 (see hysco_field_dims).  It is
+ *    float32 in device memory and expressed in PE-voxel units (b in mm = spacing[pe_dim] * b).
+ *    The objective is the paper's physical J (spacing in mm, midpoint quadrature).
+ *  - Every pointer argument is caller-owned device memory unless stated otherwise, must be
+ *    4-byte aligned (2-byte for 16-bit images), and must not alias another argument.  The handle
+ *    owns only its own device workspace (allocated in hysco_create, freed in hysco_destroy).
+ *  - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream) and is
+ *    asynchronous: argument errors are returned before anything is enqueued; numerical outcomes
+ *    (barrier infeasibility, non-finite values) are recorded on the device and returned by
+ *    hysco_last_status, which synchronises the stream.
+ *  - A handle is not thread-safe and its calls must not overlap on different streams; distinct
+ *    handles are independent.
+ *  - Return value: hysco_status (0 = success, < 0 = error, > 0 = non-error condition).
+ */
+#ifndef HYSCO_H
+#define HYSCO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hysco_ctx* hysco_t;
+typedef struct CUstream_st* hysco_stream_t;   /* identical to cudaStream_t */
+
+typedef enum {
+  HYSCO_OK = 0,
+  HYSCO_INFEASIBLE = 1,   /* some |d_v b| >= 1: the barrier of Eq. 3 makes J = +inf */
+  HYSCO_EINVAL = -1,      /* bad argument (dims, pe_dim, spacing, weights, pointer, option) */
+  HYSCO_ECUDA = -2,       /* a CUDA runtime call failed */
+  HYSCO_ENOMEM = -3,      /* device workspace allocation failed */
+  HYSCO_ENONFINITE = -4,  /* NaN met in J (non-finite input) */
+  HYSCO_ENOTREADY = -5    /* hysco_hessvec / hysco_precond before any hysco_eval */
+} hysco_status;
+
+typedef enum { HYSCO_F32 = 0, HYSCO_BF16 = 1, HYSCO_F16 = 2 } hysco_dtype;
+typedef enum { HYSCO_PC_JACOBI = 0, HYSCO_PC_COLUMN = 1 } hysco_precond_kind;
+
+/* Options of the GN-PCG solve (Sec. 2.3.1).  hysco_default_opts fills the paper's values. */
+typedef struct {
+  int32_t gn_iters;       /* fixed number of Gauss-Newton iterations (default 10) */
+  int32_t pcg_max_iters;  /* PCG iterations per GN step, <= 64 (paper: 10) */
+  int32_t ls_max_iters;   /* Armijo trials gamma = 1, 1/2, ..., <= 16 (default 10) */
+  int32_t precond;        /* hysco_precond_kind (paper default: Jacobi) */
+  int32_t init;           /* 1 = OT initialisation (Sec. 2.2), 0 = start from b_inout */
+  int32_t ot_blur;        /* 1 = 3x3x3 Gaussian blur, sigma 1 voxel, after OT (Sec. 2.4) */
+  double pcg_rtol;        /* stop PCG when ||r|| / ||r0|| < pcg_rtol (paper: 0.1) */
+  double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
+  double ot_eps;          /* OT positivity shift factor (default 1e-3) */
+} hysco_opts;
+
+/* Per-GN-iteration record written by hysco_solve when `stats` is non-NULL (device memory,
+ * gn_iters x HYSCO_NSTATS doubles): J, D, S, P at the iterate, ||grad J||, grad^T q, accepted
+ * step gamma (0 = rejected), PCG iterations, final PCG relative residual, line-search trials. */
+enum { HYSCO_NSTATS = 10 };
+
+void hysco_default_opts(hysco_opts* opts);
+const char* hysco_strerror(int status);
+/* Library version string (static storage). */
+const char* hysco_version(void);
+
+/* Create a handle for one problem geometry (Sec. 2.1, Eq. 4):
+ *   dims[3]     image dims (each >= 1, dims[pe_dim] >= 2, total < 2^31 voxels),
+ *   spacing[3]  voxel sizes in mm (> 0),
+ *   pe_dim      phase-encoding axis 0..2,
+ *   alpha, beta smoothness and barrier weights (>= 0; the paper uses 300 and 1e-4),
+ *   img_dtype   hysco_dtype of the images passed to every later call.
+ * Allocates the device workspace on the current device.  *out is NULL on failure. */
+int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, double alpha,
+                 double beta, int img_dtype, hysco_t* out);
+void hysco_destroy(hysco_t h);
+/* Field dims (image dims with the PE extent + 1). */
+int hysco_field_dims(hysco_t h, int64_t out[3]);
+
+/* 1D optimal-transport initial field (Sec. 2.2): per PE column, shift both images to positive
+ * measures (s = max(0, -min) + eps * max|I| over both images), form the normalised cumulative
+ * sums C+- at the m + 1 nodes, invert them with the linear spline, and set
+ *   b0_k = 1/4 [ (C+^{-1}(C-(k)) - k) - (C-^{-1}(C+(k)) - k) ]
+ * (half the displacement of T- minus half that of T+, T+- = C_half^{-1} o C+-).  Columns with
+ * no mass get 0.  blur != 0 applies the separable 3x3x3 Gaussian (sigma 1 voxel, replicate
+ * boundary) of Sec. 2.4.  b_out: field-shaped float32. */
+int hysco_init_ot(hysco_t h, const void* Ip, const void* Im, float* b_out, int blur, double eps,
+                  hysco_stream_t stream);
+
+/* Objective at b (Eq. 1-5): terms_dev[0..3] = J, D, S, P (device doubles).  grad (nullable,
+ * field-shaped) receives grad J = vol [Jr^T r + alpha h^2 L b + beta/2 D^T phi'(delta)].  Also
+ * stores the per-node Gauss-Newton coefficients at b in the handle, used by hysco_hessvec and
+ * hysco_precond until the next hysco_eval / hysco_solve on this handle. */
+int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double* terms_dev,
+               float* grad, hysco_stream_t stream);
+
+/* Hv = H_J v with the Gauss-Newton Hessian of Sec. 2.3.1 about the field of the last
+ * hysco_eval: H_J = vol [Jr^T Jr + alpha h^2 L + beta/2 D^T diag(phi''(delta)) D].
+ * v, Hv: field-shaped float32. */
+int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream);
+
+/* z = M^{-1} r about the field of the last hysco_eval: kind = HYSCO_PC_JACOBI divides by the
+ * diagonal of H_J (Sec. 2.3.1); HYSCO_PC_COLUMN solves with the exact tridiagonal diagonal
+ * block of H_J belonging to each PE column (the block-diagonal preconditioner mentioned at the
+ * end of Sec. 2.3.1).  HYSCO_PC_COLUMN requires m <= 1024. */
+int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t stream);
+
+/* Corrected images at b (Eq. 1, the Jacobian-modulation correction of Sec. 2.4):
+ * Tp = I+(x + b v)(1 + d_v b), Tm = I-(x - b v)(1 - d_v b), image-shaped float32. */
+int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,
+                  float* Tm, hysco_stream_t stream);
+
+/* Full solve (Sec. 2.2 + 2.3.1): optional OT init (opts->init), then opts->gn_iters Gauss-Newton
+ * iterations b <- b + gamma q with H_J q ~= -grad J from at most pcg_max_iters PCG iterations
+ * (x0 = 0, stop at relative residual < pcg_rtol) and gamma the first of 1, 1/2, 1/4, ... that
+ * satisfies the Armijo condition J(b + gamma q) <= J(b) + c1 gamma grad^T q (none, or
+ * grad^T q >= 0: the iterate is kept).  The iteration count is fixed; the loop stops early only
+ * when J(b) is not finite (hysco_last_status then reports it).  b_inout: field-shaped float32,
+ * read when opts->init == 0, always written.  stats: nullable, see HYSCO_NSTATS. */
+int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout,
+                const hysco_opts* opts, double* stats, hysco_stream_t stream);
+
+/* Synchronises `stream` and returns the numerical status of the last hysco_eval / hysco_solve /
+ * hysco_init_ot on this handle: HYSCO_OK, HYSCO_INFEASIBLE or HYSCO_ENONFINITE (or HYSCO_ECUDA
+ * when the stream reports an error). */
+int hysco_last_status(hysco_t h, hysco_stream_t stream);
+
+/* Diagnostics: the same kernels with extra outputs.
+ * hysco_cell_indices: interpolation cell indices floor(t+-) of every cell at b (image-shaped
+ * int32; positions outside [-2, m + 1] are reported clamped to that range).
+ * hysco_ot_indices: the merge indices k* = min{k : C(k+1) >= r} of the two inverse-CDF
+ * lookups C-^{-1}(C+(k)) and C+^{-1}(C-(k)) of hysco_init_ot (field-shaped int32). */
+int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell_m,
+                       hysco_stream_t stream);
+int hysco_ot_indices(hysco_t h, const void* Ip, const void* Im, double eps, int32_t* kidx_p,
+                     int32_t* kidx_m, hysco_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYSCO_H */

@@ -1,0 +1,345 @@
+// libhysco C ABI (include/hysco.h): handle, workspace, argument checks and the GN-PCG driver.
+//
+// The solve is a fixed, data-independent launch sequence: every scalar decision of Sec. 2.3.1
+// (PCG step sizes and early stop, the Armijo accept/reject, the stop on a non-finite J) is taken
+// on the device by the last block of the kernel that produces the reduction, and later kernels
+// read it from the device state and exit immediately when their work is no longer needed.  No
+// host synchronisation happens inside a solve.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "../../include/hysco.h"
+#include "hysco_internal.cuh"
+
+using namespace hysco;
+
+struct hysco_ctx {
+  Geo g;
+  int dtype;
+  int64_t dims[3];
+  double spacing[3];
+  int pe;
+  long long nimg, nfld;
+  int seg;            // nodes per thread in the column-march kernels
+  int device;
+  // field-shaped workspace
+  float *grad, *dco, *eco, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp;
+  double* partials;
+  unsigned* counter;
+  DevState* st;
+  bool have_lin, have_factor;
+  Work work() const { return Work{partials, counter, st}; }
+};
+
+namespace {
+
+const char* kVersion = "hysco-b300 0.1 (sm_103a)";
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? HYSCO_OK : HYSCO_ECUDA; }
+
+#define HYSCO_TRY(expr)                      \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return HYSCO_ECUDA; \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+size_t elem_size(int dtype) { return dtype == HYSCO_F32 ? 4 : 2; }
+
+int check_img(const hysco_ctx* h, const void* p) {
+  return (p && aligned(p, elem_size(h->dtype))) ? HYSCO_OK : HYSCO_EINVAL;
+}
+int check_f32(const void* p) { return (p && aligned(p, 4)) ? HYSCO_OK : HYSCO_EINVAL; }
+
+void free_all(hysco_ctx* h) {
+  float* bufs[] = {h->grad, h->dco, h->eco, h->x, h->r, h->z, h->p0, h->p1, h->Hp, h->invD,
+                   h->lco, h->tmp};
+  for (float* b : bufs)
+    if (b) cudaFree(b);
+  if (h->partials) cudaFree(h->partials);
+  if (h->counter) cudaFree(h->counter);
+  if (h->st) cudaFree(h->st);
+}
+
+int reset_state(hysco_ctx* h, cudaStream_t s) {
+  return check_cuda(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hysco_version(void) { return kVersion; }
+
+void hysco_default_opts(hysco_opts* o) {
+  if (!o) return;
+  o->gn_iters = 10;
+  o->pcg_max_iters = 10;
+  o->ls_max_iters = 10;
+  o->precond = HYSCO_PC_JACOBI;
+  o->init = 1;
+  o->ot_blur = 1;
+  o->pcg_rtol = 0.1;
+  o->armijo_c1 = 1e-4;
+  o->ot_eps = 1e-3;
+}
+
+const char* hysco_strerror(int status) {
+  switch (status) {
+    case HYSCO_OK: return "success";
+    case HYSCO_INFEASIBLE: return "barrier infeasible: |d_v b| >= 1 somewhere, J = +inf";
+    case HYSCO_EINVAL: return "invalid argument";
+    case HYSCO_ECUDA: return "CUDA runtime error";
+    case HYSCO_ENOMEM: return "device memory allocation failed";
+    case HYSCO_ENONFINITE: return "non-finite (NaN) objective";
+    case HYSCO_ENOTREADY: return "no Gauss-Newton linearisation yet: call hysco_eval first";
+    default: return "unknown status";
+  }
+}
+
+int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, double alpha,
+                 double beta, int img_dtype, hysco_t* out) {
+  if (!out) return HYSCO_EINVAL;
+  *out = nullptr;
+  if (!dims || !spacing || pe_dim < 0 || pe_dim > 2) return HYSCO_EINVAL;
+  if (img_dtype < HYSCO_F32 || img_dtype > HYSCO_F16) return HYSCO_EINVAL;
+  if (!(alpha >= 0.0) || !(beta >= 0.0) || !std::isfinite(alpha) || !std::isfinite(beta))
+    return HYSCO_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (dims[a] < 1) return HYSCO_EINVAL;
+    if (!(spacing[a] > 0.0) || !std::isfinite(spacing[a])) return HYSCO_EINVAL;
+  }
+  if (dims[pe_dim] < 2) return HYSCO_EINVAL;
+  long long nimg = dims[0] * dims[1] * dims[2];
+  long long m = dims[pe_dim];
+  long long nfld = nimg / m * (m + 1);
+  if (nfld >= (1LL << 31)) return HYSCO_EINVAL;
+
+  hysco_ctx* h = new (std::nothrow) hysco_ctx();
+  if (!h) return HYSCO_ENOMEM;
+  std::memcpy(h->dims, dims, sizeof(h->dims));
+  std::memcpy(h->spacing, spacing, sizeof(h->spacing));
+  h->pe = pe_dim;
+  h->dtype = img_dtype;
+  h->nimg = nimg;
+  h->nfld = nfld;
+  cudaGetDevice(&h->device);
+
+  Geo& g = h->g;
+  g.m = (int)m;
+  g.E = (int)m + 1;
+  g.ncols = (int)(nimg / m);
+  long long inner = 1;
+  for (int a = pe_dim + 1; a < 3; ++a) inner *= dims[a];
+  g.inner = (int)inner;
+  int q[2], k = 0;
+  for (int a = 0; a < 3; ++a)
+    if (a != pe_dim) q[k++] = a;
+  // column index c = cB * nA + cA with A the faster (later) non-PE axis
+  g.nA = (int)dims[q[1]];
+  g.nB = (int)dims[q[0]];
+  g.img_ostride = m * inner;
+  g.fld_ostride = (m + 1) * inner;
+  double hp = spacing[pe_dim];
+  g.wA = (float)((hp / spacing[q[1]]) * (hp / spacing[q[1]]));
+  g.wB = (float)((hp / spacing[q[0]]) * (hp / spacing[q[0]]));
+  g.vol = (float)(spacing[0] * spacing[1] * spacing[2]);
+  g.alpha = (float)alpha;
+  g.half_beta = (float)(0.5 * beta);
+  g.alpha_d = alpha;
+  g.beta_d = beta;
+  h->seg = 8;
+
+  size_t fbytes = (size_t)nfld * sizeof(float);
+  float** bufs[] = {&h->grad, &h->dco, &h->eco, &h->x, &h->r, &h->z, &h->p0, &h->p1, &h->Hp,
+                    &h->invD, &h->lco, &h->tmp};
+  for (float** b : bufs) {
+    if (cudaMalloc((void**)b, fbytes) != cudaSuccess) {
+      free_all(h);
+      delete h;
+      return HYSCO_ENOMEM;
+    }
+  }
+  // partials: the largest grid of any reducing kernel times its reduction width
+  long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, 1);
+  long long nparts = march_blocks * (3 * kLsBatch + 1) + 148 * 4 * 2 + (long long)g.ncols * 2 + 64;
+  if (cudaMalloc((void**)&h->partials, nparts * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMalloc((void**)&h->st, sizeof(DevState)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return HYSCO_ENOMEM;
+  }
+  if (cudaMemset(h->counter, 0, 64 * sizeof(unsigned)) != cudaSuccess ||
+      cudaMemset(h->st, 0, sizeof(DevState)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return HYSCO_ECUDA;
+  }
+  *out = h;
+  return HYSCO_OK;
+}
+
+void hysco_destroy(hysco_t h) {
+  if (!h) return;
+  free_all(h);
+  delete h;
+}
+
+int hysco_field_dims(hysco_t h, int64_t out[3]) {
+  if (!h || !out) return HYSCO_EINVAL;
+  for (int a = 0; a < 3; ++a) out[a] = h->dims[a] + (a == h->pe ? 1 : 0);
+  return HYSCO_OK;
+}
+
+static int init_ot_impl(hysco_t h, const void* Ip, const void* Im, float* b_out, int blur,
+                        double eps, int* kp, int* km, cudaStream_t s) {
+  Work w = h->work();
+  HYSCO_TRY(launch_ot_shift(h->g, h->dtype, Ip, Im, h->nimg, eps, w, s));
+  float* dst = blur ? h->tmp : b_out;
+  HYSCO_TRY(launch_ot(h->g, h->dtype, Ip, Im, dst, kp, km, w, s));
+  if (blur) HYSCO_TRY(launch_blur(h->g, h->tmp, b_out, h->seg, s));
+  return HYSCO_OK;
+}
+
+int hysco_init_ot(hysco_t h, const void* Ip, const void* Im, float* b_out, int blur, double eps,
+                  hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b_out)) return HYSCO_EINVAL;
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  return init_ot_impl(h, Ip, Im, b_out, blur, eps, nullptr, nullptr, s);
+}
+
+int hysco_ot_indices(hysco_t h, const void* Ip, const void* Im, double eps, int32_t* kidx_p,
+                     int32_t* kidx_m, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(kidx_p) || check_f32(kidx_m))
+    return HYSCO_EINVAL;
+  if (!(eps >= 0.0) || !std::isfinite(eps)) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  return init_ot_impl(h, Ip, Im, h->tmp, 0, eps, kidx_p, kidx_m, s);
+}
+
+int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double* terms_dev,
+               float* grad, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b)) return HYSCO_EINVAL;
+  if (!terms_dev || !aligned(terms_dev, 8)) return HYSCO_EINVAL;
+  if (grad && !aligned(grad, 4)) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  Work w = h->work();
+  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, h->dco, h->eco, h->seg, -1, w, s));
+  HYSCO_TRY(launch_publish_terms(terms_dev, w, s));
+  h->have_lin = true;
+  h->have_factor = false;
+  return HYSCO_OK;
+}
+
+int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream) {
+  if (!h || check_f32(v) || check_f32(Hv)) return HYSCO_EINVAL;
+  if (!h->have_lin) return HYSCO_ENOTREADY;
+  HYSCO_TRY(launch_hessvec(h->g, v, Hv, h->dco, h->eco, h->seg, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t stream) {
+  if (!h || check_f32(r) || check_f32(z)) return HYSCO_EINVAL;
+  if (kind != HYSCO_PC_JACOBI && kind != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (kind == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
+  if (!h->have_lin) return HYSCO_ENOTREADY;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (kind == HYSCO_PC_JACOBI) {
+    HYSCO_TRY(launch_jacobi_apply(h->g, r, z, h->dco, h->seg, s));
+    return HYSCO_OK;
+  }
+  if (!h->have_factor) {
+    HYSCO_TRY(launch_col_factor(h->g, h->dco, h->eco, h->invD, h->lco, s));
+    h->have_factor = true;
+  }
+  HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, (float*)r, nullptr, nullptr, z, h->invD,
+                             h->lco, 0, 0.0, h->work(), s));
+  return HYSCO_OK;
+}
+
+int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,
+                  float* Tm, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(Tp) ||
+      check_f32(Tm))
+    return HYSCO_EINVAL;
+  HYSCO_TRY(launch_correct(h->g, h->dtype, Ip, Im, b, Tp, Tm, h->seg, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell_m,
+                       hysco_stream_t stream) {
+  if (!h || check_f32(b) || check_f32(cell_p) || check_f32(cell_m)) return HYSCO_EINVAL;
+  HYSCO_TRY(launch_cells(h->g, b, cell_p, cell_m, h->seg, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
+                double* stats, hysco_stream_t stream) {
+  if (!h || !o || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout)) return HYSCO_EINVAL;
+  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
+  if (o->gn_iters < 0 || o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
+      o->ls_max_iters > kMaxTrials)
+    return HYSCO_EINVAL;
+  if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
+  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const Geo& g = h->g;
+  Work w = h->work();
+  if (int rc = reset_state(h, s)) return rc;
+  if (o->init) {
+    if (int rc = init_ot_impl(h, Ip, Im, b_inout, o->ot_blur, o->ot_eps, nullptr, nullptr, s))
+      return rc;
+  }
+  const int seg = h->seg;
+  for (int it = 0; it < o->gn_iters; ++it) {
+    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, seg, it, w, s));
+    if (o->precond == HYSCO_PC_JACOBI) {
+      HYSCO_TRY(launch_pcg_init_jacobi(g, h->grad, h->x, h->r, h->z, h->dco, seg, w, s));
+    } else {
+      HYSCO_TRY(launch_col_factor(g, h->dco, h->eco, h->invD, h->lco, s));
+      HYSCO_TRY(launch_col_solve(g, 1, h->grad, h->x, h->r, nullptr, nullptr, h->z, h->invD,
+                                 h->lco, 0, o->pcg_rtol, w, s));
+    }
+    for (int i = 0; i < o->pcg_max_iters; ++i) {
+      float* pold = (i & 1) ? h->p0 : h->p1;
+      float* pnew = (i & 1) ? h->p1 : h->p0;
+      HYSCO_TRY(launch_pcg_hp(g, h->z, pold, pnew, h->Hp, h->dco, h->eco, i == 0, seg, w, s));
+      if (o->precond == HYSCO_PC_JACOBI)
+        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, pnew, h->Hp, h->z, h->dco, i == 0,
+                                           o->pcg_rtol, seg, w, s));
+      else
+        HYSCO_TRY(launch_col_solve(g, 2, nullptr, h->x, h->r, pnew, h->Hp, h->z, h->invD, h->lco,
+                                   i == 0, o->pcg_rtol, w, s));
+    }
+    for (int t0 = 0; t0 < o->ls_max_iters; t0 += kLsBatch)
+      HYSCO_TRY(launch_linesearch(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, t0,
+                                  o->ls_max_iters, o->armijo_c1, seg, w, s));
+    HYSCO_TRY(launch_update(g, b_inout, h->x, h->nfld, it, stats, w, s));
+  }
+  // the stored linearisation belongs to the iterate before the last update: invalidate it
+  h->have_lin = false;
+  h->have_factor = false;
+  return HYSCO_OK;
+}
+
+int hysco_last_status(hysco_t h, hysco_stream_t stream) {
+  if (!h) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return HYSCO_ECUDA;
+  DevState st;
+  if (cudaMemcpy(&st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return HYSCO_ECUDA;
+  return st.status;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Internal declarations shared by the libhysco CUDA translation units.
+//
+// Geometry: a problem with image dims (d0, d1, d2), PE axis p, m = d_p is seen as `ncols` PE
+// columns of m cells (image) and E = m + 1 nodes (field).  Column c has in-plane coordinates
+// cA = c % nA (the faster of the two non-PE axes) and cB = c / nA.  Element k of column c sits
+// at  (c / inner) * (len * inner) + k * inner + (c % inner)  where inner = product of the dims
+// after p and len = m (image) or E (field); `inner` is therefore also the PE stride.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hysco {
+
+struct Geo {
+  int m;                 // cells along PE
+  int E;                 // nodes along PE (m + 1)
+  int ncols;             // PE columns
+  int inner;             // PE stride (product of dims after the PE axis)
+  int nA, nB;            // in-plane extents, c = cB * nA + cA
+  long long img_ostride; // m * inner
+  long long fld_ostride; // E * inner
+  float wA, wB;          // (h_p / h_A)^2, (h_p / h_B)^2: in-plane Laplacian weights, PE-voxel units
+  float vol;             // h0 h1 h2, midpoint quadrature weight
+  float alpha;           // smoothness weight
+  float half_beta;       // beta / 2 (barrier Hessian / gradient factor)
+  double alpha_d, beta_d;
+};
+
+// Device-resident scalar state of a solve (and of single hysco_eval calls).
+struct DevState {
+  double J, D, S, P, gnorm;   // at the current iterate (last eval)
+  double gq;                  // grad^T q
+  double rho, rr0, rr, relres, alpha_cg, beta_cg;
+  double gamma;               // accepted step of the current GN iteration
+  double ot_shift;            // positivity shift of the OT initialisation
+  int pcg_iter, pcg_done;
+  int ls_done, ls_trials;
+  int status;                 // hysco_status of the last numerical evaluation
+  int stop, stop_iter;        // solve stopped (J not finite) at GN iteration stop_iter
+  int gn_iter;
+};
+
+constexpr int kBlock = 256;   // threads of every column-march kernel
+constexpr int kMaxTrials = 16;
+constexpr int kLsBatch = 4;   // Armijo trials evaluated per line-search launch
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ long long col_base(int c, int inner, long long ostride) {
+  int o = c / inner;
+  return (long long)o * ostride + (c - o * inner);
+}
+
+__device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float ldf(const __half* p) { return __half2float(__ldg(p)); }
+
+// ------------------------------------------------------------------------------------------
+// deterministic reductions: warp shuffle -> shared memory -> per-block partial -> the last
+// block to finish (atomic ticket) sums all partials in a fixed order and "finishes".
+// ------------------------------------------------------------------------------------------
+
+template <int K>
+__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+}
+
+__device__ __forceinline__ int linear_tid() {
+  return threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+}
+__device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
+
+// Sum over the block; the result is valid in thread 0.  blockDim total must be a multiple of 32.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* >= 32*K */) {
+  int tid = linear_tid(), nw = block_threads() >> 5;
+  warp_sum<K>(v);
+  __syncthreads();
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < K; ++i) sh[(tid >> 5) * K + i] = v[i];
+  __syncthreads();
+  if (tid < 32) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) v[i] = tid < nw ? sh[tid * K + i] : 0.0;
+    warp_sum<K>(v);
+  }
+}
+
+// Grid-wide sum.  Every thread of every block must call it.  Returns true in thread 0 of the
+// last block only, with tot[] holding the grid totals; the ticket counter is reset there.
+template <int K>
+__device__ bool grid_sum(double (&v)[K], double* partials, unsigned* counter, double (&tot)[K]) {
+  __shared__ double sh[32 * K];
+  __shared__ int is_last;
+  int tid = linear_tid();
+  int nblk = gridDim.x * gridDim.y * gridDim.z;
+  int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  block_sum<K>(v, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) partials[(long long)bid * K + i] = v[i];
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (int b = tid; b < nblk; b += block_threads())
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] += __ldcg(partials + (long long)b * K + i);
+  block_sum<K>(acc, sh);
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) tot[i] = acc[i];
+    *counter = 0u;
+    return true;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers (one translation unit each)
+// ------------------------------------------------------------------------------------------
+
+struct Work {        // device buffers the launchers need
+  double* partials;
+  unsigned* counter;
+  DevState* st;
+};
+
+// k_eval.cu
+cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
+                        float* grad, float* dco, float* eco, int seg, int it, const Work& w,
+                        cudaStream_t s);
+cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
+                              const float* b, const float* q, const float* grad, int t0,
+                              int ls_max, double c1, int seg, const Work& w, cudaStream_t s);
+cudaError_t launch_update(const Geo& g, float* b, const float* q, long long nf, int it,
+                          double* stats, const Work& w, cudaStream_t s);
+cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
+                           const float* b, float* Tp, float* Tm, int seg, cudaStream_t s);
+cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, int seg, cudaStream_t s);
+cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
+
+// k_pcg.cu
+cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
+                           const float* eco, int seg, cudaStream_t s);
+cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
+                                   const float* dco, int seg, const Work& w, cudaStream_t s);
+cudaError_t launch_pcg_hp(const Geo& g, const float* z, const float* pold, float* pnew, float* Hp,
+                          const float* dco, const float* eco, int first, int seg, const Work& w,
+                          cudaStream_t s);
+cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
+                                     const float* Hp, float* z, const float* dco, int first,
+                                     double rtol, int seg, const Work& w, cudaStream_t s);
+cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* dco, int seg,
+                                cudaStream_t s);
+int column_tile_width(int E);
+cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
+                              float* lco, cudaStream_t s);
+// mode 0 = apply z = M^{-1} r;  1 = PCG init (r = -grad, x = 0);  2 = PCG update
+cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
+                             const float* p, const float* Hp, float* z, const float* invD,
+                             const float* lco, int first, double rtol, const Work& w,
+                             cudaStream_t s);
+
+// k_ot.cu
+cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void* Im,
+                            long long n, double eps, const Work& w, cudaStream_t s);
+int ot_tile_width(int E);
+cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
+                      int* kp, int* km, const Work& w, cudaStream_t s);
+cudaError_t launch_blur(const Geo& g, const float* in, float* out, int seg, cudaStream_t s);
+
+}  // namespace hysco

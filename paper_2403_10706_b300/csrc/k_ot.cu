@@ -1,0 +1,247 @@
+// Optimal-transport field-map initialisation (Sec. 2.2) and the 3x3x3 Gaussian blur (Sec. 2.4).
+//
+// k_ot_shift: one pass over both images for min and max|I|; the last block forms the positivity
+//   shift s = max(0, -min) + eps * max|I| in single precision.
+// k_ot: one CTA per tile of CW consecutive PE columns.  The shifted intensities of both images are
+//   staged in shared memory with coalesced row loads; one thread per column forms the cumulative
+//   sums left to right (single precision, the order a sequential loop uses, so the result is
+//   bit-reproducible); all threads normalise, and every node k looks up
+//     k* = min{j in [0, m-1] : C(j+1) >= r}    (binary search on the other image's CDF)
+//   and C^{-1}(r) = k* + (r - C(k*)) / (C(k*+1) - C(k*)), capped at m.  Then
+//     b0_k = 1/4 [ (C+^{-1}(C-(k)) - k) - (C-^{-1}(C+(k)) - k) ].
+// k_blur: separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
+//   voxel), replicate boundary, evaluated as one 27-point pass.
+#include <cmath>
+
+#include "hysco_internal.cuh"
+
+namespace hysco {
+
+template <typename TI>
+__global__ void __launch_bounds__(kBlock)
+k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, long long n, float eps,
+           double* partials, unsigned* counter, DevState* st) {
+  float mn = __int_as_float(0x7f800000), mx = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float a = ldf(Ip + i), b = ldf(Im + i);
+    mn = fminf(mn, fminf(a, b));
+    mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(b)));
+  }
+  // min / max reduction through the same deterministic machinery (max(-min) and max|I|)
+  __shared__ float smn[32], smx[32];
+  __shared__ int is_last;
+  for (int off = 16; off > 0; off >>= 1) {
+    mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, off));
+    mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  }
+  int tid = threadIdx.x, nw = blockDim.x >> 5;
+  if ((tid & 31) == 0) { smn[tid >> 5] = mn; smx[tid >> 5] = mx; }
+  __syncthreads();
+  if (tid < 32) {
+    mn = tid < nw ? smn[tid] : __int_as_float(0x7f800000);
+    mx = tid < nw ? smx[tid] : 0.f;
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = fminf(mn, __shfl_down_sync(0xffffffffu, mn, off));
+      mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    }
+  }
+  if (tid == 0) {
+    partials[2 * blockIdx.x] = mn;
+    partials[2 * blockIdx.x + 1] = mx;
+    __threadfence();
+    unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  if (tid == 0) {
+    float gmn = __int_as_float(0x7f800000), gmx = 0.f;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      gmn = fminf(gmn, (float)__ldcg(partials + 2 * b));
+      gmx = fmaxf(gmx, (float)__ldcg(partials + 2 * b + 1));
+    }
+    float neg = -gmn > 0.f ? -gmn : 0.f;
+    float s = __fadd_rn(neg, __fmul_rn(eps, gmx));
+    st->ot_shift = (double)s;
+    *counter = 0u;
+  }
+}
+
+int ot_tile_width(int E) {
+  if (8LL * E * 32 <= 200 * 1024) return 32;
+  if (8LL * E * 16 <= 200 * 1024) return 16;
+  if (8LL * E * 8 <= 200 * 1024) return 8;
+  return 4;
+}
+
+// smallest j in [0, m-1] with C[j+1] >= r (m - 1 if none); C has stride CW
+__device__ __forceinline__ int cdf_bracket(const float* C, int CW, int m, float r) {
+  int lo = 0, hi = m - 1;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (C[(mid + 1) * CW] >= r) hi = mid; else lo = mid + 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float cdf_inverse(const float* C, int CW, int m, float r, int& kstar) {
+  if (r <= 0.f) { kstar = 0; return 0.f; }
+  int k = cdf_bracket(C, CW, m, r);
+  kstar = k;
+  float c0 = C[k * CW], c1 = C[(k + 1) * CW];
+  float x = (float)k + (r - c0) / (c1 - c0);
+  return fminf(x, (float)m);
+}
+
+template <typename TI, bool INDICES>
+__global__ void __launch_bounds__(kBlock)
+k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restrict__ b0,
+     int* __restrict__ kp, int* __restrict__ km, const DevState* st) {
+  extern __shared__ float sm[];
+  const int CW = blockDim.x, E = g.E, m = g.m;
+  float* Cp = sm;            // [E][CW]
+  float* Cm = sm + E * CW;   // [E][CW]
+  int tx = threadIdx.x, ty = threadIdx.y;
+  int c = blockIdx.x * CW + tx;
+  bool act = c < g.ncols;
+  float s = (float)st->ot_shift;
+  long long ib = act ? col_base(c, g.inner, g.img_ostride) : 0;
+  for (int k = ty; k < m; k += blockDim.y) {
+    float a = 0.f, b = 0.f;
+    if (act) {
+      a = __fadd_rn(ldf(Ip + ib + (long long)k * g.inner), s);
+      b = __fadd_rn(ldf(Im + ib + (long long)k * g.inner), s);
+    }
+    Cp[(k + 1) * CW + tx] = a;
+    Cm[(k + 1) * CW + tx] = b;
+  }
+  __syncthreads();
+  if (ty == 0) {
+    float ap = 0.f, am = 0.f;
+    Cp[tx] = 0.f;
+    Cm[tx] = 0.f;
+    for (int k = 1; k <= m; ++k) {
+      ap = __fadd_rn(ap, Cp[k * CW + tx]);
+      am = __fadd_rn(am, Cm[k * CW + tx]);
+      Cp[k * CW + tx] = ap;
+      Cm[k * CW + tx] = am;
+    }
+  }
+  __syncthreads();
+  float tp = Cp[m * CW + tx], tm = Cm[m * CW + tx];
+  bool ok = tp > 0.f && tm > 0.f;
+  __syncthreads();
+  if (ok)
+    for (int k = ty; k <= m; k += blockDim.y) {
+      Cp[k * CW + tx] = __fdiv_rn(Cp[k * CW + tx], tp);
+      Cm[k * CW + tx] = __fdiv_rn(Cm[k * CW + tx], tm);
+    }
+  __syncthreads();
+  if (!act) return;
+  long long fb = col_base(c, g.inner, g.fld_ostride);
+  for (int k = ty; k <= m; k += blockDim.y) {
+    long long i = fb + (long long)k * g.inner;
+    if (!ok) {
+      b0[i] = 0.f;
+      if (INDICES) { kp[i] = 0; km[i] = 0; }
+      continue;
+    }
+    int jp, jm;
+    float xp = cdf_inverse(Cm + tx, CW, m, Cp[k * CW + tx], jp);   // C-^{-1}(C+(k))
+    float xm = cdf_inverse(Cp + tx, CW, m, Cm[k * CW + tx], jm);   // C+^{-1}(C-(k))
+    float kf = (float)k;
+    b0[i] = 0.25f * ((xm - kf) - (xp - kf));
+    if (INDICES) { kp[i] = jp; km[i] = jm; }
+  }
+}
+
+// 27-point separable Gaussian with replicate boundary on the field grid
+__global__ void __launch_bounds__(kBlock)
+k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, int seg, float w0, float w1) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
+  if (c >= g.ncols) return;
+  int cA = c % g.nA, cB = c / g.nA;
+  long long base[3][3];
+  float wt[3] = {w1, w0, w1};
+#pragma unroll
+  for (int db = -1; db <= 1; ++db)
+#pragma unroll
+    for (int da = -1; da <= 1; ++da) {
+      int a = min(max(cA + da, 0), g.nA - 1), bb = min(max(cB + db, 0), g.nB - 1);
+      base[db + 1][da + 1] = col_base(bb * g.nA + a, g.inner, g.fld_ostride);
+    }
+  for (int k = k0; k < k1; ++k) {
+    int kk[3] = {max(k - 1, 0), k, min(k + 1, g.E - 1)};
+    float acc = 0.f;
+#pragma unroll
+    for (int db = 0; db < 3; ++db) {
+      float accb = 0.f;
+#pragma unroll
+      for (int da = 0; da < 3; ++da) {
+        float acca = 0.f;
+#pragma unroll
+        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * __ldg(in + base[db][da] + (long long)kk[dk] * g.inner);
+        accb += wt[da] * acca;
+      }
+      acc += wt[db] * accb;
+    }
+    out[col_base(c, g.inner, g.fld_ostride) + (long long)k * g.inner] = acc;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+
+cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void* Im,
+                            long long n, double eps, const Work& w, cudaStream_t s) {
+  (void)g;
+  int blocks = (int)((n + kBlock - 1) / kBlock);
+  if (blocks > 148 * 4) blocks = 148 * 4;
+  if (dtype == 0)
+    k_ot_shift<float><<<blocks, kBlock, 0, s>>>((const float*)Ip, (const float*)Im, n, (float)eps,
+                                                w.partials, w.counter, w.st);
+  else if (dtype == 1)
+    k_ot_shift<__nv_bfloat16><<<blocks, kBlock, 0, s>>>((const __nv_bfloat16*)Ip,
+                                                        (const __nv_bfloat16*)Im, n, (float)eps,
+                                                        w.partials, w.counter, w.st);
+  else
+    k_ot_shift<__half><<<blocks, kBlock, 0, s>>>((const __half*)Ip, (const __half*)Im, n,
+                                                 (float)eps, w.partials, w.counter, w.st);
+  return cudaGetLastError();
+}
+
+template <typename T, bool IDX>
+static cudaError_t ot_one(const Geo& g, const void* Ip, const void* Im, float* b0, int* kp,
+                          int* km, const Work& w, cudaStream_t s) {
+  int CW = ot_tile_width(g.E);
+  size_t smem = 2ull * g.E * CW * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(k_ot<T, IDX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_ot<T, IDX><<<ceil_div(g.ncols, CW), dim3(CW, kBlock / CW), smem, s>>>(
+      g, (const T*)Ip, (const T*)Im, b0, kp, km, w.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
+                      int* kp, int* km, const Work& w, cudaStream_t s) {
+  bool idx = kp != nullptr;
+  if (dtype == 0) return idx ? ot_one<float, true>(g, Ip, Im, b0, kp, km, w, s)
+                             : ot_one<float, false>(g, Ip, Im, b0, kp, km, w, s);
+  if (dtype == 1) return idx ? ot_one<__nv_bfloat16, true>(g, Ip, Im, b0, kp, km, w, s)
+                             : ot_one<__nv_bfloat16, false>(g, Ip, Im, b0, kp, km, w, s);
+  return idx ? ot_one<__half, true>(g, Ip, Im, b0, kp, km, w, s)
+             : ot_one<__half, false>(g, Ip, Im, b0, kp, km, w, s);
+}
+
+cudaError_t launch_blur(const Geo& g, const float* in, float* out, int seg, cudaStream_t s) {
+  double e = std::exp(-0.5);   // the sigma = 1 Gaussian at distance 1 voxel
+  float w0 = (float)(1.0 / (1.0 + 2.0 * e)), w1 = (float)(e / (1.0 + 2.0 * e));
+  k_blur<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, seg)), kBlock, 0, s>>>(g, in, out, seg,
+                                                                                w0, w1);
+  return cudaGetLastError();
+}
+
+}  // namespace hysco

@@ -1,0 +1,147 @@
+"""Torch-facing binding of libhysco: one method per C-ABI entry point, same names.
+
+Tensors are passed as raw device pointers together with the current CUDA stream; every
+computation runs in libhysco's kernels.  PyTorch only provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+
+_DTYPES = {torch.float32: _lib.F32, torch.bfloat16: _lib.BF16, torch.float16: _lib.F16}
+
+
+def _stream(device):
+    return C.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+class Hysco:
+    """One problem geometry (image dims, spacing in mm, PE axis) with weights alpha, beta (Eq. 4)
+    and the image element type.  Owns the library handle (device workspace)."""
+
+    def __init__(self, dims, spacing, pe_dim, alpha=300.0, beta=1e-4, dtype=torch.float32,
+                 device=None):
+        self.lib = _lib.load()
+        device = torch.device("cuda") if device is None else torch.device(device)
+        if device.index is None:
+            device = torch.device("cuda", torch.cuda.current_device())
+        self.device = device
+        if dtype not in _DTYPES:
+            raise TypeError(f"unsupported image dtype {dtype}")
+        self.dtype = dtype
+        self.dims = tuple(int(x) for x in dims)
+        self.spacing = tuple(float(x) for x in spacing)
+        self.pe_dim = int(pe_dim)
+        self.alpha, self.beta = float(alpha), float(beta)
+        self._h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(self.lib.hysco_create((C.c_int64 * 3)(*self.dims),
+                                             (C.c_double * 3)(*self.spacing), self.pe_dim,
+                                             self.alpha, self.beta, _DTYPES[dtype],
+                                             C.byref(self._h)), "hysco_create")
+        fd = (C.c_int64 * 3)()
+        _lib.check(self.lib.hysco_field_dims(self._h, fd), "hysco_field_dims")
+        self.field_dims = tuple(fd)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.lib.hysco_destroy(h)
+            self._h = None
+
+    # -- argument checks (marshalling only) ---------------------------------------------------
+    def _img(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype
+                and tuple(t.shape) == self.dims and t.is_contiguous()):
+            raise ValueError(f"{name}: expected contiguous {self.dtype} CUDA tensor {self.dims}")
+        return C.c_void_p(t.data_ptr())
+
+    def _fld(self, t, name, dtype=torch.float32):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype
+                and tuple(t.shape) == self.field_dims and t.is_contiguous()):
+            raise ValueError(f"{name}: expected contiguous {dtype} CUDA tensor {self.field_dims}")
+        return C.c_void_p(t.data_ptr())
+
+    def _new_fld(self, dtype=torch.float32):
+        return torch.empty(self.field_dims, dtype=dtype, device=self.device)
+
+    # -- entry points -------------------------------------------------------------------------
+    def init_ot(self, Ip, Im, blur=True, eps=1e-3, out=None):
+        out = self._new_fld() if out is None else out
+        _lib.check(self.lib.hysco_init_ot(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                          self._fld(out, "out"), int(blur), float(eps),
+                                          _stream(self.device)), "hysco_init_ot")
+        return out
+
+    def eval(self, Ip, Im, b, grad=True, terms=None):
+        """Returns (terms[J, D, S, P] float64 CUDA tensor, grad or None)."""
+        terms = torch.empty(4, dtype=torch.float64, device=self.device) if terms is None else terms
+        g = self._new_fld() if grad is True else (grad if isinstance(grad, torch.Tensor) else None)
+        _lib.check(self.lib.hysco_eval(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                       self._fld(b, "b"), C.c_void_p(terms.data_ptr()),
+                                       None if g is None else self._fld(g, "grad"),
+                                       _stream(self.device)), "hysco_eval")
+        return terms, g
+
+    def hessvec(self, v, out=None):
+        out = self._new_fld() if out is None else out
+        _lib.check(self.lib.hysco_hessvec(self._h, self._fld(v, "v"), self._fld(out, "Hv"),
+                                          _stream(self.device)), "hysco_hessvec")
+        return out
+
+    def precond(self, r, kind=_lib.PC_JACOBI, out=None):
+        out = self._new_fld() if out is None else out
+        _lib.check(self.lib.hysco_precond(self._h, self._fld(r, "r"), self._fld(out, "z"),
+                                          int(kind), _stream(self.device)), "hysco_precond")
+        return out
+
+    def correct(self, Ip, Im, b):
+        Tp = torch.empty(self.dims, dtype=torch.float32, device=self.device)
+        Tm = torch.empty_like(Tp)
+        _lib.check(self.lib.hysco_correct(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                          self._fld(b, "b"), C.c_void_p(Tp.data_ptr()),
+                                          C.c_void_p(Tm.data_ptr()), _stream(self.device)),
+                   "hysco_correct")
+        return Tp, Tm
+
+    def solve(self, Ip, Im, b=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10,
+              precond=_lib.PC_JACOBI, init=None, ot_blur=True, pcg_rtol=0.1, armijo_c1=1e-4,
+              ot_eps=1e-3, stats=True):
+        """GN-PCG solve.  init defaults to OT when b is None.  Returns (b, stats or None)."""
+        if init is None:
+            init = b is None
+        b = self._new_fld() if b is None else b
+        o = _lib.Opts(gn_iters, pcg_max_iters, ls_max_iters, int(precond), int(init),
+                      int(ot_blur), pcg_rtol, armijo_c1, ot_eps)
+        st = (torch.full((max(gn_iters, 1), _lib.NSTATS), float("nan"), dtype=torch.float64,
+                         device=self.device) if stats else None)
+        _lib.check(self.lib.hysco_solve(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                        self._fld(b, "b"), C.byref(o),
+                                        None if st is None else C.c_void_p(st.data_ptr()),
+                                        _stream(self.device)), "hysco_solve")
+        return b, (st[:gn_iters] if st is not None else None)
+
+    def last_status(self):
+        return _lib.check(self.lib.hysco_last_status(self._h, _stream(self.device)),
+                          "hysco_last_status")
+
+    def cell_indices(self, b):
+        cp = torch.empty(self.dims, dtype=torch.int32, device=self.device)
+        cm = torch.empty_like(cp)
+        _lib.check(self.lib.hysco_cell_indices(self._h, self._fld(b, "b"),
+                                               C.c_void_p(cp.data_ptr()),
+                                               C.c_void_p(cm.data_ptr()), _stream(self.device)),
+                   "hysco_cell_indices")
+        return cp, cm
+
+    def ot_indices(self, Ip, Im, eps=1e-3):
+        kp = self._new_fld(torch.int32)
+        km = self._new_fld(torch.int32)
+        _lib.check(self.lib.hysco_ot_indices(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                             float(eps), C.c_void_p(kp.data_ptr()),
+                                             C.c_void_p(km.data_ptr()), _stream(self.device)),
+                   "hysco_ot_indices")
+        return kp, km

@@ -1,0 +1,177 @@
+"""Parity of the CUDA path (through the C ABI) with the double-precision oracle.
+
+Tolerances (derived from single-precision arithmetic, unit roundoff u = 6e-8):
+  - cell indices and OT merge indices: bit-exact (both sides take those decisions in the same
+    single-precision operations);
+  - J, D, S, P: relative 1e-5 (sums of non-negative single-precision terms);
+  - gradient, Hessian-vector product, preconditioner: relative 1e-5 in the 2-norm, and every
+    element within 2e-4 of the largest magnitude (a handful of roundings of terms that cancel);
+  - corrected images: 1e-5 of the largest intensity;
+  - OT field: 2e-4 voxel before / after blur (single-precision spline inversion, the CDF
+    decisions being identical);
+  - final field after the full GN solve: relative 1e-3 in the 2-norm.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2403_10706_b300 import phantom as ph  # noqa: E402
+
+ALPHA, BETA = 300.0, 1e4
+SHAPES = [  # (dims, spacing, pe): ragged sizes, every PE axis, single columns
+    ((7, 13, 5), (1.0, 1.25, 0.9), 1),
+    ((9, 6, 11), (1.1, 1.0, 1.2), 0),
+    ((5, 4, 17), (0.9, 1.3, 1.0), 2),
+    ((1, 33, 1), (1.0, 1.0, 1.0), 1),
+    ((40, 3, 37), (1.0, 1.5, 1.0), 1),
+    ((2, 2, 2), (1.0, 1.0, 1.0), 0),
+]
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2403_10706_b300 import build
+    build.build()
+    from paper_2403_10706_b300.hysco import Hysco
+    return Hysco
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return t if dtype is None else t.to(dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def case(dims, p, seed, bscale=2.0):
+    Ip, Im = ph.random_images(dims, seed, 0.1, 1.0)
+    b = ph.random_field(dims, p, seed + 1, scale=bscale, smooth=1.0)
+    return Ip, Im, b
+
+
+def check_field(got, ref, what, rtol=1e-5, etol=2e-4):
+    r = rel(got, ref)
+    e = np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300)
+    assert r <= rtol and e <= etol, f"{what}: rel {r:.3e}, max elem {e:.3e}"
+
+
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES)
+def test_cell_indices_bit_exact(H, orc, dims, spacing, p):
+    Ip, Im, b = case(dims, p, 100)
+    b = (np.random.default_rng(1).uniform(-4, 4, size=b.shape)).astype(np.float32)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    cp, cm = h.cell_indices(dev(b))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    e = P.eval(Ip, Im, b, contract=True, grad=False, cells=True)
+    m = dims[p]
+    assert np.array_equal(host(cp), np.clip(e["cell_p"], -2, m + 1))
+    assert np.array_equal(host(cm), np.clip(e["cell_m"], -2, m + 1))
+
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES)
+def test_eval_matches_oracle(H, orc, dims, spacing, p):
+    Ip, Im, b = case(dims, p, 200)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    terms, g = h.eval(dev(Ip), dev(Im), dev(b))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    e = P.eval(Ip, Im, b, contract=True)
+    t = host(terms)
+    for i, k in enumerate("JDSP"):
+        assert abs(t[i] - e[k]) <= 1e-5 * abs(e[k]) + 1e-12, (k, t[i], e[k])
+    assert h.last_status() == 0
+    check_field(host(g), e["grad"], "grad")
+
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES)
+def test_hessvec_and_preconditioners_match_oracle(H, orc, dims, spacing, p):
+    Ip, Im, b = case(dims, p, 300)
+    v = np.random.default_rng(7).normal(size=b.shape).astype(np.float32)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    h.eval(dev(Ip), dev(Im), dev(b))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    check_field(host(h.hessvec(dev(v))), P.hessvec(Ip, Im, b, v), "Hv")
+    check_field(host(h.precond(dev(v), 0)), P.precond(Ip, Im, b, v, 0), "jacobi")
+    check_field(host(h.precond(dev(v), 1)), P.precond(Ip, Im, b, v, 1), "column", 1e-4, 1e-3)
+
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES)
+def test_corrected_images_match_oracle(H, orc, dims, spacing, p):
+    Ip, Im, b = case(dims, p, 400)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    Tp, Tm = h.correct(dev(Ip), dev(Im), dev(b))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    e = P.eval(Ip, Im, b, contract=True, grad=False, corrected=True)
+    assert np.abs(host(Tp) - e["Tp"]).max() <= 1e-5 * np.abs(e["Tp"]).max()
+    assert np.abs(host(Tm) - e["Tm"]).max() <= 1e-5 * np.abs(e["Tm"]).max()
+
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES[:5])
+@pytest.mark.parametrize("blur", [False, True])
+def test_ot_init_matches_oracle(H, orc, dims, spacing, p, blur):
+    pr_I = ph.random_images(dims, 500, -0.05, 1.0)
+    Ip, Im = pr_I
+    h = H(dims, spacing, p, ALPHA, BETA)
+    b0 = host(h.init_ot(dev(Ip), dev(Im), blur=blur, eps=1e-3))
+    kp, km = h.ot_indices(dev(Ip), dev(Im), eps=1e-3)
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    ref, rkp, rkm = P.ot_init(Ip, Im, 1e-3, contract=True, blur=blur, indices=True)
+    assert np.array_equal(host(kp), rkp)
+    assert np.array_equal(host(km), rkm)
+    assert np.abs(b0 - ref).max() <= 2e-4
+
+
+def test_infeasible_and_nonfinite_status(H, orc):
+    dims, p = (6, 10, 5), 1
+    Ip, Im, b = case(dims, p, 600)
+    h = H(dims, (1.0, 1.0, 1.0), p, ALPHA, BETA)
+    bad = b.copy()
+    bad[2, 4, 3] += 1.5     # one PE difference beyond the barrier
+    terms, _ = h.eval(dev(Ip), dev(Im), dev(bad))
+    assert h.last_status() == 1
+    assert np.isinf(host(terms)[0])
+    Ipn = Ip.copy()
+    Ipn[1, 1, 1] = np.nan
+    h.eval(dev(Ipn), dev(Im), dev(b))
+    assert h.last_status() == -4
+
+
+@pytest.mark.parametrize("dtype", ["bfloat16", "float16"])
+def test_half_precision_images_match_oracle_on_the_same_values(H, orc, dtype):
+    dims, spacing, p = (9, 14, 7), (1.0, 1.25, 1.0), 1
+    Ip, Im, b = case(dims, p, 700)
+    td = getattr(torch, dtype)
+    Ipq, Imq = dev(Ip, td), dev(Im, td)
+    h = H(dims, spacing, p, ALPHA, BETA, dtype=td)
+    terms, g = h.eval(Ipq, Imq, dev(b))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    e = P.eval(host(Ipq.float()), host(Imq.float()), b, contract=True)
+    assert abs(host(terms)[0] - e["J"]) <= 1e-5 * abs(e["J"])
+    check_field(host(g), e["grad"], "grad " + dtype)
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_tiny_solve_matches_oracle(H, orc, precond):
+    """BASELINE tiny case: 32x32x16, OT init, 10 GN-PCG iterations."""
+    pr = ph.make_pair("tiny")
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=10, precond=precond)
+    assert h.last_status() == 0
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=10, precond=precond, contract=False)
+    gs = host(st)
+    assert status == 0
+    assert np.array_equal(gs[:, 6], rst[:, 6]), (gs[:, 6], rst[:, 6])        # accepted steps
+    assert np.array_equal(gs[:, 7], rst[:, 7]), (gs[:, 7], rst[:, 7])        # PCG iterations
+    assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4)
+    assert rel(host(b), ref) <= 1e-3
