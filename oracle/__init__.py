@@ -56,6 +56,7 @@ def lib():
         _lib.orc_hessdiag.argtypes = [P, P, P, P, C.c_int, P]
         _lib.orc_precond.argtypes = [P, P, P, P, C.c_int, C.c_int, P, P]
         _lib.orc_column_block.argtypes = [P, P, P, P, C.c_int, C.c_int64, P, P]
+        _lib.orc_column_blocks.argtypes = [P, P, P, P, C.c_int, P, P]
         _lib.orc_apply_laplacian.argtypes = [P, P, P]
         _lib.orc_ot_init.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
         _lib.orc_blur.argtypes = [P, P]
@@ -139,6 +140,13 @@ class Problem:
         dia, off = np.zeros(m + 1), np.zeros(m)
         lib().orc_column_block(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
                                int(contract), int(col), _p(dia), _p(off))
+        return dia, off
+
+    def column_blocks(self, Ip, Im, b, contract=True):
+        """(dia, off) field shaped: the tridiagonal diagonal block of every PE column."""
+        dia, off = np.zeros(self.fdims), np.zeros(self.fdims)
+        lib().orc_column_blocks(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                int(contract), _p(dia), _p(off))
         return dia, off
 
     def laplacian(self, x):

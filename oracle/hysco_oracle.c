@@ -566,6 +566,33 @@ int orc_column_block(const orc_geom* g, const float* Ip, const float* Im, const 
   return 0;
 }
 
+/* all column blocks at once, field shaped: dia at every node, off between node k and k+1 stored
+ * at node k (0 at the last node) */
+int orc_column_blocks(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                      int contract, double* dia_f, double* off_f) {
+  int64_t m = g->d[g->p];
+  int64_t sf[3]; fld_strides(g, sf);
+  orc_lin lin;
+  if (!lin_alloc(&lin, img_count(g))) return -1;
+  double D, P;
+  residual_pass(g, Ip, Im, b, contract, &D, &P, &lin, NULL, NULL, NULL, NULL);
+  double* dia = malloc((m + 1) * sizeof(double));
+  double* off = malloc((m + 1) * sizeof(double));
+  int64_t ncols = column_count(g);
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    column_block(g, &lin, col, dia, off);
+    for (int64_t k = 0; k <= m; ++k) {
+      dia_f[of + k * sf[g->p]] = dia[k];
+      off_f[of + k * sf[g->p]] = k < m ? off[k] : 0.0;
+    }
+  }
+  free(dia); free(off);
+  lin_free(&lin);
+  return 0;
+}
+
 /* negative Laplacian of the field (exported for the null-space pin) */
 void orc_apply_laplacian(const orc_geom* g, const double* x, double* y) { orc_laplacian(g, x, y); }
 

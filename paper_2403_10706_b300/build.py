@@ -33,6 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+           "-Xlinker", "--no-undefined",
            "-o", LIB, *sources()]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")

@@ -23,10 +23,9 @@ struct hysco_ctx {
   double spacing[3];
   int pe;
   long long nimg, nfld;
-  int seg;            // nodes per thread in the column-march kernels
   int device;
   // field-shaped workspace
-  float *grad, *dco, *eco, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp;
+  float *grad, *dco, *eco, *invd, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp;
   double* partials;
   unsigned* counter;
   DevState* st;
@@ -56,8 +55,8 @@ int check_img(const hysco_ctx* h, const void* p) {
 int check_f32(const void* p) { return (p && aligned(p, 4)) ? HYSCO_OK : HYSCO_EINVAL; }
 
 void free_all(hysco_ctx* h) {
-  float* bufs[] = {h->grad, h->dco, h->eco, h->x, h->r, h->z, h->p0, h->p1, h->Hp, h->invD,
-                   h->lco, h->tmp};
+  float* bufs[] = {h->grad, h->dco, h->eco, h->invd, h->x, h->r, h->z, h->p0, h->p1, h->Hp,
+                   h->invD, h->lco, h->tmp};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
@@ -152,11 +151,20 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   g.half_beta = (float)(0.5 * beta);
   g.alpha_d = alpha;
   g.beta_d = beta;
-  h->seg = 8;
+  for (int a = 0; a < 3; ++a) g.fe[a] = (int)(dims[a] + (a == pe_dim ? 1 : 0));
+  g.fs[2] = 1;
+  g.fs[1] = g.fe[2];
+  g.fs[0] = g.fe[1] * g.fe[2];
+  for (int a = 0; a < 3; ++a)
+    g.w[a] = a == pe_dim ? 1.0f : (float)((hp / spacing[a]) * (hp / spacing[a]));
+  g.p = pe_dim;
+  g.nf = (int)nfld;
+  g.div0 = make_fastdiv((unsigned)g.fs[0]);
+  g.div1 = make_fastdiv((unsigned)g.fs[1]);
 
   size_t fbytes = (size_t)nfld * sizeof(float);
-  float** bufs[] = {&h->grad, &h->dco, &h->eco, &h->x, &h->r, &h->z, &h->p0, &h->p1, &h->Hp,
-                    &h->invD, &h->lco, &h->tmp};
+  float** bufs[] = {&h->grad, &h->dco, &h->eco, &h->invd, &h->x, &h->r, &h->z, &h->p0, &h->p1,
+                    &h->Hp, &h->invD, &h->lco, &h->tmp};
   for (float** b : bufs) {
     if (cudaMalloc((void**)b, fbytes) != cudaSuccess) {
       free_all(h);
@@ -165,8 +173,10 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
     }
   }
   // partials: the largest grid of any reducing kernel times its reduction width
-  long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, 1);
-  long long nparts = march_blocks * (3 * kLsBatch + 1) + 148 * 4 * 2 + (long long)g.ncols * 2 + 64;
+  long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, kSeg);
+  long long flat_blocks = (long long)ceil_div(g.nf, kBlock) + 1;
+  long long nparts = march_blocks * (3 * kLsBatch + 1) + flat_blocks * 2 + 148 * 4 * 2 +
+                     (long long)g.ncols * 2 + 64;
   if (cudaMalloc((void**)&h->partials, nparts * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc((void**)&h->st, sizeof(DevState)) != cudaSuccess) {
@@ -202,7 +212,7 @@ static int init_ot_impl(hysco_t h, const void* Ip, const void* Im, float* b_out,
   HYSCO_TRY(launch_ot_shift(h->g, h->dtype, Ip, Im, h->nimg, eps, w, s));
   float* dst = blur ? h->tmp : b_out;
   HYSCO_TRY(launch_ot(h->g, h->dtype, Ip, Im, dst, kp, km, w, s));
-  if (blur) HYSCO_TRY(launch_blur(h->g, h->tmp, b_out, h->seg, s));
+  if (blur) HYSCO_TRY(launch_blur(h->g, h->tmp, b_out, s));
   return HYSCO_OK;
 }
 
@@ -233,7 +243,7 @@ int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = reset_state(h, s)) return rc;
   Work w = h->work();
-  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, h->dco, h->eco, h->seg, -1, w, s));
+  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, h->dco, h->eco, h->invd, -1, w, s));
   HYSCO_TRY(launch_publish_terms(terms_dev, w, s));
   h->have_lin = true;
   h->have_factor = false;
@@ -243,7 +253,7 @@ int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double
 int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream) {
   if (!h || check_f32(v) || check_f32(Hv)) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
-  HYSCO_TRY(launch_hessvec(h->g, v, Hv, h->dco, h->eco, h->seg, (cudaStream_t)stream));
+  HYSCO_TRY(launch_hessvec(h->g, v, Hv, h->dco, h->eco, (cudaStream_t)stream));
   return HYSCO_OK;
 }
 
@@ -254,7 +264,7 @@ int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t 
   if (!h->have_lin) return HYSCO_ENOTREADY;
   cudaStream_t s = (cudaStream_t)stream;
   if (kind == HYSCO_PC_JACOBI) {
-    HYSCO_TRY(launch_jacobi_apply(h->g, r, z, h->dco, h->seg, s));
+    HYSCO_TRY(launch_jacobi_apply(h->g, r, z, h->invd, s));
     return HYSCO_OK;
   }
   if (!h->have_factor) {
@@ -271,14 +281,14 @@ int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, flo
   if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(Tp) ||
       check_f32(Tm))
     return HYSCO_EINVAL;
-  HYSCO_TRY(launch_correct(h->g, h->dtype, Ip, Im, b, Tp, Tm, h->seg, (cudaStream_t)stream));
+  HYSCO_TRY(launch_correct(h->g, h->dtype, Ip, Im, b, Tp, Tm, (cudaStream_t)stream));
   return HYSCO_OK;
 }
 
 int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell_m,
                        hysco_stream_t stream) {
   if (!h || check_f32(b) || check_f32(cell_p) || check_f32(cell_m)) return HYSCO_EINVAL;
-  HYSCO_TRY(launch_cells(h->g, b, cell_p, cell_m, h->seg, (cudaStream_t)stream));
+  HYSCO_TRY(launch_cells(h->g, b, cell_p, cell_m, (cudaStream_t)stream));
   return HYSCO_OK;
 }
 
@@ -300,11 +310,11 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
     if (int rc = init_ot_impl(h, Ip, Im, b_inout, o->ot_blur, o->ot_eps, nullptr, nullptr, s))
       return rc;
   }
-  const int seg = h->seg;
   for (int it = 0; it < o->gn_iters; ++it) {
-    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, seg, it, w, s));
+    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, h->invd, it, w,
+                          s));
     if (o->precond == HYSCO_PC_JACOBI) {
-      HYSCO_TRY(launch_pcg_init_jacobi(g, h->grad, h->x, h->r, h->z, h->dco, seg, w, s));
+      HYSCO_TRY(launch_pcg_init_jacobi(g, h->grad, h->x, h->r, h->z, h->invd, w, s));
     } else {
       HYSCO_TRY(launch_col_factor(g, h->dco, h->eco, h->invD, h->lco, s));
       HYSCO_TRY(launch_col_solve(g, 1, h->grad, h->x, h->r, nullptr, nullptr, h->z, h->invD,
@@ -313,18 +323,18 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
     for (int i = 0; i < o->pcg_max_iters; ++i) {
       float* pold = (i & 1) ? h->p0 : h->p1;
       float* pnew = (i & 1) ? h->p1 : h->p0;
-      HYSCO_TRY(launch_pcg_hp(g, h->z, pold, pnew, h->Hp, h->dco, h->eco, i == 0, seg, w, s));
+      HYSCO_TRY(launch_pcg_hp(g, h->z, pold, pnew, h->Hp, h->dco, h->eco, i == 0, w, s));
       if (o->precond == HYSCO_PC_JACOBI)
-        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, pnew, h->Hp, h->z, h->dco, i == 0,
-                                           o->pcg_rtol, seg, w, s));
+        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, pnew, h->Hp, h->z, h->invd, i == 0,
+                                           o->pcg_rtol, w, s));
       else
         HYSCO_TRY(launch_col_solve(g, 2, nullptr, h->x, h->r, pnew, h->Hp, h->z, h->invD, h->lco,
                                    i == 0, o->pcg_rtol, w, s));
     }
-    for (int t0 = 0; t0 < o->ls_max_iters; t0 += kLsBatch)
+    for (int t0 = 0; t0 < o->ls_max_iters; t0 += (t0 == 0 ? 1 : kLsBatch))
       HYSCO_TRY(launch_linesearch(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, t0,
-                                  o->ls_max_iters, o->armijo_c1, seg, w, s));
-    HYSCO_TRY(launch_update(g, b_inout, h->x, h->nfld, it, stats, w, s));
+                                  o->ls_max_iters, o->armijo_c1, w, s));
+    HYSCO_TRY(launch_update(g, b_inout, h->x, it, stats, w, s));
   }
   // the stored linearisation belongs to the iterate before the last update: invalidate it
   h->have_lin = false;

@@ -14,6 +14,21 @@
 
 namespace hysco {
 
+// n / d for 0 <= n < 2^31 by multiply-high (Granlund & Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994): s = ceil(log2 d), mul = floor(2^32 (2^s - d) / d) + 1.
+struct FastDiv {
+  unsigned d, mul, shift;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned s = 0;
+  while ((1ull << s) < d) ++s;
+  unsigned long long mul = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+  return FastDiv{d, (unsigned)mul, s};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+  return (__umulhi(n, f.mul) + n) >> f.shift;
+}
+
 struct Geo {
   int m;                 // cells along PE
   int E;                 // nodes along PE (m + 1)
@@ -27,6 +42,13 @@ struct Geo {
   float alpha;           // smoothness weight
   float half_beta;       // beta / 2 (barrier Hessian / gradient factor)
   double alpha_d, beta_d;
+  // flat view of the field: extents fe, C-order strides fs, per-axis Laplacian weight w
+  // (w[p] = 1, in-plane (h_p / h_a)^2), the PE axis p, and dividers by fs[0], fs[1]
+  int fe[3], fs[3];
+  float w[3];
+  int p;
+  int nf;                // field nodes
+  FastDiv div0, div1;
 };
 
 // Device-resident scalar state of a solve (and of single hysco_eval calls).
@@ -43,15 +65,18 @@ struct DevState {
   int gn_iter;
 };
 
-constexpr int kBlock = 256;   // threads of every column-march kernel
+constexpr int kBlock = 256;   // threads per block of every kernel
 constexpr int kMaxTrials = 16;
-constexpr int kLsBatch = 4;   // Armijo trials evaluated per line-search launch
+constexpr int kSeg = 4;       // PE nodes per thread in the column-march kernels
+constexpr int kNpt = 2;       // nodes per thread in the flat stencil kernels
+constexpr int kLsBatch = 3;   // Armijo trials per line-search launch after the first (gamma = 1)
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-__device__ __forceinline__ long long col_base(int c, int inner, long long ostride) {
+// offsets fit in 32 bits: the field has fewer than 2^31 nodes (checked at handle creation)
+__device__ __forceinline__ int col_base(int c, int inner, long long ostride) {
   int o = c / inner;
-  return (long long)o * ostride + (c - o * inner);
+  return o * (int)ostride + (c - o * inner);
 }
 
 __device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
@@ -59,12 +84,15 @@ __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat16
 __device__ __forceinline__ float ldf(const __half* p) { return __half2float(__ldg(p)); }
 
 // ------------------------------------------------------------------------------------------
-// deterministic reductions: warp shuffle -> shared memory -> per-block partial -> the last
-// block to finish (atomic ticket) sums all partials in a fixed order and "finishes".
+// deterministic reductions: per-thread and per-block partial sums in single precision (a warp
+// shuffle tree, then one warp over the block's warp sums); the last block to finish (atomic
+// ticket) adds the per-block partials in double precision in a fixed order and "finishes".
+// Double precision is confined to that one block: this GPU's FP64 rate is a small fraction of
+// its FP32 rate, and an FP64 tree in every block dominated the reducing kernels.
 // ------------------------------------------------------------------------------------------
 
-template <int K>
-__device__ __forceinline__ void warp_sum(double (&v)[K]) {
+template <int K, typename T>
+__device__ __forceinline__ void warp_sum(T (&v)[K]) {
 #pragma unroll
   for (int i = 0; i < K; ++i)
 #pragma unroll
@@ -77,10 +105,10 @@ __device__ __forceinline__ int linear_tid() {
 __device__ __forceinline__ int block_threads() { return blockDim.x * blockDim.y * blockDim.z; }
 
 // Sum over the block; the result is valid in thread 0.  blockDim total must be a multiple of 32.
-template <int K>
-__device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* >= 32*K */) {
+template <int K, typename T>
+__device__ __forceinline__ void block_sum(T (&v)[K], T* sh /* >= 32*K */) {
   int tid = linear_tid(), nw = block_threads() >> 5;
-  warp_sum<K>(v);
+  warp_sum<K, T>(v);
   __syncthreads();
   if ((tid & 31) == 0)
 #pragma unroll
@@ -88,24 +116,26 @@ __device__ __forceinline__ void block_sum(double (&v)[K], double* sh /* >= 32*K 
   __syncthreads();
   if (tid < 32) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) v[i] = tid < nw ? sh[tid * K + i] : 0.0;
-    warp_sum<K>(v);
+    for (int i = 0; i < K; ++i) v[i] = tid < nw ? sh[tid * K + i] : T(0);
+    warp_sum<K, T>(v);
   }
 }
 
-// Grid-wide sum.  Every thread of every block must call it.  Returns true in thread 0 of the
-// last block only, with tot[] holding the grid totals; the ticket counter is reset there.
+// Grid-wide sum of single-precision per-thread values.  Every thread of every block must call
+// it.  Returns true in thread 0 of the last block only, with tot[] holding the grid totals
+// (double); the ticket counter is reset there.
 template <int K>
-__device__ bool grid_sum(double (&v)[K], double* partials, unsigned* counter, double (&tot)[K]) {
-  __shared__ double sh[32 * K];
+__device__ bool grid_sum(float (&v)[K], double* partials, unsigned* counter, double (&tot)[K]) {
+  __shared__ float shf[32 * K];
+  __shared__ double shd[32 * K];
   __shared__ int is_last;
   int tid = linear_tid();
   int nblk = gridDim.x * gridDim.y * gridDim.z;
   int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
-  block_sum<K>(v, sh);
+  block_sum<K, float>(v, shf);
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) partials[(long long)bid * K + i] = v[i];
+    for (int i = 0; i < K; ++i) partials[(long long)bid * K + i] = (double)v[i];
     __threadfence();
     unsigned t = atomicAdd(counter, 1u);
     is_last = (t == (unsigned)(nblk - 1));
@@ -119,7 +149,7 @@ __device__ bool grid_sum(double (&v)[K], double* partials, unsigned* counter, do
   for (int b = tid; b < nblk; b += block_threads())
 #pragma unroll
     for (int i = 0; i < K; ++i) acc[i] += __ldcg(partials + (long long)b * K + i);
-  block_sum<K>(acc, sh);
+  block_sum<K, double>(acc, shd);
   if (tid == 0) {
 #pragma unroll
     for (int i = 0; i < K; ++i) tot[i] = acc[i];
@@ -127,6 +157,16 @@ __device__ bool grid_sum(double (&v)[K], double* partials, unsigned* counter, do
     return true;
   }
   return false;
+}
+
+// coordinates of field node n (C order)
+__device__ __forceinline__ void field_coords(const Geo& g, int n, int (&i)[3]) {
+  unsigned q0 = fdiv((unsigned)n, g.div0);
+  unsigned r = (unsigned)n - q0 * (unsigned)g.fs[0];
+  unsigned q1 = fdiv(r, g.div1);
+  i[0] = (int)q0;
+  i[1] = (int)q1;
+  i[2] = (int)(r - q1 * (unsigned)g.fs[1]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -141,30 +181,31 @@ struct Work {        // device buffers the launchers need
 
 // k_eval.cu
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
-                        float* grad, float* dco, float* eco, int seg, int it, const Work& w,
+                        float* grad, float* dco, float* eco, float* invd, int it, const Work& w,
                         cudaStream_t s);
+// trials t0 .. t0 + T - 1 with T = 1 when t0 == 0, else kLsBatch
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
-                              int ls_max, double c1, int seg, const Work& w, cudaStream_t s);
-cudaError_t launch_update(const Geo& g, float* b, const float* q, long long nf, int it,
-                          double* stats, const Work& w, cudaStream_t s);
+                              int ls_max, double c1, const Work& w, cudaStream_t s);
+cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
+                          const Work& w, cudaStream_t s);
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
-                           const float* b, float* Tp, float* Tm, int seg, cudaStream_t s);
-cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, int seg, cudaStream_t s);
+                           const float* b, float* Tp, float* Tm, cudaStream_t s);
+cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s);
 cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
 
 // k_pcg.cu
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
-                           const float* eco, int seg, cudaStream_t s);
+                           const float* eco, cudaStream_t s);
 cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
-                                   const float* dco, int seg, const Work& w, cudaStream_t s);
+                                   const float* invd, const Work& w, cudaStream_t s);
 cudaError_t launch_pcg_hp(const Geo& g, const float* z, const float* pold, float* pnew, float* Hp,
-                          const float* dco, const float* eco, int first, int seg, const Work& w,
+                          const float* dco, const float* eco, int first, const Work& w,
                           cudaStream_t s);
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
-                                     const float* Hp, float* z, const float* dco, int first,
-                                     double rtol, int seg, const Work& w, cudaStream_t s);
-cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* dco, int seg,
+                                     const float* Hp, float* z, const float* invd, int first,
+                                     double rtol, const Work& w, cudaStream_t s);
+cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s);
 int column_tile_width(int E);
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
@@ -181,6 +222,6 @@ cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void*
 int ot_tile_width(int E);
 cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
                       int* kp, int* km, const Work& w, cudaStream_t s);
-cudaError_t launch_blur(const Geo& g, const float* in, float* out, int seg, cudaStream_t s);
+cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s);
 
 }  // namespace hysco

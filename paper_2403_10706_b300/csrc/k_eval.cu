@@ -1,11 +1,13 @@
 // Objective kernels: J(b) = D + alpha S + beta P with gradient and Gauss-Newton coefficients
-// (Sec. 2.1 Eq. 1-5, Sec. 2.3.1), the multi-trial Armijo line search, the GN update, the
-// corrected images (Sec. 2.4) and the interpolation cell indices.
+// (Sec. 2.1 Eq. 1-5, Sec. 2.3.1), the Armijo line search, the GN update, the corrected images
+// (Sec. 2.4) and the interpolation cell indices.
 //
-// Thread mapping ("column march"): thread = (PE column c, segment of `seg` nodes along PE).
+// Thread mapping ("column march"): thread = (PE column c, segment of kSeg nodes along PE).
 // Consecutive threads own consecutive columns, so for pe_dim != 2 every PE step is a coalesced
-// row access.  A thread walks its segment keeping the two field nodes of the current cell and the
-// previous cell's residual row in registers; in-plane Laplacian neighbours are read through L1.
+// row access.  The segment loop is fully unrolled and every load is unconditional: indices are
+// clamped into range and absent neighbours are read at the node itself (zero Laplacian
+// difference), out-of-image interpolation taps are selected to zero after the load.  So a thread
+// issues all of its field loads, then all of its image gathers, with no serialising branches.
 // Per cell j (nodes j, j+1):
 //   bc = (b_j + b_{j+1}) / 2, delta = b_{j+1} - b_j, t+- = j +- bc      (averaging / FD operators)
 //   I(t) = I[i] + w (I[i+1] - I[i]), i = floor(t), w = t - i, I = 0 outside 0..m-1
@@ -13,7 +15,8 @@
 //   a = I+'(1 + delta) + I-'(1 - delta), c = I+(t+) + I-(t-);  dr/db_j = a/2 - c, dr/db_{j+1} = a/2 + c
 // Per node k the Gauss-Newton Hessian restricted to the column is tridiagonal:
 //   d_k = (dr_{k-1}/db_k)^2 + (dr_k/db_k)^2 + psi_{k-1} + psi_k,   e_k = dr_k/db_k * dr_k/db_{k+1} - psi_k
-// with psi = beta/2 phi''(delta); H v = vol [e_{k-1} v_{k-1} + d_k v_k + e_k v_{k+1} + alpha (L v)_k].
+// with psi = beta/2 phi''(delta); H v = vol [e_{k-1} v_{k-1} + d_k v_k + e_k v_{k+1} + alpha (L v)_k],
+// and the Jacobi preconditioner is 1 / (vol [d_k + alpha L_kk]).
 #include "hysco_internal.cuh"
 
 namespace hysco {
@@ -37,8 +40,11 @@ __device__ __forceinline__ int cell_index(float t, int m, float& w) {
 template <typename TI>
 __device__ __forceinline__ void interp(const TI* col, int inner, int m, int i, float w,
                                        float& val, float& slope) {
-  float I0 = (i >= 0 && i < m) ? ldf(col + (long long)i * inner) : 0.0f;
-  float I1 = (i >= -1 && i + 1 < m) ? ldf(col + (long long)(i + 1) * inner) : 0.0f;
+  int i0 = min(max(i, 0), m - 1), i1 = min(max(i + 1, 0), m - 1);
+  float I0 = ldf(col + i0 * inner);
+  float I1 = ldf(col + i1 * inner);
+  I0 = (i >= 0 && i < m) ? I0 : 0.0f;
+  I1 = (i >= -1 && i + 1 < m) ? I1 : 0.0f;
   slope = I1 - I0;
   val = fmaf(w, slope, I0);
 }
@@ -53,7 +59,7 @@ __device__ __forceinline__ void barrier(float z, float& f, float& df, float& d2f
   }
   float z2 = z * z;
   float q = (1.0f - z) * (1.0f + z);
-  float iq = 1.0f / q;
+  float iq = __frcp_rn(q);
   float z4 = z2 * z2;
   f = z4 * iq;
   df = (4.0f * z2 * z - 2.0f * z4 * z) * (iq * iq);
@@ -103,80 +109,95 @@ __device__ __forceinline__ void cell_residual(const TI* Ipc, const TI* Imc, int 
   barrier(delta, phi, df, d2);
 }
 
-struct Nbrs {   // in-plane neighbour columns of the field (base pointers, nullptr if absent)
-  const float *Am, *Ap, *Bm, *Bp;
-  float nin;    // wA * (#A neighbours) + wB * (#B neighbours)
+// in-plane neighbour columns of column c, clamped: an absent neighbour is the column itself
+struct ColNbrs {
+  int Am, Ap, Bm, Bp;
+  float nin;   // wA * (#A neighbours) + wB * (#B neighbours): in-plane part of L_kk
 };
 
-__device__ __forceinline__ Nbrs make_nbrs(const Geo& g, const float* f, int c) {
+__device__ __forceinline__ ColNbrs col_nbrs(const Geo& g, int c, int own) {
   int cA = c % g.nA, cB = c / g.nA;
-  Nbrs n;
-  n.Am = cA > 0 ? f + col_base(c - 1, g.inner, g.fld_ostride) : nullptr;
-  n.Ap = cA < g.nA - 1 ? f + col_base(c + 1, g.inner, g.fld_ostride) : nullptr;
-  n.Bm = cB > 0 ? f + col_base(c - g.nA, g.inner, g.fld_ostride) : nullptr;
-  n.Bp = cB < g.nB - 1 ? f + col_base(c + g.nA, g.inner, g.fld_ostride) : nullptr;
+  ColNbrs n;
+  n.Am = cA > 0 ? col_base(c - 1, g.inner, g.fld_ostride) : own;
+  n.Ap = cA < g.nA - 1 ? col_base(c + 1, g.inner, g.fld_ostride) : own;
+  n.Bm = cB > 0 ? col_base(c - g.nA, g.inner, g.fld_ostride) : own;
+  n.Bp = cB < g.nB - 1 ? col_base(c + g.nA, g.inner, g.fld_ostride) : own;
   n.nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
   return n;
 }
 
 // ------------------------------------------------------------------------------------------
-// J, grad J and the tridiagonal GN coefficients (d, e)
+// J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
 // ------------------------------------------------------------------------------------------
 
-template <typename TI>
+template <typename TI, int SEG>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-       float* __restrict__ grad, float* __restrict__ dco, float* __restrict__ eco, int seg,
-       int it, double* partials, unsigned* counter, DevState* st) {
+       float* __restrict__ grad, float* __restrict__ dco, float* __restrict__ eco,
+       float* __restrict__ invd, int it, double* partials, unsigned* counter, DevState* st) {
   if (it >= 0 && st->stop) return;
+  const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
-  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
-  if (c < g.ncols) {
-    const int inner = g.inner, m = g.m;
-    long long ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-    const TI* Ipc = Ip + ib;
-    const TI* Imc = Im + ib;
-    const float* bc = b + fb;
-    Nbrs nb = make_nbrs(g, b, c);
-    float jr_prev = 0.f, r_prev = 0.f, dphi_prev = 0.f, psi_prev = 0.f, b_prev = 0.f;
-    float bk = __ldg(bc + (long long)k0 * inner);
-    if (k0 > 0) {
-      b_prev = __ldg(bc + (long long)(k0 - 1) * inner);
-      CellLin q = cell_lin(Ipc, Imc, inner, m, k0 - 1, b_prev, bk, g.half_beta);
-      jr_prev = q.jr; r_prev = q.r; dphi_prev = q.dphi; psi_prev = q.psi;
-    }
-    for (int k = k0; k < k1; ++k) {
-      long long o = (long long)k * inner;
-      float bn = 0.f, jl = 0.f, jr = 0.f, r = 0.f, dphi = 0.f, psi = 0.f;
-      float lap = 0.f;
-      if (k < m) {
-        bn = __ldg(bc + o + inner);
-        CellLin q = cell_lin(Ipc, Imc, inner, m, k, bk, bn, g.half_beta);
-        jl = q.jl; jr = q.jr; r = q.r; dphi = q.dphi; psi = q.psi;
-        accD += r * r;
-        accP += q.phi;
-        float dd = bn - bk;
-        accS += dd * dd;
-        lap += bk - bn;
-      }
-      if (k > 0) lap += bk - b_prev;
-      float la = 0.f, lb = 0.f;
-      if (nb.Am) la += bk - __ldg(nb.Am + o);
-      if (nb.Ap) { float v = __ldg(nb.Ap + o); la += bk - v; accS += g.wA * (v - bk) * (v - bk); }
-      if (nb.Bm) lb += bk - __ldg(nb.Bm + o);
-      if (nb.Bp) { float v = __ldg(nb.Bp + o); lb += bk - v; accS += g.wB * (v - bk) * (v - bk); }
-      lap += g.wA * la + g.wB * lb;
-      float gk = g.vol * (jr_prev * r_prev + jl * r + g.alpha * lap + g.half_beta * (dphi_prev - dphi));
-      if (grad) grad[fb + o] = gk;
-      accG += gk * gk;
-      dco[fb + o] = jr_prev * jr_prev + jl * jl + psi_prev + psi;
-      eco[fb + o] = jl * jr - psi;
-      b_prev = bk; bk = bn;
-      jr_prev = jr; r_prev = r; dphi_prev = dphi; psi_prev = psi;
-    }
+  const bool act = c < g.ncols;
+  c = act ? c : g.ncols - 1;
+  const int k0 = blockIdx.y * SEG;
+  const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
+  const TI* Ipc = Ip + ib;
+  const TI* Imc = Im + ib;
+  const ColNbrs nb = col_nbrs(g, c, fb);
+
+  // field nodes k0-1 .. k0+SEG (clamped to [0, m]) and the in-plane neighbours of k0 .. k0+SEG-1
+  float bw[SEG + 2], bAm[SEG], bAp[SEG], bBm[SEG], bBp[SEG];
+#pragma unroll
+  for (int j = 0; j < SEG + 2; ++j)
+    bw[j] = __ldg(b + fb + min(max(k0 - 1 + j, 0), m) * inner);
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    int o = min(k0 + j, m) * inner;
+    bAm[j] = __ldg(b + nb.Am + o); bAp[j] = __ldg(b + nb.Ap + o);
+    bBm[j] = __ldg(b + nb.Bm + o); bBp[j] = __ldg(b + nb.Bp + o);
   }
-  double v[4] = {accD, accS, accP, accG}, tot[4];
+  // cells k0-1 .. k0+SEG-1; out-of-column cells contribute nothing
+  float cr[SEG + 1], cjl[SEG + 1], cjr[SEG + 1], cdphi[SEG + 1], cpsi[SEG + 1], cphi[SEG + 1];
+#pragma unroll
+  for (int j = 0; j <= SEG; ++j) {
+    int jc = k0 - 1 + j;
+    bool cv = jc >= 0 && jc < m;
+    CellLin q = cell_lin(Ipc, Imc, inner, m, jc, bw[j], bw[j + 1], g.half_beta);
+    cr[j] = cv ? q.r : 0.f;
+    cjl[j] = cv ? q.jl : 0.f;
+    cjr[j] = cv ? q.jr : 0.f;
+    cdphi[j] = cv ? q.dphi : 0.f;
+    cpsi[j] = cv ? q.psi : 0.f;
+    cphi[j] = cv ? q.phi : 0.f;
+  }
+  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    int k = k0 + j;
+    if (!act || k > m) continue;
+    float bk = bw[j + 1], bn = bw[j + 2];
+    float lap = (bk - bw[j]) + (bk - bn) + g.wA * ((bk - bAm[j]) + (bk - bAp[j])) +
+                g.wB * ((bk - bBm[j]) + (bk - bBp[j]));
+    float dPE = bn - bk, dA = bAp[j] - bk, dB = bBp[j] - bk;
+    accS += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
+    accD += cr[j + 1] * cr[j + 1];
+    accP += cphi[j + 1];
+    float gk = g.vol * (cjr[j] * cr[j] + cjl[j + 1] * cr[j + 1] + g.alpha * lap +
+                        g.half_beta * (cdphi[j] - cdphi[j + 1]));
+    float dk = cjr[j] * cjr[j] + cjl[j + 1] * cjl[j + 1] + cpsi[j] + cpsi[j + 1];
+    float ek = cjl[j + 1] * cjr[j + 1] - cpsi[j + 1];
+    float npe = (float)((k > 0) + (k < m));
+    float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
+    int o = fb + k * inner;
+    if (grad) grad[o] = gk;
+    dco[o] = dk;
+    eco[o] = ek;
+    invd[o] = diag > 0.f ? __frcp_rn(diag) : 1.0f;
+    accG += gk * gk;
+  }
+  float v[4] = {accD, accS, accP, accG};
+  double tot[4];
   if (grid_sum<4>(v, partials, counter, tot)) {
     double hv = 0.5 * (double)g.vol;
     double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
@@ -191,61 +212,68 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
 }
 
 // ------------------------------------------------------------------------------------------
-// Armijo line search: J(b + gamma_t q) for gamma_t = 2^-t, t = t0 .. t0+kLsBatch-1, in one pass;
-// the first accepted trial in order wins, exactly as sequential halving would pick it.
+// Armijo line search: J(b + gamma_t q) for gamma_t = 2^-t, t = t0 .. t0+T-1, in one pass; the
+// first accepted trial in order wins, exactly as sequential halving would pick it.  The first
+// launch tries gamma = 1 alone (accepted in most GN iterations); later launches try kLsBatch.
 // ------------------------------------------------------------------------------------------
 
-template <typename TI>
+template <typename TI, int SEG, int T>
 __global__ void __launch_bounds__(kBlock)
 k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
              const float* __restrict__ b, const float* __restrict__ q,
-             const float* __restrict__ grad, int t0, int ls_max, double c1, int seg,
+             const float* __restrict__ grad, int t0, int ls_max, double c1,
              double* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->ls_done) return;
-  constexpr int T = kLsBatch;
+  const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
-  float gam[T];
+  const bool act = c < g.ncols;
+  c = act ? c : g.ncols - 1;
+  const int k0 = blockIdx.y * SEG;
+  const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
+  const TI* Ipc = Ip + ib;
+  const TI* Imc = Im + ib;
+  const ColNbrs nb = col_nbrs(g, c, fb);
+  float bw[SEG + 1], qw[SEG + 1], bAp[SEG], qAp[SEG], bBp[SEG], qBp[SEG];
 #pragma unroll
-  for (int t = 0; t < T; ++t) gam[t] = ldexpf(1.0f, -(t0 + t));
+  for (int j = 0; j <= SEG; ++j) {
+    int o = fb + min(k0 + j, m) * inner;
+    bw[j] = __ldg(b + o);
+    qw[j] = __ldg(q + o);
+  }
+#pragma unroll
+  for (int j = 0; j < SEG; ++j) {
+    int o = min(k0 + j, m) * inner;
+    bAp[j] = __ldg(b + nb.Ap + o); qAp[j] = __ldg(q + nb.Ap + o);
+    bBp[j] = __ldg(b + nb.Bp + o); qBp[j] = __ldg(q + nb.Bp + o);
+  }
+  float agq = 0.f;
+  if (t0 == 0) {
+#pragma unroll
+    for (int j = 0; j < SEG; ++j)
+      if (act && k0 + j <= m) agq += __ldg(grad + fb + (k0 + j) * inner) * qw[j];
+  }
   float aD[T], aS[T], aP[T];
 #pragma unroll
-  for (int t = 0; t < T; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; }
-  float agq = 0.f;
-  if (c < g.ncols) {
-    const int inner = g.inner, m = g.m;
-    long long ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-    const TI* Ipc = Ip + ib;
-    const TI* Imc = Im + ib;
-    Nbrs nbb = make_nbrs(g, b, c);
-    Nbrs nbq = make_nbrs(g, q, c);
-    float bk = __ldg(b + fb + (long long)k0 * inner), qk = __ldg(q + fb + (long long)k0 * inner);
-    for (int k = k0; k < k1; ++k) {
-      long long o = (long long)k * inner;
-      if (t0 == 0) agq += __ldg(grad + fb + o) * qk;
-      float bn = 0.f, qn = 0.f;
-      if (k < m) { bn = __ldg(b + fb + o + inner); qn = __ldg(q + fb + o + inner); }
-      float bAp = 0.f, qAp = 0.f, bBp = 0.f, qBp = 0.f;
-      if (nbb.Ap) { bAp = __ldg(nbb.Ap + o); qAp = __ldg(nbq.Ap + o); }
-      if (nbb.Bp) { bBp = __ldg(nbb.Bp + o); qBp = __ldg(nbq.Bp + o); }
+  for (int t = 0; t < T; ++t) {
+    float gam = ldexpf(1.0f, -(t0 + t));
+    aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f;
+    float x[SEG + 1];
 #pragma unroll
-      for (int t = 0; t < T; ++t) {
-        float x0 = fmaf(gam[t], qk, bk);
-        if (k < m) {
-          float x1 = fmaf(gam[t], qn, bn);
-          float r, phi;
-          cell_residual(Ipc, Imc, inner, m, k, x0, x1, r, phi);
-          aD[t] += r * r;
-          aP[t] += phi;
-          aS[t] += (x1 - x0) * (x1 - x0);
-        }
-        if (nbb.Ap) { float y = fmaf(gam[t], qAp, bAp) - x0; aS[t] += g.wA * y * y; }
-        if (nbb.Bp) { float y = fmaf(gam[t], qBp, bBp) - x0; aS[t] += g.wB * y * y; }
-      }
-      bk = bn; qk = qn;
+    for (int j = 0; j <= SEG; ++j) x[j] = fmaf(gam, qw[j], bw[j]);
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      int k = k0 + j;
+      if (!act || k > m) continue;
+      float r = 0.f, phi = 0.f;
+      cell_residual(Ipc, Imc, inner, m, k, x[j], x[j + 1], r, phi);
+      if (k < m) { aD[t] += r * r; aP[t] += phi; }
+      float dPE = x[j + 1] - x[j];
+      float dA = fmaf(gam, qAp[j], bAp[j]) - x[j], dB = fmaf(gam, qBp[j], bBp[j]) - x[j];
+      aS[t] += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
     }
   }
-  double v[3 * T + 1], tot[3 * T + 1];
+  float v[3 * T + 1];
+  double tot[3 * T + 1];
 #pragma unroll
   for (int t = 0; t < T; ++t) { v[3 * t] = aD[t]; v[3 * t + 1] = aS[t]; v[3 * t + 2] = aP[t]; }
   v[3 * T] = agq;
@@ -264,14 +292,15 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
 }
 
 // b += gamma q; block 0 records the iteration's statistics row
-__global__ void k_update(float* __restrict__ b, const float* __restrict__ q, long long nf, int it,
-                         double* stats, DevState* st) {
+__global__ void __launch_bounds__(kBlock)
+k_update(float* __restrict__ b, const float* __restrict__ q, int nf, int it, double* stats,
+         DevState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     bool stopped_before = st->stop && st->stop_iter < it;
     bool stopped_now = st->stop && st->stop_iter == it;
     if (stats) {
-      double* row = stats + (long long)it * 10;
+      double* row = stats + it * 10;
       if (stopped_before) {
         for (int i = 0; i < 10; ++i) row[i] = nan;
       } else {
@@ -287,50 +316,63 @@ __global__ void k_update(float* __restrict__ b, const float* __restrict__ q, lon
     st->gn_iter = it + 1;
   }
   if (st->stop) return;
-  float gam = (float)st->gamma;
+  const float gam = (float)st->gamma;
   if (gam == 0.0f) return;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nf;
-       i += (long long)gridDim.x * blockDim.x)
-    b[i] = fmaf(gam, q[i], b[i]);
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (((uintptr_t)b & 15) == 0) {
+    int n4 = nf >> 2;
+    if (i < n4) {
+      float4 bv = reinterpret_cast<float4*>(b)[i];
+      float4 qv = __ldg(reinterpret_cast<const float4*>(q) + i);
+      bv.x = fmaf(gam, qv.x, bv.x); bv.y = fmaf(gam, qv.y, bv.y);
+      bv.z = fmaf(gam, qv.z, bv.z); bv.w = fmaf(gam, qv.w, bv.w);
+      reinterpret_cast<float4*>(b)[i] = bv;
+    }
+    if (i < (nf & 3)) b[4 * n4 + i] = fmaf(gam, q[4 * n4 + i], b[4 * n4 + i]);
+  } else {
+    for (int n = i; n < nf; n += gridDim.x * blockDim.x) b[n] = fmaf(gam, q[n], b[n]);
+  }
 }
 
 // corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta)
 template <typename TI>
 __global__ void __launch_bounds__(kBlock)
 k_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-          float* __restrict__ Tp, float* __restrict__ Tm, int seg) {
+          float* __restrict__ Tp, float* __restrict__ Tm) {
+  const int seg = kSeg;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int j0 = blockIdx.y * seg, j1 = min(j0 + seg, g.m);
   if (c >= g.ncols) return;
   const int inner = g.inner, m = g.m;
-  long long ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-  float bj = j0 < j1 ? __ldg(b + fb + (long long)j0 * inner) : 0.f;
+  int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
+  float bj = j0 < j1 ? __ldg(b + fb + j0 * inner) : 0.f;
   for (int j = j0; j < j1; ++j) {
-    float bn = __ldg(b + fb + (long long)(j + 1) * inner);
+    float bn = __ldg(b + fb + (j + 1) * inner);
     float tp, tm, wp, wm, vp, sp, vm, sm;
     cell_positions(bj, bn, j, tp, tm);
     int ip = cell_index(tp, m, wp), im = cell_index(tm, m, wm);
     interp(Ip + ib, inner, m, ip, wp, vp, sp);
     interp(Im + ib, inner, m, im, wm, vm, sm);
     float delta = bn - bj;
-    Tp[ib + (long long)j * inner] = vp * (1.0f + delta);
-    Tm[ib + (long long)j * inner] = vm * (1.0f - delta);
+    Tp[ib + j * inner] = vp * (1.0f + delta);
+    Tm[ib + j * inner] = vm * (1.0f - delta);
     bj = bn;
   }
 }
 
 __global__ void __launch_bounds__(kBlock)
-k_cells(Geo g, const float* __restrict__ b, int* __restrict__ cp, int* __restrict__ cm, int seg) {
+k_cells(Geo g, const float* __restrict__ b, int* __restrict__ cp, int* __restrict__ cm) {
+  const int seg = kSeg;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int j0 = blockIdx.y * seg, j1 = min(j0 + seg, g.m);
   if (c >= g.ncols) return;
-  long long ib = col_base(c, g.inner, g.img_ostride), fb = col_base(c, g.inner, g.fld_ostride);
+  int ib = col_base(c, g.inner, g.img_ostride), fb = col_base(c, g.inner, g.fld_ostride);
   for (int j = j0; j < j1; ++j) {
     float tp, tm, wp, wm;
-    cell_positions(__ldg(b + fb + (long long)j * g.inner), __ldg(b + fb + (long long)(j + 1) * g.inner),
+    cell_positions(__ldg(b + fb + j * g.inner), __ldg(b + fb + (j + 1) * g.inner),
                    j, tp, tm);
-    cp[ib + (long long)j * g.inner] = cell_index(tp, g.m, wp);
-    cm[ib + (long long)j * g.inner] = cell_index(tm, g.m, wm);
+    cp[ib + j * g.inner] = cell_index(tp, g.m, wp);
+    cm[ib + j * g.inner] = cell_index(tm, g.m, wm);
   }
 }
 
@@ -340,8 +382,8 @@ __global__ void k_publish_terms(double* terms, const DevState* st) {
 
 // ------------------------------------------------------------------------------------------
 
-static dim3 march_grid(const Geo& g, int nodes, int seg) {
-  return dim3(ceil_div(g.ncols, kBlock), ceil_div(nodes, seg));
+static dim3 march_grid(const Geo& g, int nodes) {
+  return dim3(ceil_div(g.ncols, kBlock), ceil_div(nodes, kSeg));
 }
 
 #define HYSCO_DISPATCH(dtype, T, ...)                                                  \
@@ -352,44 +394,50 @@ static dim3 march_grid(const Geo& g, int nodes, int seg) {
   }
 
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
-                        float* grad, float* dco, float* eco, int seg, int it, const Work& w,
+                        float* grad, float* dco, float* eco, float* invd, int it, const Work& w,
                         cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
-    k_eval<T><<<march_grid(g, g.E, seg), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, grad,
-                                                          dco, eco, seg, it, w.partials,
-                                                          w.counter, w.st))
+    (k_eval<T, kSeg><<<march_grid(g, g.E), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, grad,
+                                                           dco, eco, invd, it, w.partials,
+                                                           w.counter, w.st)))
   return cudaGetLastError();
 }
 
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
-                              int ls_max, double c1, int seg, const Work& w, cudaStream_t s) {
-  HYSCO_DISPATCH(dtype, T,
-    k_linesearch<T><<<march_grid(g, g.E, seg), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b,
-                                                                q, grad, t0, ls_max, c1, seg,
-                                                                w.partials, w.counter, w.st))
+                              int ls_max, double c1, const Work& w, cudaStream_t s) {
+  if (t0 == 0) {
+    HYSCO_DISPATCH(dtype, T,
+      (k_linesearch<T, kSeg, 1><<<march_grid(g, g.E), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
+          w.st)))
+  } else {
+    HYSCO_DISPATCH(dtype, T,
+      (k_linesearch<T, kSeg, kLsBatch><<<march_grid(g, g.E), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
+          w.st)))
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_update(const Geo& g, float* b, const float* q, long long nf, int it,
-                          double* stats, const Work& w, cudaStream_t s) {
-  (void)g;
-  int blocks = (int)((nf + kBlock - 1) / kBlock);
-  if (blocks > 148 * 16) blocks = 148 * 16;
-  k_update<<<blocks, kBlock, 0, s>>>(b, q, nf, it, stats, w.st);
+cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
+                          const Work& w, cudaStream_t s) {
+  int blocks = ((uintptr_t)b & 15) == 0 ? ceil_div((g.nf >> 2) > 0 ? (g.nf >> 2) : 1, kBlock)
+                                        : 148 * 8;
+  k_update<<<blocks, kBlock, 0, s>>>(b, q, g.nf, it, stats, w.st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
-                           const float* b, float* Tp, float* Tm, int seg, cudaStream_t s) {
+                           const float* b, float* Tp, float* Tm, cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
-    k_correct<T><<<march_grid(g, g.m, seg), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, Tp,
-                                                             Tm, seg))
+    (k_correct<T><<<march_grid(g, g.m), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, Tp,
+                                                         Tm)))
   return cudaGetLastError();
 }
 
-cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, int seg, cudaStream_t s) {
-  k_cells<<<march_grid(g, g.m, seg), kBlock, 0, s>>>(g, b, cp, cm, seg);
+cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s) {
+  k_cells<<<march_grid(g, g.m), kBlock, 0, s>>>(g, b, cp, cm);
   return cudaGetLastError();
 }
 

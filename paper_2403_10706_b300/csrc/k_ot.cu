@@ -19,11 +19,11 @@ namespace hysco {
 
 template <typename TI>
 __global__ void __launch_bounds__(kBlock)
-k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, long long n, float eps,
+k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, int n, float eps,
            double* partials, unsigned* counter, DevState* st) {
   float mn = __int_as_float(0x7f800000), mx = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += gridDim.x * blockDim.x) {
     float a = ldf(Ip + i), b = ldf(Im + i);
     mn = fminf(mn, fminf(a, b));
     mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(b)));
@@ -107,12 +107,12 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
   int c = blockIdx.x * CW + tx;
   bool act = c < g.ncols;
   float s = (float)st->ot_shift;
-  long long ib = act ? col_base(c, g.inner, g.img_ostride) : 0;
+  int ib = act ? col_base(c, g.inner, g.img_ostride) : 0;
   for (int k = ty; k < m; k += blockDim.y) {
     float a = 0.f, b = 0.f;
     if (act) {
-      a = __fadd_rn(ldf(Ip + ib + (long long)k * g.inner), s);
-      b = __fadd_rn(ldf(Im + ib + (long long)k * g.inner), s);
+      a = __fadd_rn(ldf(Ip + ib + k * g.inner), s);
+      b = __fadd_rn(ldf(Im + ib + k * g.inner), s);
     }
     Cp[(k + 1) * CW + tx] = a;
     Cm[(k + 1) * CW + tx] = b;
@@ -140,9 +140,9 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
     }
   __syncthreads();
   if (!act) return;
-  long long fb = col_base(c, g.inner, g.fld_ostride);
+  int fb = col_base(c, g.inner, g.fld_ostride);
   for (int k = ty; k <= m; k += blockDim.y) {
-    long long i = fb + (long long)k * g.inner;
+    int i = fb + k * g.inner;
     if (!ok) {
       b0[i] = 0.f;
       if (INDICES) { kp[i] = 0; km[i] = 0; }
@@ -159,12 +159,13 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
 
 // 27-point separable Gaussian with replicate boundary on the field grid
 __global__ void __launch_bounds__(kBlock)
-k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, int seg, float w0, float w1) {
+k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
+  const int seg = kSeg;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
   if (c >= g.ncols) return;
   int cA = c % g.nA, cB = c / g.nA;
-  long long base[3][3];
+  int base[3][3];
   float wt[3] = {w1, w0, w1};
 #pragma unroll
   for (int db = -1; db <= 1; ++db)
@@ -183,12 +184,12 @@ k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, int seg, fl
       for (int da = 0; da < 3; ++da) {
         float acca = 0.f;
 #pragma unroll
-        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * __ldg(in + base[db][da] + (long long)kk[dk] * g.inner);
+        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * __ldg(in + base[db][da] + kk[dk] * g.inner);
         accb += wt[da] * acca;
       }
       acc += wt[db] * accb;
     }
-    out[col_base(c, g.inner, g.fld_ostride) + (long long)k * g.inner] = acc;
+    out[col_base(c, g.inner, g.fld_ostride) + k * g.inner] = acc;
   }
 }
 
@@ -236,11 +237,11 @@ cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, f
              : ot_one<__half, false>(g, Ip, Im, b0, kp, km, w, s);
 }
 
-cudaError_t launch_blur(const Geo& g, const float* in, float* out, int seg, cudaStream_t s) {
+cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s) {
   double e = std::exp(-0.5);   // the sigma = 1 Gaussian at distance 1 voxel
   float w0 = (float)(1.0 / (1.0 + 2.0 * e)), w1 = (float)(e / (1.0 + 2.0 * e));
-  k_blur<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, seg)), kBlock, 0, s>>>(g, in, out, seg,
-                                                                                w0, w1);
+  k_blur<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, kSeg)), kBlock, 0, s>>>(g, in, out, w0,
+                                                                                 w1);
   return cudaGetLastError();
 }
 

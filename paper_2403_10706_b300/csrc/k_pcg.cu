@@ -17,82 +17,64 @@
 
 namespace hysco {
 
-__device__ __forceinline__ float jacobi_diag(const Geo& g, float d, int k, float nin) {
-  float npe = (float)((k > 0) + (k < g.m));
-  return g.vol * (d + g.alpha * (npe + nin));
-}
+// ------------------------------------------------------------------------------------------
+// H v: one thread per field node (kNpt nodes per thread, a block apart), coordinates by fast
+// division, and branch-free neighbours: an absent neighbour (Neumann end) is read at the node
+// itself, which zeroes its Laplacian difference, so all loads issue back to back.
+// ------------------------------------------------------------------------------------------
 
-struct NbrCols {
-  long long Am, Ap, Bm, Bp;   // field base offsets of the in-plane neighbours, -1 if absent
-  float nin;
-};
-
-__device__ __forceinline__ NbrCols nbr_cols(const Geo& g, int c) {
-  int cA = c % g.nA, cB = c / g.nA;
-  NbrCols n;
-  n.Am = cA > 0 ? col_base(c - 1, g.inner, g.fld_ostride) : -1;
-  n.Ap = cA < g.nA - 1 ? col_base(c + 1, g.inner, g.fld_ostride) : -1;
-  n.Bm = cB > 0 ? col_base(c - g.nA, g.inner, g.fld_ostride) : -1;
-  n.Bp = cB < g.nB - 1 ? col_base(c + g.nA, g.inner, g.fld_ostride) : -1;
-  n.nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
-  return n;
-}
-
-// value of the PCG direction at field offset i: p = z (first) or z + beta p_old
 template <bool PCG>
-__device__ __forceinline__ float pval(const float* z, const float* pold, long long i, float beta,
-                                      int first) {
+__device__ __forceinline__ float pval(const float* __restrict__ z, const float* __restrict__ pold,
+                                      int i, float beta, int first) {
   if (!PCG || first) return __ldg(z + i);
   return fmaf(beta, __ldg(pold + i), __ldg(z + i));
 }
 
-// Hv (PCG = false: v = z, no reduction) or the fused PCG step (PCG = true: p_new = z + beta p_old).
 template <bool PCG>
 __global__ void __launch_bounds__(kBlock)
 k_hv(Geo g, const float* __restrict__ z, const float* __restrict__ pold, float* __restrict__ pnew,
      float* __restrict__ Hp, const float* __restrict__ dco, const float* __restrict__ eco,
-     int first, int seg, double* partials, unsigned* counter, DevState* st) {
+     int first, double* partials, unsigned* counter, DevState* st) {
   float beta = 0.f;
   if (PCG) {
     if (st->stop || st->pcg_done) return;
     beta = first ? 0.f : (float)st->beta_cg;
   }
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
   float acc = 0.f;
-  if (c < g.ncols) {
-    const int inner = g.inner;
-    long long fb = col_base(c, inner, g.fld_ostride);
-    NbrCols nb = nbr_cols(g, c);
-    float p_prev = 0.f, e_prev = 0.f;
-    if (k0 > 0) {
-      p_prev = pval<PCG>(z, pold, fb + (long long)(k0 - 1) * inner, beta, first);
-      e_prev = __ldg(eco + fb + (long long)(k0 - 1) * inner);
+  const int base = blockIdx.x * (kBlock * kNpt) + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kNpt; ++u) {
+    int n = base + u * kBlock;
+    bool valid = n < g.nf;
+    n = valid ? n : g.nf - 1;
+    int ix[3];
+    field_coords(g, n, ix);
+    float pk = pval<PCG>(z, pold, n, beta, first);
+    float lap = 0.f, pe_lo = pk, pe_hi = pk;
+    int n_lo_pe = n;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      int lo = ix[a] > 0 ? n - g.fs[a] : n;
+      int hi = ix[a] < g.fe[a] - 1 ? n + g.fs[a] : n;
+      float pl = pval<PCG>(z, pold, lo, beta, first);
+      float ph = pval<PCG>(z, pold, hi, beta, first);
+      lap += g.w[a] * ((pk - pl) + (pk - ph));
+      if (a == g.p) { pe_lo = pl; pe_hi = ph; n_lo_pe = lo; }
     }
-    float pk = pval<PCG>(z, pold, fb + (long long)k0 * inner, beta, first);
-    for (int k = k0; k < k1; ++k) {
-      long long o = (long long)k * inner;
-      float pn = k < g.m ? pval<PCG>(z, pold, fb + o + inner, beta, first) : 0.f;
-      float dk = __ldg(dco + fb + o), ek = __ldg(eco + fb + o);
-      float lap = 0.f, la = 0.f, lb = 0.f;
-      if (k > 0) lap += pk - p_prev;
-      if (k < g.m) lap += pk - pn;
-      if (nb.Am >= 0) la += pk - pval<PCG>(z, pold, nb.Am + o, beta, first);
-      if (nb.Ap >= 0) la += pk - pval<PCG>(z, pold, nb.Ap + o, beta, first);
-      if (nb.Bm >= 0) lb += pk - pval<PCG>(z, pold, nb.Bm + o, beta, first);
-      if (nb.Bp >= 0) lb += pk - pval<PCG>(z, pold, nb.Bp + o, beta, first);
-      lap += g.wA * la + g.wB * lb;
-      float hv = g.vol * (e_prev * p_prev + dk * pk + ek * pn + g.alpha * lap);
-      Hp[fb + o] = hv;
+    float em1 = __ldg(eco + n_lo_pe);
+    em1 = n_lo_pe != n ? em1 : 0.f;
+    float hv = g.vol * (em1 * pe_lo + __ldg(dco + n) * pk + __ldg(eco + n) * pe_hi + g.alpha * lap);
+    if (valid) {
+      Hp[n] = hv;
       if (PCG) {
-        pnew[fb + o] = pk;
+        pnew[n] = pk;
         acc += pk * hv;
       }
-      p_prev = pk; pk = pn; e_prev = ek;
     }
   }
   if (!PCG) return;
-  double v[1] = {acc}, tot[1];
+  float v[1] = {acc};
+  double tot[1];
   if (grid_sum<1>(v, partials, counter, tot)) {
     double pHp = tot[0];
     if (!(pHp > 0.0)) {
@@ -103,28 +85,45 @@ k_hv(Geo g, const float* __restrict__ z, const float* __restrict__ pold, float* 
   }
 }
 
+// ------------------------------------------------------------------------------------------
+// elementwise PCG steps, float4 over the flat field (workspace arrays are 256-byte aligned);
+// the inverse Jacobi diagonal comes from the eval kernel.
+// ------------------------------------------------------------------------------------------
+
+__device__ __forceinline__ float4 ld4(const float* p, int i) {
+  return __ldg(reinterpret_cast<const float4*>(p) + i);
+}
+__device__ __forceinline__ void st4(float* p, int i, float4 v) {
+  reinterpret_cast<float4*>(p)[i] = v;
+}
+
 // PCG init with Jacobi: r = -grad, x = 0, z = r / diag; rr0 = r.r, rho = r.z
 __global__ void __launch_bounds__(kBlock)
 k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float* __restrict__ x,
-                  float* __restrict__ r, float* __restrict__ z, const float* __restrict__ dco,
-                  int seg, double* partials, unsigned* counter, DevState* st) {
+                  float* __restrict__ r, float* __restrict__ z, const float* __restrict__ invd,
+                  double* partials, unsigned* counter, DevState* st) {
   if (st->stop) return;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
   float arr = 0.f, arz = 0.f;
-  if (c < g.ncols) {
-    long long fb = col_base(c, g.inner, g.fld_ostride);
-    NbrCols nb = nbr_cols(g, c);
-    for (int k = k0; k < k1; ++k) {
-      long long i = fb + (long long)k * g.inner;
-      float rk = -__ldg(grad + i);
-      float dg = jacobi_diag(g, __ldg(dco + i), k, nb.nin);
-      float zk = dg > 0.f ? rk / dg : rk;
-      x[i] = 0.f; r[i] = rk; z[i] = zk;
-      arr += rk * rk; arz += rk * zk;
-    }
+  int n4 = g.nf >> 2;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n4) {
+    float4 gv = ld4(grad, i), dv = ld4(invd, i);
+    float4 rv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
+    float4 zv = make_float4(rv.x * dv.x, rv.y * dv.y, rv.z * dv.z, rv.w * dv.w);
+    st4(x, i, make_float4(0.f, 0.f, 0.f, 0.f));
+    st4(r, i, rv);
+    st4(z, i, zv);
+    arr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    arz = rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
   }
-  double v[2] = {arr, arz}, tot[2];
+  int t = 4 * n4 + i;   // tail (fewer than 4 nodes)
+  if (i < (g.nf & 3)) {
+    float rk = -__ldg(grad + t), zk = rk * __ldg(invd + t);
+    x[t] = 0.f; r[t] = rk; z[t] = zk;
+    arr += rk * rk; arz += rk * zk;
+  }
+  float v[2] = {arr, arz};
+  double tot[2];
   if (grid_sum<2>(v, partials, counter, tot)) {
     st->rr0 = tot[0]; st->rr = tot[0]; st->rho = tot[1];
     st->pcg_iter = 0;
@@ -149,45 +148,48 @@ __device__ __forceinline__ void pcg_finish(DevState* st, double rr, double rz, d
 __global__ void __launch_bounds__(kBlock)
 k_pcg_update_jacobi(Geo g, float* __restrict__ x, float* __restrict__ r,
                     const float* __restrict__ p, const float* __restrict__ Hp,
-                    float* __restrict__ z, const float* __restrict__ dco, int first, double rtol,
-                    int seg, double* partials, unsigned* counter, DevState* st) {
+                    float* __restrict__ z, const float* __restrict__ invd, int first, double rtol,
+                    double* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->pcg_done) return;
-  float a = (float)st->alpha_cg;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
+  const float a = (float)st->alpha_cg;
   float arr = 0.f, arz = 0.f;
-  if (c < g.ncols) {
-    long long fb = col_base(c, g.inner, g.fld_ostride);
-    NbrCols nb = nbr_cols(g, c);
-    for (int k = k0; k < k1; ++k) {
-      long long i = fb + (long long)k * g.inner;
-      float pk = __ldg(p + i);
-      x[i] = first ? a * pk : fmaf(a, pk, x[i]);
-      float rk = fmaf(-a, __ldg(Hp + i), r[i]);
-      r[i] = rk;
-      float dg = jacobi_diag(g, __ldg(dco + i), k, nb.nin);
-      float zk = dg > 0.f ? rk / dg : rk;
-      z[i] = zk;
-      arr += rk * rk; arz += rk * zk;
-    }
+  int n4 = g.nf >> 2;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n4) {
+    float4 pv = ld4(p, i), hv = ld4(Hp, i), dv = ld4(invd, i);
+    float4 rv = reinterpret_cast<const float4*>(r)[i];
+    float4 xv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(x)[i];
+    xv.x = fmaf(a, pv.x, xv.x); xv.y = fmaf(a, pv.y, xv.y);
+    xv.z = fmaf(a, pv.z, xv.z); xv.w = fmaf(a, pv.w, xv.w);
+    rv.x = fmaf(-a, hv.x, rv.x); rv.y = fmaf(-a, hv.y, rv.y);
+    rv.z = fmaf(-a, hv.z, rv.z); rv.w = fmaf(-a, hv.w, rv.w);
+    float4 zv = make_float4(rv.x * dv.x, rv.y * dv.y, rv.z * dv.z, rv.w * dv.w);
+    st4(x, i, xv);
+    st4(r, i, rv);
+    st4(z, i, zv);
+    arr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+    arz = rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
   }
-  double v[2] = {arr, arz}, tot[2];
+  int t = 4 * n4 + i;
+  if (i < (g.nf & 3)) {
+    float pk = p[t];
+    x[t] = first ? a * pk : fmaf(a, pk, x[t]);
+    float rk = fmaf(-a, Hp[t], r[t]);
+    r[t] = rk;
+    float zk = rk * invd[t];
+    z[t] = zk;
+    arr += rk * rk; arz += rk * zk;
+  }
+  float v[2] = {arr, arz};
+  double tot[2];
   if (grid_sum<2>(v, partials, counter, tot)) pcg_finish(st, tot[0], tot[1], rtol);
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_jacobi_apply(Geo g, const float* __restrict__ r, float* __restrict__ z,
-               const float* __restrict__ dco, int seg) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
-  if (c >= g.ncols) return;
-  long long fb = col_base(c, g.inner, g.fld_ostride);
-  NbrCols nb = nbr_cols(g, c);
-  for (int k = k0; k < k1; ++k) {
-    long long i = fb + (long long)k * g.inner;
-    float dg = jacobi_diag(g, __ldg(dco + i), k, nb.nin);
-    z[i] = dg > 0.f ? __ldg(r + i) / dg : __ldg(r + i);
-  }
+               const float* __restrict__ invd) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n < g.nf) z[n] = __ldg(r + n) * __ldg(invd + n);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -216,7 +218,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   int tx = threadIdx.x, ty = threadIdx.y;
   int c = blockIdx.x * CW + tx;
   bool act = c < g.ncols;
-  long long fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
+  int fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
   float nin = 0.f;
   if (act) {
     int cA = c % g.nA, cB = c / g.nA;
@@ -225,7 +227,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   for (int k = ty; k < E; k += blockDim.y) {
     float dv = 1.f, ov = 0.f;
     if (act) {
-      long long i = fb + (long long)k * g.inner;
+      int i = fb + k * g.inner;
       float npe = (float)((k > 0) + (k < g.m));
       dv = g.vol * (__ldg(dco + i) + g.alpha * (npe + nin));
       ov = k < g.m ? g.vol * (__ldg(eco + i) - g.alpha) : 0.f;
@@ -250,7 +252,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   __syncthreads();
   if (act)
     for (int k = ty; k < E; k += blockDim.y) {
-      long long i = fb + (long long)k * g.inner;
+      int i = fb + k * g.inner;
       invD[i] = dia[k * CW + tx];
       lco[i] = off[k * CW + tx];
     }
@@ -273,13 +275,13 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
   int tx = threadIdx.x, ty = threadIdx.y;
   int c = blockIdx.x * CW + tx;
   bool act = c < g.ncols;
-  long long fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
+  int fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
   float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
   float arr = 0.f, arz = 0.f;
   for (int k = ty; k < E; k += blockDim.y) {
     float rk = 0.f, lk = 0.f, idk = 1.f;
     if (act) {
-      long long i = fb + (long long)k * g.inner;
+      int i = fb + k * g.inner;
       if (MODE == 0) {
         rk = r[i];
       } else if (MODE == 1) {
@@ -317,13 +319,14 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
   __syncthreads();
   if (act)
     for (int k = ty; k < E; k += blockDim.y) {
-      long long i = fb + (long long)k * g.inner;
+      int i = fb + k * g.inner;
       float zk = R[k * CW + tx];
       z[i] = zk;
       if (MODE != 0) arz += r[i] * zk;
     }
   if (MODE == 0) return;
-  double v[2] = {arr, arz}, tot[2];
+  float v[2] = {arr, arz};
+  double tot[2];
   if (grid_sum<2>(v, partials, counter, tot)) {
     if (MODE == 1) {
       st->rr0 = tot[0]; st->rr = tot[0]; st->rho = tot[1];
@@ -338,43 +341,42 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
 
 // ------------------------------------------------------------------------------------------
 
-static dim3 field_grid(const Geo& g, int seg) {
-  return dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, seg));
-}
+static int flat_blocks(const Geo& g) { return ceil_div(g.nf, kBlock * kNpt); }
+static int vec_blocks(const Geo& g) { return ceil_div((g.nf >> 2) > 0 ? (g.nf >> 2) : 1, kBlock); }
 
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
-                           const float* eco, int seg, cudaStream_t s) {
-  k_hv<false><<<field_grid(g, seg), kBlock, 0, s>>>(g, v, nullptr, nullptr, Hv, dco, eco, 0, seg,
-                                                    nullptr, nullptr, nullptr);
+                           const float* eco, cudaStream_t s) {
+  k_hv<false><<<flat_blocks(g), kBlock, 0, s>>>(g, v, nullptr, nullptr, Hv, dco, eco, 0, nullptr,
+                                                nullptr, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
-                                   const float* dco, int seg, const Work& w, cudaStream_t s) {
-  k_pcg_init_jacobi<<<field_grid(g, seg), kBlock, 0, s>>>(g, grad, x, r, z, dco, seg, w.partials,
-                                                          w.counter, w.st);
+                                   const float* invd, const Work& w, cudaStream_t s) {
+  k_pcg_init_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, grad, x, r, z, invd, w.partials,
+                                                     w.counter, w.st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_hp(const Geo& g, const float* z, const float* pold, float* pnew, float* Hp,
-                          const float* dco, const float* eco, int first, int seg, const Work& w,
+                          const float* dco, const float* eco, int first, const Work& w,
                           cudaStream_t s) {
-  k_hv<true><<<field_grid(g, seg), kBlock, 0, s>>>(g, z, pold, pnew, Hp, dco, eco, first, seg,
-                                                   w.partials, w.counter, w.st);
+  k_hv<true><<<flat_blocks(g), kBlock, 0, s>>>(g, z, pold, pnew, Hp, dco, eco, first, w.partials,
+                                               w.counter, w.st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
-                                     const float* Hp, float* z, const float* dco, int first,
-                                     double rtol, int seg, const Work& w, cudaStream_t s) {
-  k_pcg_update_jacobi<<<field_grid(g, seg), kBlock, 0, s>>>(g, x, r, p, Hp, z, dco, first, rtol,
-                                                            seg, w.partials, w.counter, w.st);
+                                     const float* Hp, float* z, const float* invd, int first,
+                                     double rtol, const Work& w, cudaStream_t s) {
+  k_pcg_update_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, x, r, p, Hp, z, invd, first, rtol,
+                                                       w.partials, w.counter, w.st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* dco, int seg,
+cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s) {
-  k_jacobi_apply<<<field_grid(g, seg), kBlock, 0, s>>>(g, r, z, dco, seg);
+  k_jacobi_apply<<<ceil_div(g.nf, kBlock), kBlock, 0, s>>>(g, r, z, invd);
   return cudaGetLastError();
 }
 

@@ -125,8 +125,12 @@ class Hysco:
         return b, (st[:gn_iters] if st is not None else None)
 
     def last_status(self):
-        return _lib.check(self.lib.hysco_last_status(self._h, _stream(self.device)),
-                          "hysco_last_status")
+        """Numerical status of the last eval / solve / init_ot: 0 ok, 1 infeasible (J = +inf),
+        -4 NaN.  Synchronises the current stream; raises only on a CUDA error."""
+        st = self.lib.hysco_last_status(self._h, _stream(self.device))
+        if st in (_lib.ECUDA, _lib.EINVAL):
+            _lib.check(st, "hysco_last_status")
+        return st
 
     def cell_indices(self, b):
         cp = torch.empty(self.dims, dtype=torch.int32, device=self.device)

@@ -102,7 +102,22 @@ def test_hessvec_and_preconditioners_match_oracle(H, orc, dims, spacing, p):
     P = orc.Problem(dims, spacing, p, ALPHA, BETA)
     check_field(host(h.hessvec(dev(v))), P.hessvec(Ip, Im, b, v), "Hv")
     check_field(host(h.precond(dev(v), 0)), P.precond(Ip, Im, b, v, 0), "jacobi")
-    check_field(host(h.precond(dev(v), 1)), P.precond(Ip, Im, b, v, 1), "column", 1e-4, 1e-3)
+    # column blocks: FP32 Thomas is backward stable; its forward error grows with the block's
+    # condition number (a lone column has only the weak data term against the constant null
+    # space of alpha * L), so the check is on the residual of the oracle's blocks
+    # (backward error  max|M z - r| / max(|M| |z| + |r|), M = the oracle's blocks)
+    zc = host(h.precond(dev(v), 1)).astype(np.float64)
+    dia, off = P.column_blocks(Ip, Im, b)
+    Mz, Maz = dia * zc, np.abs(dia * zc)
+    lo = [slice(None)] * 3; hi = [slice(None)] * 3
+    lo[p] = slice(0, -1); hi[p] = slice(1, None)
+    lo, hi = tuple(lo), tuple(hi)
+    Mz[lo] += off[lo] * zc[hi]; Maz[lo] += np.abs(off[lo] * zc[hi])
+    Mz[hi] += off[lo] * zc[lo]; Maz[hi] += np.abs(off[lo] * zc[lo])
+    eta = np.abs(Mz - v).max() / (Maz + np.abs(v)).max()
+    assert eta <= 1e-5, eta
+    if dims[0] * dims[1] * dims[2] // dims[p] > 1:
+        check_field(zc, P.precond(Ip, Im, b, v, 1), "column", 1e-4, 1e-3)
 
 
 @pytest.mark.parametrize("dims,spacing,p", SHAPES)
