@@ -144,6 +144,25 @@ int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell
 int hysco_ot_indices(hysco_t h, const void* Ip, const void* Im, double eps, int32_t* kidx_p,
                      int32_t* kidx_m, hysco_stream_t stream);
 
+/* Allocation-free objective: J, D, S, P (terms_dev, 4 device doubles) and, when grad is
+ * non-NULL, the gradient, for callers that cannot allocate device memory -- for example code
+ * running under a memory manager that owns the whole device budget, or latency-critical callers
+ * for which cudaMalloc's implicit synchronisation is unacceptable.  The paper has no counterpart:
+ * this is a library convenience around the same per-cell arithmetic as hysco_eval.
+ * Takes the geometry of hysco_create by value and needs no handle.  Its only scratch (the
+ * per-block partial sums of the reduction and a ticket counter, 1 MiB plus 256 bytes) lives in a
+ * static device array that every GPU loading this library holds until the process exits; the
+ * call allocates nothing.  The first call on each device (with that device current) looks up the
+ * array's device address, so make that first call before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU (two streams, or two host threads) race and give
+ * wrong results; calls ordered on one stream are safe.  Volumes whose reduction grid exceeds
+ * 32768 blocks (ceil(columns / 256) * ceil((m + 1) / 4)) return HYSCO_EINVAL.  No status word is
+ * kept: J = +inf means barrier-infeasible, NaN means non-finite input.  No Gauss-Newton
+ * coefficients are stored (use the handle-based hysco_eval for hysco_hessvec / hysco_precond). */
+int hysco_eval_static(const int64_t dims[3], const double spacing[3], int pe_dim, double alpha,
+                      double beta, int img_dtype, const void* Ip, const void* Im, const float* b,
+                      double* terms_dev, float* grad, hysco_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

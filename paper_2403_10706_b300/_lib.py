@@ -63,6 +63,7 @@ def load():
         "hysco_last_status": (I, [P, P]),
         "hysco_cell_indices": (I, [P, P, P, P, P]),
         "hysco_ot_indices": (I, [P, P, P, D, P, P, P]),
+        "hysco_eval_static": (I, [I64P, C.POINTER(C.c_double), I, D, D, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -17,114 +17,9 @@
 //   d_k = (dr_{k-1}/db_k)^2 + (dr_k/db_k)^2 + psi_{k-1} + psi_k,   e_k = dr_k/db_k * dr_k/db_{k+1} - psi_k
 // with psi = beta/2 phi''(delta); H v = vol [e_{k-1} v_{k-1} + d_k v_k + e_k v_{k+1} + alpha (L v)_k],
 // and the Jacobi preconditioner is 1 / (vol [d_k + alpha L_kk]).
-#include "hysco_internal.cuh"
+#include "eval_common.cuh"
 
 namespace hysco {
-
-// positions of cell j: single-precision, no contraction (bit-reproducible cell indices)
-__device__ __forceinline__ void cell_positions(float bj, float bj1, int j, float& tp, float& tm) {
-  float bc = __fmul_rn(__fadd_rn(bj, bj1), 0.5f);
-  float jf = (float)j;
-  tp = __fadd_rn(jf, bc);
-  tm = __fsub_rn(jf, bc);
-}
-
-// floor(t) clamped to [-2, m + 1] (zero interpolation beyond), and the exact weight t - floor(t)
-__device__ __forceinline__ int cell_index(float t, int m, float& w) {
-  float f = floorf(t);
-  w = __fsub_rn(t, f);
-  f = fminf(fmaxf(f, -2.0f), (float)(m + 1));
-  return (int)f;
-}
-
-template <typename TI>
-__device__ __forceinline__ void interp(const TI* col, int inner, int m, int i, float w,
-                                       float& val, float& slope) {
-  int i0 = min(max(i, 0), m - 1), i1 = min(max(i + 1, 0), m - 1);
-  float I0 = ldf(col + i0 * inner);
-  float I1 = ldf(col + i1 * inner);
-  I0 = (i >= 0 && i < m) ? I0 : 0.0f;
-  I1 = (i >= -1 && i + 1 < m) ? I1 : 0.0f;
-  slope = I1 - I0;
-  val = fmaf(w, slope, I0);
-}
-
-// phi(z) = z^4 / (1 - z^2) on (-1, 1), +inf outside (Eq. 3), and its first two derivatives
-__device__ __forceinline__ void barrier(float z, float& f, float& df, float& d2f) {
-  if (!(fabsf(z) < 1.0f)) {
-    f = (z != z) ? z : __int_as_float(0x7f800000);
-    df = 0.0f;
-    d2f = 0.0f;
-    return;
-  }
-  float z2 = z * z;
-  float q = (1.0f - z) * (1.0f + z);
-  float iq = __frcp_rn(q);
-  float z4 = z2 * z2;
-  f = z4 * iq;
-  df = (4.0f * z2 * z - 2.0f * z4 * z) * (iq * iq);
-  d2f = (12.0f * z2 - 6.0f * z4 + 2.0f * z4 * z2) * (iq * iq * iq);
-}
-
-struct CellLin {
-  float r, jl, jr, dphi, psi, phi;
-};
-
-template <typename TI>
-__device__ __forceinline__ CellLin cell_lin(const TI* Ipc, const TI* Imc, int inner, int m, int j,
-                                            float bj, float bj1, float half_beta) {
-  float tp, tm, wp, wm;
-  cell_positions(bj, bj1, j, tp, tm);
-  int ip = cell_index(tp, m, wp), im = cell_index(tm, m, wm);
-  float vp, sp, vm, sm;
-  interp(Ipc, inner, m, ip, wp, vp, sp);
-  interp(Imc, inner, m, im, wm, vm, sm);
-  float delta = bj1 - bj;
-  float op = 1.0f + delta, om = 1.0f - delta;
-  CellLin q;
-  q.r = vp * op - vm * om;
-  float a = sp * op + sm * om;
-  float c = vp + vm;
-  q.jl = 0.5f * a - c;
-  q.jr = 0.5f * a + c;
-  float d2;
-  barrier(delta, q.phi, q.dphi, d2);
-  q.psi = half_beta * d2;
-  return q;
-}
-
-// r and phi only (line-search trials)
-template <typename TI>
-__device__ __forceinline__ void cell_residual(const TI* Ipc, const TI* Imc, int inner, int m,
-                                              int j, float bj, float bj1, float& r, float& phi) {
-  float tp, tm, wp, wm;
-  cell_positions(bj, bj1, j, tp, tm);
-  int ip = cell_index(tp, m, wp), im = cell_index(tm, m, wm);
-  float vp, sp, vm, sm;
-  interp(Ipc, inner, m, ip, wp, vp, sp);
-  interp(Imc, inner, m, im, wm, vm, sm);
-  float delta = bj1 - bj;
-  r = vp * (1.0f + delta) - vm * (1.0f - delta);
-  float df, d2;
-  barrier(delta, phi, df, d2);
-}
-
-// in-plane neighbour columns of column c, clamped: an absent neighbour is the column itself
-struct ColNbrs {
-  int Am, Ap, Bm, Bp;
-  float nin;   // wA * (#A neighbours) + wB * (#B neighbours): in-plane part of L_kk
-};
-
-__device__ __forceinline__ ColNbrs col_nbrs(const Geo& g, int c, int own) {
-  int cA = c % g.nA, cB = c / g.nA;
-  ColNbrs n;
-  n.Am = cA > 0 ? col_base(c - 1, g.inner, g.fld_ostride) : own;
-  n.Ap = cA < g.nA - 1 ? col_base(c + 1, g.inner, g.fld_ostride) : own;
-  n.Bm = cB > 0 ? col_base(c - g.nA, g.inner, g.fld_ostride) : own;
-  n.Bp = cB < g.nB - 1 ? col_base(c + g.nA, g.inner, g.fld_ostride) : own;
-  n.nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
-  return n;
-}
 
 // ------------------------------------------------------------------------------------------
 // J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
