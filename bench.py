@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3t", choices=list(GN_ITERS))
     ap.add_argument("--precond", type=int, default=0)
+    ap.add_argument("--pcg-path", type=int, default=0,
+                    help="0 auto (persistent PCG kernel when possible), 1 separate kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -200,7 +202,8 @@ def run_ours(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
 
     def step():
-        h.solve(Ip, Im, b=b_out, gn_iters=gn, init=True, precond=args.precond, stats=False)
+        h.solve(Ip, Im, b=b_out, gn_iters=gn, init=True, precond=args.precond, stats=False,
+                pcg_path=args.pcg_path)
 
     for _ in range(args.warmup):
         step()

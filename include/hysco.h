@@ -44,7 +44,8 @@ typedef enum {
   HYSCO_ECUDA = -2,       /* a CUDA runtime call failed */
   HYSCO_ENOMEM = -3,      /* device workspace allocation failed */
   HYSCO_ENONFINITE = -4,  /* NaN met in J (non-finite input) */
-  HYSCO_ENOTREADY = -5    /* hysco_hessvec / hysco_precond before any hysco_eval */
+  HYSCO_ENOTREADY = -5,   /* hysco_hessvec / hysco_precond before any hysco_eval */
+  HYSCO_ETIMEOUT = -6     /* a device-wide barrier of the persistent PCG kernel timed out */
 } hysco_status;
 
 typedef enum { HYSCO_F32 = 0, HYSCO_BF16 = 1, HYSCO_F16 = 2 } hysco_dtype;
@@ -61,6 +62,10 @@ typedef struct {
   double pcg_rtol;        /* stop PCG when ||r|| / ||r0|| < pcg_rtol (paper: 0.1) */
   double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
   double ot_eps;          /* OT positivity shift factor (default 1e-3) */
+  int32_t pcg_path;       /* Jacobi PCG: 0 = one persistent cooperative kernel per GN step when the
+                             device supports it, else separate kernels (default); 1 = separate
+                             kernels; 2 = persistent kernel or HYSCO_EINVAL.  Same arithmetic. */
+  int32_t reserved_;
 } hysco_opts;
 
 /* Per-GN-iteration record written by hysco_solve when `stats` is non-NULL (device memory,
@@ -130,8 +135,8 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout,
                 const hysco_opts* opts, double* stats, hysco_stream_t stream);
 
 /* Synchronises `stream` and returns the numerical status of the last hysco_eval / hysco_solve /
- * hysco_init_ot on this handle: HYSCO_OK, HYSCO_INFEASIBLE or HYSCO_ENONFINITE (or HYSCO_ECUDA
- * when the stream reports an error). */
+ * hysco_init_ot on this handle: HYSCO_OK, HYSCO_INFEASIBLE, HYSCO_ENONFINITE or HYSCO_ETIMEOUT
+ * (or HYSCO_ECUDA when the stream reports an error). */
 int hysco_last_status(hysco_t h, hysco_stream_t stream);
 
 /* Diagnostics: the same kernels with extra outputs.

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhysco.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hysco.h")
 
-OK, INFEASIBLE, EINVAL, ECUDA, ENOMEM, ENONFINITE, ENOTREADY = 0, 1, -1, -2, -3, -4, -5
+OK, INFEASIBLE, EINVAL, ECUDA, ENOMEM, ENONFINITE, ENOTREADY, ETIMEOUT = 0, 1, -1, -2, -3, -4, -5, -6
 F32, BF16, F16 = 0, 1, 2
 PC_JACOBI, PC_COLUMN = 0, 1
 NSTATS = 10
@@ -25,7 +25,7 @@ class Opts(C.Structure):
     _fields_ = [("gn_iters", C.c_int32), ("pcg_max_iters", C.c_int32),
                 ("ls_max_iters", C.c_int32), ("precond", C.c_int32), ("init", C.c_int32),
                 ("ot_blur", C.c_int32), ("pcg_rtol", C.c_double), ("armijo_c1", C.c_double),
-                ("ot_eps", C.c_double)]
+                ("ot_eps", C.c_double), ("pcg_path", C.c_int32), ("reserved_", C.c_int32)]
 
 
 class HyscoError(RuntimeError):

@@ -29,6 +29,9 @@ struct hysco_ctx {
   double* partials;
   unsigned* counter;
   DevState* st;
+  int pgrid;          // persistent PCG grid (0: not available on this device)
+  float* ppart;       // its per-block partials (2 slots)
+  unsigned* pbar;     // its barrier words
   bool have_lin, have_factor;
   Work work() const { return Work{partials, counter, st}; }
 };
@@ -61,6 +64,8 @@ void free_all(hysco_ctx* h) {
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
   if (h->counter) cudaFree(h->counter);
+  if (h->ppart) cudaFree(h->ppart);
+  if (h->pbar) cudaFree(h->pbar);
   if (h->st) cudaFree(h->st);
 }
 
@@ -85,6 +90,8 @@ void hysco_default_opts(hysco_opts* o) {
   o->pcg_rtol = 0.1;
   o->armijo_c1 = 1e-4;
   o->ot_eps = 1e-3;
+  o->pcg_path = 0;
+  o->reserved_ = 0;
 }
 
 const char* hysco_strerror(int status) {
@@ -96,6 +103,7 @@ const char* hysco_strerror(int status) {
     case HYSCO_ENOMEM: return "device memory allocation failed";
     case HYSCO_ENONFINITE: return "non-finite (NaN) objective";
     case HYSCO_ENOTREADY: return "no Gauss-Newton linearisation yet: call hysco_eval first";
+    case HYSCO_ETIMEOUT: return "a device-wide barrier of the persistent PCG kernel timed out";
     default: return "unknown status";
   }
 }
@@ -180,6 +188,14 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   if (cudaMalloc((void**)&h->partials, nparts * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc((void**)&h->st, sizeof(DevState)) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return HYSCO_ENOMEM;
+  }
+  h->pgrid = pcg_persistent_grid(h->device);
+  if (h->pgrid > 0 &&
+      (cudaMalloc((void**)&h->ppart, 4ull * h->pgrid * sizeof(float)) != cudaSuccess ||
+       cudaMalloc((void**)&h->pbar, 64 * sizeof(unsigned)) != cudaSuccess)) {
     free_all(h);
     delete h;
     return HYSCO_ENOMEM;
@@ -302,6 +318,9 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
   if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
   if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
   if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
+  if (o->pcg_path < 0 || o->pcg_path > 2) return HYSCO_EINVAL;
+  const bool persistent = o->precond == HYSCO_PC_JACOBI && h->pgrid > 0 && o->pcg_path != 1;
+  if (o->pcg_path == 2 && !persistent) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   const Geo& g = h->g;
   Work w = h->work();
@@ -313,22 +332,24 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
   for (int it = 0; it < o->gn_iters; ++it) {
     HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, h->invd, it, w,
                           s));
-    if (o->precond == HYSCO_PC_JACOBI) {
+    if (persistent) {
+      HYSCO_TRY(launch_pcg_persistent(g, h->pgrid, h->grad, h->x, h->r, h->z, h->p0, h->p1,
+                                      h->Hp, h->dco, h->eco, h->invd, h->ppart, h->pbar,
+                                      o->pcg_max_iters, o->pcg_rtol, h->st, s));
+    } else if (o->precond == HYSCO_PC_JACOBI) {
       HYSCO_TRY(launch_pcg_init_jacobi(g, h->grad, h->x, h->r, h->z, h->invd, w, s));
     } else {
       HYSCO_TRY(launch_col_factor(g, h->dco, h->eco, h->invD, h->lco, s));
       HYSCO_TRY(launch_col_solve(g, 1, h->grad, h->x, h->r, nullptr, nullptr, h->z, h->invD,
                                  h->lco, 0, o->pcg_rtol, w, s));
     }
-    for (int i = 0; i < o->pcg_max_iters; ++i) {
-      float* pold = (i & 1) ? h->p0 : h->p1;
-      float* pnew = (i & 1) ? h->p1 : h->p0;
-      HYSCO_TRY(launch_pcg_hp(g, h->z, pold, pnew, h->Hp, h->dco, h->eco, i == 0, w, s));
+    for (int i = 0; i < (persistent ? 0 : o->pcg_max_iters); ++i) {
+      HYSCO_TRY(launch_pcg_hp(g, h->z, h->p0, h->Hp, h->dco, h->eco, i == 0, w, s));
       if (o->precond == HYSCO_PC_JACOBI)
-        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, pnew, h->Hp, h->z, h->invd, i == 0,
+        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, h->p0, h->Hp, h->z, h->invd, i == 0,
                                            o->pcg_rtol, w, s));
       else
-        HYSCO_TRY(launch_col_solve(g, 2, nullptr, h->x, h->r, pnew, h->Hp, h->z, h->invD, h->lco,
+        HYSCO_TRY(launch_col_solve(g, 2, nullptr, h->x, h->r, h->p0, h->Hp, h->z, h->invD, h->lco,
                                    i == 0, o->pcg_rtol, w, s));
     }
     for (int t0 = 0; t0 < o->ls_max_iters; t0 += (t0 == 0 ? 1 : kLsBatch))

@@ -199,9 +199,8 @@ cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float*
                            const float* eco, cudaStream_t s);
 cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
                                    const float* invd, const Work& w, cudaStream_t s);
-cudaError_t launch_pcg_hp(const Geo& g, const float* z, const float* pold, float* pnew, float* Hp,
-                          const float* dco, const float* eco, int first, const Work& w,
-                          cudaStream_t s);
+cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, const float* dco,
+                          const float* eco, int first, const Work& w, cudaStream_t s);
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
                                      const float* Hp, float* z, const float* invd, int first,
                                      double rtol, const Work& w, cudaStream_t s);
@@ -215,6 +214,14 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const float* p, const float* Hp, float* z, const float* invD,
                              const float* lco, int first, double rtol, const Work& w,
                              cudaStream_t s);
+
+// k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible)
+int pcg_persistent_grid(int device);
+cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float* x, float* r,
+                                  float* z, float* p0, float* p1, float* Hp, const float* dco,
+                                  const float* eco, const float* invd, float* part,
+                                  unsigned* bar, int max_it, double rtol, DevState* st,
+                                  cudaStream_t s);
 
 // k_ot.cu
 cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void* Im,

@@ -7,12 +7,13 @@
 //
 // PCG (Hestenes-Stiefel, x0 = 0) is split in two kernels per iteration i so that every global
 // inner product is reduced exactly once, in the kernel that produces it:
-//   k_pcg_hp:     p = z + beta p (p = z when i = 0), Hp = H p, partial p.Hp
-//                 -> last block: alpha = rho / p.Hp (stop if p.Hp <= 0)
+//   k_pcg_hp:     w = H z, p = z + beta p, Hp = w + beta Hp (p = z, Hp = w when i = 0),
+//                 partial p.Hp -> last block: alpha = rho / p.Hp (stop if p.Hp <= 0)
 //   k_pcg_update: x += alpha p, r -= alpha Hp, partial r.r; z = M^{-1} r, partial r.z
 //                 -> last block: stop if ||r|| / ||r0|| < rtol, else beta = r.z / rho, rho = r.z
-// The direction is double-buffered (p_old -> p_new alternate between two arrays), and the in-plane
-// neighbours of p needed by H p are recomputed from z and p_old, so no launch reads what it writes.
+// H p is kept by the recurrence H p = H z + beta H p_old (H is linear, so this is the same vector
+// as applying the stencil to p, up to rounding): the stencil reads only z, and p, Hp are updated
+// in place by their owning thread.
 #include "hysco_internal.cuh"
 
 namespace hysco {
@@ -23,18 +24,12 @@ namespace hysco {
 // itself, which zeroes its Laplacian difference, so all loads issue back to back.
 // ------------------------------------------------------------------------------------------
 
-template <bool PCG>
-__device__ __forceinline__ float pval(const float* __restrict__ z, const float* __restrict__ pold,
-                                      int i, float beta, int first) {
-  if (!PCG || first) return __ldg(z + i);
-  return fmaf(beta, __ldg(pold + i), __ldg(z + i));
-}
-
+// Hv (PCG = false) or the PCG step (PCG = true): w = H z; p = z + beta p; Hp = w + beta Hp.
 template <bool PCG>
 __global__ void __launch_bounds__(kBlock)
-k_hv(Geo g, const float* __restrict__ z, const float* __restrict__ pold, float* __restrict__ pnew,
-     float* __restrict__ Hp, const float* __restrict__ dco, const float* __restrict__ eco,
-     int first, double* partials, unsigned* counter, DevState* st) {
+k_hv(Geo g, const float* __restrict__ z, float* __restrict__ p, float* __restrict__ Hp,
+     const float* __restrict__ dco, const float* __restrict__ eco, int first, double* partials,
+     unsigned* counter, DevState* st) {
   float beta = 0.f;
   if (PCG) {
     if (st->stop || st->pcg_done) return;
@@ -49,27 +44,30 @@ k_hv(Geo g, const float* __restrict__ z, const float* __restrict__ pold, float* 
     n = valid ? n : g.nf - 1;
     int ix[3];
     field_coords(g, n, ix);
-    float pk = pval<PCG>(z, pold, n, beta, first);
-    float lap = 0.f, pe_lo = pk, pe_hi = pk;
-    int n_lo_pe = n;
+    float zk = __ldg(z + n);
+    float lap = 0.f, zlo = zk, zhi = zk;
+    int nlo = n;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       int lo = ix[a] > 0 ? n - g.fs[a] : n;
       int hi = ix[a] < g.fe[a] - 1 ? n + g.fs[a] : n;
-      float pl = pval<PCG>(z, pold, lo, beta, first);
-      float ph = pval<PCG>(z, pold, hi, beta, first);
-      lap += g.w[a] * ((pk - pl) + (pk - ph));
-      if (a == g.p) { pe_lo = pl; pe_hi = ph; n_lo_pe = lo; }
+      float zl = __ldg(z + lo), zh = __ldg(z + hi);
+      lap += g.w[a] * ((zk - zl) + (zk - zh));
+      if (a == g.p) { zlo = zl; zhi = zh; nlo = lo; }
     }
-    float em1 = __ldg(eco + n_lo_pe);
-    em1 = n_lo_pe != n ? em1 : 0.f;
-    float hv = g.vol * (em1 * pe_lo + __ldg(dco + n) * pk + __ldg(eco + n) * pe_hi + g.alpha * lap);
+    float em1 = __ldg(eco + nlo);
+    em1 = nlo != n ? em1 : 0.f;
+    float w = g.vol * (em1 * zlo + __ldg(dco + n) * zk + __ldg(eco + n) * zhi + g.alpha * lap);
+    if (!PCG) {
+      if (valid) Hp[n] = w;
+      continue;
+    }
+    float pk = first ? zk : fmaf(beta, p[n], zk);
+    float hk = first ? w : fmaf(beta, Hp[n], w);
     if (valid) {
-      Hp[n] = hv;
-      if (PCG) {
-        pnew[n] = pk;
-        acc += pk * hv;
-      }
+      Hp[n] = hk;
+      p[n] = pk;
+      acc += pk * hk;
     }
   }
   if (!PCG) return;
@@ -346,8 +344,8 @@ static int vec_blocks(const Geo& g) { return ceil_div((g.nf >> 2) > 0 ? (g.nf >>
 
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
                            const float* eco, cudaStream_t s) {
-  k_hv<false><<<flat_blocks(g), kBlock, 0, s>>>(g, v, nullptr, nullptr, Hv, dco, eco, 0, nullptr,
-                                                nullptr, nullptr);
+  k_hv<false><<<flat_blocks(g), kBlock, 0, s>>>(g, v, nullptr, Hv, dco, eco, 0, nullptr, nullptr,
+                                                nullptr);
   return cudaGetLastError();
 }
 
@@ -358,11 +356,10 @@ cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, fl
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_hp(const Geo& g, const float* z, const float* pold, float* pnew, float* Hp,
-                          const float* dco, const float* eco, int first, const Work& w,
-                          cudaStream_t s) {
-  k_hv<true><<<flat_blocks(g), kBlock, 0, s>>>(g, z, pold, pnew, Hp, dco, eco, first, w.partials,
-                                               w.counter, w.st);
+cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, const float* dco,
+                          const float* eco, int first, const Work& w, cudaStream_t s) {
+  k_hv<true><<<flat_blocks(g), kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, w.partials, w.counter,
+                                               w.st);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,328 @@
+// The whole Jacobi-preconditioned CG of one Gauss-Newton step (Sec. 2.3.1) in one persistent,
+// cooperatively launched kernel.
+//
+// At 3T size every PCG kernel is short (tens of microseconds) and a kernel boundary costs about
+// as much as a third of the work, so PCG init and all iterations run in one launch whose phases
+// are separated by device-wide barriers:
+//   init   r = -grad, x = 0, z = r / diag            partials r.r, r.z      | barrier
+//   iter   A: w = H z, p = z + beta p, Hp = w + beta Hp (p = z, Hp = w at i = 0), partial p.Hp
+//                                                                                     | barrier
+//          B: x += alpha p, r -= alpha Hp, z = r / diag  partials r.r, r.z  | barrier
+// After each barrier every block adds all blocks' partials itself, in the same fixed order and in
+// double precision, so every block takes the same scalar decision (alpha, beta, the relative-
+// residual stop, p.Hp <= 0) without another round trip.  H p is kept by the recurrence
+// H p = H z + beta H p_old (H is linear), so the stencil reads one array (z) and p, Hp are
+// updated in place.  The arithmetic per node is that of the separate kernels in k_pcg.cu.
+//
+// Memory: arrays written inside the launch (x, r, z, p, Hp) are read with ordinary (coherent)
+// loads after a barrier, never through the read-only path; d, e, 1/diag and grad are read-only.
+// Barriers spin with a bounded clock budget: on expiry a block records an error in the device
+// state and returns; every other block then also times out at its next barrier, so the launch
+// always ends.
+#include <cuda/atomic>
+
+#include "hysco_internal.cuh"
+
+namespace hysco {
+
+constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kPcgUnroll = 4;
+
+struct PcgArgs {
+  const float* grad;
+  float* x;
+  float* r;
+  float* z;
+  float* p0;
+  float* p1;
+  float* Hp;
+  const float* dco;
+  const float* eco;
+  const float* invd;
+  float* part;           // 2 slots x gridDim.x x 2 floats
+  unsigned* bar;         // [0] arrival count, [1] generation; zeroed before every launch
+  DevState* st;
+  int max_it;
+  double rtol;
+};
+
+// Device-wide barrier.  Returns false (in every thread of the block) when the spin budget ran
+// out; the block must then stop.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    cuda::atomic_ref<unsigned, cuda::thread_scope_device> count(bar[0]), g(bar[1]);
+    unsigned arrived = count.fetch_add(1u, cuda::memory_order_acq_rel);
+    if (arrived == gridDim.x - 1) {
+      count.store(0u, cuda::memory_order_relaxed);
+      g.store(gen + 1, cuda::memory_order_release);
+    } else {
+      long long t0 = clock64();
+      while (g.load(cuda::memory_order_acquire) == gen) {
+        if (clock64() - t0 > kBarrierSpinCycles) { ok = 0; break; }
+      }
+    }
+  }
+  __syncthreads();
+  gen += 1;
+  return ok != 0;
+}
+
+// block sum of K floats, result broadcast through shared memory to every thread
+template <int K>
+__device__ __forceinline__ void block_reduce_f(float (&v)[K], float* sh) {
+  block_sum<K, float>(v, sh);
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < K; ++i) sh[i] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = sh[i];
+  __syncthreads();
+}
+
+// every block: sum of the K-float partials of all blocks in a fixed order, in double precision
+template <int K>
+__device__ __forceinline__ void all_partials(const float* part, double (&tot)[K], double* shd) {
+  double acc[K];
+#pragma unroll
+  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] += (double)part[b * K + i];
+  block_sum<K, double>(acc, shd);
+  __syncthreads();
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int i = 0; i < K; ++i) shd[i] = acc[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < K; ++i) tot[i] = shd[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ float pdir(const float* z, const float* pold, int i, float beta,
+                                      bool first) {
+  return first ? z[i] : fmaf(beta, pold[i], z[i]);
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_pcg_persistent(Geo g, PcgArgs a) {
+  __shared__ float shf[32 * 2];
+  __shared__ double shd[32 * 2];
+  DevState* st = a.st;
+  if (st->stop) return;
+  const int T = gridDim.x * blockDim.x;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nf = g.nf, n4 = nf >> 2;
+  unsigned gen = 0;
+  int slot = 0;
+  auto part = [&](int s) { return a.part + s * gridDim.x * 2; };
+
+  // ---- init --------------------------------------------------------------------------------
+  {
+    float arr = 0.f, arz = 0.f;
+    for (int i0 = gtid; i0 < n4; i0 += kPcgUnroll * T) {
+      float4 gv[kPcgUnroll], dv[kPcgUnroll];
+#pragma unroll
+      for (int u = 0; u < kPcgUnroll; ++u) {
+        int i = min(i0 + u * T, n4 - 1);
+        gv[u] = __ldg(reinterpret_cast<const float4*>(a.grad) + i);
+        dv[u] = __ldg(reinterpret_cast<const float4*>(a.invd) + i);
+      }
+#pragma unroll
+      for (int u = 0; u < kPcgUnroll; ++u) {
+        int i = i0 + u * T;
+        float4 rv = make_float4(-gv[u].x, -gv[u].y, -gv[u].z, -gv[u].w);
+        float4 zv = make_float4(rv.x * dv[u].x, rv.y * dv[u].y, rv.z * dv[u].z, rv.w * dv[u].w);
+        if (i < n4) {
+          reinterpret_cast<float4*>(a.x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+          reinterpret_cast<float4*>(a.r)[i] = rv;
+          reinterpret_cast<float4*>(a.z)[i] = zv;
+          arr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
+          arz += rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
+        }
+      }
+    }
+    if (gtid < (nf & 3)) {
+      int t = 4 * n4 + gtid;
+      float rk = -__ldg(a.grad + t), zk = rk * __ldg(a.invd + t);
+      a.x[t] = 0.f; a.r[t] = rk; a.z[t] = zk;
+      arr += rk * rk; arz += rk * zk;
+    }
+    float v[2] = {arr, arz};
+    block_reduce_f<2>(v, shf);
+    if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v[0]; part(slot)[blockIdx.x * 2 + 1] = v[1]; }
+  }
+  if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
+  double tot[2];
+  all_partials<2>(part(slot), tot, shd);
+  slot ^= 1;
+  const double rr0 = tot[0];
+  double rho = tot[1], beta = 0.0, relres = rr0 > 0.0 ? 1.0 : 0.0;
+  bool done = !(rr0 > 0.0);
+  int it = 0;
+
+  for (int i = 0; i < a.max_it && !done; ++i) {
+    const bool first = i == 0;
+    float* pv_ = a.p0;
+    const float fb = (float)beta;
+    // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp ---------------------------------------
+    // all loads of kPcgUnroll nodes are issued before any store (the stores could alias them)
+    float acc = 0.f;
+    for (int n0 = gtid; n0 < nf; n0 += kPcgUnroll * T) {
+      float zk[kPcgUnroll], lap[kPcgUnroll], zlo[kPcgUnroll], zhi[kPcgUnroll];
+      float dk[kPcgUnroll], ek[kPcgUnroll], em[kPcgUnroll], po[kPcgUnroll], ho[kPcgUnroll];
+#pragma unroll
+      for (int u = 0; u < kPcgUnroll; ++u) {
+        int n = min(n0 + u * T, nf - 1);
+        int ix[3];
+        field_coords(g, n, ix);
+        zk[u] = a.z[n];
+        lap[u] = 0.f;
+        int nlo = n;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+          int lo = ix[ax] > 0 ? n - g.fs[ax] : n;
+          int hi = ix[ax] < g.fe[ax] - 1 ? n + g.fs[ax] : n;
+          float zl = a.z[lo], zh = a.z[hi];
+          lap[u] += g.w[ax] * ((zk[u] - zl) + (zk[u] - zh));
+          if (ax == g.p) { zlo[u] = zl; zhi[u] = zh; nlo = lo; }
+        }
+        dk[u] = __ldg(a.dco + n);
+        ek[u] = __ldg(a.eco + n);
+        float e1 = __ldg(a.eco + nlo);
+        em[u] = nlo != n ? e1 : 0.f;
+        po[u] = first ? 0.f : pv_[n];
+        ho[u] = first ? 0.f : a.Hp[n];
+      }
+#pragma unroll
+      for (int u = 0; u < kPcgUnroll; ++u) {
+        int n = n0 + u * T;
+        float w = g.vol * (em[u] * zlo[u] + dk[u] * zk[u] + ek[u] * zhi[u] + g.alpha * lap[u]);
+        float pk = first ? zk[u] : fmaf(fb, po[u], zk[u]);
+        float hk = first ? w : fmaf(fb, ho[u], w);
+        if (n < nf) {
+          a.Hp[n] = hk;
+          pv_[n] = pk;
+          acc += pk * hk;
+        }
+      }
+    }
+    {
+      float v[1] = {acc};
+      block_reduce_f<1>(v, shf);
+      if (threadIdx.x == 0) part(slot)[blockIdx.x * 2] = v[0];
+    }
+    if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
+    {
+      double t1[1];
+      // partials of phase A sit at stride 2 in their slot
+      double accd = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) accd += (double)part(slot)[b * 2];
+      double v[1] = {accd};
+      block_sum<1, double>(v, shd);
+      __syncthreads();
+      if (threadIdx.x == 0) shd[0] = v[0];
+      __syncthreads();
+      t1[0] = shd[0];
+      __syncthreads();
+      slot ^= 1;
+      if (!(t1[0] > 0.0)) { done = true; break; }
+      const float al = (float)(rho / t1[0]);
+      // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
+      float arr = 0.f, arz = 0.f;
+      for (int j0 = gtid; j0 < n4; j0 += kPcgUnroll * T) {
+        float4 pv[kPcgUnroll], hv[kPcgUnroll], dv[kPcgUnroll], rv[kPcgUnroll], xv[kPcgUnroll];
+#pragma unroll
+        for (int u = 0; u < kPcgUnroll; ++u) {
+          int j = min(j0 + u * T, n4 - 1);
+          pv[u] = reinterpret_cast<const float4*>(pv_)[j];
+          hv[u] = reinterpret_cast<const float4*>(a.Hp)[j];
+          dv[u] = __ldg(reinterpret_cast<const float4*>(a.invd) + j);
+          rv[u] = reinterpret_cast<const float4*>(a.r)[j];
+          xv[u] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(a.x)[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kPcgUnroll; ++u) {
+          int j = j0 + u * T;
+          float4 X = xv[u], R = rv[u];
+          X.x = fmaf(al, pv[u].x, X.x); X.y = fmaf(al, pv[u].y, X.y);
+          X.z = fmaf(al, pv[u].z, X.z); X.w = fmaf(al, pv[u].w, X.w);
+          R.x = fmaf(-al, hv[u].x, R.x); R.y = fmaf(-al, hv[u].y, R.y);
+          R.z = fmaf(-al, hv[u].z, R.z); R.w = fmaf(-al, hv[u].w, R.w);
+          float4 Z = make_float4(R.x * dv[u].x, R.y * dv[u].y, R.z * dv[u].z, R.w * dv[u].w);
+          if (j < n4) {
+            reinterpret_cast<float4*>(a.x)[j] = X;
+            reinterpret_cast<float4*>(a.r)[j] = R;
+            reinterpret_cast<float4*>(a.z)[j] = Z;
+            arr += R.x * R.x + R.y * R.y + R.z * R.z + R.w * R.w;
+            arz += R.x * Z.x + R.y * Z.y + R.z * Z.z + R.w * Z.w;
+          }
+        }
+      }
+      if (gtid < (nf & 3)) {
+        int t = 4 * n4 + gtid;
+        float pk = pv_[t];
+        a.x[t] = first ? al * pk : fmaf(al, pk, a.x[t]);
+        float rk = fmaf(-al, a.Hp[t], a.r[t]);
+        a.r[t] = rk;
+        float zk = rk * __ldg(a.invd + t);
+        a.z[t] = zk;
+        arr += rk * rk; arz += rk * zk;
+      }
+      float v2[2] = {arr, arz};
+      block_reduce_f<2>(v2, shf);
+      if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v2[0]; part(slot)[blockIdx.x * 2 + 1] = v2[1]; }
+    }
+    if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
+    all_partials<2>(part(slot), tot, shd);
+    slot ^= 1;
+    it = i + 1;
+    relres = sqrt(tot[0]) / sqrt(rr0);
+    if (relres < a.rtol) {
+      done = true;
+    } else {
+      beta = tot[1] / rho;
+      rho = tot[1];
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rr0 = rr0;
+    st->rho = rho;
+    st->beta_cg = beta;
+    st->pcg_iter = it;
+    st->relres = relres;
+    st->pcg_done = 1;
+  }
+}
+
+int pcg_persistent_grid(int device) {
+  int sms = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kBlock, 0) !=
+      cudaSuccess)
+    return 0;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+    return 0;
+  return sms * per_sm;
+}
+
+cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float* x, float* r,
+                                  float* z, float* p0, float* p1, float* Hp, const float* dco,
+                                  const float* eco, const float* invd, float* part,
+                                  unsigned* bar, int max_it, double rtol, DevState* st,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  PcgArgs a{grad, x, r, z, p0, p1, Hp, dco, eco, invd, part, bar, st, max_it, rtol};
+  Geo gg = g;
+  void* args[] = {&gg, &a};
+  return cudaLaunchCooperativeKernel((void*)k_pcg_persistent, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+}  // namespace hysco

@@ -175,12 +175,13 @@ def test_half_precision_images_match_oracle_on_the_same_values(H, orc, dtype):
     check_field(host(g), e["grad"], "grad " + dtype)
 
 
-@pytest.mark.parametrize("precond", [0, 1])
-def test_tiny_solve_matches_oracle(H, orc, precond):
-    """BASELINE tiny case: 32x32x16, OT init, 10 GN-PCG iterations."""
+@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (1, 0)])
+def test_tiny_solve_matches_oracle(H, orc, precond, path):
+    """Tiny case: 32x32x16, OT init, 10 GN-PCG iterations (path 1: separate PCG kernels,
+    path 2: the persistent cooperative PCG kernel)."""
     pr = ph.make_pair("tiny")
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
-    b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=10, precond=precond)
+    b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=10, precond=precond, pcg_path=path)
     assert h.last_status() == 0
     P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
     ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=10, precond=precond, contract=False)
@@ -190,3 +191,19 @@ def test_tiny_solve_matches_oracle(H, orc, precond):
     assert np.array_equal(gs[:, 7], rst[:, 7]), (gs[:, 7], rst[:, 7])        # PCG iterations
     assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4)
     assert rel(host(b), ref) <= 1e-3
+
+
+@pytest.mark.parametrize("name", ["small", "7t"])
+def test_persistent_and_separate_pcg_agree(H, name):
+    """Both PCG paths compute the same iteration; they differ only in how per-block partial sums
+    are grouped, so the fields agree to single-precision rounding."""
+    pr = ph.make_pair(name)
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    out = []
+    for path in (1, 2):
+        b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=4, pcg_path=path)
+        assert h.last_status() == 0
+        out.append((host(b), host(st)))
+    (b1, s1), (b2, s2) = out
+    assert np.array_equal(s1[:, 7], s2[:, 7]) and np.array_equal(s1[:, 6], s2[:, 6])
+    assert rel(b2, b1) <= 1e-4
