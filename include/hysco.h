@@ -155,7 +155,7 @@ int hysco_ot_indices(hysco_t h, const void* Ip, const void* Im, double eps, int3
  * for which cudaMalloc's implicit synchronisation is unacceptable.  The paper has no counterpart:
  * this is a library convenience around the same per-cell arithmetic as hysco_eval.
  * Takes the geometry of hysco_create by value and needs no handle.  Its only scratch (the
- * per-block partial sums of the reduction and a ticket counter, 1 MiB plus 256 bytes) lives in a
+ * per-block partial sums of the reduction and a ticket counter, 512 KiB plus 256 bytes) lives in a
  * static device array that every GPU loading this library holds until the process exits; the
  * call allocates nothing.  The first call on each device (with that device current) looks up the
  * array's device address, so make that first call before any stream capture.  All calls share the

@@ -26,7 +26,7 @@ struct hysco_ctx {
   int device;
   // field-shaped workspace
   float *grad, *dco, *eco, *invd, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp;
-  double* partials;
+  float* partials;
   unsigned* counter;
   DevState* st;
   int pgrid;          // persistent PCG grid (0: not available on this device)
@@ -185,7 +185,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   long long flat_blocks = (long long)ceil_div(g.nf, kBlock) + 1;
   long long nparts = march_blocks * (3 * kLsBatch + 1) + flat_blocks * 2 + 148 * 4 * 2 +
                      (long long)g.ncols * 2 + 64;
-  if (cudaMalloc((void**)&h->partials, nparts * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc((void**)&h->partials, nparts * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
       cudaMalloc((void**)&h->st, sizeof(DevState)) != cudaSuccess) {
     free_all(h);

@@ -86,9 +86,9 @@ __device__ __forceinline__ float ldf(const __half* p) { return __half2float(__ld
 // ------------------------------------------------------------------------------------------
 // deterministic reductions: per-thread and per-block partial sums in single precision (a warp
 // shuffle tree, then one warp over the block's warp sums); the last block to finish (atomic
-// ticket) adds the per-block partials in double precision in a fixed order and "finishes".
-// Double precision is confined to that one block: this GPU's FP64 rate is a small fraction of
-// its FP32 rate, and an FP64 tree in every block dominated the reducing kernels.
+// ticket) adds the per-block partials in double-float (see df32) in a fixed order and
+// "finishes".  No double precision on the reduction path: this GPU's FP64 rate is a small
+// fraction of its FP32 rate, and FP64 trees dominated the reducing kernels when they had them.
 // ------------------------------------------------------------------------------------------
 
 template <int K, typename T>
@@ -121,13 +121,54 @@ __device__ __forceinline__ void block_sum(T (&v)[K], T* sh /* >= 32*K */) {
   }
 }
 
+// Double-float accumulation: an unevaluated sum hi + lo of two floats, added with Knuth's
+// TwoSum (error-free transformation of the hi parts), giving close to double-precision sums of
+// single-precision partials at single-precision speed.
+struct df32 {
+  float hi, lo;
+};
+__device__ __forceinline__ df32 df_add(df32 a, df32 b) {
+  float s = a.hi + b.hi;
+  if (!isfinite(s)) return df32{s, 0.f};   // +-inf and NaN pass through unchanged
+  float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  float hi = s + e;
+  return df32{hi, e - (hi - s)};
+}
+__device__ __forceinline__ df32 df_shfl_down(df32 v, int off) {
+  return df32{__shfl_down_sync(0xffffffffu, v.hi, off), __shfl_down_sync(0xffffffffu, v.lo, off)};
+}
+// block sum of K double-float values; result valid in thread 0
+template <int K>
+__device__ __forceinline__ void block_sum_df(df32 (&v)[K], df32* sh /* >= 32*K */) {
+  int tid = linear_tid(), nw = block_threads() >> 5;
+#pragma unroll
+  for (int i = 0; i < K; ++i)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[i] = df_add(v[i], df_shfl_down(v[i], off));
+  __syncthreads();
+  if ((tid & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < K; ++i) sh[(tid >> 5) * K + i] = v[i];
+  __syncthreads();
+  if (tid < 32) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+      v[i] = tid < nw ? sh[tid * K + i] : df32{0.f, 0.f};
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[i] = df_add(v[i], df_shfl_down(v[i], off));
+    }
+  }
+}
+
 // Grid-wide sum of single-precision per-thread values.  Every thread of every block must call
 // it.  Returns true in thread 0 of the last block only, with tot[] holding the grid totals
 // (double); the ticket counter is reset there.
 template <int K>
-__device__ bool grid_sum(float (&v)[K], double* partials, unsigned* counter, double (&tot)[K]) {
+__device__ bool grid_sum(float (&v)[K], float* partials, unsigned* counter, double (&tot)[K]) {
   __shared__ float shf[32 * K];
-  __shared__ double shd[32 * K];
+  __shared__ df32 shd[32 * K];
   __shared__ int is_last;
   int tid = linear_tid();
   int nblk = gridDim.x * gridDim.y * gridDim.z;
@@ -135,7 +176,7 @@ __device__ bool grid_sum(float (&v)[K], double* partials, unsigned* counter, dou
   block_sum<K, float>(v, shf);
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) partials[(long long)bid * K + i] = (double)v[i];
+    for (int i = 0; i < K; ++i) partials[(long long)bid * K + i] = v[i];
     __threadfence();
     unsigned t = atomicAdd(counter, 1u);
     is_last = (t == (unsigned)(nblk - 1));
@@ -143,16 +184,16 @@ __device__ bool grid_sum(float (&v)[K], double* partials, unsigned* counter, dou
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  double acc[K];
+  df32 acc[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = 0.0;
+  for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
   for (int b = tid; b < nblk; b += block_threads())
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] += __ldcg(partials + (long long)b * K + i);
-  block_sum<K, double>(acc, shd);
+    for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{__ldcg(partials + (long long)b * K + i), 0.f});
+  block_sum_df<K>(acc, shd);
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) tot[i] = acc[i];
+    for (int i = 0; i < K; ++i) tot[i] = (double)acc[i].hi + (double)acc[i].lo;
     *counter = 0u;
     return true;
   }
@@ -174,7 +215,7 @@ __device__ __forceinline__ void field_coords(const Geo& g, int n, int (&i)[3]) {
 // ------------------------------------------------------------------------------------------
 
 struct Work {        // device buffers the launchers need
-  double* partials;
+  float* partials;
   unsigned* counter;
   DevState* st;
 };

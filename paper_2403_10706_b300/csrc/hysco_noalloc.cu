@@ -18,11 +18,11 @@
 namespace hysco {
 namespace {
 
-constexpr int kStaticMaxBlocks = 32768;   // largest reduction grid served (1 MiB of partials)
+constexpr int kStaticMaxBlocks = 32768;   // largest reduction grid served (512 KiB of partials)
 constexpr int kStaticTerms = 4;           // D, S, P and sum of squared gradient entries
 constexpr size_t kCounterBytes = 256;     // ticket counter, padded to keep the partials aligned
 constexpr size_t kStaticScratchBytes =
-    kCounterBytes + sizeof(double) * (size_t)kStaticMaxBlocks * kStaticTerms;
+    kCounterBytes + sizeof(float) * (size_t)kStaticMaxBlocks * kStaticTerms;
 
 static __device__ __align__(256) unsigned char g_eval_scratch[kStaticScratchBytes];
 
@@ -55,7 +55,7 @@ k_eval_static(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
               const float* __restrict__ b, float* __restrict__ grad, double* terms,
               unsigned char* scratch) {
   unsigned* counter = reinterpret_cast<unsigned*>(scratch);
-  double* partials = reinterpret_cast<double*>(scratch + kCounterBytes);
+  float* partials = reinterpret_cast<float*>(scratch + kCounterBytes);
   const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = c < g.ncols;

@@ -29,7 +29,7 @@ template <typename TI, int SEG>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
        float* __restrict__ grad, float* __restrict__ dco, float* __restrict__ eco,
-       float* __restrict__ invd, int it, double* partials, unsigned* counter, DevState* st) {
+       float* __restrict__ invd, int it, float* partials, unsigned* counter, DevState* st) {
   if (it >= 0 && st->stop) return;
   const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBlock)
 k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
              const float* __restrict__ b, const float* __restrict__ q,
              const float* __restrict__ grad, int t0, int ls_max, double c1,
-             double* partials, unsigned* counter, DevState* st) {
+             float* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->ls_done) return;
   const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;

@@ -20,7 +20,7 @@ namespace hysco {
 template <typename TI>
 __global__ void __launch_bounds__(kBlock)
 k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, int n, float eps,
-           double* partials, unsigned* counter, DevState* st) {
+           float* partials, unsigned* counter, DevState* st) {
   float mn = __int_as_float(0x7f800000), mx = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += gridDim.x * blockDim.x) {
@@ -59,8 +59,8 @@ k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, int n, float ep
   if (tid == 0) {
     float gmn = __int_as_float(0x7f800000), gmx = 0.f;
     for (unsigned b = 0; b < gridDim.x; ++b) {
-      gmn = fminf(gmn, (float)__ldcg(partials + 2 * b));
-      gmx = fmaxf(gmx, (float)__ldcg(partials + 2 * b + 1));
+      gmn = fminf(gmn, __ldcg(partials + 2 * b));
+      gmx = fmaxf(gmx, __ldcg(partials + 2 * b + 1));
     }
     float neg = -gmn > 0.f ? -gmn : 0.f;
     float s = __fadd_rn(neg, __fmul_rn(eps, gmx));

@@ -28,7 +28,7 @@ namespace hysco {
 template <bool PCG>
 __global__ void __launch_bounds__(kBlock)
 k_hv(Geo g, const float* __restrict__ z, float* __restrict__ p, float* __restrict__ Hp,
-     const float* __restrict__ dco, const float* __restrict__ eco, int first, double* partials,
+     const float* __restrict__ dco, const float* __restrict__ eco, int first, float* partials,
      unsigned* counter, DevState* st) {
   float beta = 0.f;
   if (PCG) {
@@ -99,7 +99,7 @@ __device__ __forceinline__ void st4(float* p, int i, float4 v) {
 __global__ void __launch_bounds__(kBlock)
 k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float* __restrict__ x,
                   float* __restrict__ r, float* __restrict__ z, const float* __restrict__ invd,
-                  double* partials, unsigned* counter, DevState* st) {
+                  float* partials, unsigned* counter, DevState* st) {
   if (st->stop) return;
   float arr = 0.f, arz = 0.f;
   int n4 = g.nf >> 2;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kBlock)
 k_pcg_update_jacobi(Geo g, float* __restrict__ x, float* __restrict__ r,
                     const float* __restrict__ p, const float* __restrict__ Hp,
                     float* __restrict__ z, const float* __restrict__ invd, int first, double rtol,
-                    double* partials, unsigned* counter, DevState* st) {
+                    float* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->pcg_done) return;
   const float a = (float)st->alpha_cg;
   float arr = 0.f, arz = 0.f;
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kBlock)
 k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float* r,
             const float* __restrict__ p, const float* __restrict__ Hp, float* __restrict__ z,
             const float* __restrict__ invD, const float* __restrict__ lco, int first,
-            double rtol, double* partials, unsigned* counter, DevState* st) {
+            double rtol, float* partials, unsigned* counter, DevState* st) {
   extern __shared__ float sm[];
   if (MODE != 0 && st->stop) return;
   if (MODE == 2 && st->pcg_done) return;

@@ -9,8 +9,8 @@
 //                                                                                     | barrier
 //          B: x += alpha p, r -= alpha Hp, z = r / diag  partials r.r, r.z  | barrier
 // After each barrier every block adds all blocks' partials itself, in the same fixed order and in
-// double precision, so every block takes the same scalar decision (alpha, beta, the relative-
-// residual stop, p.Hp <= 0) without another round trip.  H p is kept by the recurrence
+// double-float (compensated single precision), so every block takes the same scalar decisions
+// (alpha, beta, the relative-residual stop, p.Hp <= 0) without another round trip.  H p is kept by the recurrence
 // H p = H z + beta H p_old (H is linear), so the stencil reads one array (z) and p, Hp are
 // updated in place.  The arithmetic per node is that of the separate kernels in k_pcg.cu.
 //
@@ -84,35 +84,31 @@ __device__ __forceinline__ void block_reduce_f(float (&v)[K], float* sh) {
   __syncthreads();
 }
 
-// every block: sum of the K-float partials of all blocks in a fixed order, in double precision
+// every block: sum of the K-float partials of all blocks in a fixed order (double-float), so
+// that every block obtains the same totals
 template <int K>
-__device__ __forceinline__ void all_partials(const float* part, double (&tot)[K], double* shd) {
-  double acc[K];
+__device__ __forceinline__ void all_partials(const float* part, float (&tot)[K], df32* sh) {
+  df32 acc[K];
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
+  for (int b = linear_tid(); b < (int)gridDim.x; b += block_threads())
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] += (double)part[b * K + i];
-  block_sum<K, double>(acc, shd);
+    for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{part[b * K + i], 0.f});
+  block_sum_df<K>(acc, sh);
   __syncthreads();
-  if (threadIdx.x == 0)
+  if (linear_tid() == 0)
 #pragma unroll
-    for (int i = 0; i < K; ++i) shd[i] = acc[i];
+    for (int i = 0; i < K; ++i) sh[i] = acc[i];
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < K; ++i) tot[i] = shd[i];
+  for (int i = 0; i < K; ++i) tot[i] = sh[i].hi + sh[i].lo;
   __syncthreads();
-}
-
-__device__ __forceinline__ float pdir(const float* z, const float* pold, int i, float beta,
-                                      bool first) {
-  return first ? z[i] : fmaf(beta, pold[i], z[i]);
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_pcg_persistent(Geo g, PcgArgs a) {
   __shared__ float shf[32 * 2];
-  __shared__ double shd[32 * 2];
+  __shared__ df32 shd[32 * 2];
   DevState* st = a.st;
   if (st->stop) return;
   const int T = gridDim.x * blockDim.x;
@@ -158,18 +154,19 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v[0]; part(slot)[blockIdx.x * 2 + 1] = v[1]; }
   }
   if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
-  double tot[2];
+  // scalars in single precision (the sums themselves are double-float accurate)
+  float tot[2];
   all_partials<2>(part(slot), tot, shd);
   slot ^= 1;
-  const double rr0 = tot[0];
-  double rho = tot[1], beta = 0.0, relres = rr0 > 0.0 ? 1.0 : 0.0;
-  bool done = !(rr0 > 0.0);
+  const float rr0 = tot[0];
+  float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
+  bool done = !(rr0 > 0.f);
   int it = 0;
 
   for (int i = 0; i < a.max_it && !done; ++i) {
     const bool first = i == 0;
     float* pv_ = a.p0;
-    const float fb = (float)beta;
+    const float fb = beta;
     // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp ---------------------------------------
     // all loads of kPcgUnroll nodes are issued before any store (the stores could alias them)
     float acc = 0.f;
@@ -215,24 +212,15 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     {
       float v[1] = {acc};
       block_reduce_f<1>(v, shf);
-      if (threadIdx.x == 0) part(slot)[blockIdx.x * 2] = v[0];
+      if (threadIdx.x == 0) part(slot)[blockIdx.x] = v[0];
     }
     if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
     {
-      double t1[1];
-      // partials of phase A sit at stride 2 in their slot
-      double accd = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) accd += (double)part(slot)[b * 2];
-      double v[1] = {accd};
-      block_sum<1, double>(v, shd);
-      __syncthreads();
-      if (threadIdx.x == 0) shd[0] = v[0];
-      __syncthreads();
-      t1[0] = shd[0];
-      __syncthreads();
+      float t1[1];
+      all_partials<1>(part(slot), t1, shd);
       slot ^= 1;
-      if (!(t1[0] > 0.0)) { done = true; break; }
-      const float al = (float)(rho / t1[0]);
+      if (!(t1[0] > 0.f)) { done = true; break; }
+      const float al = rho / t1[0];
       // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
       float arr = 0.f, arz = 0.f;
       for (int j0 = gtid; j0 < n4; j0 += kPcgUnroll * T) {
@@ -282,8 +270,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     all_partials<2>(part(slot), tot, shd);
     slot ^= 1;
     it = i + 1;
-    relres = sqrt(tot[0]) / sqrt(rr0);
-    if (relres < a.rtol) {
+    relres = sqrtf(tot[0]) / sqrtf(rr0);
+    if (relres < (float)a.rtol) {
       done = true;
     } else {
       beta = tot[1] / rho;

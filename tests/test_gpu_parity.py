@@ -194,16 +194,18 @@ def test_tiny_solve_matches_oracle(H, orc, precond, path):
 
 
 @pytest.mark.parametrize("name", ["small", "7t"])
-def test_persistent_and_separate_pcg_agree(H, name):
-    """Both PCG paths compute the same iteration; they differ only in how per-block partial sums
-    are grouped, so the fields agree to single-precision rounding."""
+def test_both_pcg_paths_match_oracle_on_larger_volumes(H, orc, name):
+    """Small (96x96x60, PE axis 1) and 7T-shaped (130x130x85, PE axis 0) pairs, OT init + 4 GN
+    iterations, through the separate PCG kernels and the persistent PCG kernel, against the
+    oracle's own double-precision trajectory."""
     pr = ph.make_pair(name)
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=4, contract=False)
+    assert status == 0
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
-    out = []
     for path in (1, 2):
         b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=4, pcg_path=path)
         assert h.last_status() == 0
-        out.append((host(b), host(st)))
-    (b1, s1), (b2, s2) = out
-    assert np.array_equal(s1[:, 7], s2[:, 7]) and np.array_equal(s1[:, 6], s2[:, 6])
-    assert rel(b2, b1) <= 1e-4
+        gs = host(st)
+        assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4), (path, gs[:, 0], rst[:, 0])
+        assert rel(host(b), ref) <= 1e-3, (path, rel(host(b), ref), gs[:, 6], rst[:, 6])
