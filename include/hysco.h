@@ -119,6 +119,14 @@ int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream);
  * end of Sec. 2.3.1).  HYSCO_PC_COLUMN requires m <= 1024. */
 int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t stream);
 
+/* The PCG step of Sec. 2.3.1 on its own: q ~= H_J^{-1} rhs about the field of the last
+ * hysco_eval, x0 = 0, at most max_iters (<= 64) iterations, stop when ||r|| / ||r0|| < rtol or
+ * p^T H p <= 0; preconditioner `precond` (hysco_precond_kind); pcg_path as in hysco_opts.  In a
+ * Gauss-Newton step rhs = -grad J.  rhs, q: field-shaped float32, 16-byte aligned, distinct.
+ * hysco_last_status afterwards also reports a persistent-kernel barrier timeout. */
+int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters, double rtol,
+              int pcg_path, hysco_stream_t stream);
+
 /* Corrected images at b (Eq. 1, the Jacobian-modulation correction of Sec. 2.4):
  * Tp = I+(x + b v)(1 + d_v b), Tm = I-(x - b v)(1 - d_v b), image-shaped float32. */
 int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,

@@ -58,6 +58,7 @@ def load():
         "hysco_eval": (I, [P, P, P, P, P, P, P]),
         "hysco_hessvec": (I, [P, P, P, P]),
         "hysco_precond": (I, [P, P, P, I, P]),
+        "hysco_pcg": (I, [P, P, P, I, I, D, I, P]),
         "hysco_correct": (I, [P, P, P, P, P, P, P]),
         "hysco_solve": (I, [P, P, P, P, C.POINTER(Opts), P, P]),
         "hysco_last_status": (I, [P, P]),

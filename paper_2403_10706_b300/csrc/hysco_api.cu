@@ -73,6 +73,37 @@ int reset_state(hysco_ctx* h, cudaStream_t s) {
   return check_cuda(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
 }
 
+// PCG for H q = sign * g about the handle's linearisation (Sec. 2.3.1); q is written to x.
+int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int max_it,
+            double rtol, bool persistent, cudaStream_t s) {
+  const Geo& geo = h->g;
+  Work w = h->work();
+  if (persistent) {
+    HYSCO_TRY(launch_pcg_persistent(geo, h->pgrid, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
+                                    h->dco, h->eco, h->invd, h->ppart, h->pbar, max_it, rtol,
+                                    h->st, s));
+    return HYSCO_OK;
+  }
+  if (precond == HYSCO_PC_JACOBI) {
+    HYSCO_TRY(launch_pcg_init_jacobi(geo, g, sign, x, h->r, h->z, h->invd, w, s));
+  } else {
+    if (!h->have_factor) HYSCO_TRY(launch_col_factor(geo, h->dco, h->eco, h->invD, h->lco, s));
+    h->have_factor = true;
+    HYSCO_TRY(launch_col_solve(geo, 1, g, x, h->r, nullptr, nullptr, h->z, h->invD, h->lco, 0,
+                               rtol, sign, w, s));
+  }
+  for (int i = 0; i < max_it; ++i) {
+    HYSCO_TRY(launch_pcg_hp(geo, h->z, h->p0, h->Hp, h->dco, h->eco, i == 0, w, s));
+    if (precond == HYSCO_PC_JACOBI)
+      HYSCO_TRY(launch_pcg_update_jacobi(geo, x, h->r, h->p0, h->Hp, h->z, h->invd, i == 0, rtol,
+                                         w, s));
+    else
+      HYSCO_TRY(launch_col_solve(geo, 2, nullptr, x, h->r, h->p0, h->Hp, h->z, h->invD, h->lco,
+                                 i == 0, rtol, 1.0f, w, s));
+  }
+  return HYSCO_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -183,7 +214,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   // partials: the largest grid of any reducing kernel times its reduction width
   long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, kSeg);
   long long flat_blocks = (long long)ceil_div(g.nf, kBlock) + 1;
-  long long nparts = march_blocks * (3 * kLsBatch + 1) + flat_blocks * 2 + 148 * 4 * 2 +
+  long long nparts = march_blocks * (3 * kLsBatch + 1) + flat_blocks * 2 + 148 * 8 * 2 +
                      (long long)g.ncols * 2 + 64;
   if (cudaMalloc((void**)&h->partials, nparts * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
@@ -288,8 +319,23 @@ int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t 
     h->have_factor = true;
   }
   HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, (float*)r, nullptr, nullptr, z, h->invD,
-                             h->lco, 0, 0.0, h->work(), s));
+                             h->lco, 0, 0.0, 1.0f, h->work(), s));
   return HYSCO_OK;
+}
+
+int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters, double rtol,
+              int pcg_path, hysco_stream_t stream) {
+  if (!h || !rhs || !q || !aligned(rhs, 16) || !aligned(q, 16)) return HYSCO_EINVAL;
+  if (precond != HYSCO_PC_JACOBI && precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
+  if (max_iters < 1 || max_iters > 64 || !(rtol >= 0.0) || pcg_path < 0 || pcg_path > 2)
+    return HYSCO_EINVAL;
+  if (!h->have_lin) return HYSCO_ENOTREADY;
+  const bool persistent = precond == HYSCO_PC_JACOBI && h->pgrid > 0 && pcg_path != 1;
+  if (pcg_path == 2 && !persistent) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  return run_pcg(h, rhs, 1.0f, q, precond, max_iters, rtol, persistent, s);
 }
 
 int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,
@@ -332,26 +378,10 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
   for (int it = 0; it < o->gn_iters; ++it) {
     HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, h->invd, it, w,
                           s));
-    if (persistent) {
-      HYSCO_TRY(launch_pcg_persistent(g, h->pgrid, h->grad, h->x, h->r, h->z, h->p0, h->p1,
-                                      h->Hp, h->dco, h->eco, h->invd, h->ppart, h->pbar,
-                                      o->pcg_max_iters, o->pcg_rtol, h->st, s));
-    } else if (o->precond == HYSCO_PC_JACOBI) {
-      HYSCO_TRY(launch_pcg_init_jacobi(g, h->grad, h->x, h->r, h->z, h->invd, w, s));
-    } else {
-      HYSCO_TRY(launch_col_factor(g, h->dco, h->eco, h->invD, h->lco, s));
-      HYSCO_TRY(launch_col_solve(g, 1, h->grad, h->x, h->r, nullptr, nullptr, h->z, h->invD,
-                                 h->lco, 0, o->pcg_rtol, w, s));
-    }
-    for (int i = 0; i < (persistent ? 0 : o->pcg_max_iters); ++i) {
-      HYSCO_TRY(launch_pcg_hp(g, h->z, h->p0, h->Hp, h->dco, h->eco, i == 0, w, s));
-      if (o->precond == HYSCO_PC_JACOBI)
-        HYSCO_TRY(launch_pcg_update_jacobi(g, h->x, h->r, h->p0, h->Hp, h->z, h->invd, i == 0,
-                                           o->pcg_rtol, w, s));
-      else
-        HYSCO_TRY(launch_col_solve(g, 2, nullptr, h->x, h->r, h->p0, h->Hp, h->z, h->invD, h->lco,
-                                   i == 0, o->pcg_rtol, w, s));
-    }
+    h->have_factor = false;
+    if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
+                         persistent, s))
+      return rc;
     for (int t0 = 0; t0 < o->ls_max_iters; t0 += (t0 == 0 ? 1 : kLsBatch))
       HYSCO_TRY(launch_linesearch(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, t0,
                                   o->ls_max_iters, o->armijo_c1, w, s));

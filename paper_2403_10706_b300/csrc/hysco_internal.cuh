@@ -238,8 +238,8 @@ cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
 // k_pcg.cu
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
                            const float* eco, cudaStream_t s);
-cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
-                                   const float* invd, const Work& w, cudaStream_t s);
+cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float sign, float* x, float* r,
+                                   float* z, const float* invd, const Work& w, cudaStream_t s);
 cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, const float* dco,
                           const float* eco, int first, const Work& w, cudaStream_t s);
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
@@ -250,15 +250,16 @@ cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const fl
 int column_tile_width(int E);
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
                               float* lco, cudaStream_t s);
-// mode 0 = apply z = M^{-1} r;  1 = PCG init (r = -grad, x = 0);  2 = PCG update
+// mode 0 = apply z = M^{-1} r;  1 = PCG init (r = sign * grad, x = 0);  2 = PCG update
 cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
                              const float* p, const float* Hp, float* z, const float* invD,
-                             const float* lco, int first, double rtol, const Work& w,
-                             cudaStream_t s);
+                             const float* lco, int first, double rtol, float sign,
+                             const Work& w, cudaStream_t s);
 
 // k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible)
 int pcg_persistent_grid(int device);
-cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float* x, float* r,
+cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
+                                  float* x, float* r,
                                   float* z, float* p0, float* p1, float* Hp, const float* dco,
                                   const float* eco, const float* invd, float* part,
                                   unsigned* bar, int max_it, double rtol, DevState* st,

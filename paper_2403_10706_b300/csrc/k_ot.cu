@@ -22,11 +22,21 @@ __global__ void __launch_bounds__(kBlock)
 k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, int n, float eps,
            float* partials, unsigned* counter, DevState* st) {
   float mn = __int_as_float(0x7f800000), mx = 0.f;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += gridDim.x * blockDim.x) {
-    float a = ldf(Ip + i), b = ldf(Im + i);
-    mn = fminf(mn, fminf(a, b));
-    mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(b)));
+  const int T = gridDim.x * blockDim.x;
+  // four independent loads per image in flight per thread
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * T) {
+    float a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      int i = min(i0 + u * T, n - 1);
+      a[u] = ldf(Ip + i);
+      b[u] = ldf(Im + i);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      mn = fminf(mn, fminf(a[u], b[u]));
+      mx = fmaxf(mx, fmaxf(fabsf(a[u]), fabsf(b[u])));
+    }
   }
   // min / max reduction through the same deterministic machinery (max(-min) and max|I|)
   __shared__ float smn[32], smx[32];
@@ -199,7 +209,7 @@ cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void*
                             long long n, double eps, const Work& w, cudaStream_t s) {
   (void)g;
   int blocks = (int)((n + kBlock - 1) / kBlock);
-  if (blocks > 148 * 4) blocks = 148 * 4;
+  if (blocks > 148 * 8) blocks = 148 * 8;
   if (dtype == 0)
     k_ot_shift<float><<<blocks, kBlock, 0, s>>>((const float*)Ip, (const float*)Im, n, (float)eps,
                                                 w.partials, w.counter, w.st);

@@ -95,9 +95,10 @@ __device__ __forceinline__ void st4(float* p, int i, float4 v) {
   reinterpret_cast<float4*>(p)[i] = v;
 }
 
-// PCG init with Jacobi: r = -grad, x = 0, z = r / diag; rr0 = r.r, rho = r.z
+// PCG init with Jacobi: r = sign * grad (sign = -1 in a GN step), x = 0, z = r / diag;
+// rr0 = r.r, rho = r.z
 __global__ void __launch_bounds__(kBlock)
-k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float* __restrict__ x,
+k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float sign, float* __restrict__ x,
                   float* __restrict__ r, float* __restrict__ z, const float* __restrict__ invd,
                   float* partials, unsigned* counter, DevState* st) {
   if (st->stop) return;
@@ -106,7 +107,7 @@ k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float* __restrict__ x,
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n4) {
     float4 gv = ld4(grad, i), dv = ld4(invd, i);
-    float4 rv = make_float4(-gv.x, -gv.y, -gv.z, -gv.w);
+    float4 rv = make_float4(sign * gv.x, sign * gv.y, sign * gv.z, sign * gv.w);
     float4 zv = make_float4(rv.x * dv.x, rv.y * dv.y, rv.z * dv.z, rv.w * dv.w);
     st4(x, i, make_float4(0.f, 0.f, 0.f, 0.f));
     st4(r, i, rv);
@@ -116,7 +117,7 @@ k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float* __restrict__ x,
   }
   int t = 4 * n4 + i;   // tail (fewer than 4 nodes)
   if (i < (g.nf & 3)) {
-    float rk = -__ldg(grad + t), zk = rk * __ldg(invd + t);
+    float rk = sign * __ldg(grad + t), zk = rk * __ldg(invd + t);
     x[t] = 0.f; r[t] = rk; z[t] = zk;
     arr += rk * rk; arz += rk * zk;
   }
@@ -256,13 +257,13 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
     }
 }
 
-// mode 0: z = M^{-1} r.  mode 1: PCG init (r = -grad, x = 0).  mode 2: PCG update.
+// mode 0: z = M^{-1} r.  mode 1: PCG init (r = sign * grad, x = 0).  mode 2: PCG update.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float* r,
             const float* __restrict__ p, const float* __restrict__ Hp, float* __restrict__ z,
             const float* __restrict__ invD, const float* __restrict__ lco, int first,
-            double rtol, float* partials, unsigned* counter, DevState* st) {
+            double rtol, float sign, float* partials, unsigned* counter, DevState* st) {
   extern __shared__ float sm[];
   if (MODE != 0 && st->stop) return;
   if (MODE == 2 && st->pcg_done) return;
@@ -283,7 +284,7 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
       if (MODE == 0) {
         rk = r[i];
       } else if (MODE == 1) {
-        rk = -__ldg(grad + i);
+        rk = sign * __ldg(grad + i);
         x[i] = 0.f;
         r[i] = rk;
       } else {
@@ -349,9 +350,9 @@ cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float*
   return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float* x, float* r, float* z,
-                                   const float* invd, const Work& w, cudaStream_t s) {
-  k_pcg_init_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, grad, x, r, z, invd, w.partials,
+cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float sign, float* x, float* r,
+                                   float* z, const float* invd, const Work& w, cudaStream_t s) {
+  k_pcg_init_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, grad, sign, x, r, z, invd, w.partials,
                                                      w.counter, w.st);
   return cudaGetLastError();
 }
@@ -390,8 +391,8 @@ cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, 
 
 cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
                              const float* p, const float* Hp, float* z, const float* invD,
-                             const float* lco, int first, double rtol, const Work& w,
-                             cudaStream_t s) {
+                             const float* lco, int first, double rtol, float sign,
+                             const Work& w, cudaStream_t s) {
   int CW = column_tile_width(g.E);
   size_t smem = 3ull * g.E * CW * sizeof(float);
   dim3 grid(ceil_div(g.ncols, CW)), block(CW, kBlock / CW);
@@ -401,7 +402,7 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                            (int)smem);                                                       \
   if (e != cudaSuccess) return e;                                                            \
   k_col_solve<M><<<grid, block, smem, s>>>(g, grad, x, r, p, Hp, z, invD, lco, first, rtol,  \
-                                           w.partials, w.counter, w.st);
+                                           sign, w.partials, w.counter, w.st);
   if (mode == 0) { HYSCO_COLSOLVE(0) }
   else if (mode == 1) { HYSCO_COLSOLVE(1) }
   else { HYSCO_COLSOLVE(2) }

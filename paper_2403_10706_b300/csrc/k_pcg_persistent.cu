@@ -4,7 +4,7 @@
 // At 3T size every PCG kernel is short (tens of microseconds) and a kernel boundary costs about
 // as much as a third of the work, so PCG init and all iterations run in one launch whose phases
 // are separated by device-wide barriers:
-//   init   r = -grad, x = 0, z = r / diag            partials r.r, r.z      | barrier
+//   init   r = rhs (-grad in a GN step), x = 0, z = r / diag  partials r.r, r.z | barrier
 //   iter   A: w = H z, p = z + beta p, Hp = w + beta Hp (p = z, Hp = w at i = 0), partial p.Hp
 //                                                                                     | barrier
 //          B: x += alpha p, r -= alpha Hp, z = r / diag  partials r.r, r.z  | barrier
@@ -29,7 +29,8 @@ constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
 constexpr int kPcgUnroll = 4;
 
 struct PcgArgs {
-  const float* grad;
+  const float* grad;     // right-hand side is rhs_sign * grad
+  float rhs_sign;
   float* x;
   float* r;
   float* z;
@@ -132,7 +133,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
 #pragma unroll
       for (int u = 0; u < kPcgUnroll; ++u) {
         int i = i0 + u * T;
-        float4 rv = make_float4(-gv[u].x, -gv[u].y, -gv[u].z, -gv[u].w);
+        float4 rv = make_float4(a.rhs_sign * gv[u].x, a.rhs_sign * gv[u].y, a.rhs_sign * gv[u].z,
+                                a.rhs_sign * gv[u].w);
         float4 zv = make_float4(rv.x * dv[u].x, rv.y * dv[u].y, rv.z * dv[u].z, rv.w * dv[u].w);
         if (i < n4) {
           reinterpret_cast<float4*>(a.x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -145,7 +147,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     }
     if (gtid < (nf & 3)) {
       int t = 4 * n4 + gtid;
-      float rk = -__ldg(a.grad + t), zk = rk * __ldg(a.invd + t);
+      float rk = a.rhs_sign * __ldg(a.grad + t), zk = rk * __ldg(a.invd + t);
       a.x[t] = 0.f; a.r[t] = rk; a.z[t] = zk;
       arr += rk * rk; arz += rk * zk;
     }
@@ -300,14 +302,15 @@ int pcg_persistent_grid(int device) {
   return sms * per_sm;
 }
 
-cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float* x, float* r,
+cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
+                                  float* x, float* r,
                                   float* z, float* p0, float* p1, float* Hp, const float* dco,
                                   const float* eco, const float* invd, float* part,
                                   unsigned* bar, int max_it, double rtol, DevState* st,
                                   cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  PcgArgs a{grad, x, r, z, p0, p1, Hp, dco, eco, invd, part, bar, st, max_it, rtol};
+  PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, part, bar, st, max_it, rtol};
   Geo gg = g;
   void* args[] = {&gg, &a};
   return cudaLaunchCooperativeKernel((void*)k_pcg_persistent, dim3(grid), dim3(kBlock), args, 0, s);

@@ -98,6 +98,14 @@ class Hysco:
                                           int(kind), _stream(self.device)), "hysco_precond")
         return out
 
+    def pcg(self, rhs, precond=_lib.PC_JACOBI, max_iters=10, rtol=0.1, pcg_path=0, out=None):
+        """q ~= H^{-1} rhs by PCG about the field of the last eval (rhs = -grad in a GN step)."""
+        out = self._new_fld() if out is None else out
+        _lib.check(self.lib.hysco_pcg(self._h, self._fld(rhs, "rhs"), self._fld(out, "q"),
+                                      int(precond), int(max_iters), float(rtol), int(pcg_path),
+                                      _stream(self.device)), "hysco_pcg")
+        return out
+
     def correct(self, Ip, Im, b):
         Tp = torch.empty(self.dims, dtype=torch.float32, device=self.device)
         Tm = torch.empty_like(Tp)

@@ -209,3 +209,19 @@ def test_both_pcg_paths_match_oracle_on_larger_volumes(H, orc, name):
         gs = host(st)
         assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4), (path, gs[:, 0], rst[:, 0])
         assert rel(host(b), ref) <= 1e-3, (path, rel(host(b), ref), gs[:, 6], rst[:, 6])
+
+
+@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("dims,spacing,p", [SHAPES[0], SHAPES[1], SHAPES[2], SHAPES[4]])
+def test_pcg_step_matches_oracle(H, orc, precond, path, dims, spacing, p):
+    """hysco_pcg: q ~= H^{-1} rhs with <= 10 PCG iterations, against the oracle's PCG on the same
+    linearisation (the two differ only by single-precision rounding through 10 iterations)."""
+    Ip, Im, b = case(dims, p, 900)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    terms, g = h.eval(dev(Ip), dev(Im), dev(b))
+    rhs = -host(g).astype(np.float32)
+    q = host(h.pcg(dev(rhs), precond=precond, max_iters=10, rtol=0.1, pcg_path=path))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    qref, it, relres = P.pcg(Ip, Im, b, rhs.astype(np.float64), precond=precond, max_it=10,
+                             rtol=0.1)
+    assert rel(q, qref) <= 1e-4, (rel(q, qref), it, relres)
