@@ -122,7 +122,7 @@ int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t 
 /* The PCG step of Sec. 2.3.1 on its own: q ~= H_J^{-1} rhs about the field of the last
  * hysco_eval, x0 = 0, at most max_iters (<= 64) iterations, stop when ||r|| / ||r0|| < rtol or
  * p^T H p <= 0; preconditioner `precond` (hysco_precond_kind); pcg_path as in hysco_opts.  In a
- * Gauss-Newton step rhs = -grad J.  rhs, q: field-shaped float32, 16-byte aligned, distinct.
+ * Gauss-Newton step rhs = -grad J.  rhs, q: field-shaped float32, distinct.
  * hysco_last_status afterwards also reports a persistent-kernel barrier timeout. */
 int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters, double rtol,
               int pcg_path, hysco_stream_t stream);

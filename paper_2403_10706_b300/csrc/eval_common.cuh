@@ -112,4 +112,16 @@ __device__ __forceinline__ ColNbrs col_nbrs(const Geo& g, int c, int own) {
   return n;
 }
 
+// the same neighbours as pitched bases (solver arrays)
+__device__ __forceinline__ ColNbrs col_nbrs_pitched(const Geo& g, int c, int own) {
+  int cA = c % g.nA, cB = c / g.nA;
+  ColNbrs n;
+  n.Am = cA > 0 ? own - g.psA : own;
+  n.Ap = cA < g.nA - 1 ? own + g.psA : own;
+  n.Bm = cB > 0 ? own - g.psB : own;
+  n.Bp = cB < g.nB - 1 ? own + g.psB : own;
+  n.nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
+  return n;
+}
+
 }  // namespace hysco

@@ -200,12 +200,30 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   g.nf = (int)nfld;
   g.div0 = make_fastdiv((unsigned)g.fs[0]);
   g.div1 = make_fastdiv((unsigned)g.fs[1]);
+  g.P2 = (g.fe[2] + 3) / 4 * 4;
+  g.G4 = g.P2 / 4;
+  g.ps[2] = 1;
+  g.ps[1] = g.P2;
+  g.ps[0] = g.fe[1] * g.P2;
+  g.psA = g.ps[q[1]];
+  g.psB = g.ps[q[0]];
+  g.psP = g.ps[pe_dim];
+  g.divG4 = make_fastdiv((unsigned)g.G4);
+  g.divfe1 = make_fastdiv((unsigned)g.fe[1]);
+  long long nfp = (long long)g.fe[0] * g.fe[1] * g.P2;
+  if (nfp >= (1LL << 31)) {
+    delete h;
+    return HYSCO_EINVAL;
+  }
+  g.nfp = (int)nfp;
 
-  size_t fbytes = (size_t)nfld * sizeof(float);
+  // solver arrays use the pitched layout (>= nfld entries); zeroed once so that every padding
+  // entry starts, and stays, at zero
+  size_t fbytes = (size_t)(nfp > nfld ? nfp : nfld) * sizeof(float);
   float** bufs[] = {&h->grad, &h->dco, &h->eco, &h->invd, &h->x, &h->r, &h->z, &h->p0, &h->p1,
                     &h->Hp, &h->invD, &h->lco, &h->tmp};
   for (float** b : bufs) {
-    if (cudaMalloc((void**)b, fbytes) != cudaSuccess) {
+    if (cudaMalloc((void**)b, fbytes) != cudaSuccess || cudaMemset(*b, 0, fbytes) != cudaSuccess) {
       free_all(h);
       delete h;
       return HYSCO_ENOMEM;
@@ -223,7 +241,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
     delete h;
     return HYSCO_ENOMEM;
   }
-  h->pgrid = pcg_persistent_grid(h->device);
+  h->pgrid = pcg_persistent_grid(h->device, pe_dim);
   if (h->pgrid > 0 &&
       (cudaMalloc((void**)&h->ppart, 4ull * h->pgrid * sizeof(float)) != cudaSuccess ||
        cudaMalloc((void**)&h->pbar, 64 * sizeof(unsigned)) != cudaSuccess)) {
@@ -290,7 +308,8 @@ int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = reset_state(h, s)) return rc;
   Work w = h->work();
-  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, h->dco, h->eco, h->invd, -1, w, s));
+  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, nullptr, h->dco, h->eco, h->invd, -1, w,
+                        s));
   HYSCO_TRY(launch_publish_terms(terms_dev, w, s));
   h->have_lin = true;
   h->have_factor = false;
@@ -300,7 +319,10 @@ int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double
 int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream) {
   if (!h || check_f32(v) || check_f32(Hv)) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
-  HYSCO_TRY(launch_hessvec(h->g, v, Hv, h->dco, h->eco, (cudaStream_t)stream));
+  cudaStream_t s = (cudaStream_t)stream;
+  HYSCO_TRY(launch_to_pitched(h->g, v, h->r, s));
+  HYSCO_TRY(launch_hessvec(h->g, h->r, h->z, h->dco, h->eco, s));
+  HYSCO_TRY(launch_from_pitched(h->g, h->z, Hv, s));
   return HYSCO_OK;
 }
 
@@ -310,22 +332,24 @@ int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t 
   if (kind == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
   cudaStream_t s = (cudaStream_t)stream;
+  HYSCO_TRY(launch_to_pitched(h->g, r, h->r, s));
   if (kind == HYSCO_PC_JACOBI) {
-    HYSCO_TRY(launch_jacobi_apply(h->g, r, z, h->invd, s));
-    return HYSCO_OK;
+    HYSCO_TRY(launch_jacobi_apply(h->g, h->r, h->z, h->invd, s));
+  } else {
+    if (!h->have_factor) {
+      HYSCO_TRY(launch_col_factor(h->g, h->dco, h->eco, h->invD, h->lco, s));
+      h->have_factor = true;
+    }
+    HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, h->r, nullptr, nullptr, h->z, h->invD,
+                               h->lco, 0, 0.0, 1.0f, h->work(), s));
   }
-  if (!h->have_factor) {
-    HYSCO_TRY(launch_col_factor(h->g, h->dco, h->eco, h->invD, h->lco, s));
-    h->have_factor = true;
-  }
-  HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, (float*)r, nullptr, nullptr, z, h->invD,
-                             h->lco, 0, 0.0, 1.0f, h->work(), s));
+  HYSCO_TRY(launch_from_pitched(h->g, h->z, z, s));
   return HYSCO_OK;
 }
 
 int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters, double rtol,
               int pcg_path, hysco_stream_t stream) {
-  if (!h || !rhs || !q || !aligned(rhs, 16) || !aligned(q, 16)) return HYSCO_EINVAL;
+  if (!h || check_f32(rhs) || check_f32(q)) return HYSCO_EINVAL;
   if (precond != HYSCO_PC_JACOBI && precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
   if (precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
   if (max_iters < 1 || max_iters > 64 || !(rtol >= 0.0) || pcg_path < 0 || pcg_path > 2)
@@ -335,7 +359,10 @@ int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters,
   if (pcg_path == 2 && !persistent) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = reset_state(h, s)) return rc;
-  return run_pcg(h, rhs, 1.0f, q, precond, max_iters, rtol, persistent, s);
+  HYSCO_TRY(launch_to_pitched(h->g, rhs, h->tmp, s));
+  if (int rc = run_pcg(h, h->tmp, 1.0f, h->x, precond, max_iters, rtol, persistent, s)) return rc;
+  HYSCO_TRY(launch_from_pitched(h->g, h->x, q, s));
+  return HYSCO_OK;
 }
 
 int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,
@@ -376,8 +403,8 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
       return rc;
   }
   for (int it = 0; it < o->gn_iters; ++it) {
-    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, h->grad, h->dco, h->eco, h->invd, it, w,
-                          s));
+    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, nullptr, h->grad, h->dco, h->eco, h->invd,
+                          it, w, s));
     h->have_factor = false;
     if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
                          persistent, s))

@@ -49,6 +49,15 @@ struct Geo {
   int p;
   int nf;                // field nodes
   FastDiv div0, div1;
+  // Pitched internal layout of the solver's field arrays: the caller's C order with the innermost
+  // extent padded to P2 = 4 * ceil(fe[2] / 4), so every row starts 16-byte aligned and a group of 4
+  // consecutive nodes never straddles rows.  Padding entries are kept at exactly zero.
+  int P2;                // pitch of the innermost axis
+  int G4;                // float4 groups per row (P2 / 4)
+  int nfp;               // fe[0] * fe[1] * P2
+  int ps[3];             // pitched strides (ps[2] = 1)
+  int psA, psB, psP;     // pitched strides of the in-plane axes A, B and of the PE axis
+  FastDiv divG4, divfe1;
 };
 
 // Device-resident scalar state of a solve (and of single hysco_eval calls).
@@ -210,6 +219,90 @@ __device__ __forceinline__ void field_coords(const Geo& g, int n, int (&i)[3]) {
   i[2] = (int)(r - q1 * (unsigned)g.fs[1]);
 }
 
+// pitched index of node k of PE column c
+__device__ __forceinline__ int col_pbase(const Geo& g, int c) {
+  int cB = c / g.nA;
+  return cB * g.psB + (c - cB * g.nA) * g.psA;
+}
+
+// position of float4 group t of the pitched field: row (i0, i1) and first innermost index x0
+struct GroupPos {
+  int row, x0, i0, i1;
+};
+__device__ __forceinline__ GroupPos group_pos(const Geo& g, int t) {
+  GroupPos q;
+  q.row = (int)fdiv((unsigned)t, g.divG4);
+  q.x0 = 4 * (t - q.row * g.G4);
+  q.i0 = (int)fdiv((unsigned)q.row, g.divfe1);
+  q.i1 = q.row - q.i0 * g.fe[1];
+  return q;
+}
+
+__device__ __forceinline__ float f4get(const float4& v, int u) {
+  return u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w));
+}
+
+// H z at the four nodes of group t (pitched layout), with the PCG direction update
+// p = z + beta p, Hp = H z + beta Hp (PCG) or Hv = H z (plain).  P is the PE axis.  Arrays that a
+// persistent kernel writes (z, p, Hp) are read with ordinary loads; d, e with the read-only path.
+// Padding lanes produce zeros.  Returns sum over the group of p * Hp (PCG).
+template <int P, bool PCG>
+__device__ __forceinline__ float hv_group(const Geo& g, int t, const float* z, float* p, float* Hp,
+                                          const float* __restrict__ dco,
+                                          const float* __restrict__ eco, float beta, bool first) {
+  const GroupPos q = group_pos(g, t);
+  const int n = 4 * t, fe2 = g.fe[2];
+  const int s1 = g.G4, s0 = g.fe[1] * g.G4;          // group strides of axes 1 and 0
+  const float4* z4p = reinterpret_cast<const float4*>(z);
+  const float4 zc = z4p[t];
+  const float4 z1m = q.i1 > 0 ? z4p[t - s1] : zc, z1p = q.i1 < g.fe[1] - 1 ? z4p[t + s1] : zc;
+  const float4 z0m = q.i0 > 0 ? z4p[t - s0] : zc, z0p = q.i0 < g.fe[0] - 1 ? z4p[t + s0] : zc;
+  const float zl = q.x0 > 0 ? z[n - 1] : 0.f;
+  const float zr = q.x0 + 4 < g.P2 ? z[n + 4] : 0.f;
+  const float4 d4 = __ldg(reinterpret_cast<const float4*>(dco) + t);
+  const float4 e4 = __ldg(reinterpret_cast<const float4*>(eco) + t);
+  float4 em4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float el = 0.f;
+  if (P == 0 && q.i0 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s0);
+  if (P == 1 && q.i1 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s1);
+  if (P == 2 && q.x0 > 0) el = __ldg(eco + n - 1);
+  float4 po = make_float4(0.f, 0.f, 0.f, 0.f), ho = po;
+  if (PCG && !first) {
+    po = reinterpret_cast<const float4*>(p)[t];
+    ho = reinterpret_cast<const float4*>(Hp)[t];
+  }
+  float outp[4], outh[4], acc = 0.f;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int x = q.x0 + u;
+    const float zk = f4get(zc, u);
+    const float a2m = x > 0 ? (u == 0 ? zl : f4get(zc, u - 1)) : zk;
+    const float a2p = x < fe2 - 1 ? (u == 3 ? zr : f4get(zc, u + 1)) : zk;
+    const float a1m = f4get(z1m, u), a1p = f4get(z1p, u);
+    const float a0m = f4get(z0m, u), a0p = f4get(z0p, u);
+    const float lap = g.w[0] * ((zk - a0m) + (zk - a0p)) + g.w[1] * ((zk - a1m) + (zk - a1p)) +
+                      g.w[2] * ((zk - a2m) + (zk - a2p));
+    float elo = P == 2 ? (u == 0 ? el : f4get(e4, u - 1)) : f4get(em4, u);
+    if (P == 2 && x == 0) elo = 0.f;
+    const float zlo = P == 0 ? a0m : (P == 1 ? a1m : a2m);
+    const float zhi = P == 0 ? a0p : (P == 1 ? a1p : a2p);
+    const float w = g.vol * (elo * zlo + f4get(d4, u) * zk + f4get(e4, u) * zhi + g.alpha * lap);
+    const bool real = x < fe2;
+    if (PCG) {
+      float pk = first ? zk : fmaf(beta, f4get(po, u), zk);
+      float hk = first ? w : fmaf(beta, f4get(ho, u), w);
+      outp[u] = real ? pk : 0.f;
+      outh[u] = real ? hk : 0.f;
+      acc += outp[u] * outh[u];
+    } else {
+      outh[u] = real ? w : 0.f;
+    }
+  }
+  reinterpret_cast<float4*>(Hp)[t] = make_float4(outh[0], outh[1], outh[2], outh[3]);
+  if (PCG) reinterpret_cast<float4*>(p)[t] = make_float4(outp[0], outp[1], outp[2], outp[3]);
+  return acc;
+}
+
 // ------------------------------------------------------------------------------------------
 // host-side launchers (one translation unit each)
 // ------------------------------------------------------------------------------------------
@@ -221,9 +314,10 @@ struct Work {        // device buffers the launchers need
 };
 
 // k_eval.cu
+// grad: caller layout (nullable); grad_p: pitched solver copy (nullable); dco, eco, invd pitched
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
-                        float* grad, float* dco, float* eco, float* invd, int it, const Work& w,
-                        cudaStream_t s);
+                        float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
+                        const Work& w, cudaStream_t s);
 // trials t0 .. t0 + T - 1 with T = 1 when t0 == 0, else kLsBatch
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
@@ -247,6 +341,9 @@ cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const flo
                                      double rtol, const Work& w, cudaStream_t s);
 cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s);
+// caller layout <-> pitched layout of a field-shaped array
+cudaError_t launch_to_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s);
+cudaError_t launch_from_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s);
 int column_tile_width(int E);
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
                               float* lco, cudaStream_t s);
@@ -257,13 +354,12 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const Work& w, cudaStream_t s);
 
 // k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible)
-int pcg_persistent_grid(int device);
+int pcg_persistent_grid(int device, int pe_axis);
 cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
-                                  float* x, float* r,
-                                  float* z, float* p0, float* p1, float* Hp, const float* dco,
-                                  const float* eco, const float* invd, float* part,
-                                  unsigned* bar, int max_it, double rtol, DevState* st,
-                                  cudaStream_t s);
+                                  float* x, float* r, float* z, float* p0, float* p1, float* Hp,
+                                  const float* dco, const float* eco, const float* invd,
+                                  float* part, unsigned* bar, int max_it, double rtol,
+                                  DevState* st, cudaStream_t s);
 
 // k_ot.cu
 cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void* Im,

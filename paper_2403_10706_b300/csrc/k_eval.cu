@@ -28,8 +28,9 @@ namespace hysco {
 template <typename TI, int SEG>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-       float* __restrict__ grad, float* __restrict__ dco, float* __restrict__ eco,
-       float* __restrict__ invd, int it, float* partials, unsigned* counter, DevState* st) {
+       float* __restrict__ grad, float* __restrict__ grad_p, float* __restrict__ dco,
+       float* __restrict__ eco, float* __restrict__ invd, int it, float* partials,
+       unsigned* counter, DevState* st) {
   if (it >= 0 && st->stop) return;
   const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -40,6 +41,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   const TI* Ipc = Ip + ib;
   const TI* Imc = Im + ib;
   const ColNbrs nb = col_nbrs(g, c, fb);
+  const int pb = col_pbase(g, c);
 
   // field nodes k0-1 .. k0+SEG (clamped to [0, m]) and the in-plane neighbours of k0 .. k0+SEG-1
   float bw[SEG + 2], bAm[SEG], bAp[SEG], bBm[SEG], bBp[SEG];
@@ -84,11 +86,12 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     float ek = cjl[j + 1] * cjr[j + 1] - cpsi[j + 1];
     float npe = (float)((k > 0) + (k < m));
     float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
-    int o = fb + k * inner;
-    if (grad) grad[o] = gk;
-    dco[o] = dk;
-    eco[o] = ek;
-    invd[o] = diag > 0.f ? __frcp_rn(diag) : 1.0f;
+    const int pi = pb + k * g.psP;   // solver arrays are pitched
+    if (grad) grad[fb + k * inner] = gk;
+    if (grad_p) grad_p[pi] = gk;
+    dco[pi] = dk;
+    eco[pi] = ek;
+    invd[pi] = diag > 0.f ? __frcp_rn(diag) : 1.0f;
     accG += gk * gk;
   }
   float v[4] = {accD, accS, accP, accG};
@@ -128,24 +131,27 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
   const TI* Ipc = Ip + ib;
   const TI* Imc = Im + ib;
   const ColNbrs nb = col_nbrs(g, c, fb);
+  const int pb = col_pbase(g, c);
+  const ColNbrs nq = col_nbrs_pitched(g, c, pb);   // q and grad are pitched solver arrays
   float bw[SEG + 1], qw[SEG + 1], bAp[SEG], qAp[SEG], bBp[SEG], qBp[SEG];
 #pragma unroll
   for (int j = 0; j <= SEG; ++j) {
-    int o = fb + min(k0 + j, m) * inner;
-    bw[j] = __ldg(b + o);
-    qw[j] = __ldg(q + o);
+    int kk = min(k0 + j, m);
+    bw[j] = __ldg(b + fb + kk * inner);
+    qw[j] = __ldg(q + pb + kk * g.psP);
   }
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
-    int o = min(k0 + j, m) * inner;
-    bAp[j] = __ldg(b + nb.Ap + o); qAp[j] = __ldg(q + nb.Ap + o);
-    bBp[j] = __ldg(b + nb.Bp + o); qBp[j] = __ldg(q + nb.Bp + o);
+    int kk = min(k0 + j, m);
+    int o = kk * inner, op = kk * g.psP;
+    bAp[j] = __ldg(b + nb.Ap + o); qAp[j] = __ldg(q + nq.Ap + op);
+    bBp[j] = __ldg(b + nb.Bp + o); qBp[j] = __ldg(q + nq.Bp + op);
   }
   float agq = 0.f;
   if (t0 == 0) {
 #pragma unroll
     for (int j = 0; j < SEG; ++j)
-      if (act && k0 + j <= m) agq += __ldg(grad + fb + (k0 + j) * inner) * qw[j];
+      if (act && k0 + j <= m) agq += __ldg(grad + pb + (k0 + j) * g.psP) * qw[j];
   }
   float aD[T], aS[T], aP[T];
 #pragma unroll
@@ -186,9 +192,9 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
   }
 }
 
-// b += gamma q; block 0 records the iteration's statistics row
+// b += gamma q (b in the caller's layout, q pitched); block 0 records the iteration's statistics
 __global__ void __launch_bounds__(kBlock)
-k_update(float* __restrict__ b, const float* __restrict__ q, int nf, int it, double* stats,
+k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, double* stats,
          DevState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
@@ -213,19 +219,17 @@ k_update(float* __restrict__ b, const float* __restrict__ q, int nf, int it, dou
   if (st->stop) return;
   const float gam = (float)st->gamma;
   if (gam == 0.0f) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (((uintptr_t)b & 15) == 0) {
-    int n4 = nf >> 2;
-    if (i < n4) {
-      float4 bv = reinterpret_cast<float4*>(b)[i];
-      float4 qv = __ldg(reinterpret_cast<const float4*>(q) + i);
-      bv.x = fmaf(gam, qv.x, bv.x); bv.y = fmaf(gam, qv.y, bv.y);
-      bv.z = fmaf(gam, qv.z, bv.z); bv.w = fmaf(gam, qv.w, bv.w);
-      reinterpret_cast<float4*>(b)[i] = bv;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (g.nfp >> 2)) return;
+  const GroupPos pos = group_pos(g, t);
+  const float4 qv = __ldg(reinterpret_cast<const float4*>(q) + t);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int x = pos.x0 + u;
+    if (x < g.fe[2]) {
+      int i = pos.row * g.fe[2] + x;
+      b[i] = fmaf(gam, f4get(qv, u), b[i]);
     }
-    if (i < (nf & 3)) b[4 * n4 + i] = fmaf(gam, q[4 * n4 + i], b[4 * n4 + i]);
-  } else {
-    for (int n = i; n < nf; n += gridDim.x * blockDim.x) b[n] = fmaf(gam, q[n], b[n]);
   }
 }
 
@@ -289,12 +293,12 @@ static dim3 march_grid(const Geo& g, int nodes) {
   }
 
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
-                        float* grad, float* dco, float* eco, float* invd, int it, const Work& w,
-                        cudaStream_t s) {
+                        float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
+                        const Work& w, cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
     (k_eval<T, kSeg><<<march_grid(g, g.E), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, grad,
-                                                           dco, eco, invd, it, w.partials,
-                                                           w.counter, w.st)))
+                                                           grad_p, dco, eco, invd, it,
+                                                           w.partials, w.counter, w.st)))
   return cudaGetLastError();
 }
 
@@ -317,9 +321,7 @@ cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const voi
 
 cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
                           const Work& w, cudaStream_t s) {
-  int blocks = ((uintptr_t)b & 15) == 0 ? ceil_div((g.nf >> 2) > 0 ? (g.nf >> 2) : 1, kBlock)
-                                        : 148 * 8;
-  k_update<<<blocks, kBlock, 0, s>>>(b, q, g.nf, it, stats, w.st);
+  k_update<<<ceil_div(g.nfp >> 2, kBlock), kBlock, 0, s>>>(g, b, q, it, stats, w.st);
   return cudaGetLastError();
 }
 

@@ -3,7 +3,8 @@
 // The GN Hessian about the last evaluated field is
 //   H = vol [T + alpha L],  T = per-column tridiagonal (d_k on the diagonal, e_k between k, k+1),
 // with d, e written by the eval kernel and L the 7-point negative Laplacian in PE-voxel units
-// (PE weight 1, in-plane weights wA, wB).  Vectors are field-shaped float32.
+// (PE weight 1, in-plane weights wA, wB).  Vectors are field-shaped float32 in the pitched layout
+// (Geo::P2): one thread handles one aligned group of 4 nodes of a row (see hv_group).
 //
 // PCG (Hestenes-Stiefel, x0 = 0) is split in two kernels per iteration i so that every global
 // inner product is reduced exactly once, in the kernel that produces it:
@@ -19,57 +20,25 @@
 namespace hysco {
 
 // ------------------------------------------------------------------------------------------
-// H v: one thread per field node (kNpt nodes per thread, a block apart), coordinates by fast
-// division, and branch-free neighbours: an absent neighbour (Neumann end) is read at the node
-// itself, which zeroes its Laplacian difference, so all loads issue back to back.
+// H v: one thread per aligned group of 4 nodes of the pitched field (hv_group): neighbours along
+// the two outer axes are float4 loads, along the row they come from the group and one scalar on
+// each side; an absent neighbour (Neumann end) is the node itself, which zeroes its difference.
 // ------------------------------------------------------------------------------------------
 
 // Hv (PCG = false) or the PCG step (PCG = true): w = H z; p = z + beta p; Hp = w + beta Hp.
-template <bool PCG>
+template <int P, bool PCG>
 __global__ void __launch_bounds__(kBlock)
-k_hv(Geo g, const float* __restrict__ z, float* __restrict__ p, float* __restrict__ Hp,
-     const float* __restrict__ dco, const float* __restrict__ eco, int first, float* partials,
-     unsigned* counter, DevState* st) {
+k_hv(Geo g, const float* z, float* p, float* Hp, const float* __restrict__ dco,
+     const float* __restrict__ eco, int first, float* partials, unsigned* counter,
+     DevState* st) {
   float beta = 0.f;
   if (PCG) {
     if (st->stop || st->pcg_done) return;
     beta = first ? 0.f : (float)st->beta_cg;
   }
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   float acc = 0.f;
-  const int base = blockIdx.x * (kBlock * kNpt) + threadIdx.x;
-#pragma unroll
-  for (int u = 0; u < kNpt; ++u) {
-    int n = base + u * kBlock;
-    bool valid = n < g.nf;
-    n = valid ? n : g.nf - 1;
-    int ix[3];
-    field_coords(g, n, ix);
-    float zk = __ldg(z + n);
-    float lap = 0.f, zlo = zk, zhi = zk;
-    int nlo = n;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      int lo = ix[a] > 0 ? n - g.fs[a] : n;
-      int hi = ix[a] < g.fe[a] - 1 ? n + g.fs[a] : n;
-      float zl = __ldg(z + lo), zh = __ldg(z + hi);
-      lap += g.w[a] * ((zk - zl) + (zk - zh));
-      if (a == g.p) { zlo = zl; zhi = zh; nlo = lo; }
-    }
-    float em1 = __ldg(eco + nlo);
-    em1 = nlo != n ? em1 : 0.f;
-    float w = g.vol * (em1 * zlo + __ldg(dco + n) * zk + __ldg(eco + n) * zhi + g.alpha * lap);
-    if (!PCG) {
-      if (valid) Hp[n] = w;
-      continue;
-    }
-    float pk = first ? zk : fmaf(beta, p[n], zk);
-    float hk = first ? w : fmaf(beta, Hp[n], w);
-    if (valid) {
-      Hp[n] = hk;
-      p[n] = pk;
-      acc += pk * hk;
-    }
-  }
+  if (t < (g.nfp >> 2)) acc = hv_group<P, PCG>(g, t, z, p, Hp, dco, eco, beta, first != 0);
   if (!PCG) return;
   float v[1] = {acc};
   double tot[1];
@@ -84,7 +53,7 @@ k_hv(Geo g, const float* __restrict__ z, float* __restrict__ p, float* __restric
 }
 
 // ------------------------------------------------------------------------------------------
-// elementwise PCG steps, float4 over the flat field (workspace arrays are 256-byte aligned);
+// elementwise PCG steps, float4 over the pitched field (a multiple of 4 long, padding zero);
 // the inverse Jacobi diagonal comes from the eval kernel.
 // ------------------------------------------------------------------------------------------
 
@@ -103,9 +72,8 @@ k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float sign, float* __re
                   float* partials, unsigned* counter, DevState* st) {
   if (st->stop) return;
   float arr = 0.f, arz = 0.f;
-  int n4 = g.nf >> 2;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n4) {
+  if (i < (g.nfp >> 2)) {
     float4 gv = ld4(grad, i), dv = ld4(invd, i);
     float4 rv = make_float4(sign * gv.x, sign * gv.y, sign * gv.z, sign * gv.w);
     float4 zv = make_float4(rv.x * dv.x, rv.y * dv.y, rv.z * dv.z, rv.w * dv.w);
@@ -114,12 +82,6 @@ k_pcg_init_jacobi(Geo g, const float* __restrict__ grad, float sign, float* __re
     st4(z, i, zv);
     arr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     arz = rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
-  }
-  int t = 4 * n4 + i;   // tail (fewer than 4 nodes)
-  if (i < (g.nf & 3)) {
-    float rk = sign * __ldg(grad + t), zk = rk * __ldg(invd + t);
-    x[t] = 0.f; r[t] = rk; z[t] = zk;
-    arr += rk * rk; arz += rk * zk;
   }
   float v[2] = {arr, arz};
   double tot[2];
@@ -152,9 +114,8 @@ k_pcg_update_jacobi(Geo g, float* __restrict__ x, float* __restrict__ r,
   if (st->stop || st->pcg_done) return;
   const float a = (float)st->alpha_cg;
   float arr = 0.f, arz = 0.f;
-  int n4 = g.nf >> 2;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n4) {
+  if (i < (g.nfp >> 2)) {
     float4 pv = ld4(p, i), hv = ld4(Hp, i), dv = ld4(invd, i);
     float4 rv = reinterpret_cast<const float4*>(r)[i];
     float4 xv = first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(x)[i];
@@ -169,16 +130,6 @@ k_pcg_update_jacobi(Geo g, float* __restrict__ x, float* __restrict__ r,
     arr = rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
     arz = rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
   }
-  int t = 4 * n4 + i;
-  if (i < (g.nf & 3)) {
-    float pk = p[t];
-    x[t] = first ? a * pk : fmaf(a, pk, x[t]);
-    float rk = fmaf(-a, Hp[t], r[t]);
-    r[t] = rk;
-    float zk = rk * invd[t];
-    z[t] = zk;
-    arr += rk * rk; arz += rk * zk;
-  }
   float v[2] = {arr, arz};
   double tot[2];
   if (grid_sum<2>(v, partials, counter, tot)) pcg_finish(st, tot[0], tot[1], rtol);
@@ -188,7 +139,35 @@ __global__ void __launch_bounds__(kBlock)
 k_jacobi_apply(Geo g, const float* __restrict__ r, float* __restrict__ z,
                const float* __restrict__ invd) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < g.nf) z[n] = __ldg(r + n) * __ldg(invd + n);
+  if (n < g.nfp) z[n] = __ldg(r + n) * __ldg(invd + n);
+}
+
+// caller layout <-> pitched layout (padding written as zero)
+__global__ void __launch_bounds__(kBlock)
+k_to_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (g.nfp >> 2)) return;
+  GroupPos q = group_pos(g, t);
+  float v[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int x = q.x0 + u;
+    v[u] = x < g.fe[2] ? __ldg(src + q.row * g.fe[2] + x) : 0.f;
+  }
+  reinterpret_cast<float4*>(dst)[t] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_from_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (g.nfp >> 2)) return;
+  GroupPos q = group_pos(g, t);
+  float4 v = __ldg(reinterpret_cast<const float4*>(src) + t);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    int x = q.x0 + u;
+    if (x < g.fe[2]) dst[q.row * g.fe[2] + x] = f4get(v, u);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -217,7 +196,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   int tx = threadIdx.x, ty = threadIdx.y;
   int c = blockIdx.x * CW + tx;
   bool act = c < g.ncols;
-  int fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
+  int fb = act ? col_pbase(g, c) : 0;
   float nin = 0.f;
   if (act) {
     int cA = c % g.nA, cB = c / g.nA;
@@ -226,7 +205,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   for (int k = ty; k < E; k += blockDim.y) {
     float dv = 1.f, ov = 0.f;
     if (act) {
-      int i = fb + k * g.inner;
+      int i = fb + k * g.psP;
       float npe = (float)((k > 0) + (k < g.m));
       dv = g.vol * (__ldg(dco + i) + g.alpha * (npe + nin));
       ov = k < g.m ? g.vol * (__ldg(eco + i) - g.alpha) : 0.f;
@@ -251,7 +230,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   __syncthreads();
   if (act)
     for (int k = ty; k < E; k += blockDim.y) {
-      int i = fb + k * g.inner;
+      int i = fb + k * g.psP;
       invD[i] = dia[k * CW + tx];
       lco[i] = off[k * CW + tx];
     }
@@ -274,13 +253,13 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
   int tx = threadIdx.x, ty = threadIdx.y;
   int c = blockIdx.x * CW + tx;
   bool act = c < g.ncols;
-  int fb = act ? col_base(c, g.inner, g.fld_ostride) : 0;
+  int fb = act ? col_pbase(g, c) : 0;
   float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
   float arr = 0.f, arz = 0.f;
   for (int k = ty; k < E; k += blockDim.y) {
     float rk = 0.f, lk = 0.f, idk = 1.f;
     if (act) {
-      int i = fb + k * g.inner;
+      int i = fb + k * g.psP;
       if (MODE == 0) {
         rk = r[i];
       } else if (MODE == 1) {
@@ -318,7 +297,7 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
   __syncthreads();
   if (act)
     for (int k = ty; k < E; k += blockDim.y) {
-      int i = fb + k * g.inner;
+      int i = fb + k * g.psP;
       float zk = R[k * CW + tx];
       z[i] = zk;
       if (MODE != 0) arz += r[i] * zk;
@@ -340,41 +319,60 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
 
 // ------------------------------------------------------------------------------------------
 
-static int flat_blocks(const Geo& g) { return ceil_div(g.nf, kBlock * kNpt); }
-static int vec_blocks(const Geo& g) { return ceil_div((g.nf >> 2) > 0 ? (g.nf >> 2) : 1, kBlock); }
+static int group_blocks(const Geo& g) { return ceil_div(g.nfp >> 2, kBlock); }
+
+template <bool PCG>
+static void hv_launch(const Geo& g, const float* z, float* p, float* Hp, const float* dco,
+                      const float* eco, int first, const Work* w, cudaStream_t s) {
+  float* pa = w ? w->partials : nullptr;
+  unsigned* ct = w ? w->counter : nullptr;
+  DevState* st = w ? w->st : nullptr;
+  const int nb = group_blocks(g);
+  if (g.p == 0) k_hv<0, PCG><<<nb, kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, pa, ct, st);
+  else if (g.p == 1) k_hv<1, PCG><<<nb, kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, pa, ct, st);
+  else k_hv<2, PCG><<<nb, kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, pa, ct, st);
+}
 
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
                            const float* eco, cudaStream_t s) {
-  k_hv<false><<<flat_blocks(g), kBlock, 0, s>>>(g, v, nullptr, Hv, dco, eco, 0, nullptr, nullptr,
-                                                nullptr);
+  hv_launch<false>(g, v, nullptr, Hv, dco, eco, 0, nullptr, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float sign, float* x, float* r,
                                    float* z, const float* invd, const Work& w, cudaStream_t s) {
-  k_pcg_init_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, grad, sign, x, r, z, invd, w.partials,
-                                                     w.counter, w.st);
+  k_pcg_init_jacobi<<<group_blocks(g), kBlock, 0, s>>>(g, grad, sign, x, r, z, invd, w.partials,
+                                                       w.counter, w.st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, const float* dco,
                           const float* eco, int first, const Work& w, cudaStream_t s) {
-  k_hv<true><<<flat_blocks(g), kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, w.partials, w.counter,
-                                               w.st);
+  hv_launch<true>(g, z, p, Hp, dco, eco, first, &w, s);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
                                      const float* Hp, float* z, const float* invd, int first,
                                      double rtol, const Work& w, cudaStream_t s) {
-  k_pcg_update_jacobi<<<vec_blocks(g), kBlock, 0, s>>>(g, x, r, p, Hp, z, invd, first, rtol,
-                                                       w.partials, w.counter, w.st);
+  k_pcg_update_jacobi<<<group_blocks(g), kBlock, 0, s>>>(g, x, r, p, Hp, z, invd, first, rtol,
+                                                         w.partials, w.counter, w.st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s) {
-  k_jacobi_apply<<<ceil_div(g.nf, kBlock), kBlock, 0, s>>>(g, r, z, invd);
+  k_jacobi_apply<<<ceil_div(g.nfp, kBlock), kBlock, 0, s>>>(g, r, z, invd);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s) {
+  k_to_pitched<<<group_blocks(g), kBlock, 0, s>>>(g, src, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s) {
+  k_from_pitched<<<group_blocks(g), kBlock, 0, s>>>(g, src, dst);
   return cudaGetLastError();
 }
 

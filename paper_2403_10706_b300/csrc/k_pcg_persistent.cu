@@ -106,6 +106,7 @@ __device__ __forceinline__ void all_partials(const float* part, float (&tot)[K],
   __syncthreads();
 }
 
+template <int P>
 __global__ void __launch_bounds__(kBlock)
 k_pcg_persistent(Geo g, PcgArgs a) {
   __shared__ float shf[32 * 2];
@@ -114,7 +115,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   if (st->stop) return;
   const int T = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int nf = g.nf, n4 = nf >> 2;
+  const int n4 = g.nfp >> 2;   // float4 groups of the pitched field (padding is zero)
   unsigned gen = 0;
   int slot = 0;
   auto part = [&](int s) { return a.part + s * gridDim.x * 2; };
@@ -145,12 +146,6 @@ k_pcg_persistent(Geo g, PcgArgs a) {
         }
       }
     }
-    if (gtid < (nf & 3)) {
-      int t = 4 * n4 + gtid;
-      float rk = a.rhs_sign * __ldg(a.grad + t), zk = rk * __ldg(a.invd + t);
-      a.x[t] = 0.f; a.r[t] = rk; a.z[t] = zk;
-      arr += rk * rk; arz += rk * zk;
-    }
     float v[2] = {arr, arz};
     block_reduce_f<2>(v, shf);
     if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v[0]; part(slot)[blockIdx.x * 2 + 1] = v[1]; }
@@ -169,48 +164,9 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     const bool first = i == 0;
     float* pv_ = a.p0;
     const float fb = beta;
-    // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp ---------------------------------------
-    // all loads of kPcgUnroll nodes are issued before any store (the stores could alias them)
+    // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp (groups of 4 pitched nodes) ----------
     float acc = 0.f;
-    for (int n0 = gtid; n0 < nf; n0 += kPcgUnroll * T) {
-      float zk[kPcgUnroll], lap[kPcgUnroll], zlo[kPcgUnroll], zhi[kPcgUnroll];
-      float dk[kPcgUnroll], ek[kPcgUnroll], em[kPcgUnroll], po[kPcgUnroll], ho[kPcgUnroll];
-#pragma unroll
-      for (int u = 0; u < kPcgUnroll; ++u) {
-        int n = min(n0 + u * T, nf - 1);
-        int ix[3];
-        field_coords(g, n, ix);
-        zk[u] = a.z[n];
-        lap[u] = 0.f;
-        int nlo = n;
-#pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-          int lo = ix[ax] > 0 ? n - g.fs[ax] : n;
-          int hi = ix[ax] < g.fe[ax] - 1 ? n + g.fs[ax] : n;
-          float zl = a.z[lo], zh = a.z[hi];
-          lap[u] += g.w[ax] * ((zk[u] - zl) + (zk[u] - zh));
-          if (ax == g.p) { zlo[u] = zl; zhi[u] = zh; nlo = lo; }
-        }
-        dk[u] = __ldg(a.dco + n);
-        ek[u] = __ldg(a.eco + n);
-        float e1 = __ldg(a.eco + nlo);
-        em[u] = nlo != n ? e1 : 0.f;
-        po[u] = first ? 0.f : pv_[n];
-        ho[u] = first ? 0.f : a.Hp[n];
-      }
-#pragma unroll
-      for (int u = 0; u < kPcgUnroll; ++u) {
-        int n = n0 + u * T;
-        float w = g.vol * (em[u] * zlo[u] + dk[u] * zk[u] + ek[u] * zhi[u] + g.alpha * lap[u]);
-        float pk = first ? zk[u] : fmaf(fb, po[u], zk[u]);
-        float hk = first ? w : fmaf(fb, ho[u], w);
-        if (n < nf) {
-          a.Hp[n] = hk;
-          pv_[n] = pk;
-          acc += pk * hk;
-        }
-      }
-    }
+    for (int t = gtid; t < n4; t += T) acc += hv_group<P, true>(g, t, a.z, pv_, a.Hp, a.dco, a.eco, fb, first);
     {
       float v[1] = {acc};
       block_reduce_f<1>(v, shf);
@@ -254,16 +210,6 @@ k_pcg_persistent(Geo g, PcgArgs a) {
           }
         }
       }
-      if (gtid < (nf & 3)) {
-        int t = 4 * n4 + gtid;
-        float pk = pv_[t];
-        a.x[t] = first ? al * pk : fmaf(al, pk, a.x[t]);
-        float rk = fmaf(-al, a.Hp[t], a.r[t]);
-        a.r[t] = rk;
-        float zk = rk * __ldg(a.invd + t);
-        a.z[t] = zk;
-        arr += rk * rk; arz += rk * zk;
-      }
       float v2[2] = {arr, arz};
       block_reduce_f<2>(v2, shf);
       if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v2[0]; part(slot)[blockIdx.x * 2 + 1] = v2[1]; }
@@ -290,30 +236,36 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   }
 }
 
-int pcg_persistent_grid(int device) {
-  int sms = 0, per_sm = 0;
+template <int P>
+static int grid_for(int device) {
+  int sms = 0, per_sm = 0, coop = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kBlock, 0) !=
-      cudaSuccess)
-    return 0;
-  int coop = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kBlock, 0) !=
+      cudaSuccess)
     return 0;
   return sms * per_sm;
 }
 
+int pcg_persistent_grid(int device, int pe_axis) {
+  return pe_axis == 0 ? grid_for<0>(device) : (pe_axis == 1 ? grid_for<1>(device)
+                                                            : grid_for<2>(device));
+}
+
 cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
-                                  float* x, float* r,
-                                  float* z, float* p0, float* p1, float* Hp, const float* dco,
-                                  const float* eco, const float* invd, float* part,
-                                  unsigned* bar, int max_it, double rtol, DevState* st,
-                                  cudaStream_t s) {
+                                  float* x, float* r, float* z, float* p0, float* p1, float* Hp,
+                                  const float* dco, const float* eco, const float* invd,
+                                  float* part, unsigned* bar, int max_it, double rtol,
+                                  DevState* st, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, part, bar, st, max_it, rtol};
   Geo gg = g;
   void* args[] = {&gg, &a};
-  return cudaLaunchCooperativeKernel((void*)k_pcg_persistent, dim3(grid), dim3(kBlock), args, 0, s);
+  void* fn = g.p == 0 ? (void*)k_pcg_persistent<0>
+                      : (g.p == 1 ? (void*)k_pcg_persistent<1> : (void*)k_pcg_persistent<2>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
 }
 
 }  // namespace hysco
