@@ -210,6 +210,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   g.psP = g.ps[pe_dim];
   g.divG4 = make_fastdiv((unsigned)g.G4);
   g.divfe1 = make_fastdiv((unsigned)g.fe[1]);
+  g.divfe2 = make_fastdiv((unsigned)g.fe[2]);
   long long nfp = (long long)g.fe[0] * g.fe[1] * g.P2;
   if (nfp >= (1LL << 31)) {
     delete h;
@@ -409,7 +410,11 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
     if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
                          persistent, s))
       return rc;
-    for (int t0 = 0; t0 < o->ls_max_iters; t0 += (t0 == 0 ? 1 : kLsBatch))
+    // gamma = 1 as a full evaluation at b + q (its coefficients serve the next GN step when
+    // accepted), then the halvings in batches of kLsBatch, J only
+    HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, h->dco, h->eco,
+                                h->invd, o->ls_max_iters, o->armijo_c1, w, s));
+    for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
       HYSCO_TRY(launch_linesearch(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, t0,
                                   o->ls_max_iters, o->armijo_c1, w, s));
     HYSCO_TRY(launch_update(g, b_inout, h->x, it, stats, w, s));

@@ -57,7 +57,7 @@ struct Geo {
   int nfp;               // fe[0] * fe[1] * P2
   int ps[3];             // pitched strides (ps[2] = 1)
   int psA, psB, psP;     // pitched strides of the in-plane axes A, B and of the PE axis
-  FastDiv divG4, divfe1;
+  FastDiv divG4, divfe1, divfe2;
 };
 
 // Device-resident scalar state of a solve (and of single hysco_eval calls).
@@ -72,6 +72,10 @@ struct DevState {
   int status;                 // hysco_status of the last numerical evaluation
   int stop, stop_iter;        // solve stopped (J not finite) at GN iteration stop_iter
   int gn_iter;
+  // set by the gamma = 1 line-search pass when it accepts: the GN coefficients it wrote (at
+  // b + q) are those of the next iterate, whose J, D, S, P, ||grad|| are stashed here
+  int coef_fresh, status_n;
+  double Jn, Dn, Sn, Pn, gnorm_n;
 };
 
 constexpr int kBlock = 256;   // threads per block of every kernel
@@ -318,6 +322,13 @@ struct Work {        // device buffers the launchers need
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
                         const Work& w, cudaStream_t s);
+// The gamma = 1 Armijo trial as a full evaluation at b + q (q pitched): J, grad, d, e, 1/diag at
+// b + q overwrite the solver arrays (grad_p is read first for grad^T q), and the Armijo decision
+// for gamma = 1 is taken; on acceptance the next launch_eval only promotes the stashed terms.
+cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const void* Im,
+                              const float* b, const float* q, float* grad_p, float* dco,
+                              float* eco, float* invd, int ls_max, double c1, const Work& w,
+                              cudaStream_t s);
 // trials t0 .. t0 + T - 1 with T = 1 when t0 == 0, else kLsBatch
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,

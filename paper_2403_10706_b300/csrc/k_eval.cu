@@ -25,13 +25,32 @@ namespace hysco {
 // J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
 // ------------------------------------------------------------------------------------------
 
-template <typename TI, int SEG>
+// TRIAL = false: evaluation at b (GN iteration `it`, or it < 0 for a single hysco_eval call).  In a
+// solve, when the previous gamma = 1 trial was accepted the coefficients at this iterate are
+// already in place: one thread promotes the stashed terms and every block returns at once (no
+// block enters the reduction, so the ticket counter is untouched).
+// TRIAL = true: the gamma = 1 Armijo trial, an evaluation at b + q.
+template <typename TI, int SEG, bool TRIAL>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-       float* __restrict__ grad, float* __restrict__ grad_p, float* __restrict__ dco,
-       float* __restrict__ eco, float* __restrict__ invd, int it, float* partials,
-       unsigned* counter, DevState* st) {
-  if (it >= 0 && st->stop) return;
+       const float* __restrict__ q, float* __restrict__ grad, float* __restrict__ grad_p,
+       float* __restrict__ dco, float* __restrict__ eco, float* __restrict__ invd, int it,
+       int ls_max, double c1, float* partials, unsigned* counter, DevState* st) {
+  if (TRIAL) {
+    if (st->stop || st->ls_done) return;
+  } else if (it >= 0) {
+    if (st->stop) return;
+    if (st->coef_fresh) {
+      if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        st->J = st->Jn; st->D = st->Dn; st->S = st->Sn; st->P = st->Pn;
+        st->gnorm = st->gnorm_n;
+        st->status = st->status_n;
+        st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
+        st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
+      }
+      return;
+    }
+  }
   const int inner = g.inner, m = g.m;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = c < g.ncols;
@@ -42,17 +61,36 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   const TI* Imc = Im + ib;
   const ColNbrs nb = col_nbrs(g, c, fb);
   const int pb = col_pbase(g, c);
+  const ColNbrs nq = col_nbrs_pitched(g, c, pb);
+  // field value at node kk of the column with user offset uo and pitched offset po
+  auto fld = [&](int uo, int po) {
+    float v = __ldg(b + uo);
+    return TRIAL ? fmaf(1.0f, __ldg(q + po), v) : v;
+  };
 
   // field nodes k0-1 .. k0+SEG (clamped to [0, m]) and the in-plane neighbours of k0 .. k0+SEG-1
   float bw[SEG + 2], bAm[SEG], bAp[SEG], bBm[SEG], bBp[SEG];
 #pragma unroll
-  for (int j = 0; j < SEG + 2; ++j)
-    bw[j] = __ldg(b + fb + min(max(k0 - 1 + j, 0), m) * inner);
+  for (int j = 0; j < SEG + 2; ++j) {
+    int kk = min(max(k0 - 1 + j, 0), m);
+    bw[j] = fld(fb + kk * inner, pb + kk * g.psP);
+  }
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
-    int o = min(k0 + j, m) * inner;
-    bAm[j] = __ldg(b + nb.Am + o); bAp[j] = __ldg(b + nb.Ap + o);
-    bBm[j] = __ldg(b + nb.Bm + o); bBp[j] = __ldg(b + nb.Bp + o);
+    int kk = min(k0 + j, m);
+    int o = kk * inner, op = kk * g.psP;
+    bAm[j] = fld(nb.Am + o, nq.Am + op); bAp[j] = fld(nb.Ap + o, nq.Ap + op);
+    bBm[j] = fld(nb.Bm + o, nq.Bm + op); bBp[j] = fld(nb.Bp + o, nq.Bp + op);
+  }
+  // grad^T q with the gradient at b (trial only), loaded before this thread overwrites it
+  float accGQ = 0.f;
+  if (TRIAL) {
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      int kk = min(k0 + j, m);
+      float gv = grad_p[pb + kk * g.psP], qv = __ldg(q + pb + kk * g.psP);
+      accGQ += (act && k0 + j <= m) ? gv * qv : 0.f;
+    }
   }
   // cells k0-1 .. k0+SEG-1; out-of-column cells contribute nothing
   float cr[SEG + 1], cjl[SEG + 1], cjr[SEG + 1], cdphi[SEG + 1], cpsi[SEG + 1], cphi[SEG + 1];
@@ -60,13 +98,13 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   for (int j = 0; j <= SEG; ++j) {
     int jc = k0 - 1 + j;
     bool cv = jc >= 0 && jc < m;
-    CellLin q = cell_lin(Ipc, Imc, inner, m, jc, bw[j], bw[j + 1], g.half_beta);
-    cr[j] = cv ? q.r : 0.f;
-    cjl[j] = cv ? q.jl : 0.f;
-    cjr[j] = cv ? q.jr : 0.f;
-    cdphi[j] = cv ? q.dphi : 0.f;
-    cpsi[j] = cv ? q.psi : 0.f;
-    cphi[j] = cv ? q.phi : 0.f;
+    CellLin cl = cell_lin(Ipc, Imc, inner, m, jc, bw[j], bw[j + 1], g.half_beta);
+    cr[j] = cv ? cl.r : 0.f;
+    cjl[j] = cv ? cl.jl : 0.f;
+    cjr[j] = cv ? cl.jr : 0.f;
+    cdphi[j] = cv ? cl.dphi : 0.f;
+    cpsi[j] = cv ? cl.psi : 0.f;
+    cphi[j] = cv ? cl.phi : 0.f;
   }
   float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
 #pragma unroll
@@ -94,18 +132,39 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     invd[pi] = diag > 0.f ? __frcp_rn(diag) : 1.0f;
     accG += gk * gk;
   }
-  float v[4] = {accD, accS, accP, accG};
-  double tot[4];
-  if (grid_sum<4>(v, partials, counter, tot)) {
+  float v[5] = {accD, accS, accP, accG, accGQ};
+  double tot[5];
+  if (grid_sum<5>(v, partials, counter, tot)) {
     double hv = 0.5 * (double)g.vol;
     double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
     double J = D + g.alpha_d * S + g.beta_d * P;
-    st->J = J; st->D = D; st->S = S; st->P = P;
-    st->gnorm = sqrt(tot[3]);
-    st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
-    st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
-    st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
-    if (it >= 0 && !isfinite(J)) { st->stop = 1; st->stop_iter = it; }
+    if (!TRIAL) {
+      st->J = J; st->D = D; st->S = S; st->P = P;
+      st->gnorm = sqrt(tot[3]);
+      st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
+      st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
+      st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
+      st->coef_fresh = 0;
+      if (it >= 0 && !isfinite(J)) { st->stop = 1; st->stop_iter = it; }
+    } else {
+      double gq = tot[4];
+      st->gq = gq;
+      st->coef_fresh = 0;
+      if (!(gq < 0.0)) {             // not a descent direction: keep the iterate
+        st->ls_done = 1; st->gamma = 0.0; st->ls_trials = 0;
+      } else {
+        st->ls_trials = 1;
+        if (J <= st->J + c1 * gq) {  // Armijo with gamma = 1
+          st->ls_done = 1; st->gamma = 1.0;
+          st->coef_fresh = 1;
+          st->Jn = J; st->Dn = D; st->Sn = S; st->Pn = P;
+          st->gnorm_n = sqrt(tot[3]);
+          st->status_n = 0;
+        } else if (ls_max <= 1) {
+          st->ls_done = 1; st->gamma = 0.0;
+        }
+      }
+    }
   }
 }
 
@@ -219,17 +278,22 @@ k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, doub
   if (st->stop) return;
   const float gam = (float)st->gamma;
   if (gam == 0.0f) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (g.nfp >> 2)) return;
-  const GroupPos pos = group_pos(g, t);
-  const float4 qv = __ldg(reinterpret_cast<const float4*>(q) + t);
+  // lanes walk consecutive caller-layout nodes (coalesced b); q's pitched index by one division
+  const int T = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < g.nf; i0 += 4 * T) {
+    float bv[4], qv[4];
+    int idx[4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    int x = pos.x0 + u;
-    if (x < g.fe[2]) {
-      int i = pos.row * g.fe[2] + x;
-      b[i] = fmaf(gam, f4get(qv, u), b[i]);
+    for (int u = 0; u < 4; ++u) {
+      int i = min(i0 + u * T, g.nf - 1);
+      int row = (int)fdiv((unsigned)i, g.divfe2);
+      idx[u] = i;
+      bv[u] = b[i];
+      qv[u] = __ldg(q + row * g.P2 + (i - row * g.fe[2]));
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (i0 + u * T < g.nf) b[idx[u]] = fmaf(gam, qv[u], bv[u]);
   }
 }
 
@@ -296,9 +360,20 @@ cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
                         const Work& w, cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
-    (k_eval<T, kSeg><<<march_grid(g, g.E), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, grad,
-                                                           grad_p, dco, eco, invd, it,
-                                                           w.partials, w.counter, w.st)))
+    (k_eval<T, kSeg, false><<<march_grid(g, g.E), kBlock, 0, s>>>(
+        g, (const T*)Ip, (const T*)Im, b, nullptr, grad, grad_p, dco, eco, invd, it, 0, 0.0,
+        w.partials, w.counter, w.st)))
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const void* Im,
+                              const float* b, const float* q, float* grad_p, float* dco,
+                              float* eco, float* invd, int ls_max, double c1, const Work& w,
+                              cudaStream_t s) {
+  HYSCO_DISPATCH(dtype, T,
+    (k_eval<T, kSeg, true><<<march_grid(g, g.E), kBlock, 0, s>>>(
+        g, (const T*)Ip, (const T*)Im, b, q, nullptr, grad_p, dco, eco, invd, 0, ls_max, c1,
+        w.partials, w.counter, w.st)))
   return cudaGetLastError();
 }
 
@@ -321,7 +396,9 @@ cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const voi
 
 cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
                           const Work& w, cudaStream_t s) {
-  k_update<<<ceil_div(g.nfp >> 2, kBlock), kBlock, 0, s>>>(g, b, q, it, stats, w.st);
+  int blocks = ceil_div(g.nf, 4 * kBlock);
+  if (blocks > 148 * 8) blocks = 148 * 8;
+  k_update<<<blocks, kBlock, 0, s>>>(g, b, q, it, stats, w.st);
   return cudaGetLastError();
 }
 
