@@ -334,11 +334,13 @@ def run_ours(args):
     clk.__exit__(None, None, None)   # sampled over the timed solves, e2e and roofline launches
 
     if rank == 0:
-        # OT: shift, OT, blur; per GN step: eval, PCG (1 persistent launch, or init + 2 per
-        # iteration), 4 line-search launches (gamma = 1, then 3 batches), update
+        # OT: shift, OT, blur; per GN step: eval (a no-op when the previous gamma = 1 trial was
+        # accepted), PCG (1 persistent launch, or init + 2 per iteration), the gamma = 1 trial
+        # evaluation, one launch for the remaining halvings (a no-op when gamma = 1 is accepted),
+        # update.  Kernels replayed from the CUDA graph count as launches.
         persistent = args.precond == 0 and args.pcg_path != 1
         pcg_launches = 1 if persistent else 1 + 2 * 10 + (1 if args.precond else 0)
-        launches_per_step = 3 + gn * (1 + pcg_launches + 4 + 1)
+        launches_per_step = 3 + gn * (1 + pcg_launches + 2 + 1)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,

@@ -65,7 +65,9 @@ typedef struct {
   int32_t pcg_path;       /* Jacobi PCG: 0 = one persistent cooperative kernel per GN step when the
                              device supports it, else separate kernels (default); 1 = separate
                              kernels; 2 = persistent kernel or HYSCO_EINVAL.  Same arithmetic. */
-  int32_t reserved_;
+  int32_t no_graph;       /* 0 (default): the solve's fixed launch sequence is captured once in a
+                             CUDA graph per (images, field, stats, options) and replayed; 1: launch
+                             the kernels directly every call.  Same kernels either way. */
 } hysco_opts;
 
 /* Per-GN-iteration record written by hysco_solve when `stats` is non-NULL (device memory,

@@ -25,7 +25,7 @@ class Opts(C.Structure):
     _fields_ = [("gn_iters", C.c_int32), ("pcg_max_iters", C.c_int32),
                 ("ls_max_iters", C.c_int32), ("precond", C.c_int32), ("init", C.c_int32),
                 ("ot_blur", C.c_int32), ("pcg_rtol", C.c_double), ("armijo_c1", C.c_double),
-                ("ot_eps", C.c_double), ("pcg_path", C.c_int32), ("reserved_", C.c_int32)]
+                ("ot_eps", C.c_double), ("pcg_path", C.c_int32), ("no_graph", C.c_int32)]
 
 
 class HyscoError(RuntimeError):

@@ -33,6 +33,13 @@ struct hysco_ctx {
   float* ppart;       // its per-block partials (2 slots)
   unsigned* pbar;     // its barrier words
   bool have_lin, have_factor;
+  // CUDA graph of the last solve's launch sequence and the arguments it was captured with
+  cudaStream_t cap;
+  cudaGraphExec_t gexec;
+  const void *g_Ip, *g_Im;
+  float* g_b;
+  double* g_stats;
+  hysco_opts g_opts;
   Work work() const { return Work{partials, counter, st}; }
 };
 
@@ -66,6 +73,8 @@ void free_all(hysco_ctx* h) {
   if (h->counter) cudaFree(h->counter);
   if (h->ppart) cudaFree(h->ppart);
   if (h->pbar) cudaFree(h->pbar);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->st) cudaFree(h->st);
 }
 
@@ -122,7 +131,7 @@ void hysco_default_opts(hysco_opts* o) {
   o->armijo_c1 = 1e-4;
   o->ot_eps = 1e-3;
   o->pcg_path = 0;
-  o->reserved_ = 0;
+  o->no_graph = 0;
 }
 
 const char* hysco_strerror(int status) {
@@ -249,6 +258,11 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
     free_all(h);
     delete h;
     return HYSCO_ENOMEM;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    free_all(h);
+    delete h;
+    return HYSCO_ECUDA;
   }
   if (cudaMemset(h->counter, 0, 64 * sizeof(unsigned)) != cudaSuccess ||
       cudaMemset(h->st, 0, sizeof(DevState)) != cudaSuccess) {
@@ -382,20 +396,14 @@ int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell
   return HYSCO_OK;
 }
 
-int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
-                double* stats, hysco_stream_t stream) {
-  if (!h || !o || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout)) return HYSCO_EINVAL;
-  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
-  if (o->gn_iters < 0 || o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
-      o->ls_max_iters > kMaxTrials)
-    return HYSCO_EINVAL;
-  if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
-  if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
-  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
-  if (o->pcg_path < 0 || o->pcg_path > 2) return HYSCO_EINVAL;
-  const bool persistent = o->precond == HYSCO_PC_JACOBI && h->pgrid > 0 && o->pcg_path != 1;
-  if (o->pcg_path == 2 && !persistent) return HYSCO_EINVAL;
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// The solve's launch sequence (fixed for given arguments; every data-dependent decision is taken
+// on the device).
+int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
+                  double* stats, bool persistent, cudaStream_t s) {
   const Geo& g = h->g;
   Work w = h->work();
   if (int rc = reset_state(h, s)) return rc;
@@ -411,7 +419,7 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
                          persistent, s))
       return rc;
     // gamma = 1 as a full evaluation at b + q (its coefficients serve the next GN step when
-    // accepted), then the halvings in batches of kLsBatch, J only
+    // accepted), then the remaining halvings in batches of kLsBatch, J only
     HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, h->dco, h->eco,
                                 h->invd, o->ls_max_iters, o->armijo_c1, w, s));
     for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
@@ -419,9 +427,65 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
                                   o->ls_max_iters, o->armijo_c1, w, s));
     HYSCO_TRY(launch_update(g, b_inout, h->x, it, stats, w, s));
   }
+  return HYSCO_OK;
+}
+
+bool same_opts(const hysco_opts& a, const hysco_opts& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
+                double* stats, hysco_stream_t stream) {
+  if (!h || !o || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout)) return HYSCO_EINVAL;
+  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
+  if (o->gn_iters < 0 || o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
+      o->ls_max_iters > kMaxTrials)
+    return HYSCO_EINVAL;
+  if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
+  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
+  if (o->pcg_path < 0 || o->pcg_path > 2 || o->no_graph < 0 || o->no_graph > 1)
+    return HYSCO_EINVAL;
+  const bool persistent = o->precond == HYSCO_PC_JACOBI && h->pgrid > 0 && o->pcg_path != 1;
+  if (o->pcg_path == 2 && !persistent) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
   // the stored linearisation belongs to the iterate before the last update: invalidate it
   h->have_lin = false;
-  h->have_factor = false;
+  if (o->no_graph) {
+    int rc = enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, s);
+    h->have_factor = false;
+    return rc;
+  }
+  const bool cached = h->gexec && h->g_Ip == Ip && h->g_Im == Im && h->g_b == b_inout &&
+                      h->g_stats == stats && same_opts(h->g_opts, *o);
+  if (!cached) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = ok ? enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, h->cap) : HYSCO_ECUDA;
+    cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+    ok = ok && rc == HYSCO_OK && ec == cudaSuccess && graph != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    h->have_factor = false;
+    if (!ok) {
+      // capture unavailable: launch directly (same kernels)
+      h->gexec = nullptr;
+      cudaGetLastError();
+      int rc2 = enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, s);
+      h->have_factor = false;
+      return rc2;
+    }
+    h->g_Ip = Ip;
+    h->g_Im = Im;
+    h->g_b = b_inout;
+    h->g_stats = stats;
+    h->g_opts = *o;
+  }
+  HYSCO_TRY(cudaGraphLaunch(h->gexec, s));
   return HYSCO_OK;
 }
 

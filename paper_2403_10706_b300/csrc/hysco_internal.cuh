@@ -82,7 +82,7 @@ constexpr int kBlock = 256;   // threads per block of every kernel
 constexpr int kMaxTrials = 16;
 constexpr int kSeg = 4;       // PE nodes per thread in the column-march kernels
 constexpr int kNpt = 2;       // nodes per thread in the flat stencil kernels
-constexpr int kLsBatch = 3;   // Armijo trials per line-search launch after the first (gamma = 1)
+constexpr int kLsBatch = 9;   // Armijo trials per line-search launch after the first (gamma = 1)
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
@@ -329,7 +329,7 @@ cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const voi
                               const float* b, const float* q, float* grad_p, float* dco,
                               float* eco, float* invd, int ls_max, double c1, const Work& w,
                               cudaStream_t s);
-// trials t0 .. t0 + T - 1 with T = 1 when t0 == 0, else kLsBatch
+// trials t0 .. t0 + kLsBatch - 1 (J only); the gamma = 1 trial is launch_eval_trial
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
                               int ls_max, double c1, const Work& w, cudaStream_t s);

@@ -171,7 +171,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
 // ------------------------------------------------------------------------------------------
 // Armijo line search: J(b + gamma_t q) for gamma_t = 2^-t, t = t0 .. t0+T-1, in one pass; the
 // first accepted trial in order wins, exactly as sequential halving would pick it.  The first
-// launch tries gamma = 1 alone (accepted in most GN iterations); later launches try kLsBatch.
+// gamma = 1 trial is a full evaluation (launch_eval_trial); this kernel tries the halvings.
 // ------------------------------------------------------------------------------------------
 
 template <typename TI, int SEG, int T>

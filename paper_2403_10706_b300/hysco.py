@@ -117,13 +117,13 @@ class Hysco:
 
     def solve(self, Ip, Im, b=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10,
               precond=_lib.PC_JACOBI, init=None, ot_blur=True, pcg_rtol=0.1, armijo_c1=1e-4,
-              ot_eps=1e-3, stats=True, pcg_path=0):
+              ot_eps=1e-3, stats=True, pcg_path=0, graph=True):
         """GN-PCG solve.  init defaults to OT when b is None.  Returns (b, stats or None)."""
         if init is None:
             init = b is None
         b = self._new_fld() if b is None else b
         o = _lib.Opts(gn_iters, pcg_max_iters, ls_max_iters, int(precond), int(init),
-                      int(ot_blur), pcg_rtol, armijo_c1, ot_eps, int(pcg_path), 0)
+                      int(ot_blur), pcg_rtol, armijo_c1, ot_eps, int(pcg_path), int(not graph))
         st = (torch.full((max(gn_iters, 1), _lib.NSTATS), float("nan"), dtype=torch.float64,
                          device=self.device) if stats else None)
         _lib.check(self.lib.hysco_solve(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),

@@ -225,3 +225,24 @@ def test_pcg_step_matches_oracle(H, orc, precond, path, dims, spacing, p):
     qref, it, relres = P.pcg(Ip, Im, b, rhs.astype(np.float64), precond=precond, max_it=10,
                              rtol=0.1)
     assert rel(q, qref) <= 1e-4, (rel(q, qref), it, relres)
+
+
+def test_graph_replay_equals_direct_launches(H):
+    """The CUDA graph of a solve replays exactly the kernels a direct solve launches, and the
+    kernels are deterministic: the fields and statistics are bit-identical, also on a second
+    replay of the cached graph."""
+    pr = ph.make_pair("small")
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    Ip, Im = dev(pr.Ip), dev(pr.Im)
+    out = []
+    for graph in (False, True, True):
+        b = torch.empty(h.field_dims, dtype=torch.float32, device="cuda")
+        st = torch.empty((5, 10), dtype=torch.float64, device="cuda")
+        if out:   # same buffers for the two graph calls, so the second one replays the cache
+            b, st = out[-1][2], out[-1][3]
+        h.solve(Ip, Im, b=b, gn_iters=5, init=True, graph=graph)
+        assert h.last_status() == 0
+        bb, ss = h.solve(Ip, Im, b=b, gn_iters=5, init=True, graph=graph)
+        out.append((host(bb).copy(), host(ss).copy(), b, st))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[2][0])
+    assert np.array_equal(out[0][1], out[1][1], equal_nan=True)
