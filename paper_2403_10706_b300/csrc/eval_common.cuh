@@ -43,13 +43,14 @@ __device__ __forceinline__ void barrier(float z, float& f, float& df, float& d2f
     d2f = 0.0f;
     return;
   }
+  // phi = z^4 / q, phi' = 2 z^3 (2 - z^2) / q^2, phi'' = 2 z^2 (6 - 3 z^2 + z^4) / q^3, q = 1 - z^2
   float z2 = z * z;
   float q = (1.0f - z) * (1.0f + z);
-  float iq = __frcp_rn(q);
-  float z4 = z2 * z2;
-  f = z4 * iq;
-  df = (4.0f * z2 * z - 2.0f * z4 * z) * (iq * iq);
-  d2f = (12.0f * z2 - 6.0f * z4 + 2.0f * z4 * z2) * (iq * iq * iq);
+  float iq = __fdividef(1.0f, q);
+  float z2q = z2 * iq;
+  f = z2 * z2q;
+  df = 2.0f * z * z2q * (2.0f - z2) * iq;
+  d2f = 2.0f * z2q * fmaf(z2, z2 - 3.0f, 6.0f) * (iq * iq);
 }
 
 struct CellLin {

@@ -30,6 +30,8 @@ namespace hysco {
 // already in place: one thread promotes the stashed terms and every block returns at once (no
 // block enters the reduction, so the ticket counter is untouched).
 // TRIAL = true: the gamma = 1 Armijo trial, an evaluation at b + q.
+// Each thread keeps only the previous cell (rolling window); the in-plane neighbours along the
+// column index's fast axis A are the adjacent lanes (warp shuffle; an edge lane loads).
 template <typename TI, int SEG, bool TRIAL>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
@@ -52,6 +54,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     }
   }
   const int inner = g.inner, m = g.m;
+  const int lane = threadIdx.x & 31;
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = c < g.ncols;
   c = act ? c : g.ncols - 1;
@@ -62,14 +65,17 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   const ColNbrs nb = col_nbrs(g, c, fb);
   const int pb = col_pbase(g, c);
   const ColNbrs nq = col_nbrs_pitched(g, c, pb);
-  // field value at node kk of the column with user offset uo and pitched offset po
+  const int cA = c % g.nA;
+  const bool hasAm = cA > 0, hasAp = cA < g.nA - 1;
+  // field value at user offset uo / pitched offset po (b, or b + q in the trial)
   auto fld = [&](int uo, int po) {
     float v = __ldg(b + uo);
     return TRIAL ? fmaf(1.0f, __ldg(q + po), v) : v;
   };
 
-  // field nodes k0-1 .. k0+SEG (clamped to [0, m]) and the in-plane neighbours of k0 .. k0+SEG-1
-  float bw[SEG + 2], bAm[SEG], bAp[SEG], bBm[SEG], bBp[SEG];
+  // column nodes k0-1 .. k0+SEG (clamped to [0, m]); B neighbours of k0 .. k0+SEG-1 by loads,
+  // A neighbours from the lanes beside (edge lanes load)
+  float bw[SEG + 2], bBm[SEG], bBp[SEG], eAm[SEG], eAp[SEG];
 #pragma unroll
   for (int j = 0; j < SEG + 2; ++j) {
     int kk = min(max(k0 - 1 + j, 0), m);
@@ -79,8 +85,10 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   for (int j = 0; j < SEG; ++j) {
     int kk = min(k0 + j, m);
     int o = kk * inner, op = kk * g.psP;
-    bAm[j] = fld(nb.Am + o, nq.Am + op); bAp[j] = fld(nb.Ap + o, nq.Ap + op);
-    bBm[j] = fld(nb.Bm + o, nq.Bm + op); bBp[j] = fld(nb.Bp + o, nq.Bp + op);
+    bBm[j] = fld(nb.Bm + o, nq.Bm + op);
+    bBp[j] = fld(nb.Bp + o, nq.Bp + op);
+    eAm[j] = (lane == 0 && hasAm) ? fld(nb.Am + o, nq.Am + op) : 0.f;
+    eAp[j] = (lane == 31 && hasAp) ? fld(nb.Ap + o, nq.Ap + op) : 0.f;
   }
   // grad^T q with the gradient at b (trial only), loaded before this thread overwrites it
   float accGQ = 0.f;
@@ -92,45 +100,49 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
       accGQ += (act && k0 + j <= m) ? gv * qv : 0.f;
     }
   }
-  // cells k0-1 .. k0+SEG-1; out-of-column cells contribute nothing
-  float cr[SEG + 1], cjl[SEG + 1], cjr[SEG + 1], cdphi[SEG + 1], cpsi[SEG + 1], cphi[SEG + 1];
-#pragma unroll
-  for (int j = 0; j <= SEG; ++j) {
-    int jc = k0 - 1 + j;
-    bool cv = jc >= 0 && jc < m;
-    CellLin cl = cell_lin(Ipc, Imc, inner, m, jc, bw[j], bw[j + 1], g.half_beta);
-    cr[j] = cv ? cl.r : 0.f;
-    cjl[j] = cv ? cl.jl : 0.f;
-    cjr[j] = cv ? cl.jr : 0.f;
-    cdphi[j] = cv ? cl.dphi : 0.f;
-    cpsi[j] = cv ? cl.psi : 0.f;
-    cphi[j] = cv ? cl.phi : 0.f;
+  // the cell left of node k0 (cell k0 - 1)
+  float pr, pjr, pdphi, ppsi;
+  {
+    CellLin cl = cell_lin(Ipc, Imc, inner, m, k0 - 1, bw[0], bw[1], g.half_beta);
+    bool cv = k0 >= 1;
+    pr = cv ? cl.r : 0.f; pjr = cv ? cl.jr : 0.f;
+    pdphi = cv ? cl.dphi : 0.f; ppsi = cv ? cl.psi : 0.f;
   }
   float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
-    int k = k0 + j;
-    if (!act || k > m) continue;
-    float bk = bw[j + 1], bn = bw[j + 2];
-    float lap = (bk - bw[j]) + (bk - bn) + g.wA * ((bk - bAm[j]) + (bk - bAp[j])) +
-                g.wB * ((bk - bBm[j]) + (bk - bBp[j]));
-    float dPE = bn - bk, dA = bAp[j] - bk, dB = bBp[j] - bk;
-    accS += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
-    accD += cr[j + 1] * cr[j + 1];
-    accP += cphi[j + 1];
-    float gk = g.vol * (cjr[j] * cr[j] + cjl[j + 1] * cr[j + 1] + g.alpha * lap +
-                        g.half_beta * (cdphi[j] - cdphi[j + 1]));
-    float dk = cjr[j] * cjr[j] + cjl[j + 1] * cjl[j + 1] + cpsi[j] + cpsi[j + 1];
-    float ek = cjl[j + 1] * cjr[j + 1] - cpsi[j + 1];
-    float npe = (float)((k > 0) + (k < m));
-    float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
-    const int pi = pb + k * g.psP;   // solver arrays are pitched
-    if (grad) grad[fb + k * inner] = gk;
-    if (grad_p) grad_p[pi] = gk;
-    dco[pi] = dk;
-    eco[pi] = ek;
-    invd[pi] = diag > 0.f ? __frcp_rn(diag) : 1.0f;
-    accG += gk * gk;
+    const int k = k0 + j;
+    // the cell right of node k (cell k)
+    CellLin cl = cell_lin(Ipc, Imc, inner, m, k, bw[j + 1], bw[j + 2], g.half_beta);
+    const bool cv = k < m;
+    const float cr = cv ? cl.r : 0.f, cjl = cv ? cl.jl : 0.f, cjr = cv ? cl.jr : 0.f;
+    const float cdphi = cv ? cl.dphi : 0.f, cpsi = cv ? cl.psi : 0.f, cphi = cv ? cl.phi : 0.f;
+    const float bk = bw[j + 1], bn = bw[j + 2];
+    const float fromL = __shfl_up_sync(0xffffffffu, bk, 1);
+    const float fromR = __shfl_down_sync(0xffffffffu, bk, 1);
+    const float bAm = hasAm ? (lane > 0 ? fromL : eAm[j]) : bk;
+    const float bAp = hasAp ? (lane < 31 ? fromR : eAp[j]) : bk;
+    if (act && k <= m) {
+      float lap = (bk - bw[j]) + (bk - bn) + g.wA * ((bk - bAm) + (bk - bAp)) +
+                  g.wB * ((bk - bBm[j]) + (bk - bBp[j]));
+      float dPE = bn - bk, dA = bAp - bk, dB = bBp[j] - bk;
+      accS += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
+      accD += cr * cr;
+      accP += cphi;
+      float gk = g.vol * (pjr * pr + cjl * cr + g.alpha * lap + g.half_beta * (pdphi - cdphi));
+      float dk = pjr * pjr + cjl * cjl + ppsi + cpsi;
+      float ek = cjl * cjr - cpsi;
+      float npe = (float)((k > 0) + (k < m));
+      float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
+      const int pi = pb + k * g.psP;   // solver arrays are pitched
+      if (grad) grad[fb + k * inner] = gk;
+      if (grad_p) grad_p[pi] = gk;
+      dco[pi] = dk;
+      eco[pi] = ek;
+      invd[pi] = diag > 0.f ? __fdividef(1.0f, diag) : 1.0f;
+      accG += gk * gk;
+    }
+    pr = cr; pjr = cjr; pdphi = cdphi; ppsi = cpsi;
   }
   float v[5] = {accD, accS, accP, accG, accGQ};
   double tot[5];
