@@ -44,7 +44,8 @@ def parse():
     ap.add_argument("--workload", default="3t", choices=list(GN_ITERS))
     ap.add_argument("--precond", type=int, default=0)
     ap.add_argument("--pcg-path", type=int, default=0,
-                    help="0 auto (persistent PCG kernel when possible), 1 separate kernels")
+                    help="0 auto (= 2 when possible), 1 separate kernels, 2 persistent kernel, "
+                         "3 persistent one-barrier-per-iteration kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -310,15 +311,26 @@ def run_ours(args):
         torch.cuda.synchronize()
         return statistics.mean(e0.elapsed_time(e1) for e0, e1 in evs)
 
+    # The one-barrier form (--pcg-path 3) moves per node: phase 0 reads grad, 1/diag, d, e and
+    # writes r, w (24); phase 1 reads r, w, 1/diag, d, e and writes x, p, q, r, w (40); phases
+    # 2..9 read r, w, q, 1/diag, p, x, d, e and write x, p, q, r, w (52); the last phase skips
+    # the stencil: reads r, w, q, 1/diag, p, x and writes x, p, q, r (40).
     pcg_iters = 10
-    pcg_bytes = nfld * (20 + 20 + 28 + (pcg_iters - 1) * (28 + 32))
-    pcg_ms = time_launches(lambda: h.pcg(rhs, max_iters=pcg_iters, rtol=0.0, out=q))
+    fused = args.pcg_path == 3
+    if fused:
+        pcg_bytes = nfld * (24 + 40 + (pcg_iters - 2) * 52 + 40)
+    else:
+        pcg_bytes = nfld * (20 + 20 + 28 + (pcg_iters - 1) * (28 + 32))
+    pcg_ms = time_launches(lambda: h.pcg(rhs, max_iters=pcg_iters, rtol=0.0, out=q,
+                                         pcg_path=args.pcg_path))
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9
+    kname = {1: "k_hv + k_pcg_update_jacobi (separate)", 3: "k_pcg_fused<jacobi>"}.get(
+        args.pcg_path, "k_pcg_persistent<jacobi>")
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": recorded_traffic("k_pcg_persistent_3t.md", PCG_SOURCES)
-            if args.workload == "3t" else None,
-            "kernel": "k_pcg_persistent<jacobi>",
+            if args.workload == "3t" and args.pcg_path in (0, 2) else None,
+            "kernel": kname,
             "peak_source": peak_src, "alg_bytes_per_launch": pcg_bytes, "launch_ms": pcg_ms,
             "note": "10 PCG iterations per launch; the 86 MB working set is L2-resident within "
                     "a launch, so achieved algorithmic bandwidth may exceed the HBM copy peak"}
@@ -338,7 +350,7 @@ def run_ours(args):
         # accepted), PCG (1 persistent launch, or init + 2 per iteration), the gamma = 1 trial
         # evaluation, one launch for the remaining halvings (a no-op when gamma = 1 is accepted),
         # update.  Kernels replayed from the CUDA graph count as launches.
-        persistent = args.precond == 0 and args.pcg_path != 1
+        persistent = args.precond == 0 and args.pcg_path != 1   # 0, 2 and 3 are one launch
         pcg_launches = 1 if persistent else 1 + 2 * 10 + (1 if args.precond else 0)
         launches_per_step = 3 + gn * (1 + pcg_launches + 2 + 1)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,

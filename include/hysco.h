@@ -62,9 +62,14 @@ typedef struct {
   double pcg_rtol;        /* stop PCG when ||r|| / ||r0|| < pcg_rtol (paper: 0.1) */
   double armijo_c1;       /* sufficient-decrease constant (default 1e-4) */
   double ot_eps;          /* OT positivity shift factor (default 1e-3) */
-  int32_t pcg_path;       /* Jacobi PCG: 0 = one persistent cooperative kernel per GN step when the
-                             device supports it, else separate kernels (default); 1 = separate
-                             kernels; 2 = persistent kernel or HYSCO_EINVAL.  Same arithmetic. */
+  int32_t pcg_path;       /* Jacobi PCG: 0 = the fastest form the device supports (default: 2,
+                             else 1); 1 = separate kernels per phase; 2 = one persistent
+                             cooperative kernel per GN step with two device-wide barriers per PCG
+                             iteration, or HYSCO_EINVAL; 3 = one persistent kernel with one
+                             barrier per iteration (the direction product p.Hp taken from its
+                             bilinear expansion in H z, see k_pcg_persistent.cu), or HYSCO_EINVAL.
+                             1 and 2 have the same arithmetic; 3 gives the same iterates in exact
+                             arithmetic.  The column preconditioner always uses 1. */
   int32_t no_graph;       /* 0 (default): the solve's fixed launch sequence is captured once in a
                              CUDA graph per (images, field, stats, options) and replayed; 1: launch
                              the kernels directly every call.  Same kernels either way. */

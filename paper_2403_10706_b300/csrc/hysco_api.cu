@@ -25,13 +25,13 @@ struct hysco_ctx {
   long long nimg, nfld;
   int device;
   // field-shaped workspace
-  float *grad, *dco, *eco, *invd, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp;
+  float *grad, *dco, *eco, *invd, *x, *r, *z, *p0, *p1, *Hp, *invD, *lco, *tmp, *q0, *q1;
   float* partials;
   unsigned* counter;
   DevState* st;
   int pgrid;          // persistent PCG grid (0: not available on this device)
-  float* ppart;       // its per-block partials (2 slots)
-  unsigned* pbar;     // its barrier words
+  int fgrid;          // one-barrier persistent PCG grid (0: not available)
+  unsigned* psync;    // their barrier / reduction words
   bool have_lin, have_factor;
   // CUDA graph of the last solve's launch sequence and the arguments it was captured with
   cudaStream_t cap;
@@ -66,13 +66,12 @@ int check_f32(const void* p) { return (p && aligned(p, 4)) ? HYSCO_OK : HYSCO_EI
 
 void free_all(hysco_ctx* h) {
   float* bufs[] = {h->grad, h->dco, h->eco, h->invd, h->x, h->r, h->z, h->p0, h->p1, h->Hp,
-                   h->invD, h->lco, h->tmp};
+                   h->invD, h->lco, h->tmp, h->q0, h->q1};
   for (float* b : bufs)
     if (b) cudaFree(b);
   if (h->partials) cudaFree(h->partials);
   if (h->counter) cudaFree(h->counter);
-  if (h->ppart) cudaFree(h->ppart);
-  if (h->pbar) cudaFree(h->pbar);
+  if (h->psync) cudaFree(h->psync);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->st) cudaFree(h->st);
@@ -82,14 +81,40 @@ int reset_state(hysco_ctx* h, cudaStream_t s) {
   return check_cuda(cudaMemsetAsync(h->st, 0, sizeof(DevState), s));
 }
 
+// How a Jacobi or column PCG runs: separate kernels per phase, one persistent kernel with two
+// barriers per iteration, or one persistent kernel with one barrier per iteration.
+enum PcgMode { kPcgSeparate = 0, kPcgPersistent = 1, kPcgFused = 2 };
+
+// pcg_path (hysco_opts) -> mode; HYSCO_EINVAL when the requested kernel cannot run here
+int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
+  const bool jac = precond == HYSCO_PC_JACOBI;
+  switch (path) {
+    case 0:   // measured fastest on B300 at 3T and 7T sizes: the two-barrier persistent kernel
+      *mode = jac && h->pgrid > 0 ? kPcgPersistent : kPcgSeparate;
+      return HYSCO_OK;
+    case 1: *mode = kPcgSeparate; return HYSCO_OK;
+    case 2: *mode = kPcgPersistent; return jac && h->pgrid > 0 ? HYSCO_OK : HYSCO_EINVAL;
+    case 3: *mode = kPcgFused; return jac && h->fgrid > 0 ? HYSCO_OK : HYSCO_EINVAL;
+    default: return HYSCO_EINVAL;
+  }
+}
+
 // PCG for H q = sign * g about the handle's linearisation (Sec. 2.3.1); q is written to x.
 int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int max_it,
-            double rtol, bool persistent, cudaStream_t s) {
+            double rtol, PcgMode mode, cudaStream_t s) {
   const Geo& geo = h->g;
   Work w = h->work();
-  if (persistent) {
+  if (mode == kPcgFused) {
+    float* const rb[2] = {h->r, h->z};
+    float* const wb[2] = {h->Hp, h->p1};
+    float* const qb[2] = {h->q0, h->q1};
+    HYSCO_TRY(launch_pcg_fused(geo, h->fgrid, g, sign, x, h->p0, rb, wb, qb, h->dco, h->eco,
+                               h->invd, h->psync, max_it, rtol, h->st, s));
+    return HYSCO_OK;
+  }
+  if (mode == kPcgPersistent) {
     HYSCO_TRY(launch_pcg_persistent(geo, h->pgrid, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
-                                    h->dco, h->eco, h->invd, h->ppart, h->pbar, max_it, rtol,
+                                    h->dco, h->eco, h->invd, h->psync, max_it, rtol,
                                     h->st, s));
     return HYSCO_OK;
   }
@@ -231,7 +256,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   // entry starts, and stays, at zero
   size_t fbytes = (size_t)(nfp > nfld ? nfp : nfld) * sizeof(float);
   float** bufs[] = {&h->grad, &h->dco, &h->eco, &h->invd, &h->x, &h->r, &h->z, &h->p0, &h->p1,
-                    &h->Hp, &h->invD, &h->lco, &h->tmp};
+                    &h->Hp, &h->invD, &h->lco, &h->tmp, &h->q0, &h->q1};
   for (float** b : bufs) {
     if (cudaMalloc((void**)b, fbytes) != cudaSuccess || cudaMemset(*b, 0, fbytes) != cudaSuccess) {
       free_all(h);
@@ -252,9 +277,11 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
     return HYSCO_ENOMEM;
   }
   h->pgrid = pcg_persistent_grid(h->device, pe_dim);
-  if (h->pgrid > 0 &&
-      (cudaMalloc((void**)&h->ppart, 4ull * h->pgrid * sizeof(float)) != cudaSuccess ||
-       cudaMalloc((void**)&h->pbar, 64 * sizeof(unsigned)) != cudaSuccess)) {
+  h->fgrid = pcg_fused_grid(h->device, pe_dim);
+  const int sync_grid = h->pgrid > h->fgrid ? h->pgrid : h->fgrid;
+  if (sync_grid > 0 &&
+      cudaMalloc((void**)&h->psync, pcg_sync_words(sync_grid) * sizeof(unsigned)) !=
+          cudaSuccess) {
     free_all(h);
     delete h;
     return HYSCO_ENOMEM;
@@ -367,15 +394,14 @@ int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters,
   if (!h || check_f32(rhs) || check_f32(q)) return HYSCO_EINVAL;
   if (precond != HYSCO_PC_JACOBI && precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
   if (precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
-  if (max_iters < 1 || max_iters > 64 || !(rtol >= 0.0) || pcg_path < 0 || pcg_path > 2)
-    return HYSCO_EINVAL;
+  if (max_iters < 1 || max_iters > 64 || !(rtol >= 0.0)) return HYSCO_EINVAL;
+  PcgMode mode;
+  if (pcg_mode(h, precond, pcg_path, &mode)) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
-  const bool persistent = precond == HYSCO_PC_JACOBI && h->pgrid > 0 && pcg_path != 1;
-  if (pcg_path == 2 && !persistent) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = reset_state(h, s)) return rc;
   HYSCO_TRY(launch_to_pitched(h->g, rhs, h->tmp, s));
-  if (int rc = run_pcg(h, h->tmp, 1.0f, h->x, precond, max_iters, rtol, persistent, s)) return rc;
+  if (int rc = run_pcg(h, h->tmp, 1.0f, h->x, precond, max_iters, rtol, mode, s)) return rc;
   HYSCO_TRY(launch_from_pitched(h->g, h->x, q, s));
   return HYSCO_OK;
 }
@@ -403,7 +429,7 @@ namespace {
 // The solve's launch sequence (fixed for given arguments; every data-dependent decision is taken
 // on the device).
 int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
-                  double* stats, bool persistent, cudaStream_t s) {
+                  double* stats, PcgMode mode, cudaStream_t s) {
   const Geo& g = h->g;
   Work w = h->work();
   if (int rc = reset_state(h, s)) return rc;
@@ -416,7 +442,7 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
                           it, w, s));
     h->have_factor = false;
     if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
-                         persistent, s))
+                         mode, s))
       return rc;
     // gamma = 1 as a full evaluation at b + q (its coefficients serve the next GN step when
     // accepted), then the remaining halvings in batches of kLsBatch, J only
@@ -446,15 +472,14 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
   if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
   if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
   if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
-  if (o->pcg_path < 0 || o->pcg_path > 2 || o->no_graph < 0 || o->no_graph > 1)
-    return HYSCO_EINVAL;
-  const bool persistent = o->precond == HYSCO_PC_JACOBI && h->pgrid > 0 && o->pcg_path != 1;
-  if (o->pcg_path == 2 && !persistent) return HYSCO_EINVAL;
+  if (o->no_graph < 0 || o->no_graph > 1) return HYSCO_EINVAL;
+  PcgMode mode;
+  if (pcg_mode(h, o->precond, o->pcg_path, &mode)) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
   // the stored linearisation belongs to the iterate before the last update: invalidate it
   h->have_lin = false;
   if (o->no_graph) {
-    int rc = enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, s);
+    int rc = enqueue_solve(h, Ip, Im, b_inout, o, stats, mode, s);
     h->have_factor = false;
     return rc;
   }
@@ -465,7 +490,7 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
     h->gexec = nullptr;
     cudaGraph_t graph = nullptr;
     bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    int rc = ok ? enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, h->cap) : HYSCO_ECUDA;
+    int rc = ok ? enqueue_solve(h, Ip, Im, b_inout, o, stats, mode, h->cap) : HYSCO_ECUDA;
     cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
     ok = ok && rc == HYSCO_OK && ec == cudaSuccess && graph != nullptr;
     if (ok) ok = cudaGraphInstantiate(&h->gexec, graph, 0) == cudaSuccess;
@@ -475,7 +500,7 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
       // capture unavailable: launch directly (same kernels)
       h->gexec = nullptr;
       cudaGetLastError();
-      int rc2 = enqueue_solve(h, Ip, Im, b_inout, o, stats, persistent, s);
+      int rc2 = enqueue_solve(h, Ip, Im, b_inout, o, stats, mode, s);
       h->have_factor = false;
       return rc2;
     }

@@ -364,13 +364,24 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const float* lco, int first, double rtol, float sign,
                              const Work& w, cudaStream_t s);
 
-// k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible)
+// k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible), and the number of
+// 32-bit barrier/reduction words a launch of that grid needs
 int pcg_persistent_grid(int device, int pe_axis);
+constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arrival counter's line)
+constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused reduction)
+inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid; }
 cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
                                   float* x, float* r, float* z, float* p0, float* p1, float* Hp,
                                   const float* dco, const float* eco, const float* invd,
-                                  float* part, unsigned* bar, int max_it, double rtol,
+                                  unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s);
+// the one-barrier-per-iteration form of the same PCG (r, w, q alternate between two buffers)
+int pcg_fused_grid(int device, int pe_axis);
+cudaError_t launch_pcg_fused(const Geo& g, int grid, const float* grad, float rhs_sign, float* x,
+                             float* p, float* const rb[2], float* const wb[2], float* const qb[2],
+                             const float* dco, const float* eco, const float* invd,
+                             unsigned* sync, int max_it, double rtol, DevState* st,
+                             cudaStream_t s);
 
 // k_ot.cu
 cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void* Im,

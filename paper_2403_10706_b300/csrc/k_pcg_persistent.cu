@@ -8,18 +8,21 @@
 //   iter   A: w = H z, p = z + beta p, Hp = w + beta Hp (p = z, Hp = w at i = 0), partial p.Hp
 //                                                                                     | barrier
 //          B: x += alpha p, r -= alpha Hp, z = r / diag  partials r.r, r.z  | barrier
-// After each barrier every block adds all blocks' partials itself, in the same fixed order and in
-// double-float (compensated single precision), so every block takes the same scalar decisions
-// (alpha, beta, the relative-residual stop, p.Hp <= 0) without another round trip.  H p is kept by the recurrence
-// H p = H z + beta H p_old (H is linear), so the stencil reads one array (z) and p, Hp are
-// updated in place.  The arithmetic per node is that of the separate kernels in k_pcg.cu.
+// Each barrier is also the reduction of that phase's dot products: a block publishes its partial
+// sums as 64-bit words that carry the barrier's generation next to the value, and every block
+// waits until it has seen every block's words of that generation and adds them itself, in the
+// same fixed order and in double-float (compensated single precision), so every block takes the
+// same scalar decisions (alpha, beta, the relative-residual stop, p.Hp <= 0) without another
+// round trip.  H p is kept by the recurrence H p = H z + beta H p_old (H is linear), so the
+// stencil reads one array (z) and p, Hp are updated in place.  The arithmetic per node is that
+// of the separate kernels in k_pcg.cu.
 //
 // Memory: arrays written inside the launch (x, r, z, p, Hp) are read with ordinary (coherent)
 // loads after a barrier, never through the read-only path; d, e, 1/diag and grad are read-only.
-// Barriers spin with a bounded clock budget: on expiry a block records an error in the device
-// state and returns; every other block then also times out at its next barrier, so the launch
-// always ends.
-#include <cuda/atomic>
+// A block releases its phase's writes with a fence before it publishes its words; a reader
+// fences after it has seen them.  Barriers spin with a bounded clock budget: on expiry a block
+// records an error in the device state and returns; every other block then also times out at
+// its next barrier, so the launch always ends.
 
 #include "hysco_internal.cuh"
 
@@ -40,70 +43,73 @@ struct PcgArgs {
   const float* dco;
   const float* eco;
   const float* invd;
-  float* part;           // 2 slots x gridDim.x x 2 floats
-  unsigned* bar;         // [0] arrival count, [1] generation; zeroed before every launch
+  unsigned* sync;        // arrival counter + 2 slots of partial sums; zeroed before every launch
   DevState* st;
   int max_it;
   double rtol;
 };
 
-// Device-wide barrier.  Returns false (in every thread of the block) when the spin budget ran
-// out; the block must then stop.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    cuda::atomic_ref<unsigned, cuda::thread_scope_device> count(bar[0]), g(bar[1]);
-    unsigned arrived = count.fetch_add(1u, cuda::memory_order_acq_rel);
-    if (arrived == gridDim.x - 1) {
-      count.store(0u, cuda::memory_order_relaxed);
-      g.store(gen + 1, cuda::memory_order_release);
-    } else {
-      long long t0 = clock64();
-      while (g.load(cuda::memory_order_acquire) == gen) {
-        if (clock64() - t0 > kBarrierSpinCycles) { ok = 0; break; }
-      }
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier fused with the sum of K floats over all threads of the grid.  Every thread
+// of every block calls it with its own values v and the barrier's generation gen (1, 2, ... within
+// a launch).  Layout of `sync`: an arrival counter (its own 128-byte line), then two slots of
+// gridDim.x x kSyncMaxK floats.  Block b stores its block sums at slot gen & 1, b * K, then adds one to
+// the counter with release semantics; the barrier of generation gen is complete when the counter
+// reaches gen * gridDim.x.  A block can overwrite a slot only two generations later, by which
+// time every block has read it.  Warp 0 then reads all blocks' sums through L2 and adds them in
+// a fixed order (lane l takes blocks l, l + 32, ... in turn, then a fixed shuffle tree), in
+// double-float.  On return v holds the grid totals, identical in every thread of every block.
+// Returns false in every thread of the block when the spin budget ran out.
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
+                                               float* shf, df32* shd) {
+  static_assert(K >= 1 && K <= kSyncMaxK, "grid_allreduce: K exceeds the slot width");
+  const int tid = threadIdx.x, nb = gridDim.x;
+  unsigned* counter = sync;
+  float* slot = reinterpret_cast<float*>(sync + kSyncHeader) + (size_t)(gen & 1u) * nb * kSyncMaxK;
+  __shared__ int ok_sh;
+  block_sum<K, float>(v, shf);   // its barrier orders this block's phase writes before the release
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) __stcg(slot + blockIdx.x * K + i, v[i]);
+    red_release_add(counter, 1u);
+    const unsigned target = gen * (unsigned)nb;
+    const long long t0 = clock64();
+    int ok = 1;
+    while ((int)(ld_acquire(counter) - target) < 0) {
+      if (clock64() - t0 > kBarrierSpinCycles) { ok = 0; break; }
     }
+    ok_sh = ok;
   }
   __syncthreads();
-  gen += 1;
-  return ok != 0;
-}
-
-// block sum of K floats, result broadcast through shared memory to every thread
-template <int K>
-__device__ __forceinline__ void block_reduce_f(float (&v)[K], float* sh) {
-  block_sum<K, float>(v, sh);
-  __syncthreads();
-  if (threadIdx.x == 0)
+  if (!ok_sh) return false;
+  if (tid < 32) {
+    df32 acc[K];
 #pragma unroll
-    for (int i = 0; i < K; ++i) sh[i] = v[i];
-  __syncthreads();
+    for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
+    for (int b = tid; b < nb; b += 32)
 #pragma unroll
-  for (int i = 0; i < K; ++i) v[i] = sh[i];
-  __syncthreads();
-}
-
-// every block: sum of the K-float partials of all blocks in a fixed order (double-float), so
-// that every block obtains the same totals
-template <int K>
-__device__ __forceinline__ void all_partials(const float* part, float (&tot)[K], df32* sh) {
-  df32 acc[K];
+      for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{__ldcg(slot + b * K + i), 0.f});
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
-  for (int b = linear_tid(); b < (int)gridDim.x; b += block_threads())
+    for (int i = 0; i < K; ++i)
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{part[b * K + i], 0.f});
-  block_sum_df<K>(acc, sh);
-  __syncthreads();
-  if (linear_tid() == 0)
+      for (int off = 16; off > 0; off >>= 1) acc[i] = df_add(acc[i], df_shfl_down(acc[i], off));
+    if (tid == 0)
 #pragma unroll
-    for (int i = 0; i < K; ++i) sh[i] = acc[i];
+      for (int i = 0; i < K; ++i) shd[i] = acc[i];
+  }
   __syncthreads();
 #pragma unroll
-  for (int i = 0; i < K; ++i) tot[i] = sh[i].hi + sh[i].lo;
-  __syncthreads();
+  for (int i = 0; i < K; ++i) v[i] = shd[i].hi + shd[i].lo;
+  return true;
 }
 
 template <int P>
@@ -117,9 +123,9 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int n4 = g.nfp >> 2;   // float4 groups of the pitched field (padding is zero)
   unsigned gen = 0;
-  int slot = 0;
-  auto part = [&](int s) { return a.part + s * gridDim.x * 2; };
+  auto timed_out = [&]() { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } };
 
+  float tot[2];
   // ---- init --------------------------------------------------------------------------------
   {
     float arr = 0.f, arz = 0.f;
@@ -146,15 +152,10 @@ k_pcg_persistent(Geo g, PcgArgs a) {
         }
       }
     }
-    float v[2] = {arr, arz};
-    block_reduce_f<2>(v, shf);
-    if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v[0]; part(slot)[blockIdx.x * 2 + 1] = v[1]; }
+    tot[0] = arr; tot[1] = arz;
   }
-  if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
+  if (!grid_allreduce<2>(tot, a.sync, ++gen, shf, shd)) { timed_out(); return; }
   // scalars in single precision (the sums themselves are double-float accurate)
-  float tot[2];
-  all_partials<2>(part(slot), tot, shd);
-  slot ^= 1;
   const float rr0 = tot[0];
   float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
   bool done = !(rr0 > 0.f);
@@ -168,15 +169,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     float acc = 0.f;
     for (int t = gtid; t < n4; t += T) acc += hv_group<P, true>(g, t, a.z, pv_, a.Hp, a.dco, a.eco, fb, first);
     {
-      float v[1] = {acc};
-      block_reduce_f<1>(v, shf);
-      if (threadIdx.x == 0) part(slot)[blockIdx.x] = v[0];
-    }
-    if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
-    {
-      float t1[1];
-      all_partials<1>(part(slot), t1, shd);
-      slot ^= 1;
+      float t1[1] = {acc};
+      if (!grid_allreduce<1>(t1, a.sync, ++gen, shf, shd)) { timed_out(); return; }
       if (!(t1[0] > 0.f)) { done = true; break; }
       const float al = rho / t1[0];
       // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
@@ -210,13 +204,9 @@ k_pcg_persistent(Geo g, PcgArgs a) {
           }
         }
       }
-      float v2[2] = {arr, arz};
-      block_reduce_f<2>(v2, shf);
-      if (threadIdx.x == 0) { part(slot)[blockIdx.x * 2] = v2[0]; part(slot)[blockIdx.x * 2 + 1] = v2[1]; }
+      tot[0] = arr; tot[1] = arz;
     }
-    if (!grid_barrier(a.bar, gen)) { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } return; }
-    all_partials<2>(part(slot), tot, shd);
-    slot ^= 1;
+    if (!grid_allreduce<2>(tot, a.sync, ++gen, shf, shd)) { timed_out(); return; }
     it = i + 1;
     relres = sqrtf(tot[0]) / sqrtf(rr0);
     if (relres < (float)a.rtol) {
@@ -225,6 +215,244 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       beta = tot[1] / rho;
       rho = tot[1];
     }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rr0 = rr0;
+    st->rho = rho;
+    st->beta_cg = beta;
+    st->pcg_iter = it;
+    st->relres = relres;
+    st->pcg_done = 1;
+  }
+}
+
+// ==========================================================================================
+// One-barrier-per-iteration form of the same Jacobi PCG (same iterates in exact arithmetic).
+//
+// With w = H z and the direction product q = H p kept by q = w + beta q_old, iteration k's
+// updates of p, q, x, r, z need only alpha_{k-1} and beta_{k-2}, and the next H z_k needs z_k at
+// the stencil neighbours, which every thread recomputes from r_{k-1}, w_{k-1}, q_{k-2} and 1/diag
+// there with the owner's own operations (bit-identical values).  So one phase per iteration does
+//   p_{k-1} = z_{k-1} + beta_{k-2} p_{k-2}      q_{k-1} = w_{k-1} + beta_{k-2} q_{k-2}
+//   x_k = x_{k-1} + alpha_{k-1} p_{k-1}         r_k = r_{k-1} - alpha_{k-1} q_{k-1}
+//   z_k = r_k / diag                            w_k = H z_k
+// and one fused barrier + reduction yields r.z, r.r and the pieces of the next denominator,
+//   p_k.q_k = z_k.w_k + beta_{k-1} (z_k.q_{k-1} + p_{k-1}.w_k) + beta_{k-1}^2 p_{k-1}.q_{k-1},
+// the bilinear expansion of p_k.H p_k.  Vectors read at neighbours while their owners write the
+// next iterate (r, w, q) alternate between two buffers; p and x are updated in place.  Phase 0
+// forms r_0 = rhs, z_0, w_0 = H z_0; the last phase (k = max_it) skips the stencil.
+// ==========================================================================================
+
+struct FusedArgs {
+  const float* grad;   // right-hand side is rhs_sign * grad
+  float rhs_sign;
+  float* x;
+  float* p;
+  float* rb[2];
+  float* wb[2];
+  float* qb[2];
+  const float* dco;
+  const float* eco;
+  const float* invd;
+  unsigned* sync;
+  DevState* st;
+  int max_it;
+  double rtol;
+};
+
+// w = H z at the four nodes of group t from z at the group, its axis-0/axis-1 neighbour groups and
+// the innermost-axis neighbours zl (node 4t - 1) and zr (node 4t + 4); padding nodes give 0.
+template <int P>
+__device__ __forceinline__ void hz_group(const Geo& g, const GroupPos& q, int t, float4 zc,
+                                         float4 z1m, float4 z1p, float4 z0m, float4 z0p, float zl,
+                                         float zr, const float* __restrict__ dco,
+                                         const float* __restrict__ eco, float (&w)[4]) {
+  const int n = 4 * t, fe2 = g.fe[2];
+  const int s1 = g.G4, s0 = g.fe[1] * g.G4;
+  const float4 d4 = __ldg(reinterpret_cast<const float4*>(dco) + t);
+  const float4 e4 = __ldg(reinterpret_cast<const float4*>(eco) + t);
+  float4 em4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float el = 0.f;
+  if (P == 0 && q.i0 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s0);
+  if (P == 1 && q.i1 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s1);
+  if (P == 2 && q.x0 > 0) el = __ldg(eco + n - 1);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int x = q.x0 + u;
+    const float zk = f4get(zc, u);
+    const float a2m = x > 0 ? (u == 0 ? zl : f4get(zc, u - 1)) : zk;
+    const float a2p = x < fe2 - 1 ? (u == 3 ? zr : f4get(zc, u + 1)) : zk;
+    const float a1m = f4get(z1m, u), a1p = f4get(z1p, u);
+    const float a0m = f4get(z0m, u), a0p = f4get(z0p, u);
+    const float lap = g.w[0] * ((zk - a0m) + (zk - a0p)) + g.w[1] * ((zk - a1m) + (zk - a1p)) +
+                      g.w[2] * ((zk - a2m) + (zk - a2p));
+    float elo = P == 2 ? (u == 0 ? el : f4get(e4, u - 1)) : f4get(em4, u);
+    if (P == 2 && x == 0) elo = 0.f;
+    const float zlo = P == 0 ? a0m : (P == 1 ? a1m : a2m);
+    const float zhi = P == 0 ? a0p : (P == 1 ? a1p : a2p);
+    const float v = g.vol * (elo * zlo + f4get(d4, u) * zk + f4get(e4, u) * zhi + g.alpha * lap);
+    w[u] = x < fe2 ? v : 0.f;
+  }
+}
+
+// z_k at one node from the previous iterate (the owner's arithmetic, in this order)
+__device__ __forceinline__ float z_next(float r, float w, float q, float id, float al, float be) {
+  return id * fmaf(-al, fmaf(be, q, w), r);
+}
+__device__ __forceinline__ float4 z_next4(const float* r, const float* w, const float* q,
+                                          const float* __restrict__ invd, int s, float al,
+                                          float be, bool has_q) {
+  const float4 rv = reinterpret_cast<const float4*>(r)[s];
+  const float4 wv = reinterpret_cast<const float4*>(w)[s];
+  const float4 qv = has_q ? reinterpret_cast<const float4*>(q)[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float4 iv = __ldg(reinterpret_cast<const float4*>(invd) + s);
+  return make_float4(z_next(rv.x, wv.x, qv.x, iv.x, al, be), z_next(rv.y, wv.y, qv.y, iv.y, al, be),
+                     z_next(rv.z, wv.z, qv.z, iv.z, al, be), z_next(rv.w, wv.w, qv.w, iv.w, al, be));
+}
+__device__ __forceinline__ float4 z_init4(const float* __restrict__ grad,
+                                          const float* __restrict__ invd, int s, float sign) {
+  const float4 gv = __ldg(reinterpret_cast<const float4*>(grad) + s);
+  const float4 iv = __ldg(reinterpret_cast<const float4*>(invd) + s);
+  return make_float4(iv.x * (sign * gv.x), iv.y * (sign * gv.y), iv.z * (sign * gv.z),
+                     iv.w * (sign * gv.w));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBlock)
+k_pcg_fused(Geo g, FusedArgs a) {
+  __shared__ float shf[32 * 6];
+  __shared__ df32 shd[32 * 6];
+  DevState* st = a.st;
+  if (st->stop) return;
+  const int T = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  const int wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31);   // first group of this warp
+  const int n4 = g.nfp >> 2;
+  const int s1 = g.G4, s0 = g.fe[1] * g.G4, fe2 = g.fe[2];
+  const unsigned full = 0xffffffffu;
+  unsigned gen = 0;
+  auto timed_out = [&]() { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } };
+  const float sign = a.rhs_sign;
+
+  // ---- phase 0: r_0 = rhs, z_0 = r_0 / diag, w_0 = H z_0 ------------------------------------
+  float t0[3] = {0.f, 0.f, 0.f};   // r.z, r.r, z.w
+  for (int base = wbase; base < n4; base += T) {
+    const int t = min(base + lane, n4 - 1);
+    const bool own = base + lane < n4;
+    const GroupPos q = group_pos(g, t);
+    const int n = 4 * t;
+    const float4 gc = __ldg(reinterpret_cast<const float4*>(a.grad) + t);
+    const float4 ic = __ldg(reinterpret_cast<const float4*>(a.invd) + t);
+    const float rc[4] = {sign * gc.x, sign * gc.y, sign * gc.z, sign * gc.w};
+    const float4 zc = make_float4(ic.x * rc[0], ic.y * rc[1], ic.z * rc[2], ic.w * rc[3]);
+    const float4 z1m = q.i1 > 0 ? z_init4(a.grad, a.invd, t - s1, sign) : zc;
+    const float4 z1p = q.i1 < g.fe[1] - 1 ? z_init4(a.grad, a.invd, t + s1, sign) : zc;
+    const float4 z0m = q.i0 > 0 ? z_init4(a.grad, a.invd, t - s0, sign) : zc;
+    const float4 z0p = q.i0 < g.fe[0] - 1 ? z_init4(a.grad, a.invd, t + s0, sign) : zc;
+    float zl = __shfl_up_sync(full, zc.w, 1), zr = __shfl_down_sync(full, zc.x, 1);
+    if (lane == 0 && q.x0 > 0) zl = __ldg(a.invd + n - 1) * (sign * __ldg(a.grad + n - 1));
+    if (lane == 31 && q.x0 + 4 < g.P2) zr = __ldg(a.invd + n + 4) * (sign * __ldg(a.grad + n + 4));
+    float w[4];
+    hz_group<P>(g, q, t, zc, z1m, z1p, z0m, z0p, zl, zr, a.dco, a.eco, w);
+    if (own) {
+      float ro[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool real = q.x0 + u < fe2;
+        ro[u] = real ? rc[u] : 0.f;
+        const float zk = real ? f4get(zc, u) : 0.f;
+        t0[0] += ro[u] * zk;
+        t0[1] += ro[u] * ro[u];
+        t0[2] += zk * w[u];
+      }
+      reinterpret_cast<float4*>(a.rb[0])[t] = make_float4(ro[0], ro[1], ro[2], ro[3]);
+      reinterpret_cast<float4*>(a.wb[0])[t] = make_float4(w[0], w[1], w[2], w[3]);
+    }
+  }
+  if (!grid_allreduce<3>(t0, a.sync, ++gen, shf, shd)) { timed_out(); return; }
+  const float rr0 = t0[1];
+  float rho = t0[0], pq = t0[2];   // p_0 = z_0, q_0 = w_0
+  float al = 0.f, be = 0.f, beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
+  bool done = !(rr0 > 0.f) || !(pq > 0.f) || a.max_it < 1;
+  if (!done) al = rho / pq;
+  int it = 0;
+
+  for (int k = 1; !done; ++k) {
+    const bool last = k == a.max_it, has_q = k > 1;
+    const float* rold = a.rb[(k - 1) & 1];
+    const float* wold = a.wb[(k - 1) & 1];
+    const float* qold = a.qb[k & 1];
+    float* rnew = a.rb[k & 1];
+    float* wnew = a.wb[k & 1];
+    float* qnew = a.qb[(k - 1) & 1];
+    float v[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};   // r.z, r.r, z.w, z.q_old, p_old.w, p_old.q_old
+    for (int base = wbase; base < n4; base += T) {
+      const int t = min(base + lane, n4 - 1);
+      const bool own = base + lane < n4;
+      const GroupPos q = group_pos(g, t);
+      const int n = 4 * t;
+      const float4 r4 = reinterpret_cast<const float4*>(rold)[t];
+      const float4 w4 = reinterpret_cast<const float4*>(wold)[t];
+      const float4 q4 = has_q ? reinterpret_cast<const float4*>(qold)[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 p4 = has_q ? reinterpret_cast<const float4*>(a.p)[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 x4 = has_q ? reinterpret_cast<const float4*>(a.x)[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 i4 = __ldg(reinterpret_cast<const float4*>(a.invd) + t);
+      float pn[4], qn[4], xn[4], rn[4], zn[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float ri = f4get(r4, u), ii = f4get(i4, u);
+        qn[u] = fmaf(be, f4get(q4, u), f4get(w4, u));
+        rn[u] = fmaf(-al, qn[u], ri);
+        zn[u] = ii * rn[u];
+        pn[u] = fmaf(be, f4get(p4, u), ii * ri);
+        xn[u] = fmaf(al, pn[u], f4get(x4, u));
+      }
+      float w[4] = {0.f, 0.f, 0.f, 0.f};
+      if (!last) {
+        const float4 zc = make_float4(zn[0], zn[1], zn[2], zn[3]);
+        const float4 z1m = q.i1 > 0 ? z_next4(rold, wold, qold, a.invd, t - s1, al, be, has_q) : zc;
+        const float4 z1p = q.i1 < g.fe[1] - 1 ? z_next4(rold, wold, qold, a.invd, t + s1, al, be, has_q) : zc;
+        const float4 z0m = q.i0 > 0 ? z_next4(rold, wold, qold, a.invd, t - s0, al, be, has_q) : zc;
+        const float4 z0p = q.i0 < g.fe[0] - 1 ? z_next4(rold, wold, qold, a.invd, t + s0, al, be, has_q) : zc;
+        float zl = __shfl_up_sync(full, zc.w, 1), zr = __shfl_down_sync(full, zc.x, 1);
+        if (lane == 0 && q.x0 > 0)
+          zl = z_next(rold[n - 1], wold[n - 1], has_q ? qold[n - 1] : 0.f, __ldg(a.invd + n - 1), al, be);
+        if (lane == 31 && q.x0 + 4 < g.P2)
+          zr = z_next(rold[n + 4], wold[n + 4], has_q ? qold[n + 4] : 0.f, __ldg(a.invd + n + 4), al, be);
+        hz_group<P>(g, q, t, zc, z1m, z1p, z0m, z0p, zl, zr, a.dco, a.eco, w);
+      }
+      if (own) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (q.x0 + u >= fe2) { pn[u] = qn[u] = xn[u] = rn[u] = zn[u] = 0.f; }
+          v[0] += rn[u] * zn[u];
+          v[1] += rn[u] * rn[u];
+          v[2] += zn[u] * w[u];
+          v[3] += zn[u] * qn[u];
+          v[4] += pn[u] * w[u];
+          v[5] += pn[u] * qn[u];
+        }
+        reinterpret_cast<float4*>(a.x)[t] = make_float4(xn[0], xn[1], xn[2], xn[3]);
+        reinterpret_cast<float4*>(a.p)[t] = make_float4(pn[0], pn[1], pn[2], pn[3]);
+        reinterpret_cast<float4*>(qnew)[t] = make_float4(qn[0], qn[1], qn[2], qn[3]);
+        reinterpret_cast<float4*>(rnew)[t] = make_float4(rn[0], rn[1], rn[2], rn[3]);
+        if (!last) reinterpret_cast<float4*>(wnew)[t] = make_float4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    if (!grid_allreduce<6>(v, a.sync, ++gen, shf, shd)) { timed_out(); return; }
+    it = k;
+    relres = sqrtf(v[1]) / sqrtf(rr0);
+    if (relres < (float)a.rtol || last) break;
+    beta = v[0] / rho;
+    rho = v[0];
+    const float den = v[2] + beta * (v[3] + v[4]) + beta * beta * v[5];
+    if (!(den > 0.f)) break;
+    be = beta;
+    al = rho / den;
+  }
+  if (it == 0) {   // no iteration ran: x = 0
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n4; t += T)
+      reinterpret_cast<float4*>(a.x)[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     st->rr0 = rr0;
@@ -248,6 +476,39 @@ static int grid_for(int device) {
   return sms * per_sm;
 }
 
+template <int P>
+static int fused_grid_for(int device) {
+  int sms = 0, per_sm = 0, coop = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_fused<P>, kBlock, 0) !=
+      cudaSuccess)
+    return 0;
+  return sms * per_sm;
+}
+
+int pcg_fused_grid(int device, int pe_axis) {
+  return pe_axis == 0 ? fused_grid_for<0>(device) : (pe_axis == 1 ? fused_grid_for<1>(device)
+                                                                  : fused_grid_for<2>(device));
+}
+
+cudaError_t launch_pcg_fused(const Geo& g, int grid, const float* grad, float rhs_sign, float* x,
+                             float* p, float* const rb[2], float* const wb[2], float* const qb[2],
+                             const float* dco, const float* eco, const float* invd,
+                             unsigned* sync, int max_it, double rtol, DevState* st,
+                             cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(grid) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  FusedArgs a{grad, rhs_sign, x, p, {rb[0], rb[1]}, {wb[0], wb[1]}, {qb[0], qb[1]},
+              dco, eco, invd, sync, st, max_it, rtol};
+  Geo gg = g;
+  void* args[] = {&gg, &a};
+  void* fn = g.p == 0 ? (void*)k_pcg_fused<0>
+                      : (g.p == 1 ? (void*)k_pcg_fused<1> : (void*)k_pcg_fused<2>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
 int pcg_persistent_grid(int device, int pe_axis) {
   return pe_axis == 0 ? grid_for<0>(device) : (pe_axis == 1 ? grid_for<1>(device)
                                                             : grid_for<2>(device));
@@ -256,11 +517,11 @@ int pcg_persistent_grid(int device, int pe_axis) {
 cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
                                   float* x, float* r, float* z, float* p0, float* p1, float* Hp,
                                   const float* dco, const float* eco, const float* invd,
-                                  float* part, unsigned* bar, int max_it, double rtol,
+                                  unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(grid) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, part, bar, st, max_it, rtol};
+  PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol};
   Geo gg = g;
   void* args[] = {&gg, &a};
   void* fn = g.p == 0 ? (void*)k_pcg_persistent<0>

@@ -175,10 +175,10 @@ def test_half_precision_images_match_oracle_on_the_same_values(H, orc, dtype):
     check_field(host(g), e["grad"], "grad " + dtype)
 
 
-@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (0, 3), (1, 0)])
 def test_tiny_solve_matches_oracle(H, orc, precond, path):
     """Tiny case: 32x32x16, OT init, 10 GN-PCG iterations (path 1: separate PCG kernels,
-    path 2: the persistent cooperative PCG kernel)."""
+    path 2: the persistent cooperative PCG kernel, path 3: its one-barrier form)."""
     pr = ph.make_pair("tiny")
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
     b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=10, precond=precond, pcg_path=path)
@@ -196,14 +196,14 @@ def test_tiny_solve_matches_oracle(H, orc, precond, path):
 @pytest.mark.parametrize("name", ["small", "7t"])
 def test_both_pcg_paths_match_oracle_on_larger_volumes(H, orc, name):
     """Small (96x96x60, PE axis 1) and 7T-shaped (130x130x85, PE axis 0) pairs, OT init + 4 GN
-    iterations, through the separate PCG kernels and the persistent PCG kernel, against the
+    iterations, through the separate PCG kernels and both persistent PCG kernels, against the
     oracle's own double-precision trajectory."""
     pr = ph.make_pair(name)
     P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
     ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=4, contract=False)
     assert status == 0
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
-    for path in (1, 2):
+    for path in (1, 2, 3):
         b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=4, pcg_path=path)
         assert h.last_status() == 0
         gs = host(st)
@@ -211,7 +211,7 @@ def test_both_pcg_paths_match_oracle_on_larger_volumes(H, orc, name):
         assert rel(host(b), ref) <= 1e-3, (path, rel(host(b), ref), gs[:, 6], rst[:, 6])
 
 
-@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (1, 0)])
+@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (0, 3), (1, 0)])
 @pytest.mark.parametrize("dims,spacing,p", [SHAPES[0], SHAPES[1], SHAPES[2], SHAPES[4]])
 def test_pcg_step_matches_oracle(H, orc, precond, path, dims, spacing, p):
     """hysco_pcg: q ~= H^{-1} rhs with <= 10 PCG iterations, against the oracle's PCG on the same
