@@ -47,6 +47,8 @@ def parse():
                     help="0 auto (= 2 when possible), 1 separate kernels, 2 persistent kernel, "
                          "3 persistent one-barrier-per-iteration kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the bf16 / f16 image-storage timing")
     return ap.parse_args()
 
 
@@ -199,6 +201,72 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
+def precision_sweep(args, dev, stream, flush, n_pairs=4, reps=3):
+    """Pairs/s with the images stored in f32, bf16 and f16 (field, interpolation and sums stay
+    single precision) on the first n_pairs pairs of the 3T precision sweep, device-resident and
+    end to end (pinned host images in the storage type, field out), and the relative field
+    difference of each reduced-precision solve from the f32 solve of the same pair.  The error
+    against the double-precision oracle is checked by the precision test."""
+    import torch
+
+    from paper_2403_10706_b300.hysco import Hysco
+    pairs = [ph.make_sweep_pair(i) for i in range(n_pairs)]
+    out, ref = {}, None
+    for key, td in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        hs = [Hysco(p.dims, p.spacing, p.pe_dim, ALPHA, BETA, dtype=td, device=dev) for p in pairs]
+        imgs = [(torch.from_numpy(p.Ip).to(dev).to(td), torch.from_numpy(p.Im).to(dev).to(td))
+                for p in pairs]
+        host_imgs = [(a.cpu().pin_memory(), c.cpu().pin_memory()) for a, c in imgs]
+        bs = [torch.empty(h.field_dims, dtype=torch.float32, device=dev) for h in hs]
+        hb = [torch.empty(h.field_dims, dtype=torch.float32).pin_memory() for h in hs]
+
+        def solve(i):
+            hs[i].solve(imgs[i][0], imgs[i][1], b=bs[i], gn_iters=GN_ITERS["3t"], init=True,
+                        stats=False)
+
+        for i in range(n_pairs):
+            solve(i)
+        torch.cuda.synchronize()
+        dev_ms, e2e_ms = [], []
+        for _ in range(reps):
+            for i in range(n_pairs):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                solve(i)
+                e1.record(stream)
+                dev_ms.append((e0, e1))
+        for _ in range(reps):
+            for i in range(n_pairs):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                imgs[i][0].copy_(host_imgs[i][0], non_blocking=True)
+                imgs[i][1].copy_(host_imgs[i][1], non_blocking=True)
+                solve(i)
+                hb[i].copy_(bs[i], non_blocking=True)
+                e1.record(stream)
+                e2e_ms.append((e0, e1))
+        torch.cuda.synchronize()
+        t_dev = sum(a.elapsed_time(b) for a, b in dev_ms) / 1e3
+        t_e2e = sum(a.elapsed_time(b) for a, b in e2e_ms) / 1e3
+        fields = [b.cpu().numpy() for b in bs]
+        entry = {"value": len(dev_ms) / t_dev, "e2e": len(e2e_ms) / t_e2e,
+                 "h2d_bytes_per_pair": int(imgs[0][0].numel() * imgs[0][0].element_size() * 2),
+                 "status": max(abs(h.last_status()) for h in hs)}
+        if ref is None:
+            ref = fields
+        else:
+            entry["field_rel_diff_vs_f32"] = max(
+                float(np.linalg.norm(f - r) / np.linalg.norm(r)) for f, r in zip(fields, ref))
+        out[key] = entry
+        del hs
+    out["unit"] = UNIT
+    out["sample"] = (f"sweep pairs 0..{n_pairs - 1} (3T shape, shared field map, contrast "
+                     f"U(0.2, 1), N(0, 0.03) noise), {reps} passes each, L2 flushed per solve")
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -345,6 +413,10 @@ def run_ours(args):
 
     clk.__exit__(None, None, None)   # sampled over the timed solves, e2e and roofline launches
 
+    prec = None
+    if rank == 0 and args.workload == "3t" and not args.no_precision:
+        prec = precision_sweep(args, dev, stream, flush)
+
     if rank == 0:
         # OT: shift, OT, blur; per GN step: eval (a no-op when the previous gamma = 1 trial was
         # accepted), PCG (1 persistent launch, or init + 2 per iteration), the gamma = 1 trial
@@ -361,6 +433,8 @@ def run_ours(args):
                 "config": config(args, world), "status": status,
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "eval_roofline": eval_roof}
+        if prec is not None:
+            line["precision"] = prec
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pr, args)
         print(json.dumps(line))

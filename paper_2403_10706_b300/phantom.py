@@ -178,8 +178,32 @@ def make_pair(recipe: str | dict, seed: int | None = None, bmax: float | None = 
     if r["noise"] > 0:
         Ip = Ip + nrng.normal(0.0, r["noise"], size=dims)
         Im = Im + nrng.normal(0.0, r["noise"], size=dims)
-    return Pair(Ip.astype(np.float32), Im.astype(np.float32), I.astype(np.float32),
-                b.astype(np.float32), tuple(r["spacing"]), pe, used)
+    c32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)   # noqa: E731
+    return Pair(c32(Ip), c32(Im), c32(I), c32(b), tuple(r["spacing"]), pe, used)
+
+
+# precision sweep: many diffusion-volume pairs of the 3T shape that share one field map (max 8
+# voxels), each with its own contrast c ~ U(0.2, 1) and N(0, 0.03) noise
+SWEEP = dict(recipe="3t", n_pairs=288, contrast=(0.2, 1.0), noise=0.03, seed=3000)
+
+_sweep_base = {}
+
+
+def make_sweep_pair(i: int) -> Pair:
+    """Pair i (0 <= i < 288) of the precision sweep.  The push-forward is linear in the
+    intensities, so pair i is c_i times the noise-free distorted base pair plus fresh noise."""
+    if not 0 <= i < SWEEP["n_pairs"]:
+        raise ValueError("sweep pair index out of range")
+    if "pair" not in _sweep_base:
+        _sweep_base["pair"] = make_pair(SWEEP["recipe"], noise=0.0)
+    base = _sweep_base["pair"]
+    rng = np.random.default_rng(SWEEP["seed"] + i)
+    c = rng.uniform(*SWEEP["contrast"])
+    Ip = c * base.Ip.astype(np.float64) + rng.normal(0.0, SWEEP["noise"], size=base.dims)
+    Im = c * base.Im.astype(np.float64) + rng.normal(0.0, SWEEP["noise"], size=base.dims)
+    c32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)   # noqa: E731
+    return Pair(c32(Ip), c32(Im), c32(c * base.I_true), base.b_true, base.spacing, base.pe_dim,
+                base.seed)
 
 
 def random_field(dims, pe_dim, seed, scale=1.0, smooth=2.0, max_slope=0.6):

@@ -1,0 +1,88 @@
+"""Precision sweep: the two images stored in BF16 or FP16 while the field, the interpolation and
+every accumulation stay in single precision, against the double-precision oracle, on a pair of
+the 288-pair sweep (3T shape 144x168x111, shared field map of max 8 voxels, per-pair contrast
+c ~ U(0.2, 1), N(0, 0.03) noise), OT init + 20 GN iterations.
+
+  (i) the contract: the GPU solve on quantised images against the oracle's solve on the same
+      quantised values, relative field error <= 1e-3 (the single-precision solve bound);
+  (ii) the cost of the storage precision: the same GPU solve against the oracle's solve on the
+      unquantised single-precision images, and the corrected image 1/2 (T+ + T-) at the GPU's
+      field against the oracle's at its own field: reported, not gated (quantising the inputs
+      changes the problem, not the solver).
+"""
+import threading
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from paper_2403_10706_b300 import phantom as ph  # noqa: E402
+
+ALPHA, BETA = 300.0, 1e4
+GN = 20
+DTYPES = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2403_10706_b300 import build
+    build.build()
+    from paper_2403_10706_b300.hysco import Hysco
+    return Hysco
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def quantise(a, dtype):
+    """Round-to-nearest-even storage rounding, as torch's float -> bf16 / f16 conversion."""
+    return torch.from_numpy(a).to(dtype).to(torch.float32).numpy()
+
+
+def test_precision_sweep_pair_against_oracle(H, orc):
+    pr = ph.make_sweep_pair(0)
+    inputs = {k: (quantise(pr.Ip, t), quantise(pr.Im, t)) for k, t in DTYPES.items()}
+    for k in ("bf16", "f16"):   # quantisation really changed the inputs
+        assert not np.array_equal(inputs[k][0], pr.Ip)
+
+    # the oracle's three solves run on host threads (the C oracle runs without the GIL)
+    ref = {}
+
+    def oracle_solve(key):
+        P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+        b, status, _ = P.solve(*inputs[key], gn_iters=GN, contract=False)
+        T = P.eval(*inputs["f32" if key == "f32" else key], b, contract=False, grad=False,
+                   corrected=True)
+        ref[key] = (b, status, 0.5 * (T["Tp"] + T["Tm"]))
+
+    threads = [threading.Thread(target=oracle_solve, args=(k,)) for k in DTYPES]
+    for t in threads:
+        t.start()
+
+    gpu = {}
+    for key, td in DTYPES.items():
+        h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA, dtype=td)
+        Ip = torch.from_numpy(pr.Ip).cuda().to(td)
+        Im = torch.from_numpy(pr.Im).cuda().to(td)
+        b, st = h.solve(Ip, Im, gn_iters=GN)
+        assert h.last_status() == 0, key
+        Tp, Tm = h.correct(Ip, Im, b)
+        torch.cuda.synchronize()
+        gpu[key] = (b.cpu().numpy(), (0.5 * (Tp + Tm)).cpu().numpy())
+    for t in threads:
+        t.join()
+
+    report = []
+    for key in DTYPES:
+        b_ref, status, _ = ref[key]
+        assert status == 0, key
+        err = rel(gpu[key][0], b_ref)
+        assert err <= 1e-3, (key, err)   # (i) same quantised inputs
+        cost = rel(gpu[key][0], ref["f32"][0])
+        img = rel(gpu[key][1], ref["f32"][2])
+        report.append(f"{key}: field vs oracle on the same inputs {err:.2e}, vs oracle on the "
+                      f"f32 images {cost:.2e}; corrected image vs oracle (f32 images) {img:.2e}")
+    print("\n" + "\n".join(report))
