@@ -63,6 +63,9 @@ def lib():
         _lib.orc_solve.argtypes = [P, P, P, P, P, P]
         _lib.orc_pcg.argtypes = [P, P, P, P, C.c_int, C.c_int, P, C.c_int, C.c_double, P, P]
         _lib.orc_phi.argtypes = [C.c_double, P, P, P]
+        _lib.orc_correct_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P, P, P]
+        _lib.orc_image_grad.restype = C.c_int64
+        _lib.orc_image_grad.argtypes = [P, P, P, P, C.c_int, P, P]
     return _lib
 
 
@@ -115,6 +118,25 @@ class Problem:
         if cells:
             out["cell_p"], out["cell_m"] = cp, cm
         return out
+
+    def correct_adjoint(self, Ip, Im, b, gTp=None, gTm=None, contract=True):
+        """Adjoint of the corrected images T+, T- at b for upstream sensitivities gTp, gTm
+        (None = 0): returns (dIp, dIm, db)."""
+        Ip, Im, b = _f32(Ip), _f32(Im), _f64(b)
+        gTp = None if gTp is None else _f64(gTp)
+        gTm = None if gTm is None else _f64(gTm)
+        dIp, dIm, db = np.zeros(self.dims), np.zeros(self.dims), np.zeros(self.fdims)
+        lib().orc_correct_adjoint(C.byref(self.g), _p(Ip), _p(Im), _p(b), int(contract),
+                                  _p(gTp), _p(gTm), _p(dIp), _p(dIm), _p(db))
+        return dIp, dIm, db
+
+    def image_grad(self, Ip, Im, b, contract=True):
+        """dJ/dI+ and dJ/dI- at fixed b."""
+        Ip, Im, b = _f32(Ip), _f32(Im), _f64(b)
+        dIp, dIm = np.zeros(self.dims), np.zeros(self.dims)
+        lib().orc_image_grad(C.byref(self.g), _p(Ip), _p(Im), _p(b), int(contract), _p(dIp),
+                             _p(dIm))
+        return dIp, dIm
 
     def hessvec(self, Ip, Im, b, v, contract=True):
         Hv = np.zeros(self.fdims)

@@ -510,6 +510,93 @@ int64_t orc_eval(const orc_geom* g, const float* Ip, const float* Im, const doub
   return bad;
 }
 
+/* ------------------------------------------------------------------------------------------ */
+/* adjoints (vector-Jacobian products) of the corrected images and of J, at fixed b            */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Adjoint of the corrected images of Eq. 1 at b.  Given upstream sensitivities gTp, gTm (image
+ * shaped; either may be NULL, meaning zero) it returns
+ *   dIp = (dT+/dI+)^T gTp,  dIm = (dT-/dI-)^T gTm                         (image shaped)
+ *   db  = (dT+/db)^T gTp + (dT-/db)^T gTm                                 (field shaped)
+ * each output optional (NULL).  From the definitions, per cell j of a column:
+ *   T+_j = [(1 - w) I+[i] + w I+[i+1]] (1 + delta_j),  i = floor(t+_j),  w = t+_j - i, so
+ *   dT+_j/dI+[i] = (1 - w)(1 + delta_j),  dT+_j/dI+[i+1] = w (1 + delta_j)  (entries inside the
+ *   column only: outside it the image is the constant 0);
+ *   t+_j = j + (b_j + b_{j+1})/2 and delta_j = b_{j+1} - b_j, so
+ *   dT+_j/db_j     = 1/2 I+'(t+)(1 + delta) - I+(t+),
+ *   dT+_j/db_{j+1} = 1/2 I+'(t+)(1 + delta) + I+(t+);
+ *   T-_j = I-(t-_j)(1 - delta_j), t-_j = j - (b_j + b_{j+1})/2, so
+ *   dT-_j/db_j     = -1/2 I-'(t-)(1 - delta) + I-(t-),
+ *   dT-_j/db_{j+1} = -1/2 I-'(t-)(1 - delta) - I-(t-).
+ * I' is the slope of the cell that contains t (the right-hand derivative at an integer t). */
+void orc_correct_adjoint(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                         int contract, const double* gTp, const double* gTm, double* dIp,
+                         double* dIm, double* db) {
+  int64_t m = g->d[g->p];
+  int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
+  int64_t sti = si[g->p], stf = sf[g->p];
+  int64_t ncols = column_count(g);
+  if (dIp) memset(dIp, 0, img_count(g) * sizeof(double));
+  if (dIm) memset(dIm, 0, img_count(g) * sizeof(double));
+  if (db) memset(db, 0, fld_count(g) * sizeof(double));
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    for (int64_t j = 0; j < m; ++j) {
+      double bj = b[of + j * stf], bj1 = b[of + (j + 1) * stf];
+      double tp, tm, delta;
+      cell_positions(bj, bj1, j, contract, &tp, &tm, &delta);
+      double Ipv, Ips, Imv, Ims;
+      int64_t ip, im;
+      interp1(Ip + oi, sti, m, tp, &Ipv, &Ips, &ip);
+      interp1(Im + oi, sti, m, tm, &Imv, &Ims, &im);
+      int64_t cidx = oi + j * sti;
+      double gp = gTp ? gTp[cidx] : 0.0;
+      double gm = gTm ? gTm[cidx] : 0.0;
+      double wp = tp - floor(tp), wm = tm - floor(tm);
+      if (dIp) {
+        if (ip >= 0 && ip < m) dIp[oi + ip * sti] += gp * (1.0 - wp) * (1.0 + delta);
+        if (ip + 1 >= 0 && ip + 1 < m) dIp[oi + (ip + 1) * sti] += gp * wp * (1.0 + delta);
+      }
+      if (dIm) {
+        if (im >= 0 && im < m) dIm[oi + im * sti] += gm * (1.0 - wm) * (1.0 - delta);
+        if (im + 1 >= 0 && im + 1 < m) dIm[oi + (im + 1) * sti] += gm * wm * (1.0 - delta);
+      }
+      if (db) {
+        double dTp_dbj = 0.5 * Ips * (1.0 + delta) - Ipv;
+        double dTp_dbj1 = 0.5 * Ips * (1.0 + delta) + Ipv;
+        double dTm_dbj = -0.5 * Ims * (1.0 - delta) + Imv;
+        double dTm_dbj1 = -0.5 * Ims * (1.0 - delta) - Imv;
+        db[of + j * stf] += gp * dTp_dbj + gm * dTm_dbj;
+        db[of + (j + 1) * stf] += gp * dTp_dbj1 + gm * dTm_dbj1;
+      }
+    }
+  }
+}
+
+/* Gradient of J with respect to the two images at fixed b.  Only the distance term depends on
+ * them: D = vol/2 sum_j r_j^2 with r_j = T+_j - T-_j (Eq. 2), so dJ/dI+- = (dT+-/dI+-)^T (+-vol r).
+ * Returns the number of barrier-infeasible cells (the image gradient is still that of D). */
+int64_t orc_image_grad(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                       int contract, double* dIp, double* dIm) {
+  int64_t nc = img_count(g);
+  double* Tp = malloc(nc * sizeof(double));
+  double* Tm = malloc(nc * sizeof(double));
+  double* gp = malloc(nc * sizeof(double));
+  double* gm = malloc(nc * sizeof(double));
+  double D, P;
+  int64_t bad = residual_pass(g, Ip, Im, b, contract, &D, &P, NULL, Tp, Tm, NULL, NULL);
+  double vol = cell_volume(g);
+  for (int64_t k = 0; k < nc; ++k) {
+    double r = Tp[k] - Tm[k];
+    gp[k] = vol * r;
+    gm[k] = -vol * r;
+  }
+  orc_correct_adjoint(g, Ip, Im, b, contract, gp, gm, dIp, dIm, NULL);
+  free(Tp); free(Tm); free(gp); free(gm);
+  return bad;
+}
+
 /* GN Hessian about b applied to v */
 int orc_hessvec(const orc_geom* g, const float* Ip, const float* Im, const double* b,
                 int contract, const double* v, double* Hv) {
