@@ -407,6 +407,20 @@ def run_ours(args):
     alg_eval = 8 * nimg + 20 * nfld
     eval_ms = time_launches(lambda: h.eval(Ip, Im, b_out, grad=g, terms=terms))
     ach_eval = alg_eval / (eval_ms / 1e3) / 1e9
+    # the corrected-image adjoint (backward of hysco_correct): reads I+, I-, g+, g- (16 B per
+    # voxel) and b (4 B per node, once per image pass and once for the field pass), writes dI+,
+    # dI- (8 B per voxel) and db (4 B per node)
+    gT = torch.randn(pr.dims, device=dev, dtype=torch.float32)
+    dIp, dIm, dbb = (torch.empty_like(gT), torch.empty_like(gT), torch.empty_like(b_out))
+    alg_adj = 24 * nimg + 16 * nfld
+    adj_ms = time_launches(lambda: h.lib.hysco_correct_adjoint(
+        h._h, h._img(Ip, "Ip"), h._img(Im, "Im"), h._fld(b_out, "b"), h._img_f32(gT, "gTp"),
+        h._img_f32(gT, "gTm"), h._img_f32(dIp, "dIp"), h._img_f32(dIm, "dIm"),
+        h._fld(dbb, "db"), stream.cuda_stream))
+    adjoint = {"launch_ms": adj_ms, "alg_bytes_per_launch": alg_adj,
+               "achieved": alg_adj / (adj_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+               "frac": alg_adj / (adj_ms / 1e3) / 1e9 / peak,
+               "kernel": "k_image_adjoint x2 + k_field_adjoint"}
     eval_roof = {"bound": "hbm", "achieved": ach_eval, "peak": peak, "unit": "GB/s",
                  "frac": ach_eval / peak, "kernel": "k_eval<float>",
                  "alg_bytes_per_launch": alg_eval, "launch_ms": eval_ms}
@@ -432,7 +446,7 @@ def run_ours(args):
                 "data": "synthetic (seeded phantom standing in for HCP 3T data)",
                 "config": config(args, world), "status": status,
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-                "roofline": roof, "eval_roofline": eval_roof}
+                "roofline": roof, "eval_roofline": eval_roof, "adjoint": adjoint}
         if prec is not None:
             line["precision"] = prec
         if not args.no_cpu_baseline:

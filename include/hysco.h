@@ -139,6 +139,29 @@ int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters,
 int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, float* Tp,
                   float* Tm, hysco_stream_t stream);
 
+/* Adjoint (vector-Jacobian product) of hysco_correct at b, for differentiation (Eq. 1 at fixed
+ * b).  Given the sensitivities gTp, gTm of a scalar loss to Tp and Tm (image-shaped float32,
+ * device; either may be NULL, meaning zero) it writes
+ *   dIp = (dTp/dIp)^T gTp,  dIm = (dTm/dIm)^T gTm        image-shaped float32 (sensitivity to
+ *                                                        the stored image values, whatever the
+ *                                                        handle's image dtype)
+ *   db  = (dTp/db)^T gTp + (dTm/db)^T gTm                 field-shaped float32
+ * Each output may be NULL (not computed).  Per cell, Tp depends on I+ at the two voxels around
+ * t+ with weights (1 - w, w) times (1 + d_v b), and on b through t+ (slope of I+) and d_v b; Tm
+ * likewise with t-, 1 - d_v b.  Cells and weights are recomputed from b, not stored.
+ * Deterministic (no atomics).  Outputs must not alias the inputs; they are overwritten. */
+int hysco_correct_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                          const float* gTp, const float* gTm, float* dIp, float* dIm, float* db,
+                          hysco_stream_t stream);
+
+/* Gradient of gJ * J with respect to the two images at fixed b.  Only the distance term of Eq. 2
+ * depends on them: dIp = gJ vol (dTp/dIp)^T r, dIm = -gJ vol (dTm/dIm)^T r with the residual
+ * r = Tp - Tm recomputed.  (With respect to b it is gJ times the gradient of hysco_eval; with
+ * respect to alpha and beta it is gJ S and gJ P.)  Outputs image-shaped float32, either may be
+ * NULL; they must not alias the inputs. */
+int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, double gJ,
+                     float* dIp, float* dIm, hysco_stream_t stream);
+
 /* Full solve (Sec. 2.2 + 2.3.1): optional OT init (opts->init), then opts->gn_iters Gauss-Newton
  * iterations b <- b + gamma q with H_J q ~= -grad J from at most pcg_max_iters PCG iterations
  * (x0 = 0, stop at relative residual < pcg_rtol) and gamma the first of 1, 1/2, 1/4, ... that

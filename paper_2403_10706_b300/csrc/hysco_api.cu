@@ -415,6 +415,28 @@ int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, flo
   return HYSCO_OK;
 }
 
+int hysco_correct_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                          const float* gTp, const float* gTm, float* dIp, float* dIm, float* db,
+                          hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b)) return HYSCO_EINVAL;
+  if ((gTp && !aligned(gTp, 4)) || (gTm && !aligned(gTm, 4)) || (dIp && !aligned(dIp, 4)) ||
+      (dIm && !aligned(dIm, 4)) || (db && !aligned(db, 4)))
+    return HYSCO_EINVAL;
+  HYSCO_TRY(launch_correct_adjoint(h->g, h->dtype, Ip, Im, b, gTp, gTm, dIp, dIm, db,
+                                   (size_t)h->nimg * sizeof(float), (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, double gJ,
+                     float* dIp, float* dIm, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || !std::isfinite(gJ))
+    return HYSCO_EINVAL;
+  if ((dIp && !aligned(dIp, 4)) || (dIm && !aligned(dIm, 4))) return HYSCO_EINVAL;
+  const float svol = (float)(gJ * (double)h->g.vol);
+  HYSCO_TRY(launch_image_grad(h->g, h->dtype, Ip, Im, b, svol, dIp, dIm, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
 int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell_m,
                        hysco_stream_t stream) {
   if (!h || check_f32(b) || check_f32(cell_p) || check_f32(cell_m)) return HYSCO_EINVAL;

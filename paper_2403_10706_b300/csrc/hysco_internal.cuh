@@ -337,6 +337,14 @@ cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double
                           const Work& w, cudaStream_t s);
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s);
+// k_adjoint.cu: adjoints of the corrected images and of J's distance term at fixed b
+cudaError_t launch_correct_adjoint(const Geo& g, int dtype, const void* Ip, const void* Im,
+                                   const float* b, const float* gTp, const float* gTm,
+                                   float* dIp, float* dIm, float* db, size_t img_bytes,
+                                   cudaStream_t s);
+cudaError_t launch_image_grad(const Geo& g, int dtype, const void* Ip, const void* Im,
+                              const float* b, float svol, float* dIp, float* dIm,
+                              cudaStream_t s);
 cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s);
 cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
 

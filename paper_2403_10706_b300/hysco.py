@@ -115,6 +115,37 @@ class Hysco:
                    "hysco_correct")
         return Tp, Tm
 
+    def _img_f32(self, t, name):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
+                and tuple(t.shape) == self.dims and t.is_contiguous()):
+            raise ValueError(f"{name}: expected contiguous float32 CUDA tensor {self.dims}")
+        return C.c_void_p(t.data_ptr())
+
+    def correct_adjoint(self, Ip, Im, b, gTp=None, gTm=None, want=(True, True, True)):
+        """Adjoint of correct() at b: (dIp, dIm, db) for sensitivities gTp, gTm of Tp, Tm
+        (None = 0); an output is None when its `want` flag is False."""
+        dIp = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[0] else None
+        dIm = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[1] else None
+        db = self._new_fld() if want[2] else None
+        opt = lambda t, f, name: None if t is None else f(t, name)   # noqa: E731
+        _lib.check(self.lib.hysco_correct_adjoint(
+            self._h, self._img(Ip, "Ip"), self._img(Im, "Im"), self._fld(b, "b"),
+            opt(gTp, self._img_f32, "gTp"), opt(gTm, self._img_f32, "gTm"),
+            opt(dIp, self._img_f32, "dIp"), opt(dIm, self._img_f32, "dIm"),
+            opt(db, self._fld, "db"), _stream(self.device)), "hysco_correct_adjoint")
+        return dIp, dIm, db
+
+    def image_grad(self, Ip, Im, b, gJ=1.0, want=(True, True)):
+        """gJ * dJ/dIp and gJ * dJ/dIm at fixed b (float32, image shaped)."""
+        dIp = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[0] else None
+        dIm = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[1] else None
+        _lib.check(self.lib.hysco_image_grad(
+            self._h, self._img(Ip, "Ip"), self._img(Im, "Im"), self._fld(b, "b"), float(gJ),
+            None if dIp is None else self._img_f32(dIp, "dIp"),
+            None if dIm is None else self._img_f32(dIm, "dIm"), _stream(self.device)),
+            "hysco_image_grad")
+        return dIp, dIm
+
     def solve(self, Ip, Im, b=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10,
               precond=_lib.PC_JACOBI, init=None, ot_blur=True, pcg_rtol=0.1, armijo_c1=1e-4,
               ot_eps=1e-3, stats=True, pcg_path=0, graph=True):
