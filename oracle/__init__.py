@@ -66,6 +66,8 @@ def lib():
         _lib.orc_correct_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P, P, P]
         _lib.orc_image_grad.restype = C.c_int64
         _lib.orc_image_grad.argtypes = [P, P, P, P, C.c_int, P, P]
+        _lib.orc_feasible_start.restype = C.c_double
+        _lib.orc_feasible_start.argtypes = [P, P]
     return _lib
 
 
@@ -137,6 +139,13 @@ class Problem:
         lib().orc_image_grad(C.byref(self.g), _p(Ip), _p(Im), _p(b), int(contract), _p(dIp),
                              _p(dIm))
         return dIp, dIm
+
+    def feasible_start(self, b):
+        """The solve's start rule for an OT field: returns (b scaled by 2^-k, 2^-k) with the
+        smallest k >= 0 that brings max |delta| below 1."""
+        bb = _f64(b).copy()
+        f = lib().orc_feasible_start(C.byref(self.g), _p(bb))
+        return bb, f
 
     def hessvec(self, Ip, Im, b, v, contract=True):
         Hv = np.zeros(self.fdims)

@@ -878,10 +878,38 @@ static double objective_only(const orc_geom* g, const float* Ip, const float* Im
  * A rejected line search (or a non-descent q) leaves b unchanged for that iteration.  Stops early
  * only when J(b) is not finite (returns 1 for +inf, i.e. barrier infeasible; 2 for NaN).
  * stats (nullable): gn_iters x ST_NFIELDS doubles. */
+/* Feasible start for the Gauss-Newton loop (a reading where the paper is silent): the barrier
+ * of Eq. 3 is +inf unless |delta_j| < 1 in every cell, so J is +inf at a start outside that set
+ * and no Armijo step can be accepted.  b = 0 is feasible; the start is halved until
+ * max |delta| < 1 (power-of-two factors, exact).  Returns the factor applied. */
+double orc_feasible_start(const orc_geom* g, double* b) {
+  int64_t m = g->d[g->p];
+  int64_t sf[3]; fld_strides(g, sf);
+  int64_t stf = sf[g->p];
+  int64_t ncols = column_count(g);
+  double s = 0.0;
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    for (int64_t j = 0; j < m; ++j) {
+      double delta = b[of + (j + 1) * stf] - b[of + j * stf];
+      if (fabs(delta) > s) s = fabs(delta);
+    }
+  }
+  double f = 1.0;
+  for (int k = 0; k < 64 && s * f >= 1.0; ++k) f *= 0.5;
+  if (f != 1.0)
+    for (int64_t i = 0; i < fld_count(g); ++i) b[i] *= f;
+  return f;
+}
+
 int orc_solve(const orc_geom* g, const float* Ip, const float* Im, const orc_opts* o,
               double* b, double* stats) {
   int64_t nf = fld_count(g), nc = img_count(g);
-  if (o->init) orc_ot_init(g, Ip, Im, o->ot_eps, o->contract, o->ot_blur, b, NULL, NULL);
+  if (o->init) {
+    orc_ot_init(g, Ip, Im, o->ot_eps, o->contract, o->ot_blur, b, NULL, NULL);
+    orc_feasible_start(g, b);
+  }
   orc_lin lin;
   if (!lin_alloc(&lin, nc)) return -1;
   double* grad = malloc(nf * sizeof(double));

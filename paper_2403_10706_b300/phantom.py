@@ -171,7 +171,9 @@ def make_pair(recipe: str | dict, seed: int | None = None, bmax: float | None = 
             break
         used += 100000
     else:
-        raise RuntimeError("no admissible field map drawn")
+        # a peak this large is too steep for the shape: keep the last draw, scaled down to the
+        # largest admissible slope (its peak is then below the recipe's)
+        b = b * (MAX_FIELD_SLOPE / slope)
     Ip = push_forward(I, b, pe, +1.0)
     Im = push_forward(I, b, pe, -1.0)
     nrng = np.random.default_rng(r["seed"] + 7)
@@ -204,6 +206,29 @@ def make_sweep_pair(i: int) -> Pair:
     c32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)   # noqa: E731
     return Pair(c32(Ip), c32(Im), c32(c * base.I_true), base.b_true, base.spacing, base.pe_dim,
                 base.seed)
+
+
+# batch of uneven pairs (diffusion directions / subjects of several protocols): the 3T, the
+# 7T-shaped and the 96x96x60 shapes in a seeded shuffle, PE along axis 0 or 1, each pair with its
+# own seed and field-map peak U(4, 10) voxels
+BATCH = dict(n_pairs=64, counts=(("3t", 22), ("7t", 21), ("small", 21)), bmax=(4.0, 10.0),
+             seed=2000)
+
+
+def batch_recipes(n_pairs: int | None = None) -> list:
+    """Recipe dicts of the uneven batch (the first n_pairs of the 64 when given)."""
+    rng = np.random.default_rng(BATCH["seed"])
+    shapes = [name for name, k in BATCH["counts"] for _ in range(k)]
+    order = rng.permutation(len(shapes))
+    out = []
+    for i, j in enumerate(order):
+        r = dict(RECIPES[shapes[j]])
+        r["pe_dim"] = int(rng.integers(0, 2))
+        r["bmax"] = float(rng.uniform(*BATCH["bmax"]))
+        r["seed"] = BATCH["seed"] + i
+        r["name"] = shapes[j]
+        out.append(r)
+    return out[:n_pairs] if n_pairs is not None else out
 
 
 def random_field(dims, pe_dim, seed, scale=1.0, smooth=2.0, max_slope=0.6):
