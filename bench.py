@@ -47,6 +47,8 @@ def parse():
                     help="0 auto (= 2 when possible), 1 separate kernels, 2 persistent kernel, "
                          "3 persistent one-barrier-per-iteration kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-pair uneven batch (batched vs sequential solves)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the bf16 / f16 image-storage timing")
     return ap.parse_args()
@@ -267,6 +269,67 @@ def precision_sweep(args, dev, stream, flush, n_pairs=4, reps=3):
     return out
 
 
+def batch_bench(dev, stream, flush, reps=2):
+    """The uneven batch: 64 pairs (22 of the 3T shape, 21 7T-shaped, 21 of 96x96x60, PE along
+    axis 0 or 1, field-map peaks U(4, 10) voxels), OT init + 20 GN-PCG iterations each, solved
+    by one autotuned batched solve (hysco_batch_*) and by 64 sequential plain solves
+    (hysco_solve, each its own cached graph); L2 flushed before each timed run."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import torch
+
+    from paper_2403_10706_b300.hysco import Hysco, HyscoBatch
+    recipes = ph.batch_recipes()
+    workers = max(1, min(16, len(os.sched_getaffinity(0))))
+    t0 = time.time()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        pairs = list(ex.map(ph.make_pair, recipes))
+    gen_s = time.time() - t0
+    gn = GN_ITERS["3t"]
+    hs = [Hysco(p.dims, p.spacing, p.pe_dim, ALPHA, BETA, device=dev) for p in pairs]
+    Ips = [torch.from_numpy(p.Ip).to(dev) for p in pairs]
+    Ims = [torch.from_numpy(p.Im).to(dev) for p in pairs]
+    bs = [h._new_fld() for h in hs]
+    batch = HyscoBatch(hs)
+    t0 = time.time()
+    sched = batch.tune(Ips, Ims, gn_iters=gn)
+    tune_s = time.time() - t0
+
+    def run_batch():
+        batch.solve(Ips, Ims, bs=bs, init=True, gn_iters=gn, stats=False)
+
+    def run_seq():
+        for i, h in enumerate(hs):
+            h.solve(Ips[i], Ims[i], b=bs[i], gn_iters=gn, init=True, stats=False)
+
+    out = {}
+    for name, fn in (("batched", run_batch), ("sequential", run_seq)):
+        fn()
+        torch.cuda.synchronize()
+        evs = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        out[name] = len(pairs) * reps / t
+        out[name + "_status_nonzero"] = sum(1 for h in hs if h.last_status() != 0)
+    out.update({"unit": UNIT, "speedup": out["batched"] / out["sequential"],
+                "schedule": {"branches": sched[0], "block_share_policy": sched[1],
+                             "pcg_grid_blocks": sched[2]},
+                "tune_s": tune_s, "generate_s": gen_s,
+                "workload": "64 pairs: 22x 144x168x111, 21x 130x130x85, 21x 96x96x60 (seeded "
+                            "shuffle), PE axis 0 or 1, field peaks U(4, 10) voxels; OT + 20 GN "
+                            "each", "reps": reps})
+    del batch
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -430,6 +493,9 @@ def run_ours(args):
     prec = None
     if rank == 0 and args.workload == "3t" and not args.no_precision:
         prec = precision_sweep(args, dev, stream, flush)
+    batch = None
+    if rank == 0 and args.workload == "3t" and not args.no_batch:
+        batch = batch_bench(dev, stream, flush)
 
     if rank == 0:
         # OT: shift, OT, blur; per GN step: eval (a no-op when the previous gamma = 1 trial was
@@ -449,6 +515,8 @@ def run_ours(args):
                 "roofline": roof, "eval_roofline": eval_roof, "adjoint": adjoint}
         if prec is not None:
             line["precision"] = prec
+        if batch is not None:
+            line["batch"] = batch
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(pr, args)
         print(json.dumps(line))

@@ -172,6 +172,40 @@ int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, 
 int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout,
                 const hysco_opts* opts, double* stats, hysco_stream_t stream);
 
+/* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
+ * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
+ * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):
+ * per GN iteration the per-pair evaluation, Armijo and update kernels of different pairs run on
+ * concurrent branches, and the Jacobi PCG of all pairs is one cooperative launch whose grid is
+ * shared among the pairs (the device-wide barriers are paid once for the batch).  The fixed launch
+ * sequence is captured in a CUDA graph (cached per argument set) unless opts->no_graph.  The batch
+ * holds no reference count: destroy it before any of its handles. */
+typedef struct hysco_batch_ctx* hysco_batch_t;
+
+/* n >= 1 distinct handles, at most one per block of the batched PCG grid (296 or more on a B300);
+ * HYSCO_EINVAL otherwise. */
+int hysco_batch_create(int n, const hysco_t* handles, hysco_batch_t* out);
+void hysco_batch_destroy(hysco_batch_t batch);
+
+/* Solve every pair i: images Ip[i], Im[i] (its handle's dtype and dims), field b[i] in/out, stats
+ * optional (NULL, or n pointers each NULL or a gn_iters x HYSCO_NSTATS device array as in
+ * hysco_solve).  Same options for all pairs; precond must be HYSCO_PC_JACOBI (pcg_path is ignored).
+ * Each pair's numerical status: hysco_last_status on its handle. */
+int hysco_batch_solve(hysco_batch_t batch, const void* const* Ip, const void* const* Im,
+                      float* const* b, const hysco_opts* opts, double* const* stats,
+                      hysco_stream_t stream);
+
+/* Autotuner: times short trial solves (OT + at most 2 GN iterations into scratch fields, the
+ * caller's fields untouched) of each candidate schedule -- 1, 2, 4 or 8 concurrent branches for
+ * the per-pair kernels, PCG blocks shared by field size with at least 1 or at least 2 blocks per
+ * pair -- and keeps the fastest.  Synchronises `stream`. */
+int hysco_batch_tune(hysco_batch_t batch, const void* const* Ip, const void* const* Im,
+                     const hysco_opts* opts, hysco_stream_t stream);
+
+/* The schedule in use: out[0] branches, out[1] block-share policy (0: by field size, 1: by field
+ * size with >= 2 blocks per pair), out[2] blocks of the batched PCG grid. */
+int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
+
 /* Synchronises `stream` and returns the numerical status of the last hysco_eval / hysco_solve /
  * hysco_init_ot on this handle: HYSCO_OK, HYSCO_INFEASIBLE, HYSCO_ENONFINITE or HYSCO_ETIMEOUT
  * (or HYSCO_ECUDA when the stream reports an error). */

@@ -67,6 +67,11 @@ def load():
         "hysco_cell_indices": (I, [P, P, P, P, P]),
         "hysco_ot_indices": (I, [P, P, P, D, P, P, P]),
         "hysco_eval_static": (I, [I64P, C.POINTER(C.c_double), I, D, D, I, P, P, P, P, P, P]),
+        "hysco_batch_create": (I, [I, P, C.POINTER(P)]),
+        "hysco_batch_destroy": (None, [P]),
+        "hysco_batch_solve": (I, [P, P, P, P, C.POINTER(Opts), P, P]),
+        "hysco_batch_tune": (I, [P, P, P, C.POINTER(Opts), P]),
+        "hysco_batch_schedule": (I, [P, C.POINTER(C.c_int32)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -1,0 +1,77 @@
+// Device-wide barrier fused with a deterministic reduction, for persistent cooperative kernels
+// (all blocks of the grid are co-resident).  See grid_allreduce.
+#pragma once
+
+#include "hysco_internal.cuh"
+
+namespace hysco {
+
+constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier fused with the sum of K floats over all threads of the grid.  Every thread
+// of every block calls it with its own values v and the barrier's generation gen (1, 2, ... within
+// a launch).  Layout of `sync`: an arrival counter (its own 128-byte line), then two slots of
+// gridDim.x x kSyncMaxK floats.  Block b stores its block sums at slot gen & 1, b * K, then adds one to
+// the counter with release semantics; the barrier of generation gen is complete when the counter
+// reaches gen * gridDim.x.  A block can overwrite a slot only two generations later, by which
+// time every block has read it.  Warp 0 then reads the sums of blocks first .. first + count - 1
+// (default: all) through L2 and adds them in a fixed order (lane l takes blocks first + l,
+// first + l + 32, ... in turn, then a fixed shuffle tree), in double-float.  On return v holds
+// those totals, identical in every thread of every block that passed the same range.
+// Returns false in every thread of the block when the spin budget ran out.
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
+                                               float* shf, df32* shd, int first = 0,
+                                               int count = -1) {
+  static_assert(K >= 1 && K <= kSyncMaxK, "grid_allreduce: K exceeds the slot width");
+  const int tid = threadIdx.x, nb = gridDim.x;
+  if (count < 0) count = nb;
+  unsigned* counter = sync;
+  float* slot = reinterpret_cast<float*>(sync + kSyncHeader) + (size_t)(gen & 1u) * nb * kSyncMaxK;
+  __shared__ int ok_sh;
+  block_sum<K, float>(v, shf);   // its barrier orders this block's phase writes before the release
+  if (tid == 0) {
+#pragma unroll
+    for (int i = 0; i < K; ++i) __stcg(slot + blockIdx.x * K + i, v[i]);
+    red_release_add(counter, 1u);
+    const unsigned target = gen * (unsigned)nb;
+    const long long t0 = clock64();
+    int ok = 1;
+    while ((int)(ld_acquire(counter) - target) < 0) {
+      if (clock64() - t0 > kBarrierSpinCycles) { ok = 0; break; }
+    }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  if (!ok_sh) return false;
+  if (tid < 32) {
+    df32 acc[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
+    for (int b = first + tid; b < first + count; b += 32)
+#pragma unroll
+      for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{__ldcg(slot + b * K + i), 0.f});
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) acc[i] = df_add(acc[i], df_shfl_down(acc[i], off));
+    if (tid == 0)
+#pragma unroll
+      for (int i = 0; i < K; ++i) shd[i] = acc[i];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < K; ++i) v[i] = shd[i].hi + shd[i].lo;
+  return true;
+}
+
+}  // namespace hysco

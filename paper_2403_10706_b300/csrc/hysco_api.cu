@@ -5,11 +5,13 @@
 // on the device by the last block of the kernel that produces the reduction, and later kernels
 // read it from the device state and exit immediately when their work is no longer needed.  No
 // host synchronisation happens inside a solve.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/hysco.h"
 #include "hysco_internal.cuh"
@@ -458,6 +460,7 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
   if (o->init) {
     if (int rc = init_ot_impl(h, Ip, Im, b_inout, o->ot_blur, o->ot_eps, nullptr, nullptr, s))
       return rc;
+    HYSCO_TRY(launch_feasible_start(g, b_inout, w, s));
   }
   for (int it = 0; it < o->gn_iters; ++it) {
     HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, nullptr, h->grad, h->dco, h->eco, h->invd,
@@ -480,21 +483,28 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
 
 bool same_opts(const hysco_opts& a, const hysco_opts& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
 
+// option values every solve accepts (the handle-dependent checks follow in the callers)
+int check_opts(const hysco_opts* o) {
+  if (!o) return HYSCO_EINVAL;
+  if (o->gn_iters < 0 || o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
+      o->ls_max_iters > kMaxTrials)
+    return HYSCO_EINVAL;
+  if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
+  if (o->no_graph < 0 || o->no_graph > 1) return HYSCO_EINVAL;
+  return HYSCO_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const hysco_opts* o,
                 double* stats, hysco_stream_t stream) {
-  if (!h || !o || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout)) return HYSCO_EINVAL;
-  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
-  if (o->gn_iters < 0 || o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
-      o->ls_max_iters > kMaxTrials)
+  if (!h || check_opts(o) || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout))
     return HYSCO_EINVAL;
-  if (o->precond != HYSCO_PC_JACOBI && o->precond != HYSCO_PC_COLUMN) return HYSCO_EINVAL;
+  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
   if (o->precond == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
-  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0)) return HYSCO_EINVAL;
-  if (o->no_graph < 0 || o->no_graph > 1) return HYSCO_EINVAL;
   PcgMode mode;
   if (pcg_mode(h, o->precond, o->pcg_path, &mode)) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
@@ -544,6 +554,334 @@ int hysco_last_status(hysco_t h, hysco_stream_t stream) {
   if (cudaMemcpy(&st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess)
     return HYSCO_ECUDA;
   return st.status;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batched solve: many handles (volume pairs of any sizes and PE axes) advance through the
+// Gauss-Newton loop together.  Per GN iteration the per-pair kernels (evaluation, gamma = 1 trial,
+// halvings, update) of different pairs run on concurrent branches, and the PCG of all pairs is
+// one cooperative launch of k_pcg_batched.  The fixed launch sequence is captured once in a CUDA
+// graph and replayed.  The schedule -- how many branches, and how the PCG grid's blocks are
+// shared among the pairs -- is picked by hysco_batch_tune by timing.
+// ------------------------------------------------------------------------------------------
+
+struct hysco_batch_ctx {
+  int n = 0;
+  int device = 0;
+  std::vector<hysco_ctx*> hs;
+  int grid = 0;                       // k_pcg_batched grid (co-resident blocks)
+  BatchPair* d_pairs = nullptr;
+  int* d_block_pair = nullptr;
+  unsigned* sync = nullptr;
+  int branches = 4;                   // schedule: concurrent branches of per-pair kernels
+  int policy = 0;                     // schedule: 0 blocks by field size, 1 the same with >= 2 each
+  cudaStream_t cap = nullptr;
+  std::vector<cudaStream_t> side;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> gIp, gIm;
+  std::vector<float*> gb;
+  std::vector<double*> gst;
+  hysco_opts gopts{};
+};
+
+namespace {
+
+constexpr int kMaxBranches = 8;
+
+void batch_free(hysco_batch_ctx* B) {
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->d_pairs) cudaFree(B->d_pairs);
+  if (B->d_block_pair) cudaFree(B->d_block_pair);
+  if (B->sync) cudaFree(B->sync);
+  for (cudaStream_t st : B->side) cudaStreamDestroy(st);
+  if (B->cap) cudaStreamDestroy(B->cap);
+  if (B->fork) cudaEventDestroy(B->fork);
+  for (cudaEvent_t e : B->join) cudaEventDestroy(e);
+}
+
+// blocks of the PCG grid per pair: proportional to the pitched field size (largest remainders),
+// at least `lo` each
+bool batch_shares(const hysco_batch_ctx* B, int lo, std::vector<int>& out) {
+  const int n = B->n, G = B->grid;
+  if ((long long)n * lo > G) return false;
+  double tot = 0.0;
+  for (const hysco_ctx* h : B->hs) tot += (double)h->g.nfp;
+  std::vector<double> want(n);
+  std::vector<int> idx(n);
+  int used = 0;
+  out.assign(n, lo);
+  used = n * lo;
+  const int rest = G - used;
+  std::vector<double> frac(n);
+  int given = 0;
+  for (int i = 0; i < n; ++i) {
+    want[i] = rest * (double)B->hs[i]->g.nfp / tot;
+    int k = (int)want[i];
+    out[i] += k;
+    given += k;
+    frac[i] = want[i] - k;
+    idx[i] = i;
+  }
+  // largest remainders, ties to the lower index
+  for (int r = 0; r < rest - given; ++r) {
+    int best = -1;
+    for (int i = 0; i < n; ++i)
+      if (best < 0 || frac[i] > frac[best]) best = i;
+    out[best] += 1;
+    frac[best] = -1.0;
+  }
+  return true;
+}
+
+int batch_layout(hysco_batch_ctx* B, int policy) {
+  std::vector<int> share;
+  if (!batch_shares(B, policy == 1 ? 2 : 1, share)) return HYSCO_EINVAL;
+  std::vector<BatchPair> pairs(B->n);
+  std::vector<int> block_pair(B->grid);
+  int b0 = 0;
+  for (int i = 0; i < B->n; ++i) {
+    hysco_ctx* h = B->hs[i];
+    pairs[i] = BatchPair{h->g, h->grad, h->x, h->r, h->z, h->p0, h->Hp, h->dco, h->eco, h->invd,
+                         h->st, b0, share[i]};
+    for (int k = 0; k < share[i]; ++k) block_pair[b0 + k] = i;
+    b0 += share[i];
+  }
+  if (cudaMemcpy(B->d_pairs, pairs.data(), sizeof(BatchPair) * B->n, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(B->d_block_pair, block_pair.data(), sizeof(int) * B->grid,
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return HYSCO_ECUDA;
+  B->policy = policy;
+  return HYSCO_OK;
+}
+
+// fork: branches wait for everything enqueued on s so far; join: s waits for every branch
+cudaError_t batch_fork(hysco_batch_ctx* B, cudaStream_t s) {
+  cudaError_t e = cudaEventRecord(B->fork, s);
+  for (int k = 0; k < B->branches && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(B->side[k], B->fork, 0);
+  return e;
+}
+cudaError_t batch_join(hysco_batch_ctx* B, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < B->branches && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(B->join[k], B->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, B->join[k], 0);
+  }
+  return e;
+}
+
+int enqueue_batch(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
+                  float* const* b, const hysco_opts* o, double* const* stats, cudaStream_t s) {
+  auto branch = [&](int i) { return B->side[i % B->branches]; };
+  HYSCO_TRY(batch_fork(B, s));
+  for (int i = 0; i < B->n; ++i) {
+    hysco_ctx* h = B->hs[i];
+    if (int rc = reset_state(h, branch(i))) return rc;
+    if (o->init) {
+      if (int rc = init_ot_impl(h, Ip[i], Im[i], b[i], o->ot_blur, o->ot_eps, nullptr, nullptr,
+                                branch(i)))
+        return rc;
+      HYSCO_TRY(launch_feasible_start(h->g, b[i], h->work(), branch(i)));
+    }
+  }
+  for (int it = 0; it < o->gn_iters; ++it) {
+    for (int i = 0; i < B->n; ++i) {
+      hysco_ctx* h = B->hs[i];
+      HYSCO_TRY(launch_eval(h->g, h->dtype, Ip[i], Im[i], b[i], nullptr, h->grad, h->dco, h->eco,
+                            h->invd, it, h->work(), branch(i)));
+    }
+    HYSCO_TRY(batch_join(B, s));
+    HYSCO_TRY(launch_pcg_batched(B->grid, B->d_pairs, B->d_block_pair, o->pcg_max_iters,
+                                 o->pcg_rtol, B->sync, s));
+    HYSCO_TRY(batch_fork(B, s));
+    for (int i = 0; i < B->n; ++i) {
+      hysco_ctx* h = B->hs[i];
+      const Geo& g = h->g;
+      Work w = h->work();
+      cudaStream_t bs = branch(i);
+      HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip[i], Im[i], b[i], h->x, h->grad, h->dco, h->eco,
+                                  h->invd, o->ls_max_iters, o->armijo_c1, w, bs));
+      for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
+        HYSCO_TRY(launch_linesearch(g, h->dtype, Ip[i], Im[i], b[i], h->x, h->grad, t0,
+                                    o->ls_max_iters, o->armijo_c1, w, bs));
+      HYSCO_TRY(launch_update(g, b[i], h->x, it, stats ? stats[i] : nullptr, w, bs));
+    }
+  }
+  HYSCO_TRY(batch_join(B, s));
+  return HYSCO_OK;
+}
+
+int batch_check(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
+                float* const* b, const hysco_opts* o, double* const* stats) {
+  if (!B || !Ip || !Im || !b || check_opts(o) || o->precond != HYSCO_PC_JACOBI)
+    return HYSCO_EINVAL;
+  for (int i = 0; i < B->n; ++i) {
+    hysco_ctx* h = B->hs[i];
+    if (check_img(h, Ip[i]) || check_img(h, Im[i]) || check_f32(b[i])) return HYSCO_EINVAL;
+    if (stats && stats[i] && !aligned(stats[i], 8)) return HYSCO_EINVAL;
+  }
+  return HYSCO_OK;
+}
+
+// capture the batch's launch sequence into a graph (exec out); false if capture is unavailable
+bool batch_capture(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
+                   float* const* b, const hysco_opts* o, double* const* stats,
+                   cudaGraphExec_t* out) {
+  cudaGraph_t graph = nullptr;
+  bool ok = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  int rc = ok ? enqueue_batch(B, Ip, Im, b, o, stats, B->cap) : HYSCO_ECUDA;
+  cudaError_t ec = cudaStreamEndCapture(B->cap, &graph);
+  ok = ok && rc == HYSCO_OK && ec == cudaSuccess && graph != nullptr;
+  if (ok) ok = cudaGraphInstantiate(out, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hysco_batch_create(int n, const hysco_t* handles, hysco_batch_t* out) {
+  if (!out || !handles || n < 1) return HYSCO_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i]) return HYSCO_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) return HYSCO_EINVAL;   // a pair's workspace is used once
+    if (handles[i]->device != handles[0]->device) return HYSCO_EINVAL;
+  }
+  int sms = 0;
+  const int per_sm = pcg_batched_blocks_per_sm(handles[0]->device);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, handles[0]->device) !=
+      cudaSuccess)
+    return HYSCO_ECUDA;
+  if (per_sm < 1 || n > sms * per_sm) return HYSCO_EINVAL;
+  auto* B = new (std::nothrow) hysco_batch_ctx;
+  if (!B) return HYSCO_ENOMEM;
+  B->n = n;
+  B->device = handles[0]->device;
+  B->hs.assign(handles, handles + n);
+  B->grid = sms * per_sm;
+  bool ok = cudaMalloc((void**)&B->d_pairs, sizeof(BatchPair) * n) == cudaSuccess &&
+            cudaMalloc((void**)&B->d_block_pair, sizeof(int) * B->grid) == cudaSuccess &&
+            cudaMalloc((void**)&B->sync, pcg_sync_words(B->grid) * sizeof(unsigned)) ==
+                cudaSuccess &&
+            cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < kMaxBranches; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    ok = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+    if (st) B->side.push_back(st);
+    if (ev) B->join.push_back(ev);
+  }
+  B->branches = n < 4 ? n : 4;
+  int rc = ok ? batch_layout(B, 0) : HYSCO_ENOMEM;
+  if (rc != HYSCO_OK) {
+    batch_free(B);
+    delete B;
+    return rc;
+  }
+  *out = B;
+  return HYSCO_OK;
+}
+
+void hysco_batch_destroy(hysco_batch_t B) {
+  if (!B) return;
+  batch_free(B);
+  delete B;
+}
+
+int hysco_batch_schedule(hysco_batch_t B, int32_t out[3]) {
+  if (!B || !out) return HYSCO_EINVAL;
+  out[0] = B->branches;
+  out[1] = B->policy;
+  out[2] = B->grid;
+  return HYSCO_OK;
+}
+
+int hysco_batch_solve(hysco_batch_t B, const void* const* Ip, const void* const* Im,
+                      float* const* b, const hysco_opts* o, double* const* stats,
+                      hysco_stream_t stream) {
+  if (int rc = batch_check(B, Ip, Im, b, o, stats)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (hysco_ctx* h : B->hs) h->have_lin = false;
+  std::vector<double*> st(B->n, nullptr);
+  if (stats)
+    for (int i = 0; i < B->n; ++i) st[i] = stats[i];
+  const bool cached = B->gexec && same_opts(B->gopts, *o) &&
+                      std::equal(B->gIp.begin(), B->gIp.end(), Ip) &&
+                      std::equal(B->gIm.begin(), B->gIm.end(), Im) &&
+                      std::equal(B->gb.begin(), B->gb.end(), b) && B->gst == st;
+  if (!o->no_graph && !cached) {
+    if (B->gexec) cudaGraphExecDestroy(B->gexec);
+    B->gexec = nullptr;
+    if (batch_capture(B, Ip, Im, b, o, stats, &B->gexec)) {
+      B->gIp.assign(Ip, Ip + B->n);
+      B->gIm.assign(Im, Im + B->n);
+      B->gb.assign(b, b + B->n);
+      B->gst = st;
+      B->gopts = *o;
+    }
+  }
+  if (!o->no_graph && B->gexec) {
+    HYSCO_TRY(cudaGraphLaunch(B->gexec, s));
+    return HYSCO_OK;
+  }
+  return enqueue_batch(B, Ip, Im, b, o, stats, s);
+}
+
+int hysco_batch_tune(hysco_batch_t B, const void* const* Ip, const void* const* Im,
+                     const hysco_opts* o, hysco_stream_t stream) {
+  if (!B || !Ip || !Im || check_opts(o) || o->precond != HYSCO_PC_JACOBI) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch fields: the trial solves must not touch the caller's fields
+  std::vector<float*> scratch(B->n, nullptr);
+  int rc = HYSCO_OK;
+  for (int i = 0; i < B->n && rc == HYSCO_OK; ++i)
+    if (cudaMalloc((void**)&scratch[i], (size_t)B->hs[i]->nfld * sizeof(float)) != cudaSuccess)
+      rc = HYSCO_ENOMEM;
+  if (rc == HYSCO_OK) rc = batch_check(B, Ip, Im, scratch.data(), o, nullptr);
+  hysco_opts t = *o;
+  t.init = 1;   // the trial solves start from the OT initialisation
+  t.gn_iters = o->gn_iters < 2 ? o->gn_iters : 2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == HYSCO_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    rc = HYSCO_ECUDA;
+  float best = 1e30f;
+  int best_br = B->branches, best_pol = B->policy;
+  for (int pol = 0; pol < 2 && rc == HYSCO_OK; ++pol) {
+    if (batch_layout(B, pol) != HYSCO_OK) continue;   // policy not feasible for this batch
+    for (int br = 1; br <= kMaxBranches && br <= B->n && rc == HYSCO_OK; br *= 2) {
+      B->branches = br;
+      cudaGraphExec_t ge = nullptr;
+      if (!batch_capture(B, Ip, Im, scratch.data(), &t, nullptr, &ge)) { rc = HYSCO_ECUDA; break; }
+      float ms = 0.f;
+      bool ok = cudaGraphLaunch(ge, s) == cudaSuccess && cudaEventRecord(e0, s) == cudaSuccess &&
+                cudaGraphLaunch(ge, s) == cudaSuccess && cudaGraphLaunch(ge, s) == cudaSuccess &&
+                cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      cudaGraphExecDestroy(ge);
+      if (!ok) { rc = HYSCO_ECUDA; break; }
+      if (ms < best) { best = ms; best_br = br; best_pol = pol; }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  for (float* p : scratch)
+    if (p) cudaFree(p);
+  B->branches = best_br;
+  if (int rl = batch_layout(B, best_pol)) rc = rc == HYSCO_OK ? rl : rc;
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);   // the cached graph used the old schedule
+  B->gexec = nullptr;
+  for (hysco_ctx* h : B->hs) h->have_lin = false;
+  return rc;
 }
 
 }  // extern "C"

@@ -76,6 +76,7 @@ struct DevState {
   // b + q) are those of the next iterate, whose J, D, S, P, ||grad|| are stashed here
   int coef_fresh, status_n;
   double Jn, Dn, Sn, Pn, gnorm_n;
+  float start_scale;          // factor applied to the OT start by the feasible-start rule
 };
 
 constexpr int kBlock = 256;   // threads per block of every kernel
@@ -383,6 +384,20 @@ cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, flo
                                   const float* dco, const float* eco, const float* invd,
                                   unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s);
+// k_pcg_batched.cu: the Jacobi PCG of many pairs in one cooperative launch.  Pair i is worked
+// on by blocks blk0 .. blk0 + nblk - 1 of the grid; its arrays are those of its handle.
+struct BatchPair {
+  Geo g;
+  const float* grad;          // right-hand side is -grad
+  float *x, *r, *z, *p, *Hp;
+  const float *dco, *eco, *invd;
+  DevState* st;
+  int blk0, nblk;
+};
+int pcg_batched_blocks_per_sm(int device);
+cudaError_t launch_pcg_batched(int grid, const BatchPair* pairs, const int* block_pair,
+                               int max_it, double rtol, unsigned* sync, cudaStream_t s);
+
 // the one-barrier-per-iteration form of the same PCG (r, w, q alternate between two buffers)
 int pcg_fused_grid(int device, int pe_axis);
 cudaError_t launch_pcg_fused(const Geo& g, int grid, const float* grad, float rhs_sign, float* x,
@@ -398,5 +413,7 @@ int ot_tile_width(int E);
 cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
                       int* kp, int* km, const Work& w, cudaStream_t s);
 cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s);
+// the GN loop's feasible start: b (caller layout) halved until max |delta| < 1
+cudaError_t launch_feasible_start(const Geo& g, float* b, const Work& w, cudaStream_t s);
 
 }  // namespace hysco

@@ -255,4 +255,68 @@ cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t 
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Feasible start of the GN loop (the barrier of Eq. 3 is +inf unless |delta| < 1 in every cell;
+// b = 0 is feasible): the OT field is halved until max |delta| < 1.  k_start_max: largest
+// |b_{j+1} - b_j| over all cells (exact: a maximum), the last block turns it into the factor
+// 2^-k; k_start_scale applies it.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock)
+k_start_max(Geo g, const float* __restrict__ b, float* partials, unsigned* counter,
+            DevState* st) {
+  __shared__ float wmax[kBlock / 32];
+  __shared__ int is_last;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * kSeg, j1 = min(j0 + kSeg, g.m);
+  float s = 0.f;
+  if (c < g.ncols) {
+    const int fb = col_base(c, g.inner, g.fld_ostride);
+    for (int j = j0; j < j1; ++j)
+      s = fmaxf(s, fabsf(__ldg(b + fb + (j + 1) * g.inner) - __ldg(b + fb + j * g.inner)));
+  }
+  for (int off = 16; off > 0; off >>= 1) s = fmaxf(s, __shfl_xor_sync(0xffffffffu, s, off));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = s;
+  __syncthreads();
+  const int nblk = gridDim.x * gridDim.y, bid = blockIdx.x + gridDim.x * blockIdx.y;
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int w = 0; w < kBlock / 32; ++w) m = fmaxf(m, wmax[w]);
+    partials[bid] = m;
+    __threadfence();
+    is_last = atomicAdd(counter, 1u) == (unsigned)(nblk - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  float m = 0.f;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) m = fmaxf(m, __ldcg(partials + i));
+  for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float smax = 0.f;
+    for (int w = 0; w < kBlock / 32; ++w) smax = fmaxf(smax, wmax[w]);
+    float f = 1.f;
+    for (int k = 0; k < 64 && smax * f >= 1.f; ++k) f *= 0.5f;
+    st->start_scale = f;
+    *counter = 0u;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock)
+k_start_scale(int nf, float* __restrict__ b, const DevState* st) {
+  const float f = st->start_scale;
+  if (f == 1.f) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x)
+    b[i] *= f;
+}
+
+cudaError_t launch_feasible_start(const Geo& g, float* b, const Work& w, cudaStream_t s) {
+  k_start_max<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(g.m, kSeg)), kBlock, 0, s>>>(
+      g, b, w.partials, w.counter, w.st);
+  k_start_scale<<<ceil_div(g.nf, kBlock * 4), kBlock, 0, s>>>(g.nf, b, w.st);
+  return cudaGetLastError();
+}
+
 }  // namespace hysco

@@ -188,3 +188,71 @@ class Hysco:
                                              C.c_void_p(km.data_ptr()), _stream(self.device)),
                    "hysco_ot_indices")
         return kp, km
+
+
+class HyscoBatch:
+    """Many Hysco handles (pairs of any sizes, PE axes and image dtypes, one device) solved
+    together by hysco_batch_solve.  Keeps its handles alive; argument marshalling only."""
+
+    def __init__(self, handles):
+        self.handles = list(handles)
+        if not self.handles:
+            raise ValueError("empty batch")
+        self.lib = _lib.load()
+        self.device = self.handles[0].device
+        n = len(self.handles)
+        arr = (C.c_void_p * n)(*[h._h.value for h in self.handles])
+        self._b = C.c_void_p()
+        _lib.check(self.lib.hysco_batch_create(n, arr, C.byref(self._b)), "hysco_batch_create")
+
+    def __del__(self):
+        b = getattr(self, "_b", None)
+        if b is not None and b.value:
+            self.lib.hysco_batch_destroy(b)
+            self._b = None
+
+    def _ptrs(self, items, check):
+        n = len(self.handles)
+        if len(items) != n:
+            raise ValueError(f"expected {n} tensors")
+        return (C.c_void_p * n)(*[check(h, t).value for h, t in zip(self.handles, items)])
+
+    def _opts(self, gn_iters, pcg_max_iters, ls_max_iters, init, ot_blur, pcg_rtol, armijo_c1,
+              ot_eps, graph):
+        return _lib.Opts(gn_iters, pcg_max_iters, ls_max_iters, _lib.PC_JACOBI, int(init),
+                         int(ot_blur), pcg_rtol, armijo_c1, ot_eps, 0, int(not graph))
+
+    def solve(self, Ips, Ims, bs=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10, init=None,
+              ot_blur=True, pcg_rtol=0.1, armijo_c1=1e-4, ot_eps=1e-3, stats=True, graph=True):
+        """Solve every pair; returns (fields, per-pair stats or None)."""
+        if init is None:
+            init = bs is None
+        bs = [h._new_fld() for h in self.handles] if bs is None else list(bs)
+        o = self._opts(gn_iters, pcg_max_iters, ls_max_iters, init, ot_blur, pcg_rtol, armijo_c1,
+                       ot_eps, graph)
+        sts = ([torch.full((max(gn_iters, 1), _lib.NSTATS), float("nan"), dtype=torch.float64,
+                           device=self.device) for _ in self.handles] if stats else None)
+        sp = None if sts is None else (C.c_void_p * len(sts))(*[t.data_ptr() for t in sts])
+        _lib.check(self.lib.hysco_batch_solve(
+            self._b, self._ptrs(Ips, lambda h, t: h._img(t, "Ip")),
+            self._ptrs(Ims, lambda h, t: h._img(t, "Im")),
+            self._ptrs(bs, lambda h, t: h._fld(t, "b")), C.byref(o), sp, _stream(self.device)),
+            "hysco_batch_solve")
+        return bs, (None if sts is None else [t[:gn_iters] for t in sts])
+
+    def tune(self, Ips, Ims, gn_iters=10, pcg_max_iters=10, ls_max_iters=10, ot_blur=True,
+             pcg_rtol=0.1, armijo_c1=1e-4, ot_eps=1e-3):
+        """Pick the schedule by timing short trial solves (synchronises); returns schedule()."""
+        o = self._opts(gn_iters, pcg_max_iters, ls_max_iters, True, ot_blur, pcg_rtol, armijo_c1,
+                       ot_eps, True)
+        _lib.check(self.lib.hysco_batch_tune(
+            self._b, self._ptrs(Ips, lambda h, t: h._img(t, "Ip")),
+            self._ptrs(Ims, lambda h, t: h._img(t, "Im")), C.byref(o), _stream(self.device)),
+            "hysco_batch_tune")
+        return self.schedule()
+
+    def schedule(self):
+        """(branches, block-share policy, PCG grid blocks) in use."""
+        out = (C.c_int32 * 3)()
+        _lib.check(self.lib.hysco_batch_schedule(self._b, out), "hysco_batch_schedule")
+        return tuple(out)

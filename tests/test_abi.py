@@ -80,3 +80,17 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(ImportError):
         _lib.load()
+
+
+def test_adjoint_and_batch_entry_points_reject_null_arguments(lib):
+    """Host-side validation returns before any device work (no GPU needed)."""
+    f = None
+    assert lib.hysco_correct_adjoint(None, f, f, f, f, f, f, f, f, None) == _lib.EINVAL
+    assert lib.hysco_image_grad(None, f, f, f, 1.0, f, f, None) == _lib.EINVAL
+    out = C.c_void_p()
+    assert lib.hysco_batch_create(0, None, C.byref(out)) == _lib.EINVAL
+    assert lib.hysco_batch_create(2, None, C.byref(out)) == _lib.EINVAL
+    assert lib.hysco_batch_solve(None, f, f, f, None, None, None) == _lib.EINVAL
+    assert lib.hysco_batch_tune(None, f, f, None, None) == _lib.EINVAL
+    assert lib.hysco_batch_schedule(None, (C.c_int32 * 3)()) == _lib.EINVAL
+    lib.hysco_batch_destroy(None)

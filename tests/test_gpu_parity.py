@@ -246,3 +246,33 @@ def test_graph_replay_equals_direct_launches(H):
         out.append((host(bb).copy(), host(ss).copy(), b, st))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[1][0], out[2][0])
     assert np.array_equal(out[0][1], out[1][1], equal_nan=True)
+
+
+INFEASIBLE = [dict(n_ellipsoids=4, n_blobs=3, semi_axes=(3.0, 9.0), smooth=0.5, n_gauss=4,
+                   sigma=(4.0, 7.0), spacing=(1.0, 1.0, 1.0), bmax=7.0, dims=(24, 40, 20),
+                   pe_dim=1, seed=6043, noise=0.03),
+              dict(n_ellipsoids=4, n_blobs=3, semi_axes=(3.0, 9.0), smooth=0.5, n_gauss=4,
+                   sigma=(4.0, 7.0), spacing=(1.0, 1.0, 1.0), bmax=7.0, dims=(40, 20, 24),
+                   pe_dim=0, seed=6036, noise=0.05)]
+
+
+@pytest.mark.parametrize("recipe", INFEASIBLE)
+def test_infeasible_ot_start_is_halved_like_the_oracle(H, orc, recipe):
+    """Blurred OT fields with max |delta| ~ 1.2 and 1.1: the solve starts from the OT field halved
+    until feasible (exact power-of-two factor, the oracle's), then follows the oracle."""
+    pr = ph.make_pair(recipe)
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    Ip, Im = dev(pr.Ip), dev(pr.Im)
+    b0 = host(h.init_ot(Ip, Im))
+    start, _ = h.solve(Ip, Im, gn_iters=0)
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    _, f = P.feasible_start(P.ot_init(pr.Ip, pr.Im, contract=True))
+    assert f < 1.0
+    assert np.array_equal(host(start), (f * b0).astype(np.float32))
+    b, st = h.solve(Ip, Im, gn_iters=5)
+    assert h.last_status() == 0
+    ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=5, contract=False)
+    assert status == 0
+    gs = host(st)
+    assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4), (gs[:, 0], rst[:, 0])
+    assert rel(host(b), ref) <= 1e-3
