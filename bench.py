@@ -125,8 +125,38 @@ def cpu_baseline(pr, args):
                       f"OT + {GN_ITERS[args.workload]} GN; single-threaded FP64 C oracle"}
 
 
+# ------------------------------------------------------------------------------------------
+# multi-rank host logic (replicas: every rank solves its own pairs, no data-path collective)
+# ------------------------------------------------------------------------------------------
+
+def rank_env():
+    """(world size, rank, local rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def rank_seed(workload, rank):
+    """Seed of the pair a rank solves: each rank gets its own problem."""
+    return ph.RECIPES[workload]["seed"] + 17 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself when not distributed)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, seconds):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = rank_env()
     if rank != 0:
         return
     pr = ph.make_pair(args.workload)
@@ -337,9 +367,7 @@ def run_ours(args):
     from paper_2403_10706_b300.hysco import Hysco
 
     b.build()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -348,7 +376,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    pr = ph.make_pair(args.workload, seed=ph.RECIPES[args.workload]["seed"] + 17 * rank)
+    pr = ph.make_pair(args.workload, seed=rank_seed(args.workload, rank))
     gn = GN_ITERS[args.workload]
     h = Hysco(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA, device=dev)
     Ip = torch.from_numpy(pr.Ip).to(dev)
@@ -380,12 +408,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     ms = [s0.elapsed_time(s1) for s0, s1 in evs]
-    total_s = sum(ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * args.steps / total_s
+    total_s = max_over_ranks(sum(ms) / 1e3, dist, dev)
+    value = job_throughput(world, args.steps, total_s)
 
     # end to end through the public API: pinned host images in, field out, every step
     hIp = torch.from_numpy(pr.Ip).pin_memory()
@@ -403,12 +427,8 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_s = sum(e2e_ms) / 1e3
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * len(e2e_ms) / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
+    e2e = {"value": job_throughput(world, len(e2e_ms), e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": int(Ip.numel() * 4 + Im.numel() * 4),
            "d2h_bytes_per_step": int(b_out.numel() * 4)}
 
