@@ -172,6 +172,15 @@ int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, 
 int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout,
                 const hysco_opts* opts, double* stats, hysco_stream_t stream);
 
+/* Self-test of failure detection in the persistent kernels' device-wide barrier (the one that
+ * separates their phases): launches a cooperative grid of `grid` (<= 64) blocks of which block
+ * `missing_block` never arrives (-1: all arrive); the others wait at most `spin_cycles` clock
+ * cycles, then give up.  Returns HYSCO_ETIMEOUT when the waits ran out, HYSCO_OK when the barrier
+ * completed with the correct grid-wide sum, HYSCO_ENONFINITE for a wrong sum, HYSCO_EINVAL for
+ * bad arguments.  Synchronises `stream`; the CUDA context stays usable either way. */
+int hysco_selftest_barrier(int grid, int missing_block, int64_t spin_cycles,
+                           hysco_stream_t stream);
+
 /* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):

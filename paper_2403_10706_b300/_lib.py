@@ -72,6 +72,7 @@ def load():
         "hysco_batch_solve": (I, [P, P, P, P, C.POINTER(Opts), P, P]),
         "hysco_batch_tune": (I, [P, P, P, C.POINTER(Opts), P]),
         "hysco_batch_schedule": (I, [P, C.POINTER(C.c_int32)]),
+        "hysco_selftest_barrier": (I, [I, I, C.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -20,18 +20,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // Device-wide barrier fused with the sum of K floats over all threads of the grid.  Every thread
 // of every block calls it with its own values v and the barrier's generation gen (1, 2, ... within
 // a launch).  Layout of `sync`: an arrival counter (its own 128-byte line), then two slots of
-// gridDim.x x kSyncMaxK floats.  Block b stores its block sums at slot gen & 1, b * K, then adds one to
-// the counter with release semantics; the barrier of generation gen is complete when the counter
+// gridDim.x x kSyncMaxK floats.  Block b stores its block sums at slot gen & 1, b * K, then
+// adds one to the counter with release semantics; the barrier of generation gen is complete when
+// the counter
 // reaches gen * gridDim.x.  A block can overwrite a slot only two generations later, by which
 // time every block has read it.  Warp 0 then reads the sums of blocks first .. first + count - 1
 // (default: all) through L2 and adds them in a fixed order (lane l takes blocks first + l,
 // first + l + 32, ... in turn, then a fixed shuffle tree), in double-float.  On return v holds
 // those totals, identical in every thread of every block that passed the same range.
-// Returns false in every thread of the block when the spin budget ran out.
+// Returns false in every thread of the block when the spin budget (clock cycles) ran out.
 template <int K>
 __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
                                                float* shf, df32* shd, int first = 0,
-                                               int count = -1) {
+                                               int count = -1,
+                                               long long budget = kBarrierSpinCycles) {
   static_assert(K >= 1 && K <= kSyncMaxK, "grid_allreduce: K exceeds the slot width");
   const int tid = threadIdx.x, nb = gridDim.x;
   if (count < 0) count = nb;
@@ -47,7 +49,7 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
     const long long t0 = clock64();
     int ok = 1;
     while ((int)(ld_acquire(counter) - target) < 0) {
-      if (clock64() - t0 > kBarrierSpinCycles) { ok = 0; break; }
+      if (clock64() - t0 > budget) { ok = 0; break; }
     }
     ok_sh = ok;
   }

@@ -884,4 +884,32 @@ int hysco_batch_tune(hysco_batch_t B, const void* const* Ip, const void* const* 
   return rc;
 }
 
+int hysco_selftest_barrier(int grid, int missing_block, int64_t spin_cycles,
+                           hysco_stream_t stream) {
+  if (grid < 1 || grid > 64 || missing_block < -1 || missing_block >= grid || spin_cycles < 1 ||
+      spin_cycles > 4000000000LL)
+    return HYSCO_EINVAL;
+  int dev = 0, coop = 0, per_sm = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return HYSCO_ECUDA;
+  per_sm = pcg_batched_blocks_per_sm(dev);
+  if (!coop || grid > sms * per_sm) return HYSCO_EINVAL;   // every block must be co-resident
+  unsigned* sync = nullptr;
+  int* flag = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = HYSCO_ECUDA, host_flag = 0;
+  if (cudaMalloc((void**)&sync, pcg_sync_words(grid) * sizeof(unsigned)) == cudaSuccess &&
+      cudaMalloc((void**)&flag, sizeof(int)) == cudaSuccess &&
+      launch_barrier_selftest(grid, missing_block, (long long)spin_cycles, sync, flag, s) ==
+          cudaSuccess &&
+      cudaMemcpyAsync(&host_flag, flag, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+      cudaStreamSynchronize(s) == cudaSuccess)
+    rc = host_flag == 1 ? HYSCO_ETIMEOUT : (host_flag == 0 ? HYSCO_OK : HYSCO_ENONFINITE);
+  if (sync) cudaFree(sync);
+  if (flag) cudaFree(flag);
+  return rc;
+}
+
 }  // extern "C"

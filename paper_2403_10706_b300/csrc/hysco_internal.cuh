@@ -395,6 +395,8 @@ struct BatchPair {
   int blk0, nblk;
 };
 int pcg_batched_blocks_per_sm(int device);
+cudaError_t launch_barrier_selftest(int grid, int missing, long long budget, unsigned* sync,
+                                    int* flag, cudaStream_t s);
 cudaError_t launch_pcg_batched(int grid, const BatchPair* pairs, const int* block_pair,
                                int max_it, double rtol, unsigned* sync, cudaStream_t s);
 

@@ -126,6 +126,33 @@ k_pcg_batched(const BatchPair* __restrict__ pairs, const int* __restrict__ block
   }
 }
 
+// Self-test of the barrier's timeout path: every block but `missing` takes part in one
+// grid_allreduce with a spin budget of `budget` cycles; block `missing` (if any) returns at once,
+// so the others give up and raise *flag.  Bounded: the launch always ends.
+__global__ void __launch_bounds__(kBlock)
+k_barrier_selftest(unsigned* sync, int missing, long long budget, int* flag) {
+  __shared__ float shf[32];
+  __shared__ df32 shd[32];
+  if ((int)blockIdx.x == missing) return;
+  float v[1] = {1.f};
+  if (!grid_allreduce<1>(v, sync, 1u, shf, shd, 0, -1, budget)) {
+    if (threadIdx.x == 0) atomicExch(flag, 1);
+    return;
+  }
+  if (threadIdx.x == 0 && blockIdx.x == 0 && v[0] != (float)(gridDim.x * blockDim.x))
+    atomicExch(flag, 2);   // the sum over all threads is wrong
+}
+
+cudaError_t launch_barrier_selftest(int grid, int missing, long long budget, unsigned* sync,
+                                    int* flag, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(grid) * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&sync, &missing, &budget, &flag};
+  return cudaLaunchCooperativeKernel((void*)k_barrier_selftest, dim3(grid), dim3(kBlock), args, 0,
+                                     s);
+}
+
 int pcg_batched_blocks_per_sm(int device) {
   int coop = 0, per_sm = 0;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)

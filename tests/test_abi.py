@@ -94,3 +94,9 @@ def test_adjoint_and_batch_entry_points_reject_null_arguments(lib):
     assert lib.hysco_batch_tune(None, f, f, None, None) == _lib.EINVAL
     assert lib.hysco_batch_schedule(None, (C.c_int32 * 3)()) == _lib.EINVAL
     lib.hysco_batch_destroy(None)
+
+
+def test_barrier_selftest_rejects_bad_arguments_before_any_device_call(lib):
+    for grid, missing, cycles in ((0, -1, 1000), (65, -1, 1000), (8, 8, 1000), (8, -2, 1000),
+                                  (8, -1, 0), (8, -1, 5_000_000_000)):
+        assert lib.hysco_selftest_barrier(grid, missing, cycles, None) == _lib.EINVAL
