@@ -17,6 +17,8 @@
 //   d_k = (dr_{k-1}/db_k)^2 + (dr_k/db_k)^2 + psi_{k-1} + psi_k,   e_k = dr_k/db_k * dr_k/db_{k+1} - psi_k
 // with psi = beta/2 phi''(delta); H v = vol [e_{k-1} v_{k-1} + d_k v_k + e_k v_{k+1} + alpha (L v)_k],
 // and the Jacobi preconditioner is 1 / (vol [d_k + alpha L_kk]).
+#include <algorithm>
+
 #include "eval_common.cuh"
 
 namespace hysco {
@@ -55,10 +57,14 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
   }
   const int inner = g.inner, m = g.m;
   const int lane = threadIdx.x & 31;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
+  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f, accGQ = 0.f;
+  // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+  int c = (item % ncb) * kBlock + threadIdx.x;
   const bool act = c < g.ncols;
   c = act ? c : g.ncols - 1;
-  const int k0 = blockIdx.y * SEG;
+  const int k0 = (item / ncb) * SEG;
   const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
   const TI* Ipc = Ip + ib;
   const TI* Imc = Im + ib;
@@ -91,7 +97,6 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     eAp[j] = (lane == 31 && hasAp) ? fld(nb.Ap + o, nq.Ap + op) : 0.f;
   }
   // grad^T q with the gradient at b (trial only), loaded before this thread overwrites it
-  float accGQ = 0.f;
   if (TRIAL) {
 #pragma unroll
     for (int j = 0; j < SEG; ++j) {
@@ -108,7 +113,6 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     pr = cv ? cl.r : 0.f; pjr = cv ? cl.jr : 0.f;
     pdphi = cv ? cl.dphi : 0.f; ppsi = cv ? cl.psi : 0.f;
   }
-  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     const int k = k0 + j;
@@ -144,6 +148,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     }
     pr = cr; pjr = cjr; pdphi = cdphi; ppsi = cpsi;
   }
+  }   // work items
   float v[5] = {accD, accS, accP, accG, accGQ};
   double tot[5];
   if (grid_sum<5>(v, partials, counter, tot)) {
@@ -194,10 +199,16 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
              float* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->ls_done) return;
   const int inner = g.inner, m = g.m;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
+  float aD[T], aS[T], aP[T], agq = 0.f;
+#pragma unroll
+  for (int t = 0; t < T; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; }
+  // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+  int c = (item % ncb) * kBlock + threadIdx.x;
   const bool act = c < g.ncols;
   c = act ? c : g.ncols - 1;
-  const int k0 = blockIdx.y * SEG;
+  const int k0 = (item / ncb) * SEG;
   const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
   const TI* Ipc = Ip + ib;
   const TI* Imc = Im + ib;
@@ -218,17 +229,14 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     bAp[j] = __ldg(b + nb.Ap + o); qAp[j] = __ldg(q + nq.Ap + op);
     bBp[j] = __ldg(b + nb.Bp + o); qBp[j] = __ldg(q + nq.Bp + op);
   }
-  float agq = 0.f;
   if (t0 == 0) {
 #pragma unroll
     for (int j = 0; j < SEG; ++j)
       if (act && k0 + j <= m) agq += __ldg(grad + pb + (k0 + j) * g.psP) * qw[j];
   }
-  float aD[T], aS[T], aP[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     float gam = ldexpf(1.0f, -(t0 + t));
-    aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f;
     float x[SEG + 1];
 #pragma unroll
     for (int j = 0; j <= SEG; ++j) x[j] = fmaf(gam, qw[j], bw[j]);
@@ -244,6 +252,7 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
       aS[t] += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
     }
   }
+  }   // work items
   float v[3 * T + 1];
   double tot[3 * T + 1];
 #pragma unroll
@@ -361,6 +370,21 @@ static dim3 march_grid(const Geo& g, int nodes) {
   return dim3(ceil_div(g.ncols, kBlock), ceil_div(nodes, kSeg));
 }
 
+// grid of the grid-stride march kernels (eval, trial, halvings): per_sm blocks per SM (their
+// occupancy: 4 for the evaluations at 64 registers, 2 for the 9-trial halving pass at 128), at
+// most one per work item.  An early-returning launch then costs one short wave.
+static dim3 resident_grid(const Geo& g, int per_sm = 4) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      sms = 148;
+  }
+  const int items = ceil_div(g.ncols, kBlock) * ceil_div(g.E, kSeg);
+  return dim3(std::min(items, sms * per_sm));
+}
+
 #define HYSCO_DISPATCH(dtype, T, ...)                                                  \
   switch (dtype) {                                                                     \
     case 0: { using T = float; __VA_ARGS__; break; }                                   \
@@ -372,7 +396,7 @@ cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
                         const Work& w, cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
-    (k_eval<T, kSeg, false><<<march_grid(g, g.E), kBlock, 0, s>>>(
+    (k_eval<T, kSeg, false><<<resident_grid(g), kBlock, 0, s>>>(
         g, (const T*)Ip, (const T*)Im, b, nullptr, grad, grad_p, dco, eco, invd, it, 0, 0.0,
         w.partials, w.counter, w.st)))
   return cudaGetLastError();
@@ -383,7 +407,7 @@ cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const voi
                               float* eco, float* invd, int ls_max, double c1, const Work& w,
                               cudaStream_t s) {
   HYSCO_DISPATCH(dtype, T,
-    (k_eval<T, kSeg, true><<<march_grid(g, g.E), kBlock, 0, s>>>(
+    (k_eval<T, kSeg, true><<<resident_grid(g), kBlock, 0, s>>>(
         g, (const T*)Ip, (const T*)Im, b, q, nullptr, grad_p, dco, eco, invd, 0, ls_max, c1,
         w.partials, w.counter, w.st)))
   return cudaGetLastError();
@@ -394,12 +418,12 @@ cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const voi
                               int ls_max, double c1, const Work& w, cudaStream_t s) {
   if (t0 == 0) {
     HYSCO_DISPATCH(dtype, T,
-      (k_linesearch<T, kSeg, 1><<<march_grid(g, g.E), kBlock, 0, s>>>(
+      (k_linesearch<T, kSeg, 1><<<resident_grid(g), kBlock, 0, s>>>(
           g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
           w.st)))
   } else {
     HYSCO_DISPATCH(dtype, T,
-      (k_linesearch<T, kSeg, kLsBatch><<<march_grid(g, g.E), kBlock, 0, s>>>(
+      (k_linesearch<T, kSeg, kLsBatch><<<resident_grid(g, 2), kBlock, 0, s>>>(
           g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
           w.st)))
   }
