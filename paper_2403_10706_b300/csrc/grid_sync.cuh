@@ -76,4 +76,88 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
   return true;
 }
 
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_relaxed_add(unsigned* p, unsigned v) {
+  asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+constexpr int kTagWordsPerLane = 12;   // grids of up to 384 blocks
+
+// The barrier + sum of one float per thread for a phase after which no block reads another
+// block's memory writes: only the sums cross blocks, so no release / acquire ordering is needed
+// and the arrival does not wait for the block's outstanding stores.  Block b's sum travels as a
+// 64-bit word (gen << 32 | bits) in the tagged-word area of `sync` (after the float slots), the
+// arrival count uses the same counter as grid_allreduce (relaxed).  Warp 0 reads all words; a
+// word not yet carrying this generation (its store still in flight when the count completed) is
+// read again.  Same fixed order and double-float sums as grid_allreduce.  Requires gridDim.x <=
+// 32 * kTagWordsPerLane.  Returns false in every thread of the block when the budget ran out.
+__device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* sync, unsigned gen,
+                                                         float* shf, df32* shd,
+                                                         long long budget = kBarrierSpinCycles) {
+  const int tid = threadIdx.x, nb = gridDim.x;
+  unsigned* counter = sync;
+  unsigned long long* words = reinterpret_cast<unsigned long long*>(
+      sync + kSyncHeader + 2 * (size_t)nb * kSyncMaxK) + (size_t)(gen & 1u) * nb;
+  __shared__ int ok_sh, ok2_sh;
+  float vv[1] = {v};
+  block_sum<1, float>(vv, shf);
+  if (tid == 0) {
+    st_relaxed_u64(words + blockIdx.x, ((unsigned long long)gen << 32) | __float_as_uint(vv[0]));
+    red_relaxed_add(counter, 1u);
+    const unsigned target = gen * (unsigned)nb;
+    const long long t0 = clock64();
+    int ok = 1;
+    while ((int)(ld_relaxed_u32(counter) - target) < 0) {
+      if (clock64() - t0 > budget) { ok = 0; break; }
+    }
+    ok_sh = ok;
+  }
+  __syncthreads();
+  if (!ok_sh) return false;
+  if (tid < 32) {
+    unsigned long long w[kTagWordsPerLane];
+    unsigned need = 0;
+#pragma unroll
+    for (int j = 0; j < kTagWordsPerLane; ++j) {
+      const int b = tid + 32 * j;
+      w[j] = b < nb ? ld_relaxed_u64(words + b) : 0ull;
+      if (b < nb && (unsigned)(w[j] >> 32) != gen) need |= 1u << j;
+    }
+    const long long t0 = clock64();
+    bool ok = true;
+    while (need) {
+#pragma unroll
+      for (int j = 0; j < kTagWordsPerLane; ++j)
+        if (need & (1u << j)) {
+          w[j] = ld_relaxed_u64(words + tid + 32 * j);
+          if ((unsigned)(w[j] >> 32) == gen) need &= ~(1u << j);
+        }
+      if (need && clock64() - t0 > budget) { ok = false; break; }
+    }
+    df32 acc{0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < kTagWordsPerLane; ++j)
+      if (tid + 32 * j < nb) acc = df_add(acc, df32{__uint_as_float((unsigned)w[j]), 0.f});
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = df_add(acc, df_shfl_down(acc, off));
+    if (tid == 0) { shd[0] = acc; ok2_sh = ok ? 1 : 0; }
+  }
+  __syncthreads();
+  if (!ok2_sh) return false;
+  v = shd[0].hi + shd[0].lo;
+  return true;
+}
+
 }  // namespace hysco

@@ -24,6 +24,8 @@
 // records an error in the device state and returns; every other block then also times out at
 // its next barrier, so the launch always ends.
 
+#include <algorithm>
+
 #include "grid_sync.cuh"
 
 namespace hysco {
@@ -105,8 +107,9 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     float acc = 0.f;
     for (int t = gtid; t < n4; t += T) acc += hv_group<P, true>(g, t, a.z, pv_, a.Hp, a.dco, a.eco, fb, first);
     {
+      // only p.Hp crosses blocks here (phase B reads the thread's own groups)
       float t1[1] = {acc};
-      if (!grid_allreduce<1>(t1, a.sync, ++gen, shf, shd)) { timed_out(); return; }
+      if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd)) { timed_out(); return; }
       if (!(t1[0] > 0.f)) { done = true; break; }
       const float al = rho / t1[0];
       // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
@@ -115,7 +118,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
         float4 pv[kPcgUnroll], hv[kPcgUnroll], dv[kPcgUnroll], rv[kPcgUnroll], xv[kPcgUnroll];
 #pragma unroll
         for (int u = 0; u < kPcgUnroll; ++u) {
-          int j = min(j0 + u * T, n4 - 1);
+          // out-of-range slots re-read this thread's own group j0 (never another thread's)
+          int j = j0 + u * T < n4 ? j0 + u * T : j0;
           pv[u] = reinterpret_cast<const float4*>(pv_)[j];
           hv[u] = reinterpret_cast<const float4*>(a.Hp)[j];
           dv[u] = __ldg(reinterpret_cast<const float4*>(a.invd) + j);
@@ -409,7 +413,7 @@ static int grid_for(int device) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kBlock, 0) !=
       cudaSuccess)
     return 0;
-  return sms * per_sm;
+  return std::min(sms * per_sm, 32 * kTagWordsPerLane);
 }
 
 template <int P>
