@@ -93,7 +93,7 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   return v;
 }
 
-constexpr int kTagWordsPerLane = 12;   // grids of up to 384 blocks
+constexpr int kTagWordsPerLane = kTagWordsPerLaneHost;   // block ranges of up to 512 blocks
 
 // The barrier + sum of one float per thread for a phase after which no block reads another
 // block's memory writes: only the sums cross blocks, so no release / acquire ordering is needed
@@ -101,12 +101,15 @@ constexpr int kTagWordsPerLane = 12;   // grids of up to 384 blocks
 // 64-bit word (gen << 32 | bits) in the tagged-word area of `sync` (after the float slots), the
 // arrival count uses the same counter as grid_allreduce (relaxed).  Warp 0 reads all words; a
 // word not yet carrying this generation (its store still in flight when the count completed) is
-// read again.  Same fixed order and double-float sums as grid_allreduce.  Requires gridDim.x <=
-// 32 * kTagWordsPerLane.  Returns false in every thread of the block when the budget ran out.
+// read again.  Same fixed order and double-float sums as grid_allreduce, over the blocks first ..
+// first + count - 1 (default: all).  Requires count <= 32 * kTagWordsPerLane.  Returns false in
+// every thread of the block when the budget ran out.
 __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* sync, unsigned gen,
-                                                         float* shf, df32* shd,
+                                                         float* shf, df32* shd, int first = 0,
+                                                         int count = -1,
                                                          long long budget = kBarrierSpinCycles) {
   const int tid = threadIdx.x, nb = gridDim.x;
+  if (count < 0) count = nb;
   unsigned* counter = sync;
   unsigned long long* words = reinterpret_cast<unsigned long long*>(
       sync + kSyncHeader + 2 * (size_t)nb * kSyncMaxK) + (size_t)(gen & 1u) * nb;
@@ -132,8 +135,8 @@ __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* syn
 #pragma unroll
     for (int j = 0; j < kTagWordsPerLane; ++j) {
       const int b = tid + 32 * j;
-      w[j] = b < nb ? ld_relaxed_u64(words + b) : 0ull;
-      if (b < nb && (unsigned)(w[j] >> 32) != gen) need |= 1u << j;
+      w[j] = b < count ? ld_relaxed_u64(words + first + b) : 0ull;
+      if (b < count && (unsigned)(w[j] >> 32) != gen) need |= 1u << j;
     }
     const long long t0 = clock64();
     bool ok = true;
@@ -141,7 +144,7 @@ __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* syn
 #pragma unroll
       for (int j = 0; j < kTagWordsPerLane; ++j)
         if (need & (1u << j)) {
-          w[j] = ld_relaxed_u64(words + tid + 32 * j);
+          w[j] = ld_relaxed_u64(words + first + tid + 32 * j);
           if ((unsigned)(w[j] >> 32) == gen) need &= ~(1u << j);
         }
       if (need && clock64() - t0 > budget) { ok = false; break; }
@@ -149,7 +152,7 @@ __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* syn
     df32 acc{0.f, 0.f};
 #pragma unroll
     for (int j = 0; j < kTagWordsPerLane; ++j)
-      if (tid + 32 * j < nb) acc = df_add(acc, df32{__uint_as_float((unsigned)w[j]), 0.f});
+      if (tid + 32 * j < count) acc = df_add(acc, df32{__uint_as_float((unsigned)w[j]), 0.f});
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc = df_add(acc, df_shfl_down(acc, off));
     if (tid == 0) { shd[0] = acc; ok2_sh = ok ? 1 : 0; }

@@ -761,12 +761,14 @@ int hysco_batch_create(int n, const hysco_t* handles, hysco_batch_t* out) {
       cudaSuccess)
     return HYSCO_ECUDA;
   if (per_sm < 1 || n > sms * per_sm) return HYSCO_EINVAL;
+  const int grid = std::min(sms * per_sm, 32 * kTagWordsPerLaneHost);
+  if (n > grid) return HYSCO_EINVAL;
   auto* B = new (std::nothrow) hysco_batch_ctx;
   if (!B) return HYSCO_ENOMEM;
   B->n = n;
   B->device = handles[0]->device;
   B->hs.assign(handles, handles + n);
-  B->grid = sms * per_sm;
+  B->grid = grid;
   bool ok = cudaMalloc((void**)&B->d_pairs, sizeof(BatchPair) * n) == cudaSuccess &&
             cudaMalloc((void**)&B->d_block_pair, sizeof(int) * B->grid) == cudaSuccess &&
             cudaMalloc((void**)&B->sync, pcg_sync_words(B->grid) * sizeof(unsigned)) ==

@@ -378,6 +378,7 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
 int pcg_persistent_grid(int device, int pe_axis);
 constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arrival counter's line)
 constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused reduction)
+constexpr int kTagWordsPerLaneHost = 16;   // grid_allreduce_unordered's block-range limit / 32
 // counter line, two float slots of kSyncMaxK per block, two slots of one tagged 64-bit word per block
 inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid + 4ull * (size_t)grid; }
 cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,

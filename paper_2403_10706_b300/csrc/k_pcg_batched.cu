@@ -77,7 +77,11 @@ k_pcg_batched(const BatchPair* __restrict__ pairs, const int* __restrict__ block
     if (!done)
       for (int t = gtid; t < n4; t += T)
         acc[0] += hv_any<true>(g, t, sp.z, sp.p, sp.Hp, sp.dco, sp.eco, beta, first_it);
-    if (!grid_allreduce<1>(acc, sync, ++gen, shf, shd, first, count)) { timed_out(); return; }
+    // only p.Hp crosses blocks here (phase B reads the thread's own groups)
+    if (!grid_allreduce_unordered(acc[0], sync, ++gen, shf, shd, first, count)) {
+      timed_out();
+      return;
+    }
     float al = 0.f;
     if (!done) {
       if (!(acc[0] > 0.f)) done = true;
