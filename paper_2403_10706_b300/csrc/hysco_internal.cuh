@@ -198,16 +198,30 @@ __device__ bool grid_sum(float (&v)[K], float* partials, unsigned* counter, doub
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  df32 acc[K];
+  // value i is summed by warp i % nwarps: lane l takes blocks l, l + 32, ... in order (eight
+  // loads in flight, then their sums), then a fixed shuffle tree; double-float throughout
+  const int warp = tid >> 5, lane = tid & 31, nwarps = block_threads() >> 5;
+  for (int i = warp; i < K; i += nwarps) {
+    df32 acc{0.f, 0.f};
+    for (int b0 = lane; b0 < nblk; b0 += 32 * 8) {
+      float x[8];
 #pragma unroll
-  for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
-  for (int b = tid; b < nblk; b += block_threads())
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + 32 * u;
+        x[u] = b < nblk ? __ldcg(partials + (long long)b * K + i) : 0.f;
+      }
 #pragma unroll
-    for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{__ldcg(partials + (long long)b * K + i), 0.f});
-  block_sum_df<K>(acc, shd);
+      for (int u = 0; u < 8; ++u)
+        if (b0 + 32 * u < nblk) acc = df_add(acc, df32{x[u], 0.f});
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = df_add(acc, df_shfl_down(acc, off));
+    if (lane == 0) shd[i] = acc;
+  }
+  __syncthreads();
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) tot[i] = (double)acc[i].hi + (double)acc[i].lo;
+    for (int i = 0; i < K; ++i) tot[i] = (double)shd[i].hi + (double)shd[i].lo;
     *counter = 0u;
     return true;
   }
