@@ -66,6 +66,10 @@ def lib():
         _lib.orc_correct_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P, P, P]
         _lib.orc_image_grad.restype = C.c_int64
         _lib.orc_image_grad.argtypes = [P, P, P, P, C.c_int, P, P]
+        _lib.orc_theta_dots.argtypes = [P, P, P, P, C.c_int, P, P]
+        _lib.orc_mixed_image_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P]
+        _lib.orc_solve_adjoint.argtypes = [P, P, P, P, C.c_int, P, C.c_int, C.c_double, P, P, P,
+                                           P]
         _lib.orc_feasible_start.restype = C.c_double
         _lib.orc_feasible_start.argtypes = [P, P]
     return _lib
@@ -139,6 +143,30 @@ class Problem:
         lib().orc_image_grad(C.byref(self.g), _p(Ip), _p(Im), _p(b), int(contract), _p(dIp),
                              _p(dIm))
         return dIp, dIm
+
+    def theta_dots(self, Ip, Im, b, v, contract=True):
+        """(v^T dg/dalpha, v^T dg/dbeta) at b, g the gradient of J."""
+        out = np.zeros(2)
+        lib().orc_theta_dots(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                             int(contract), _p(_f64(v)), _p(out))
+        return out[0], out[1]
+
+    def mixed_image_adjoint(self, Ip, Im, b, v, contract=True):
+        """(d(v^T g)/dI+, d(v^T g)/dI-) at b, v fixed."""
+        dIp, dIm = np.zeros(self.dims), np.zeros(self.dims)
+        lib().orc_mixed_image_adjoint(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                      int(contract), _p(_f64(v)), _p(dIp), _p(dIm))
+        return dIp, dIm
+
+    def solve_adjoint(self, Ip, Im, b, dLdb, max_it=200, rtol=1e-10, contract=True):
+        """Implicit differentiation at a solution b: returns (v, dL/dI+, dL/dI-, dL/dalpha,
+        dL/dbeta, PCG iterations) with H v = dL/db."""
+        v = np.zeros(self.fdims)
+        dIp, dIm, dth = np.zeros(self.dims), np.zeros(self.dims), np.zeros(2)
+        it = lib().orc_solve_adjoint(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                     int(contract), _p(_f64(dLdb)), int(max_it), float(rtol),
+                                     _p(v), _p(dIp), _p(dIm), _p(dth))
+        return v, dIp, dIm, dth[0], dth[1], it
 
     def feasible_start(self, b):
         """The solve's start rule for an OT field: returns (b scaled by 2^-k, 2^-k) with the

@@ -976,3 +976,114 @@ int orc_pcg(const orc_geom* g, const float* Ip, const float* Im, const double* b
   lin_free(&lin);
   return it;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* implicit differentiation through the solve                                                  */
+/* ------------------------------------------------------------------------------------------ */
+
+/* At a stationary point b* of J the gradient g(b*; theta) = 0 defines b*(theta) for every input
+ * theta (alpha, beta, the two images).  For a loss L(b*), the implicit function theorem with the
+ * Gauss-Newton Hessian H of Sec. 2.3.1 standing in for the Hessian of J gives
+ *   dL/dtheta = -(dg/dtheta)^T v,   H v = dL/db*.
+ * The pieces, for a given v: */
+
+/* v^T dg/dalpha and v^T dg/dbeta: g = vol [Jr^T r + alpha h_p^2 L b + beta/2 D^T phi'(delta)] is
+ * affine in alpha and beta, so dg/dalpha = vol h_p^2 L b and dg/dbeta = vol/2 D^T phi'(delta). */
+void orc_theta_dots(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                    int contract, const double* v, double out[2]) {
+  int64_t nf = fld_count(g), nc = img_count(g);
+  double vol = cell_volume(g), hp = g->h[g->p];
+  orc_lin lin;
+  lin_alloc(&lin, nc);
+  double D, P;
+  residual_pass(g, Ip, Im, b, contract, &D, &P, &lin, NULL, NULL, NULL, NULL);
+  double* Lb = malloc(nf * sizeof(double));
+  double* u = calloc(nf, sizeof(double));
+  orc_laplacian(g, b, Lb);
+  fd_transpose_add(g, lin.dphi, u);
+  double sa = 0.0, sb = 0.0;
+  for (int64_t k = 0; k < nf; ++k) {
+    sa += v[k] * vol * hp * hp * Lb[k];
+    sb += v[k] * 0.5 * vol * u[k];
+  }
+  out[0] = sa;
+  out[1] = sb;
+  free(Lb); free(u);
+  lin_free(&lin);
+}
+
+/* d/dI+- of F = v^T g.  Only the distance term depends on the images:
+ *   F_D = vol sum_j r_j u_j,   u_j = (Jr v)_j = jl_j v_j + jr_j v_{j+1},
+ * with r_j = I+(t+)(1 + delta) - I-(t-)(1 - delta), jl = a/2 - c, jr = a/2 + c,
+ * a = I+'(t+)(1 + delta) + I-'(t-)(1 - delta), c = I+(t+) + I-(t-).  Per cell, for the two voxels
+ * i, i+1 around t+ (weights 1 - w, w; slope I+[i+1] - I+[i]):
+ *   dr/dI+[i]   = (1 - w)(1 + delta),           dr/dI+[i+1] = w (1 + delta),
+ *   da/dI+[i]   = -(1 + delta),                 da/dI+[i+1] = (1 + delta),
+ *   dc/dI+[i]   = 1 - w,                        dc/dI+[i+1] = w,
+ * and du/dI = v_j (da/2 - dc) + v_{j+1} (da/2 + dc); likewise for I- with t-, (1 - delta) and
+ * dr/dI- = -(...).  dF/dI[k] = vol sum over cells (u_j dr_j/dI[k] + r_j du_j/dI[k]). */
+void orc_mixed_image_adjoint(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                             int contract, const double* v, double* dIp, double* dIm) {
+  int64_t m = g->d[g->p];
+  int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
+  int64_t sti = si[g->p], stf = sf[g->p];
+  int64_t ncols = column_count(g);
+  double vol = cell_volume(g);
+  memset(dIp, 0, img_count(g) * sizeof(double));
+  memset(dIm, 0, img_count(g) * sizeof(double));
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    for (int64_t j = 0; j < m; ++j) {
+      double bj = b[of + j * stf], bj1 = b[of + (j + 1) * stf];
+      double vj = v[of + j * stf], vj1 = v[of + (j + 1) * stf];
+      double tp, tm, delta;
+      cell_positions(bj, bj1, j, contract, &tp, &tm, &delta);
+      double Ipv, Ips, Imv, Ims;
+      int64_t ip, im;
+      interp1(Ip + oi, sti, m, tp, &Ipv, &Ips, &ip);
+      interp1(Im + oi, sti, m, tm, &Imv, &Ims, &im);
+      double r = Ipv * (1.0 + delta) - Imv * (1.0 - delta);
+      double a = Ips * (1.0 + delta) + Ims * (1.0 - delta);
+      double c = Ipv + Imv;
+      double u = (0.5 * a - c) * vj + (0.5 * a + c) * vj1;
+      double wp = tp - floor(tp), wm = tm - floor(tm);
+      /* the two voxels of each image model and their derivatives */
+      for (int s = 0; s < 2; ++s) {   /* s = 0: voxel i, s = 1: voxel i + 1 */
+        double wpk = s == 0 ? 1.0 - wp : wp, wmk = s == 0 ? 1.0 - wm : wm;
+        double sgn = s == 0 ? -1.0 : 1.0;   /* d(slope)/dI at voxel i, i + 1 */
+        /* I+ */
+        double dr = wpk * (1.0 + delta);
+        double da = sgn * (1.0 + delta);
+        double dc = wpk;
+        double du = vj * (0.5 * da - dc) + vj1 * (0.5 * da + dc);
+        int64_t k = ip + s;
+        if (k >= 0 && k < m) dIp[oi + k * sti] += vol * (u * dr + r * du);
+        /* I- */
+        dr = -wmk * (1.0 - delta);
+        da = sgn * (1.0 - delta);
+        dc = wmk;
+        du = vj * (0.5 * da - dc) + vj1 * (0.5 * da + dc);
+        k = im + s;
+        if (k >= 0 && k < m) dIm[oi + k * sti] += vol * (u * dr + r * du);
+      }
+    }
+  }
+}
+
+/* The whole step: v = H^{-1} dL/db* by Jacobi PCG (x0 = 0, at most max_it iterations, relative
+ * residual rtol), then dL/dI+- = -d(v^T g)/dI+-, dL/dalpha = -v^T dg/dalpha,
+ * dL/dbeta = -v^T dg/dbeta.  Returns the PCG iteration count. */
+int orc_solve_adjoint(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                      int contract, const double* dLdb, int max_it, double rtol, double* v,
+                      double* dIp, double* dIm, double* dtheta) {
+  double relres;
+  int it = orc_pcg(g, Ip, Im, b, contract, 0, dLdb, max_it, rtol, v, &relres);
+  orc_mixed_image_adjoint(g, Ip, Im, b, contract, v, dIp, dIm);
+  for (int64_t k = 0; k < img_count(g); ++k) { dIp[k] = -dIp[k]; dIm[k] = -dIm[k]; }
+  double s[2];
+  orc_theta_dots(g, Ip, Im, b, contract, v, s);
+  dtheta[0] = -s[0];
+  dtheta[1] = -s[1];
+  return it;
+}
