@@ -154,6 +154,27 @@ int hysco_correct_adjoint(hysco_t h, const void* Ip, const void* Im, const float
                           const float* gTp, const float* gTm, float* dIp, float* dIm, float* db,
                           hysco_stream_t stream);
 
+/* Implicit differentiation through a solve (the Gauss-Newton system of Sec. 2.3.1 at a solution):
+ * at a stationary point b of J the gradient g(b; theta) = 0 defines b as a function of every input
+ * theta, and for a loss L(b), with H the Gauss-Newton Hessian at b standing in for J's Hessian,
+ *   dL/dtheta = -(dg/dtheta)^T v,   H v = dL/db.
+ * hysco_implicit_parts takes v (field-shaped float32, caller's layout) and writes
+ *   dIp = -d(v^T g)/dI+, dIm = -d(v^T g)/dI-   image-shaped float32 (nullable; only the distance
+ *                                              term of Eq. 2 depends on the images)
+ *   dtheta[0] = -v^T dg/dalpha = -v^T grad S, dtheta[1] = -v^T dg/dbeta = -v^T grad P
+ *                                              (2 doubles, device, nullable).
+ * hysco_solve_adjoint computes the Gauss-Newton linearisation at b (as hysco_eval does, replacing
+ * the handle's), solves H v = dLdb by Jacobi PCG (x0 = 0, at most max_iters <= 1000 iterations,
+ * relative residual rtol), writes v to v_out when non-NULL, then the parts as above.  The total
+ * derivative of a loss of the solved field adds these to the loss's direct dependence on the
+ * images.  Outputs must not alias the inputs. */
+int hysco_implicit_parts(hysco_t h, const void* Ip, const void* Im, const float* b,
+                         const float* v, float* dIp, float* dIm, double* dtheta,
+                         hysco_stream_t stream);
+int hysco_solve_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                        const float* dLdb, int max_iters, double rtol, float* v_out, float* dIp,
+                        float* dIm, double* dtheta, hysco_stream_t stream);
+
 /* Gradient of gJ * J with respect to the two images at fixed b.  Only the distance term of Eq. 2
  * depends on them: dIp = gJ vol (dTp/dIp)^T r, dIm = -gJ vol (dTm/dIm)^T r with the residual
  * r = Tp - Tm recomputed.  (With respect to b it is gJ times the gradient of hysco_eval; with

@@ -62,6 +62,8 @@ def load():
         "hysco_correct": (I, [P, P, P, P, P, P, P]),
         "hysco_correct_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
         "hysco_image_grad": (I, [P, P, P, P, D, P, P, P]),
+        "hysco_implicit_parts": (I, [P, P, P, P, P, P, P, P, P]),
+        "hysco_solve_adjoint": (I, [P, P, P, P, P, I, D, P, P, P, P, P]),
         "hysco_solve": (I, [P, P, P, P, C.POINTER(Opts), P, P]),
         "hysco_last_status": (I, [P, P]),
         "hysco_cell_indices": (I, [P, P, P, P, P]),

@@ -3,8 +3,9 @@ objective J (Eq. 4) with respect to the two input images, the field b and the we
 beta, at fixed b.  Forward and backward run in the library's CUDA kernels (hysco_correct /
 hysco_correct_adjoint, hysco_eval / hysco_image_grad); this module only marshals tensors.
 
-Differentiating through the Gauss-Newton solve itself (the dependence of the optimal field on
-the images and on alpha) is not provided: here b is an input like the images.
+SolvedField differentiates through the Gauss-Newton solve itself: its output is the solved
+field b*, and its backward applies the implicit function theorem at b* (one adjoint PCG solve with
+the Gauss-Newton Hessian, hysco_solve_adjoint), exact when b* is a stationary point of J.
 """
 from __future__ import annotations
 
@@ -86,3 +87,47 @@ def objective(h, Ip, Im, b, alpha=None, beta=None):
     alpha = torch.tensor(h.alpha, dtype=torch.float64, device=dev) if alpha is None else alpha
     beta = torch.tensor(h.beta, dtype=torch.float64, device=dev) if beta is None else beta
     return Objective.apply(h, Ip, Im, b, alpha, beta)
+
+
+class SolvedField(torch.autograd.Function):
+    """(Ip, Im, alpha, beta) -> b*: the GN-PCG solve on handle h (whose alpha and beta the arguments
+    must equal).  Backward by implicit differentiation at b*: with H v = dL/db*,
+    dL/dI+- = -d(v^T g)/dI+-, dL/dalpha = -v^T grad S, dL/dbeta = -v^T grad P."""
+
+    @staticmethod
+    def forward(ctx, h, Ip, Im, alpha, beta, solve_kwargs, adjoint_iters, adjoint_rtol):
+        a = float(alpha) if not isinstance(alpha, torch.Tensor) else float(alpha.item())
+        be = float(beta) if not isinstance(beta, torch.Tensor) else float(beta.item())
+        if a != h.alpha or be != h.beta:
+            raise ValueError(f"alpha, beta = {a}, {be} differ from the handle's "
+                             f"{h.alpha}, {h.beta}")
+        b, _ = h.solve(Ip, Im, stats=False, **solve_kwargs)
+        ctx.h = h
+        ctx.adjoint = (adjoint_iters, adjoint_rtol)
+        ctx.weight_like = (alpha if isinstance(alpha, torch.Tensor) else None,
+                           beta if isinstance(beta, torch.Tensor) else None)
+        ctx.save_for_backward(Ip, Im, b)
+        return b
+
+    @staticmethod
+    def backward(ctx, gb):
+        Ip, Im, b = ctx.saved_tensors
+        need = ctx.needs_input_grad
+        it, rtol = ctx.adjoint
+        _, dIp, dIm, dth = ctx.h.solve_adjoint(Ip, Im, b, gb.float().contiguous(), max_iters=it,
+                                               rtol=rtol)
+        wa, wb = ctx.weight_like
+        return (None, dIp.to(Ip.dtype) if need[1] else None,
+                dIm.to(Im.dtype) if need[2] else None,
+                dth[0].to(wa.dtype).reshape(wa.shape) if need[3] else None,
+                dth[1].to(wb.dtype).reshape(wb.shape) if need[4] else None, None, None, None)
+
+
+def solved_field(h, Ip, Im, alpha=None, beta=None, adjoint_iters=200, adjoint_rtol=1e-6,
+                 **solve_kwargs):
+    """Differentiable b* = solve(Ip, Im) (OT start, the handle's weights); keyword arguments go to
+    Hysco.solve (gn_iters, pcg_max_iters, ...)."""
+    dev = Ip.device
+    alpha = torch.tensor(h.alpha, dtype=torch.float64, device=dev) if alpha is None else alpha
+    beta = torch.tensor(h.beta, dtype=torch.float64, device=dev) if beta is None else beta
+    return SolvedField.apply(h, Ip, Im, alpha, beta, solve_kwargs, adjoint_iters, adjoint_rtol)

@@ -429,6 +429,43 @@ int hysco_correct_adjoint(hysco_t h, const void* Ip, const void* Im, const float
   return HYSCO_OK;
 }
 
+int hysco_implicit_parts(hysco_t h, const void* Ip, const void* Im, const float* b,
+                         const float* v, float* dIp, float* dIm, double* dtheta,
+                         hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(v)) return HYSCO_EINVAL;
+  if ((dIp && !aligned(dIp, 4)) || (dIm && !aligned(dIm, 4)) || (dtheta && !aligned(dtheta, 8)))
+    return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  HYSCO_TRY(launch_mixed_image_adjoint(h->g, h->dtype, Ip, Im, b, v, -h->g.vol, dIp, dIm, s));
+  if (dtheta) {
+    HYSCO_TRY(launch_theta_dots(h->g, b, v, -1.0, dtheta, h->work(), s));
+  }
+  return HYSCO_OK;
+}
+
+int hysco_solve_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                        const float* dLdb, int max_iters, double rtol, float* v_out, float* dIp,
+                        float* dIm, double* dtheta, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(dLdb))
+    return HYSCO_EINVAL;
+  if (max_iters < 1 || max_iters > 1000 || !(rtol >= 0.0)) return HYSCO_EINVAL;
+  if (v_out && !aligned(v_out, 4)) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  PcgMode mode;
+  if (pcg_mode(h, HYSCO_PC_JACOBI, 0, &mode)) return HYSCO_EINVAL;
+  // the GN linearisation at b, then v = H^{-1} dL/db
+  if (int rc = reset_state(h, s)) return rc;
+  HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd, -1,
+                        h->work(), s));
+  h->have_lin = true;
+  h->have_factor = false;
+  HYSCO_TRY(launch_to_pitched(h->g, dLdb, h->tmp, s));
+  if (int rc = run_pcg(h, h->tmp, 1.0f, h->x, HYSCO_PC_JACOBI, max_iters, rtol, mode, s)) return rc;
+  float* v = v_out ? v_out : h->tmp;   // the caller's layout (tmp is free once the PCG has run)
+  HYSCO_TRY(launch_from_pitched(h->g, h->x, v, s));
+  return hysco_implicit_parts(h, Ip, Im, b, v, dIp, dIm, dtheta, stream);
+}
+
 int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, double gJ,
                      float* dIp, float* dIm, hysco_stream_t stream) {
   if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || !std::isfinite(gJ))

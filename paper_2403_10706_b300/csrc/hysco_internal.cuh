@@ -360,6 +360,13 @@ cudaError_t launch_correct_adjoint(const Geo& g, int dtype, const void* Ip, cons
 cudaError_t launch_image_grad(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, float svol, float* dIp, float* dIm,
                               cudaStream_t s);
+// implicit differentiation: sign * v^T dg/d(alpha, beta) into out[2] (device doubles), and
+// svol / vol * d(v^T g)/dI+- into dIp, dIm (b, v in the caller's field layout)
+cudaError_t launch_theta_dots(const Geo& g, const float* b, const float* v, double sign,
+                              double* out, const Work& w, cudaStream_t s);
+cudaError_t launch_mixed_image_adjoint(const Geo& g, int dtype, const void* Ip, const void* Im,
+                                       const float* b, const float* v, float svol, float* dIp,
+                                       float* dIm, cudaStream_t s);
 cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s);
 cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
 

@@ -146,6 +146,31 @@ class Hysco:
             "hysco_image_grad")
         return dIp, dIm
 
+    def implicit_parts(self, Ip, Im, b, v):
+        """(dIp, dIm, dtheta[2] float64) = -(d(v^T g)/dI+-, v^T dg/dalpha, v^T dg/dbeta) at b."""
+        dIp = torch.empty(self.dims, dtype=torch.float32, device=self.device)
+        dIm = torch.empty_like(dIp)
+        dth = torch.empty(2, dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.hysco_implicit_parts(
+            self._h, self._img(Ip, "Ip"), self._img(Im, "Im"), self._fld(b, "b"),
+            self._fld(v, "v"), self._img_f32(dIp, "dIp"), self._img_f32(dIm, "dIm"),
+            C.c_void_p(dth.data_ptr()), _stream(self.device)), "hysco_implicit_parts")
+        return dIp, dIm, dth
+
+    def solve_adjoint(self, Ip, Im, b, dLdb, max_iters=200, rtol=1e-6):
+        """Implicit differentiation at a solution b: (v, dL/dIp, dL/dIm, dL/d(alpha, beta)) with
+        H v = dLdb (the parts through b only)."""
+        v = self._new_fld()
+        dIp = torch.empty(self.dims, dtype=torch.float32, device=self.device)
+        dIm = torch.empty_like(dIp)
+        dth = torch.empty(2, dtype=torch.float64, device=self.device)
+        _lib.check(self.lib.hysco_solve_adjoint(
+            self._h, self._img(Ip, "Ip"), self._img(Im, "Im"), self._fld(b, "b"),
+            self._fld(dLdb, "dLdb"), int(max_iters), float(rtol), self._fld(v, "v"),
+            self._img_f32(dIp, "dIp"), self._img_f32(dIm, "dIm"), C.c_void_p(dth.data_ptr()),
+            _stream(self.device)), "hysco_solve_adjoint")
+        return v, dIp, dIm, dth
+
     def solve(self, Ip, Im, b=None, gn_iters=10, pcg_max_iters=10, ls_max_iters=10,
               precond=_lib.PC_JACOBI, init=None, ot_blur=True, pcg_rtol=0.1, armijo_c1=1e-4,
               ot_eps=1e-3, stats=True, pcg_path=0, graph=True):
