@@ -70,6 +70,9 @@ def lib():
         _lib.orc_mixed_image_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P]
         _lib.orc_solve_adjoint.argtypes = [P, P, P, P, C.c_int, P, C.c_int, C.c_double, P, P, P,
                                            P]
+        _lib.orc_ls_correct.restype = C.c_int64
+        _lib.orc_ls_correct.argtypes = [P, P, P, P, C.c_double, P]
+        _lib.orc_pushforward_matrix.argtypes = [P, C.c_int64, C.c_double, P]
         _lib.orc_feasible_start.restype = C.c_double
         _lib.orc_feasible_start.argtypes = [P, P]
     return _lib
@@ -168,6 +171,13 @@ class Problem:
                                      _p(v), _p(dIp), _p(dIm), _p(dth))
         return v, dIp, dIm, dth[0], dth[1], it
 
+    def ls_correct(self, Ip, Im, b, lam=1e-8):
+        """Least-squares corrected image at b (image shaped) and the count of skipped columns."""
+        out = np.zeros(self.dims)
+        bad = lib().orc_ls_correct(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                   float(lam), _p(out))
+        return out, int(bad)
+
     def feasible_start(self, b):
         """The solve's start rule for an OT field: returns (b scaled by 2^-k, 2^-k) with the
         smallest k >= 0 that brings max |delta| below 1."""
@@ -251,3 +261,12 @@ def phi(z):
     f, df, d2f = C.c_double(), C.c_double(), C.c_double()
     lib().orc_phi(float(z), C.byref(f), C.byref(df), C.byref(d2f))
     return f.value, df.value, d2f.value
+
+
+def pushforward_matrix(bcol, sign):
+    """Dense m x m push-forward matrix of one column (field values bcol, m + 1 nodes)."""
+    bcol = _f64(bcol)
+    m = bcol.size - 1
+    P = np.zeros((m, m))
+    lib().orc_pushforward_matrix(_p(bcol), m, float(sign), _p(P))
+    return P

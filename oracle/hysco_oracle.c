@@ -1087,3 +1087,97 @@ int orc_solve_adjoint(const orc_geom* g, const float* Ip, const float* Im, const
   dtheta[1] = -s[1];
   return it;
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* least-squares correction (Sec. 2.4 "Image Correction")                                     */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Push-forward matrix of one PE column for direction s = +1 / -1: true cell j (the interval
+ * [j - 1/2, j + 1/2] in cell-index coordinates, field nodes at its edges) is mapped to
+ * [e_j, e_{j+1}] with e_j = j - 1/2 + s b_j, and its mass is spread uniformly there; distorted
+ * cell i collects the part that falls in [i - 1/2, i + 1/2]:
+ *   P[i][j] = |[i - 1/2, i + 1/2] ∩ [e_j, e_{j+1}]| / (e_{j+1} - e_j).
+ * Needs e_{j+1} > e_j (|delta_j| < 1).  P is m x m, row-major, dense. */
+static void pushforward_column(const double* bcol, int64_t stf, int64_t m, double s, double* P) {
+  for (int64_t i = 0; i < m; ++i)
+    for (int64_t j = 0; j < m; ++j) {
+      double e0 = (double)j - 0.5 + s * bcol[j * stf];
+      double e1 = (double)j + 0.5 + s * bcol[(j + 1) * stf];
+      double lo = fmax(e0, (double)i - 0.5), hi = fmin(e1, (double)i + 0.5);
+      P[i * m + j] = hi > lo ? (hi - lo) / (e1 - e0) : 0.0;
+    }
+}
+
+/* Corrected image by least squares: per PE column, the true image I minimising
+ *   |P+ I - I+|^2 + |P- I - I-|^2 + lambda |I|^2,
+ * from the normal equations (P+^T P+ + P-^T P- + lambda Id) I = P+^T I+ + P-^T I- solved by a
+ * textbook Cholesky factorisation.  lambda > 0 keeps cells whose mass leaves the column in both
+ * images at 0.  Returns the number of columns whose field has |delta| >= 1 somewhere (left at 0). */
+int64_t orc_ls_correct(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                       double lambda, double* out) {
+  int64_t m = g->d[g->p];
+  int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
+  int64_t sti = si[g->p], stf = sf[g->p];
+  int64_t ncols = column_count(g);
+  double* Pp = malloc(m * m * sizeof(double));
+  double* Pm = malloc(m * m * sizeof(double));
+  double* N = malloc(m * m * sizeof(double));
+  double* rhs = malloc(m * sizeof(double));
+  int64_t bad = 0;
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    const double* bcol = b + of;
+    int ok = 1;
+    for (int64_t j = 0; j < m; ++j)
+      if (!(fabs(bcol[(j + 1) * stf] - bcol[j * stf]) < 1.0)) ok = 0;
+    if (!ok) {
+      ++bad;
+      for (int64_t j = 0; j < m; ++j) out[oi + j * sti] = 0.0;
+      continue;
+    }
+    pushforward_column(bcol, stf, m, +1.0, Pp);
+    pushforward_column(bcol, stf, m, -1.0, Pm);
+    for (int64_t j = 0; j < m; ++j) {
+      double r = 0.0;
+      for (int64_t i = 0; i < m; ++i)
+        r += Pp[i * m + j] * (double)Ip[oi + i * sti] + Pm[i * m + j] * (double)Im[oi + i * sti];
+      rhs[j] = r;
+      for (int64_t k = 0; k < m; ++k) {
+        double a = 0.0;
+        for (int64_t i = 0; i < m; ++i) a += Pp[i * m + j] * Pp[i * m + k] + Pm[i * m + j] * Pm[i * m + k];
+        N[j * m + k] = a + (j == k ? lambda : 0.0);
+      }
+    }
+    /* Cholesky N = L L^T (L in the lower triangle of N), then L y = rhs, L^T x = y */
+    for (int64_t j = 0; j < m; ++j) {
+      double d = N[j * m + j];
+      for (int64_t k = 0; k < j; ++k) d -= N[j * m + k] * N[j * m + k];
+      d = sqrt(d);
+      N[j * m + j] = d;
+      for (int64_t i = j + 1; i < m; ++i) {
+        double a = N[i * m + j];
+        for (int64_t k = 0; k < j; ++k) a -= N[i * m + k] * N[j * m + k];
+        N[i * m + j] = a / d;
+      }
+    }
+    for (int64_t j = 0; j < m; ++j) {
+      double a = rhs[j];
+      for (int64_t k = 0; k < j; ++k) a -= N[j * m + k] * rhs[k];
+      rhs[j] = a / N[j * m + j];
+    }
+    for (int64_t j = m - 1; j >= 0; --j) {
+      double a = rhs[j];
+      for (int64_t k = j + 1; k < m; ++k) a -= N[k * m + j] * rhs[k];
+      rhs[j] = a / N[j * m + j];
+    }
+    for (int64_t j = 0; j < m; ++j) out[oi + j * sti] = rhs[j];
+  }
+  free(Pp); free(Pm); free(N); free(rhs);
+  return bad;
+}
+
+/* the dense push-forward matrix of one column (test access) */
+void orc_pushforward_matrix(const double* bcol, int64_t m, double s, double* P) {
+  pushforward_column(bcol, 1, m, s, P);
+}
