@@ -183,6 +183,18 @@ int hysco_solve_adjoint(hysco_t h, const void* Ip, const void* Im, const float* 
 int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, double gJ,
                      float* dIp, float* dIm, hysco_stream_t stream);
 
+/* Least-squares corrected image at b (Sec. 2.4 "Image Correction", the alternative to hysco_correct):
+ * per PE column, the true image I minimising |P+ I - Ip|^2 + |P- I - Im|^2 + lambda |I|^2, where the
+ * push-forward matrix P+- spreads the mass of true cell j uniformly over its mapped interval
+ * [j - 1/2 +- b_j, j + 1/2 +- b_{j+1}] (cell-index coordinates, b in PE voxels) and distorted cell i
+ * collects the part inside [i - 1/2, i + 1/2].  lambda > 0 (1e-6 is negligible at single precision)
+ * sets cells whose mass leaves the column in both images to 0.  out: image-shaped float32.  A column
+ * whose field has |d_v b| >= 1 somewhere, or whose normal matrix is wider than a band of 4 (|d_v b|
+ * above about 0.75), is set to 0 and counted in *nbad (device int32, nullable).  Uses the handle's
+ * PCG scratch arrays (not the GN linearisation). */
+int hysco_ls_correct(hysco_t h, const void* Ip, const void* Im, const float* b, double lambda,
+                     float* out, int32_t* nbad, hysco_stream_t stream);
+
 /* Full solve (Sec. 2.2 + 2.3.1): optional OT init (opts->init), then opts->gn_iters Gauss-Newton
  * iterations b <- b + gamma q with H_J q ~= -grad J from at most pcg_max_iters PCG iterations
  * (x0 = 0, stop at relative residual < pcg_rtol) and gamma the first of 1, 1/2, 1/4, ... that

@@ -60,6 +60,7 @@ def load():
         "hysco_precond": (I, [P, P, P, I, P]),
         "hysco_pcg": (I, [P, P, P, I, I, D, I, P]),
         "hysco_correct": (I, [P, P, P, P, P, P, P]),
+        "hysco_ls_correct": (I, [P, P, P, P, D, P, P, P]),
         "hysco_correct_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
         "hysco_image_grad": (I, [P, P, P, P, D, P, P, P]),
         "hysco_implicit_parts": (I, [P, P, P, P, P, P, P, P, P]),

@@ -476,6 +476,21 @@ int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, 
   return HYSCO_OK;
 }
 
+int hysco_ls_correct(hysco_t h, const void* Ip, const void* Im, const float* b, double lambda,
+                     float* out, int32_t* nbad, hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(out)) return HYSCO_EINVAL;
+  if (!(lambda > 0.0) || !std::isfinite(lambda) || (nbad && !aligned(nbad, 4))) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  // scratch: five band arrays and the right-hand side in solver arrays the GN linearisation
+  // (grad, d, e, 1/diag) and the column factors do not use
+  LsBand band{{h->r, h->z, h->p0, h->p1, h->Hp}};
+  int* bad = reinterpret_cast<int*>(h->counter + 48);
+  HYSCO_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  HYSCO_TRY(launch_ls_correct(h->g, h->dtype, Ip, Im, b, (float)lambda, band, h->q0, out, bad, s));
+  if (nbad) HYSCO_TRY(cudaMemcpyAsync(nbad, bad, sizeof(int), cudaMemcpyDeviceToDevice, s));
+  return HYSCO_OK;
+}
+
 int hysco_cell_indices(hysco_t h, const float* b, int32_t* cell_p, int32_t* cell_m,
                        hysco_stream_t stream) {
   if (!h || check_f32(b) || check_f32(cell_p) || check_f32(cell_m)) return HYSCO_EINVAL;

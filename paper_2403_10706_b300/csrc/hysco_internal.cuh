@@ -438,6 +438,16 @@ int ot_tile_width(int E);
 cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
                       int* kp, int* km, const Work& w, cudaStream_t s);
 cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s);
+// k_ls.cu: least-squares correction; the normal matrix's band (half-width kLsBand) lives in
+// kLsBand + 1 image-layout scratch arrays
+constexpr int kLsBand = 4;
+struct LsBand {
+  float* d[kLsBand + 1];
+};
+cudaError_t launch_ls_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
+                              const float* b, float lambda, LsBand band, float* rhs, float* out,
+                              int* nbad, cudaStream_t s);
+
 // the GN loop's feasible start: b (caller layout) halved until max |delta| < 1
 cudaError_t launch_feasible_start(const Geo& g, float* b, const Work& w, cudaStream_t s);
 

@@ -115,6 +115,17 @@ class Hysco:
                    "hysco_correct")
         return Tp, Tm
 
+    def ls_correct(self, Ip, Im, b, lam=1e-6):
+        """Least-squares corrected image at b and the number of skipped columns."""
+        out = torch.empty(self.dims, dtype=torch.float32, device=self.device)
+        nbad = torch.zeros(1, dtype=torch.int32, device=self.device)
+        _lib.check(self.lib.hysco_ls_correct(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                             self._fld(b, "b"), float(lam),
+                                             C.c_void_p(out.data_ptr()),
+                                             C.c_void_p(nbad.data_ptr()), _stream(self.device)),
+                   "hysco_ls_correct")
+        return out, nbad
+
     def _img_f32(self, t, name):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32
                 and tuple(t.shape) == self.dims and t.is_contiguous()):
