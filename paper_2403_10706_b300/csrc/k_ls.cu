@@ -4,20 +4,24 @@
 // [e_j, e_{j+1}] = [j - 1/2 +- b_j, j + 1/2 +- b_{j+1}] and distorted cell i collects the part
 // inside [i - 1/2, i + 1/2]: P[i][j] = overlap / (e_{j+1} - e_j).
 //
-// One thread per column.  (1) Assembly of the normal equations N I = rhs with
-// N = P+^T P+ + P-^T P- + lambda Id: the mapped edges increase with j (|delta| < 1), so a
-// two-pointer march over distorted cells finds, for each, the contiguous run of true cells it
-// overlaps; every pair in a run adds P_ij P_ik to the band of N (half-width kLsBand) and P_ij I[i]
-// to rhs_j.  Band and rhs live in scratch arrays in the image layout.  (2) Banded LDL^T
-// factorisation with the forward substitution L y = rhs fused in, the last kLsBand columns of L
-// and D kept in registers; L, D^{-1} y written back to scratch.  (3) Back substitution
-// L^T x = D^{-1} y into the output.  A column whose field has |delta| >= 1, or whose band would be
-// wider than kLsBand (|delta| above about 0.75), is set to 0 and counted.
+// One thread per column, streaming along it.  Row j of the normal matrix
+// N = P+^T P+ + P-^T P- + lambda Id is formed directly: the distorted cells i that true cell j's
+// mapped interval overlaps (at most three, |delta| < 1) give N_jk += P_ij P_ik for k = j .. j + 4
+// (the band; edges kept in a rolling register window) and rhs_j += P_ij I[i].  Each row goes
+// straight into one step of a banded LDL^T factorisation with the forward substitution L y = rhs
+// fused in (the last four columns of L and D in registers); L and D^{-1} y go to scratch for the
+// back substitution L^T x = D^{-1} y into the output.  A column whose field has |delta| >= 1, or
+// whose band would be wider than kLsBand (|delta| above about 0.75), is set to 0 and counted.
 #include "eval_common.cuh"
 
 namespace hysco {
 
 constexpr int kLsColBlock = 64;
+
+// |[i - 1/2, i + 1/2] ∩ [e0, e1]|
+__device__ __forceinline__ float overlap(int i, float e0, float e1) {
+  return fmaxf(0.f, fminf(e1, (float)i + 0.5f) - fmaxf(e0, (float)i - 0.5f));
+}
 
 template <typename TI>
 __global__ void __launch_bounds__(kLsColBlock)
@@ -28,54 +32,19 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
   if (c >= g.ncols) return;
   const int inner = g.inner, m = g.m;
   const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-  auto B = [&](int d, int j) -> float& { return band.d[d][ib + j * inner]; };
-  auto R = [&](int j) -> float& { return rhs[ib + j * inner]; };
+  auto Lst = [&](int d, int j) -> float& { return band.d[d][ib + j * inner]; };   // L[j+1+d][j]
+  auto Z = [&](int j) -> float& { return rhs[ib + j * inner]; };                 // D^-1 y
   bool ok = true;
-  for (int j = 0; j < m; ++j) {
-    if (!(fabsf(__ldg(b + fb + (j + 1) * inner) - __ldg(b + fb + j * inner)) < 1.0f)) ok = false;
+  // rolling field window: bw[u] = b at node j + u, u = 0 .. kLsBand + 1; and the reciprocal
+  // lengths 1 / (e_{j+u+1} - e_{j+u}) of the mapped cells for both directions
+  float bw[kLsBand + 2], ilp[kLsBand + 1], ilm[kLsBand + 1];
 #pragma unroll
-    for (int d = 0; d <= kLsBand; ++d) B(d, j) = d == 0 ? lambda : 0.f;
-    R(j) = 0.f;
+  for (int u = 0; u < kLsBand + 2; ++u) bw[u] = __ldg(b + fb + min(u, m) * inner);
+#pragma unroll
+  for (int u = 0; u <= kLsBand; ++u) {
+    ilp[u] = 1.0f / (1.0f + (bw[u + 1] - bw[u]));
+    ilm[u] = 1.0f / (1.0f - (bw[u + 1] - bw[u]));
   }
-  // ---- (1) assembly ---------------------------------------------------------------------------
-  for (int s = 0; s < 2 && ok; ++s) {
-    const float sg = s == 0 ? 1.0f : -1.0f;
-    const TI* img = (s == 0 ? Ip : Im) + ib;
-    auto edge = [&](int j) { return (float)j - 0.5f + sg * __ldg(b + fb + j * inner); };
-    int j0 = 0;
-    for (int i = 0; i < m && ok; ++i) {
-      const float lo = (float)i - 0.5f, hi = (float)i + 0.5f;
-      while (j0 < m && edge(j0 + 1) <= lo) ++j0;
-      int js[kLsBand + 1];
-      float ps[kLsBand + 1];
-      int n = 0;
-      for (int j = j0; j < m; ++j) {
-        const float e0 = edge(j), e1 = edge(j + 1);
-        if (!(e0 < hi)) break;
-        const float ov = fminf(e1, hi) - fmaxf(e0, lo);
-        if (ov > 0.f) {
-          if (n > kLsBand) { ok = false; break; }
-          js[n] = j;
-          ps[n] = ov / (e1 - e0);
-          ++n;
-        }
-      }
-      if (!ok) break;
-      const float y = ldf(img + i * inner);
-      for (int a = 0; a < n; ++a) {
-        R(js[a]) += ps[a] * y;
-        for (int q = a; q < n; ++q) B(js[q] - js[a], js[a]) += ps[a] * ps[q];
-      }
-    }
-  }
-  if (!ok) {
-    for (int j = 0; j < m; ++j) out[ib + j * inner] = 0.f;
-    atomicAdd(nbad, 1);
-    return;
-  }
-  // ---- (2) N = L D L^T, L y = rhs --------------------------------------------------------------
-  // window: column k = j - 1 - t (t = 0..kLsBand-1) of L below the diagonal (Lw[t][d] = L[k+1+d][k])
-  // and D_k, y_k
   float Lw[kLsBand][kLsBand], Dw[kLsBand], yw[kLsBand];
 #pragma unroll
   for (int t = 0; t < kLsBand; ++t) {
@@ -84,26 +53,48 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
 #pragma unroll
     for (int d = 0; d < kLsBand; ++d) Lw[t][d] = 0.f;
   }
-  for (int j = 0; j < m; ++j) {
-    // D_j = N_jj - sum_k L[j][k]^2 D_k,  L[j][k] = Lw[j-1-k][j-1-k] for k = j-1-t
-    float dj = B(0, j), yj = R(j);
+  for (int j = 0; j < m && ok; ++j) {
+    // ---- row j of N and rhs_j -----------------------------------------------------------------
+    float N[kLsBand + 1], r = 0.f;
+#pragma unroll
+    for (int d = 0; d <= kLsBand; ++d) N[d] = d == 0 ? lambda : 0.f;
+    if (!(fabsf(bw[1] - bw[0]) < 1.0f)) ok = false;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const float sg = s == 0 ? 1.0f : -1.0f;
+      float e[kLsBand + 2];   // mapped edges of cells j .. j + kLsBand
+#pragma unroll
+      for (int u = 0; u < kLsBand + 2; ++u) e[u] = (float)(j + u) - 0.5f + sg * bw[u];
+      const float* il = s == 0 ? ilp : ilm;
+      const int ilo = max((int)floorf(e[0] + 0.5f), 0), ihi = min((int)floorf(e[1] + 0.5f), m - 1);
+      // cells past j + kLsBand must not reach the last distorted cell of this row
+      if (j + kLsBand + 1 < m && (float)ihi + 0.5f > e[kLsBand + 1]) ok = false;
+      const TI* img = (s == 0 ? Ip : Im) + ib;
+      for (int i = ilo; i <= ihi; ++i) {
+        const float pij = overlap(i, e[0], e[1]) * il[0];
+        r += pij * ldf(img + i * inner);
+#pragma unroll
+        for (int d = 0; d <= kLsBand; ++d)
+          if (j + d < m) N[d] += pij * overlap(i, e[d], e[d + 1]) * il[d];
+      }
+    }
+    // ---- one step of N = L D L^T with L y = rhs -------------------------------------------------
+    float dj = N[0], yj = r;
 #pragma unroll
     for (int t = 0; t < kLsBand; ++t) {
-      const float ljk = Lw[t][t];   // L[j][k] with k = j - 1 - t (offset j - k - 1 = t)
+      const float ljk = Lw[t][t];   // L[j][k], k = j - 1 - t
       dj -= ljk * ljk * Dw[t];
       yj -= ljk * yw[t];
     }
+    const float idj = 1.0f / dj;
     float Lnew[kLsBand];
 #pragma unroll
     for (int d = 0; d < kLsBand; ++d) {
-      // L[j+1+d][j] = (N[j+1+d][j] - sum_k L[j+1+d][k] L[j][k] D_k) / D_j
-      float a = j + 1 + d < m ? B(d + 1, j) : 0.f;
+      float a = N[d + 1];   // N[j+1+d][j]
 #pragma unroll
-      for (int t = 0; t + d + 1 < kLsBand; ++t)
-        a -= Lw[t][t + d + 1] * Lw[t][t] * Dw[t];   // L[j+1+d][k] at offset (j+1+d) - k - 1
-      Lnew[d] = j + 1 + d < m ? a / dj : 0.f;
+      for (int t = 0; t + d + 1 < kLsBand; ++t) a -= Lw[t][t + d + 1] * Lw[t][t] * Dw[t];
+      Lnew[d] = j + 1 + d < m ? a * idj : 0.f;
     }
-    // shift the window and store column j (L below the diagonal, and D_j^{-1} y_j)
 #pragma unroll
     for (int t = kLsBand - 1; t > 0; --t) {
       Dw[t] = Dw[t - 1];
@@ -116,18 +107,31 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
 #pragma unroll
     for (int d = 0; d < kLsBand; ++d) {
       Lw[0][d] = Lnew[d];
-      B(d + 1, j) = Lnew[d];
+      Lst(d, j) = Lnew[d];
     }
-    R(j) = yj / dj;
+    Z(j) = yj * idj;
+    // advance the field window
+#pragma unroll
+    for (int u = 0; u < kLsBand + 1; ++u) bw[u] = bw[u + 1];
+    bw[kLsBand + 1] = __ldg(b + fb + min(j + kLsBand + 2, m) * inner);
+#pragma unroll
+    for (int u = 0; u < kLsBand; ++u) { ilp[u] = ilp[u + 1]; ilm[u] = ilm[u + 1]; }
+    ilp[kLsBand] = 1.0f / (1.0f + (bw[kLsBand + 1] - bw[kLsBand]));
+    ilm[kLsBand] = 1.0f / (1.0f - (bw[kLsBand + 1] - bw[kLsBand]));
   }
-  // ---- (3) L^T x = D^{-1} y ---------------------------------------------------------------------
+  if (!ok) {
+    for (int j = 0; j < m; ++j) out[ib + j * inner] = 0.f;
+    atomicAdd(nbad, 1);
+    return;
+  }
+  // ---- L^T x = D^{-1} y -----------------------------------------------------------------------
   float xw[kLsBand];
 #pragma unroll
   for (int t = 0; t < kLsBand; ++t) xw[t] = 0.f;   // x_{j+1+t}
   for (int j = m - 1; j >= 0; --j) {
-    float x = R(j);
+    float x = Z(j);
 #pragma unroll
-    for (int d = 0; d < kLsBand; ++d) x -= B(d + 1, j) * xw[d];
+    for (int d = 0; d < kLsBand; ++d) x -= Lst(d, j) * xw[d];
 #pragma unroll
     for (int t = kLsBand - 1; t > 0; --t) xw[t] = xw[t - 1];
     xw[0] = x;
