@@ -64,6 +64,7 @@ def peaks():
 
 
 PCG_SOURCES = ["paper_2403_10706_b300/csrc/k_pcg_persistent.cu",
+               "paper_2403_10706_b300/csrc/grid_sync.cuh",
                "paper_2403_10706_b300/csrc/hysco_internal.cuh"]
 
 
