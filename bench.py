@@ -63,14 +63,17 @@ def peaks():
     return 6400.0, "fallback"
 
 
+EVAL_SOURCES = ["paper_2403_10706_b300/csrc/k_eval.cu",
+                "paper_2403_10706_b300/csrc/eval_common.cuh",
+                "paper_2403_10706_b300/csrc/hysco_internal.cuh"]
 PCG_SOURCES = ["paper_2403_10706_b300/csrc/k_pcg_persistent.cu",
                "paper_2403_10706_b300/csrc/grid_sync.cuh",
                "paper_2403_10706_b300/csrc/hysco_internal.cuh"]
 
 
-def recorded_traffic(profile, sources):
-    """DRAM bytes per launch from a committed ncu summary, or None when the kernel's sources have
-    changed since the counters were taken (the summary records a hash of them)."""
+def _current_profile(profile, sources):
+    """Text of a committed ncu summary, or None when the kernel's sources have changed since the
+    counters were taken (the summary records a hash of them)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", profile)
     if not os.path.exists(path):
@@ -80,11 +83,32 @@ def recorded_traffic(profile, sources):
     for f in sources:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    rec = dict(line.split(":", 1) for line in text.splitlines()
-               if line.startswith(("source-sha256:", "dram-bytes-per-launch:")))
+    rec = dict(line.split(":", 1) for line in text.splitlines() if line.startswith("source-sha256:"))
     if rec.get("source-sha256", "").split()[0:1] != [h.hexdigest()[:16]]:
         return None
+    return text
+
+
+def recorded_traffic(profile, sources):
+    """DRAM bytes per launch from a committed, current ncu summary (else None)."""
+    text = _current_profile(profile, sources)
+    if text is None:
+        return None
+    rec = dict(line.split(":", 1) for line in text.splitlines()
+               if line.startswith("dram-bytes-per-launch:"))
     return int(rec["dram-bytes-per-launch"].strip())
+
+
+def recorded_warp_instructions(profile, sources):
+    """Warp instructions executed per launch (smsp__inst_executed.sum) from a committed, current
+    ncu summary (else None)."""
+    text = _current_profile(profile, sources)
+    if text is None:
+        return None
+    for line in text.splitlines():
+        if line.startswith("| `smsp__inst_executed.sum`"):
+            return float(line.split("|")[2].split()[0])
+    return None
 
 
 def config(args, n):
@@ -471,10 +495,12 @@ def run_ours(args):
     # Roofline of the dominant kernel, the persistent Jacobi-PCG kernel (one launch per GN step),
     # timed alone through hysco_pcg on this stream with L2 flushed before each launch.  rtol = 0
     # makes every launch run exactly 10 iterations.  Algorithmic bytes per field node (4-byte
-    # floats): init reads grad, 1/diag and writes x, r, z (20); iteration 0 reads z, d, e and
-    # writes p, Hp (20), then reads p, Hp, 1/diag, r and writes x, r, z (28); every later
-    # iteration reads z, d, e, p, Hp and writes p, Hp (28), then reads p, Hp, 1/diag, r, x and
-    # writes x, r, z (32).
+    # floats) with r, p, Hp of every group on chip (shared memory for the whole launch): init
+    # reads grad, 1/diag and writes x, z (16); iteration 0 reads z, d, e (12), then reads 1/diag
+    # and writes x, z (12); every later iteration reads z, d, e (12), then reads 1/diag, x and
+    # writes x, z (16).  Groups whose r, p, Hp stay in global memory add, per node, the write of
+    # r at init (4), of p, Hp at iteration 0 (8) and the reads of p, Hp, r and write of r in
+    # every phase B (16), and the read and write of p, Hp in every later phase A (16).
     nimg = int(np.prod(pr.dims))
     nfld = int(np.prod(h.field_dims))
     peak, peak_src = peaks()
@@ -504,10 +530,18 @@ def run_ours(args):
     # the stencil: reads r, w, q, 1/diag, p, x and writes x, p, q, r (40).
     pcg_iters = 10
     fused = args.pcg_path == 3
+    grid, onchip, slots = h.pcg_plan()
+    fe = h.field_dims
+    n4 = fe[0] * fe[1] * ((fe[2] + 3) // 4)
+    f_on = min(n4, onchip * grid * 256) / n4 if grid else 0.0    # share of groups on chip
     if fused:
         pcg_bytes = nfld * (24 + 40 + (pcg_iters - 2) * 52 + 40)
-    else:
+    elif args.pcg_path == 1:
         pcg_bytes = nfld * (20 + 20 + 28 + (pcg_iters - 1) * (28 + 32))
+    else:
+        off = 1.0 - f_on
+        pcg_bytes = int(nfld * (16 + 4 * off + 12 + 8 * off + 12 + 16 * off +
+                                (pcg_iters - 1) * (12 + 16 * off + 16 + 16 * off)))
     pcg_ms = time_launches(lambda: h.pcg(rhs, max_iters=pcg_iters, rtol=0.0, out=q,
                                          pcg_path=args.pcg_path))
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9
@@ -519,8 +553,11 @@ def run_ours(args):
             if args.workload == "3t" and args.pcg_path in (0, 2) else None,
             "kernel": kname,
             "peak_source": peak_src, "alg_bytes_per_launch": pcg_bytes, "launch_ms": pcg_ms,
-            "note": "10 PCG iterations per launch; the 86 MB working set is L2-resident within "
-                    "a launch, so achieved algorithmic bandwidth may exceed the HBM copy peak"}
+            "pcg_plan": {"grid": grid, "onchip_slots": onchip, "slots": slots,
+                         "onchip_share": f_on},
+            "note": "10 PCG iterations per launch; r, p, Hp of the on-chip share stay in shared "
+                    "memory; z, x, d, e, 1/diag (54 MB) are largely L2-resident within a launch, "
+                    "so achieved algorithmic bandwidth may exceed the HBM copy peak"}
     # the eval kernel (J, grad J, GN coefficients): read I+, I- (4 B each per voxel) and b
     # (4 B per node); write grad, d, e, 1/diag (4 B each per node)
     alg_eval = 8 * nimg + 20 * nfld
@@ -555,8 +592,18 @@ def run_ours(args):
     eval_roof = {"bound": "hbm", "achieved": ach_eval, "peak": peak, "unit": "GB/s",
                  "frac": ach_eval / peak, "kernel": "k_eval<float>",
                  "alg_bytes_per_launch": alg_eval, "launch_ms": eval_ms}
-
     clk.__exit__(None, None, None)   # sampled over the timed solves, e2e and roofline launches
+    # the eval kernel is bound by instruction issue: warp instructions per launch (ncu) over the
+    # issue capacity in the measured launch time (4 schedulers per SM, one instruction per cycle,
+    # at the SM clock sampled during the run)
+    winst = recorded_warp_instructions("k_eval_3t.md", EVAL_SOURCES) \
+        if args.workload == "3t" else None
+    clk_mhz = clk.summary().get("sm_mhz") or 2032.0
+    if winst is not None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        cap = sms * 4 * clk_mhz * 1e6 * eval_ms / 1e3
+        eval_roof["issue"] = {"warp_instructions_per_launch": winst, "issue_capacity": cap,
+                              "frac": winst / cap, "sm_mhz": clk_mhz}
 
     prec = None
     if rank == 0 and args.workload == "3t" and not args.no_precision:

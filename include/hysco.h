@@ -248,6 +248,18 @@ int hysco_batch_tune(hysco_batch_t batch, const void* const* Ip, const void* con
  * size with >= 2 blocks per pair), out[2] blocks of the batched PCG grid. */
 int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
 
+/* The persistent PCG's launch plan (pcg_path 0 / 2): out[0] cooperative grid (0 when the device
+ * cannot run it), out[1] slots per thread whose r, p and H p stay in shared memory for the whole
+ * launch, out[2] slots per thread in all (float4 groups of the pitched field over grid * 256
+ * threads).  Slots past out[1] keep those vectors in global memory; the arithmetic, and so the
+ * result, is the same either way. */
+int hysco_pcg_plan(hysco_t h, int32_t out[3]);
+
+/* Limits the on-chip slots of the persistent PCG to `onchip` (0 .. the plan's maximum; -1
+ * restores the maximum), for testing and tuning.  HYSCO_EINVAL outside that range.  Drops the
+ * cached solve graph. */
+int hysco_set_pcg_onchip(hysco_t h, int onchip);
+
 /* Synchronises `stream` and returns the numerical status of the last hysco_eval / hysco_solve /
  * hysco_init_ot on this handle: HYSCO_OK, HYSCO_INFEASIBLE, HYSCO_ENONFINITE or HYSCO_ETIMEOUT
  * (or HYSCO_ECUDA when the stream reports an error). */

@@ -31,7 +31,8 @@ struct hysco_ctx {
   float* partials;
   unsigned* counter;
   DevState* st;
-  int pgrid;          // persistent PCG grid (0: not available on this device)
+  PcgPlan pplan;      // persistent PCG grid (0: not available on this device), on-chip slots
+  int onchip_max;     // the plan's on-chip slots before any hysco_set_pcg_onchip
   int fgrid;          // one-barrier persistent PCG grid (0: not available)
   unsigned* psync;    // their barrier / reduction words
   bool have_lin, have_factor;
@@ -92,10 +93,10 @@ int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
   const bool jac = precond == HYSCO_PC_JACOBI;
   switch (path) {
     case 0:   // measured fastest on B300 at 3T and 7T sizes: the two-barrier persistent kernel
-      *mode = jac && h->pgrid > 0 ? kPcgPersistent : kPcgSeparate;
+      *mode = jac && h->pplan.grid > 0 ? kPcgPersistent : kPcgSeparate;
       return HYSCO_OK;
     case 1: *mode = kPcgSeparate; return HYSCO_OK;
-    case 2: *mode = kPcgPersistent; return jac && h->pgrid > 0 ? HYSCO_OK : HYSCO_EINVAL;
+    case 2: *mode = kPcgPersistent; return jac && h->pplan.grid > 0 ? HYSCO_OK : HYSCO_EINVAL;
     case 3: *mode = kPcgFused; return jac && h->fgrid > 0 ? HYSCO_OK : HYSCO_EINVAL;
     default: return HYSCO_EINVAL;
   }
@@ -115,7 +116,7 @@ int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int
     return HYSCO_OK;
   }
   if (mode == kPcgPersistent) {
-    HYSCO_TRY(launch_pcg_persistent(geo, h->pgrid, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
+    HYSCO_TRY(launch_pcg_persistent(geo, h->pplan, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
                                     h->dco, h->eco, h->invd, h->psync, max_it, rtol,
                                     h->st, s));
     return HYSCO_OK;
@@ -278,9 +279,10 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
     delete h;
     return HYSCO_ENOMEM;
   }
-  h->pgrid = pcg_persistent_grid(h->device, pe_dim);
+  h->pplan = pcg_persistent_plan(h->device, pe_dim, (int)(nfp >> 2));
+  h->onchip_max = h->pplan.onchip;
   h->fgrid = pcg_fused_grid(h->device, pe_dim);
-  const int sync_grid = h->pgrid > h->fgrid ? h->pgrid : h->fgrid;
+  const int sync_grid = h->pplan.grid > h->fgrid ? h->pplan.grid : h->fgrid;
   if (sync_grid > 0 &&
       cudaMalloc((void**)&h->psync, pcg_sync_words(sync_grid) * sizeof(unsigned)) !=
           cudaSuccess) {
@@ -595,6 +597,23 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
     h->g_opts = *o;
   }
   HYSCO_TRY(cudaGraphLaunch(h->gexec, s));
+  return HYSCO_OK;
+}
+
+int hysco_pcg_plan(hysco_t h, int32_t out[3]) {
+  if (!h || !out) return HYSCO_EINVAL;
+  const long long T = (long long)h->pplan.grid * kBlock;
+  out[0] = h->pplan.grid;
+  out[1] = h->pplan.onchip;
+  out[2] = T > 0 ? (int32_t)(((long long)(h->g.nfp >> 2) + T - 1) / T) : 0;
+  return HYSCO_OK;
+}
+
+int hysco_set_pcg_onchip(hysco_t h, int onchip) {
+  if (!h || onchip < -1 || onchip > h->onchip_max) return HYSCO_EINVAL;
+  h->pplan.onchip = onchip < 0 ? h->onchip_max : onchip;
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);   // the cached graph used the old plan
+  h->gexec = nullptr;
   return HYSCO_OK;
 }
 

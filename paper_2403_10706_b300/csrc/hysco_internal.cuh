@@ -262,13 +262,16 @@ __device__ __forceinline__ float f4get(const float4& v, int u) {
 }
 
 // H z at the four nodes of group t (pitched layout), with the PCG direction update
-// p = z + beta p, Hp = H z + beta Hp (PCG) or Hv = H z (plain).  P is the PE axis.  Arrays that a
-// persistent kernel writes (z, p, Hp) are read with ordinary loads; d, e with the read-only path.
-// Padding lanes produce zeros.  Returns sum over the group of p * Hp (PCG).
+// p = z + beta p_old, Hp = H z + beta Hp_old (PCG; p_old, Hp_old given, ignored when first) or
+// Hv = H z (plain, into hn).  P is the PE axis.  z, which a persistent kernel writes, is read
+// with ordinary loads; d, e with the read-only path.  Padding lanes produce zeros.  Returns the
+// sum over the group of p * Hp (PCG).
 template <int P, bool PCG>
-__device__ __forceinline__ float hv_group(const Geo& g, int t, const float* z, float* p, float* Hp,
-                                          const float* __restrict__ dco,
-                                          const float* __restrict__ eco, float beta, bool first) {
+__device__ __forceinline__ float hv_core(const Geo& g, int t, const float* z,
+                                         const float* __restrict__ dco,
+                                         const float* __restrict__ eco, float beta, bool first,
+                                         const float4& po, const float4& ho, float4& pn,
+                                         float4& hn) {
   const GroupPos q = group_pos(g, t);
   const int n = 4 * t, fe2 = g.fe[2];
   const int s1 = g.G4, s0 = g.fe[1] * g.G4;          // group strides of axes 1 and 0
@@ -285,11 +288,6 @@ __device__ __forceinline__ float hv_group(const Geo& g, int t, const float* z, f
   if (P == 0 && q.i0 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s0);
   if (P == 1 && q.i1 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s1);
   if (P == 2 && q.x0 > 0) el = __ldg(eco + n - 1);
-  float4 po = make_float4(0.f, 0.f, 0.f, 0.f), ho = po;
-  if (PCG && !first) {
-    po = reinterpret_cast<const float4*>(p)[t];
-    ho = reinterpret_cast<const float4*>(Hp)[t];
-  }
   float outp[4], outh[4], acc = 0.f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -314,11 +312,28 @@ __device__ __forceinline__ float hv_group(const Geo& g, int t, const float* z, f
       outh[u] = real ? hk : 0.f;
       acc += outp[u] * outh[u];
     } else {
+      outp[u] = 0.f;
       outh[u] = real ? w : 0.f;
     }
   }
-  reinterpret_cast<float4*>(Hp)[t] = make_float4(outh[0], outh[1], outh[2], outh[3]);
-  if (PCG) reinterpret_cast<float4*>(p)[t] = make_float4(outp[0], outp[1], outp[2], outp[3]);
+  pn = make_float4(outp[0], outp[1], outp[2], outp[3]);
+  hn = make_float4(outh[0], outh[1], outh[2], outh[3]);
+  return acc;
+}
+
+// hv_core with p, Hp in global memory (read with ordinary loads, updated in place)
+template <int P, bool PCG>
+__device__ __forceinline__ float hv_group(const Geo& g, int t, const float* z, float* p, float* Hp,
+                                          const float* __restrict__ dco,
+                                          const float* __restrict__ eco, float beta, bool first) {
+  float4 po = make_float4(0.f, 0.f, 0.f, 0.f), ho = po, pn, hn;
+  if (PCG && !first) {
+    po = reinterpret_cast<const float4*>(p)[t];
+    ho = reinterpret_cast<const float4*>(Hp)[t];
+  }
+  const float acc = hv_core<P, PCG>(g, t, z, dco, eco, beta, first, po, ho, pn, hn);
+  reinterpret_cast<float4*>(Hp)[t] = hn;
+  if (PCG) reinterpret_cast<float4*>(p)[t] = pn;
   return acc;
 }
 
@@ -394,18 +409,23 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const float* lco, int first, double rtol, float sign,
                              const Work& w, cudaStream_t s);
 
-// k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible), and the number of
+// k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible) for a field of n4
+// float4 groups, and the slots per thread whose r, p, Hp stay in shared memory; the number of
 // 32-bit barrier/reduction words a launch of that grid needs
-int pcg_persistent_grid(int device, int pe_axis);
+struct PcgPlan {
+  int grid, onchip;
+};
+PcgPlan pcg_persistent_plan(int device, int pe_axis, int n4);
+inline size_t pcg_onchip_bytes(int slots) { return (size_t)slots * 3 * kBlock * 16; }   // r, p, Hp
 constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arrival counter's line)
 constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused reduction)
 constexpr int kTagWordsPerLaneHost = 16;   // grid_allreduce_unordered's block-range limit / 32
 // counter line, two float slots of kSyncMaxK per block, two slots of one tagged 64-bit word per block
 inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid + 4ull * (size_t)grid; }
-cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
-                                  float* x, float* r, float* z, float* p0, float* p1, float* Hp,
-                                  const float* dco, const float* eco, const float* invd,
-                                  unsigned* sync, int max_it, double rtol,
+cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
+                                  float rhs_sign, float* x, float* r, float* z, float* p0,
+                                  float* p1, float* Hp, const float* dco, const float* eco,
+                                  const float* invd, unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s);
 // k_pcg_batched.cu: the Jacobi PCG of many pairs in one cooperative launch.  Pair i is worked
 // on by blocks blk0 .. blk0 + nblk - 1 of the grid; its arrays are those of its handle.

@@ -17,6 +17,14 @@
 // stencil reads one array (z) and p, Hp are updated in place.  The arithmetic per node is that
 // of the separate kernels in k_pcg.cu.
 //
+// On-chip state: a thread's groups are the same in every phase (t = gtid + s T, slot s), and x, r,
+// p and Hp are only ever touched at the thread's own groups (the stencil reads z alone).  So r, p
+// and Hp of the first `onchip` slots live in dynamic shared memory for the whole launch (the
+// thread's own words, no block synchronisation) and only z, x and the read-only coefficients
+// travel through L2/HBM; slots beyond `onchip` (volumes too large for shared memory) keep r, p,
+// Hp in global memory.  At 3T size every slot is on chip: 7 instead of 15 field streams per
+// iteration.
+//
 // Memory: arrays written inside the launch (x, r, z, p, Hp) are read with ordinary (coherent)
 // loads after a barrier, never through the read-only path; d, e, 1/diag and grad are read-only.
 // A block releases its phase's writes with a fence before it publishes its words; a reader
@@ -48,6 +56,7 @@ struct PcgArgs {
   DevState* st;
   int max_it;
   double rtol;
+  int onchip;            // slots per thread whose r, p, Hp are in shared memory
 };
 
 template <int P>
@@ -55,11 +64,19 @@ __global__ void __launch_bounds__(kBlock)
 k_pcg_persistent(Geo g, PcgArgs a) {
   __shared__ float shf[32 * 2];
   __shared__ df32 shd[32 * 2];
+  extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kBlock]
   DevState* st = a.st;
   if (st->stop) return;
   const int T = gridDim.x * blockDim.x;
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int n4 = g.nfp >> 2;   // float4 groups of the pitched field (padding is zero)
+  const int G = a.onchip;
+  float4* const rS = slots + threadIdx.x;
+  float4* const pS = rS + G * kBlock;
+  float4* const hS = pS + G * kBlock;
+  float4* const r4 = reinterpret_cast<float4*>(a.r);
+  float4* const p4 = reinterpret_cast<float4*>(a.p0);
+  float4* const h4 = reinterpret_cast<float4*>(a.Hp);
   unsigned gen = 0;
   auto timed_out = [&]() { if (threadIdx.x == 0) { st->status = -6; st->stop = 1; } };
 
@@ -67,7 +84,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   // ---- init --------------------------------------------------------------------------------
   {
     float arr = 0.f, arz = 0.f;
-    for (int i0 = gtid; i0 < n4; i0 += kPcgUnroll * T) {
+    for (int i0 = gtid, s0 = 0; i0 < n4; i0 += kPcgUnroll * T, s0 += kPcgUnroll) {
       float4 gv[kPcgUnroll], dv[kPcgUnroll];
 #pragma unroll
       for (int u = 0; u < kPcgUnroll; ++u) {
@@ -77,13 +94,14 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       }
 #pragma unroll
       for (int u = 0; u < kPcgUnroll; ++u) {
-        int i = i0 + u * T;
+        int i = i0 + u * T, sl = s0 + u;
         float4 rv = make_float4(a.rhs_sign * gv[u].x, a.rhs_sign * gv[u].y, a.rhs_sign * gv[u].z,
                                 a.rhs_sign * gv[u].w);
         float4 zv = make_float4(rv.x * dv[u].x, rv.y * dv[u].y, rv.z * dv[u].z, rv.w * dv[u].w);
         if (i < n4) {
           reinterpret_cast<float4*>(a.x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          reinterpret_cast<float4*>(a.r)[i] = rv;
+          if (sl < G) rS[sl * kBlock] = rv;
+          else r4[i] = rv;
           reinterpret_cast<float4*>(a.z)[i] = zv;
           arr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
           arz += rv.x * zv.x + rv.y * zv.y + rv.z * zv.z + rv.w * zv.w;
@@ -101,11 +119,20 @@ k_pcg_persistent(Geo g, PcgArgs a) {
 
   for (int i = 0; i < a.max_it && !done; ++i) {
     const bool first = i == 0;
-    float* pv_ = a.p0;
     const float fb = beta;
     // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp (groups of 4 pitched nodes) ----------
     float acc = 0.f;
-    for (int t = gtid; t < n4; t += T) acc += hv_group<P, true>(g, t, a.z, pv_, a.Hp, a.dco, a.eco, fb, first);
+    for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
+      const bool on = sl < G;
+      float4 po = make_float4(0.f, 0.f, 0.f, 0.f), ho = po, pn, hn;
+      if (!first) {
+        po = on ? pS[sl * kBlock] : p4[t];
+        ho = on ? hS[sl * kBlock] : h4[t];
+      }
+      acc += hv_core<P, true>(g, t, a.z, a.dco, a.eco, fb, first, po, ho, pn, hn);
+      if (on) { pS[sl * kBlock] = pn; hS[sl * kBlock] = hn; }
+      else { p4[t] = pn; h4[t] = hn; }
+    }
     {
       // only p.Hp crosses blocks here (phase B reads the thread's own groups)
       float t1[1] = {acc};
@@ -114,21 +141,23 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       const float al = rho / t1[0];
       // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
       float arr = 0.f, arz = 0.f;
-      for (int j0 = gtid; j0 < n4; j0 += kPcgUnroll * T) {
+      for (int j0 = gtid, s0 = 0; j0 < n4; j0 += kPcgUnroll * T, s0 += kPcgUnroll) {
         float4 pv[kPcgUnroll], hv[kPcgUnroll], dv[kPcgUnroll], rv[kPcgUnroll], xv[kPcgUnroll];
 #pragma unroll
         for (int u = 0; u < kPcgUnroll; ++u) {
           // out-of-range slots re-read this thread's own group j0 (never another thread's)
-          int j = j0 + u * T < n4 ? j0 + u * T : j0;
-          pv[u] = reinterpret_cast<const float4*>(pv_)[j];
-          hv[u] = reinterpret_cast<const float4*>(a.Hp)[j];
+          const bool in = j0 + u * T < n4;
+          const int j = in ? j0 + u * T : j0, sl = in ? s0 + u : s0;
+          const bool on = sl < G;
+          pv[u] = on ? pS[sl * kBlock] : p4[j];
+          hv[u] = on ? hS[sl * kBlock] : h4[j];
+          rv[u] = on ? rS[sl * kBlock] : r4[j];
           dv[u] = __ldg(reinterpret_cast<const float4*>(a.invd) + j);
-          rv[u] = reinterpret_cast<const float4*>(a.r)[j];
           xv[u] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(a.x)[j];
         }
 #pragma unroll
         for (int u = 0; u < kPcgUnroll; ++u) {
-          int j = j0 + u * T;
+          const int j = j0 + u * T, sl = s0 + u;
           float4 X = xv[u], R = rv[u];
           X.x = fmaf(al, pv[u].x, X.x); X.y = fmaf(al, pv[u].y, X.y);
           X.z = fmaf(al, pv[u].z, X.z); X.w = fmaf(al, pv[u].w, X.w);
@@ -137,7 +166,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
           float4 Z = make_float4(R.x * dv[u].x, R.y * dv[u].y, R.z * dv[u].z, R.w * dv[u].w);
           if (j < n4) {
             reinterpret_cast<float4*>(a.x)[j] = X;
-            reinterpret_cast<float4*>(a.r)[j] = R;
+            if (sl < G) rS[sl * kBlock] = R;
+            else r4[j] = R;
             reinterpret_cast<float4*>(a.z)[j] = Z;
             arr += R.x * R.x + R.y * R.y + R.z * R.z + R.w * R.w;
             arz += R.x * Z.x + R.y * Z.y + R.z * Z.z + R.w * Z.w;
@@ -405,15 +435,45 @@ k_pcg_fused(Geo g, FusedArgs a) {
 }
 
 template <int P>
-static int grid_for(int device) {
-  int sms = 0, per_sm = 0, coop = 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+static PcgPlan plan_for(int device, int n4) {
+  PcgPlan pl{0, 0};
+  int sms = 0, per_sm = 0, coop = 0, optin = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return pl;
   if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kBlock, 0) !=
+    return pl;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
       cudaSuccess)
-    return 0;
-  return std::min(sms * per_sm, 32 * kTagWordsPerLane);
+    optin = 48 * 1024;
+  // blocks per SM as the registers allow, then as many on-chip slots as keep that occupancy
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kBlock, 0) !=
+          cudaSuccess || per_sm < 1)
+    return pl;
+  const int grid = std::min(sms * per_sm, 32 * kTagWordsPerLane);
+  const long long T = (long long)grid * kBlock;
+  // the launch limit is the device's opt-in maximum less the static shared memory (the same for
+  // every handle); the occupancy test below takes each candidate size explicitly
+  int G = 0;
+  cudaFuncAttributes fa;
+  const int dyn_max = cudaFuncGetAttributes(&fa, k_pcg_persistent<P>) == cudaSuccess
+                          ? optin - (int)fa.sharedSizeBytes
+                          : 0;
+  if (dyn_max > 0 && cudaFuncSetAttribute(k_pcg_persistent<P>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          dyn_max) == cudaSuccess) {
+    G = (int)std::min<long long>((n4 + T - 1) / T, dyn_max / pcg_onchip_bytes(1));
+    for (; G > 0; --G) {
+      int got = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k_pcg_persistent<P>, kBlock,
+                                                        pcg_onchip_bytes(G)) == cudaSuccess &&
+          got * sms >= grid)
+        break;
+    }
+  }
+  cudaGetLastError();
+  pl.grid = grid;
+  pl.onchip = G;
+  return pl;
 }
 
 template <int P>
@@ -449,24 +509,26 @@ cudaError_t launch_pcg_fused(const Geo& g, int grid, const float* grad, float rh
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
 }
 
-int pcg_persistent_grid(int device, int pe_axis) {
-  return pe_axis == 0 ? grid_for<0>(device) : (pe_axis == 1 ? grid_for<1>(device)
-                                                            : grid_for<2>(device));
+PcgPlan pcg_persistent_plan(int device, int pe_axis, int n4) {
+  return pe_axis == 0 ? plan_for<0>(device, n4)
+                      : (pe_axis == 1 ? plan_for<1>(device, n4) : plan_for<2>(device, n4));
 }
 
-cudaError_t launch_pcg_persistent(const Geo& g, int grid, const float* grad, float rhs_sign,
-                                  float* x, float* r, float* z, float* p0, float* p1, float* Hp,
-                                  const float* dco, const float* eco, const float* invd,
-                                  unsigned* sync, int max_it, double rtol,
+cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
+                                  float rhs_sign, float* x, float* r, float* z, float* p0,
+                                  float* p1, float* Hp, const float* dco, const float* eco,
+                                  const float* invd, unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(grid) * sizeof(unsigned), s);
+  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(pl.grid) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
-  PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol};
+  PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol,
+            pl.onchip};
   Geo gg = g;
   void* args[] = {&gg, &a};
   void* fn = g.p == 0 ? (void*)k_pcg_persistent<0>
                       : (g.p == 1 ? (void*)k_pcg_persistent<1> : (void*)k_pcg_persistent<2>);
-  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+  return cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kBlock), args,
+                                     pcg_onchip_bytes(pl.onchip), s);
 }
 
 }  // namespace hysco

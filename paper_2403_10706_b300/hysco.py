@@ -199,6 +199,16 @@ class Hysco:
                                         _stream(self.device)), "hysco_solve")
         return b, (st[:gn_iters] if st is not None else None)
 
+    def pcg_plan(self):
+        """(cooperative grid, on-chip slots per thread, slots per thread) of the persistent PCG."""
+        out = (C.c_int32 * 3)()
+        _lib.check(self.lib.hysco_pcg_plan(self._h, out), "hysco_pcg_plan")
+        return tuple(out)
+
+    def set_pcg_onchip(self, onchip):
+        """Limit the persistent PCG's on-chip slots (-1: the plan's maximum)."""
+        _lib.check(self.lib.hysco_set_pcg_onchip(self._h, int(onchip)), "hysco_set_pcg_onchip")
+
     def last_status(self):
         """Numerical status of the last eval / solve / init_ot: 0 ok, 1 infeasible (J = +inf),
         -4 NaN.  Synchronises the current stream; raises only on a CUDA error."""

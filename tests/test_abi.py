@@ -94,6 +94,8 @@ def test_adjoint_and_batch_entry_points_reject_null_arguments(lib):
     assert lib.hysco_batch_tune(None, f, f, None, None) == _lib.EINVAL
     assert lib.hysco_batch_schedule(None, (C.c_int32 * 3)()) == _lib.EINVAL
     lib.hysco_batch_destroy(None)
+    assert lib.hysco_pcg_plan(None, (C.c_int32 * 3)()) == _lib.EINVAL
+    assert lib.hysco_set_pcg_onchip(None, 0) == _lib.EINVAL
 
 
 def test_barrier_selftest_rejects_bad_arguments_before_any_device_call(lib):
