@@ -530,10 +530,10 @@ def run_ours(args):
     # the stencil: reads r, w, q, 1/diag, p, x and writes x, p, q, r (40).
     pcg_iters = 10
     fused = args.pcg_path == 3
-    grid, onchip, slots = h.pcg_plan()
+    grid, onchip, slots, pblock = h.pcg_plan()
     fe = h.field_dims
     n4 = fe[0] * fe[1] * ((fe[2] + 3) // 4)
-    f_on = min(n4, onchip * grid * 256) / n4 if grid else 0.0    # share of groups on chip
+    f_on = min(n4, onchip * grid * pblock) / n4 if grid else 0.0    # share of groups on chip
     if fused:
         pcg_bytes = nfld * (24 + 40 + (pcg_iters - 2) * 52 + 40)
     elif args.pcg_path == 1:
@@ -553,8 +553,8 @@ def run_ours(args):
             if args.workload == "3t" and args.pcg_path in (0, 2) else None,
             "kernel": kname,
             "peak_source": peak_src, "alg_bytes_per_launch": pcg_bytes, "launch_ms": pcg_ms,
-            "pcg_plan": {"grid": grid, "onchip_slots": onchip, "slots": slots,
-                         "onchip_share": f_on},
+            "pcg_plan": {"grid": grid, "block": pblock, "onchip_slots": onchip,
+                         "slots": slots, "onchip_share": f_on},
             "note": "10 PCG iterations per launch; r, p, Hp of the on-chip share stay in shared "
                     "memory; z, x, d, e, 1/diag (54 MB) are largely L2-resident within a launch, "
                     "so achieved algorithmic bandwidth may exceed the HBM copy peak"}

@@ -250,10 +250,10 @@ int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
 
 /* The persistent PCG's launch plan (pcg_path 0 / 2): out[0] cooperative grid (0 when the device
  * cannot run it), out[1] slots per thread whose r, p and H p stay in shared memory for the whole
- * launch, out[2] slots per thread in all (float4 groups of the pitched field over grid * 256
- * threads).  Slots past out[1] keep those vectors in global memory; the arithmetic, and so the
- * result, is the same either way. */
-int hysco_pcg_plan(hysco_t h, int32_t out[3]);
+ * launch, out[2] slots per thread in all (float4 groups of the pitched field over grid * out[3]
+ * threads), out[3] threads per block.  Slots past out[1] keep those vectors in global memory;
+ * the arithmetic, and so the result, is the same either way. */
+int hysco_pcg_plan(hysco_t h, int32_t out[4]);
 
 /* Limits the on-chip slots of the persistent PCG to `onchip` (0 .. the plan's maximum; -1
  * restores the maximum), for testing and tuning.  HYSCO_EINVAL outside that range.  Drops the

@@ -7,6 +7,7 @@
 namespace hysco {
 
 constexpr long long kBarrierSpinCycles = 4000000000LL;   // ~2 s at 2 GHz
+constexpr int kSumChunk = 8;   // partial-sum loads in flight per lane in grid_allreduce
 
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -59,9 +60,21 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
     df32 acc[K];
 #pragma unroll
     for (int i = 0; i < K; ++i) acc[i] = df32{0.f, 0.f};
-    for (int b = first + tid; b < first + count; b += 32)
+    // kSumChunk blocks per lane in flight per round, then added in block order
+    for (int b0 = first + tid; b0 < first + count; b0 += 32 * kSumChunk) {
+      float x[kSumChunk][K];
 #pragma unroll
-      for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{__ldcg(slot + b * K + i), 0.f});
+      for (int j = 0; j < kSumChunk; ++j) {
+        const int b = b0 + 32 * j;
+#pragma unroll
+        for (int i = 0; i < K; ++i) x[j][i] = b < first + count ? __ldcg(slot + b * K + i) : 0.f;
+      }
+#pragma unroll
+      for (int j = 0; j < kSumChunk; ++j)
+        if (b0 + 32 * j < first + count)
+#pragma unroll
+          for (int i = 0; i < K; ++i) acc[i] = df_add(acc[i], df32{x[j][i], 0.f});
+    }
 #pragma unroll
     for (int i = 0; i < K; ++i)
 #pragma unroll

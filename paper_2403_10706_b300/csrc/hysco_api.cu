@@ -600,12 +600,13 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, const
   return HYSCO_OK;
 }
 
-int hysco_pcg_plan(hysco_t h, int32_t out[3]) {
+int hysco_pcg_plan(hysco_t h, int32_t out[4]) {
   if (!h || !out) return HYSCO_EINVAL;
-  const long long T = (long long)h->pplan.grid * kBlock;
+  const long long T = (long long)h->pplan.grid * kPcgBlock;
   out[0] = h->pplan.grid;
   out[1] = h->pplan.onchip;
   out[2] = T > 0 ? (int32_t)(((long long)(h->g.nfp >> 2) + T - 1) / T) : 0;
+  out[3] = kPcgBlock;
   return HYSCO_OK;
 }
 

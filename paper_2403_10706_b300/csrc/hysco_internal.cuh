@@ -416,7 +416,9 @@ struct PcgPlan {
   int grid, onchip;
 };
 PcgPlan pcg_persistent_plan(int device, int pe_axis, int n4);
-inline size_t pcg_onchip_bytes(int slots) { return (size_t)slots * 3 * kBlock * 16; }   // r, p, Hp
+constexpr int kPcgBlock = 768;        // threads per block of the persistent PCG
+constexpr int kPcgBlocksPerSm = 1;    // its blocks per SM at most
+inline size_t pcg_onchip_bytes(int slots) { return (size_t)slots * 3 * kPcgBlock * 16; }   // r, p, Hp
 constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arrival counter's line)
 constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused reduction)
 constexpr int kTagWordsPerLaneHost = 16;   // grid_allreduce_unordered's block-range limit / 32

@@ -60,11 +60,11 @@ struct PcgArgs {
 };
 
 template <int P>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kPcgBlock)
 k_pcg_persistent(Geo g, PcgArgs a) {
   __shared__ float shf[32 * 2];
   __shared__ df32 shd[32 * 2];
-  extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kBlock]
+  extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kPcgBlock]
   DevState* st = a.st;
   if (st->stop) return;
   const int T = gridDim.x * blockDim.x;
@@ -72,8 +72,8 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   const int n4 = g.nfp >> 2;   // float4 groups of the pitched field (padding is zero)
   const int G = a.onchip;
   float4* const rS = slots + threadIdx.x;
-  float4* const pS = rS + G * kBlock;
-  float4* const hS = pS + G * kBlock;
+  float4* const pS = rS + G * kPcgBlock;
+  float4* const hS = pS + G * kPcgBlock;
   float4* const r4 = reinterpret_cast<float4*>(a.r);
   float4* const p4 = reinterpret_cast<float4*>(a.p0);
   float4* const h4 = reinterpret_cast<float4*>(a.Hp);
@@ -100,7 +100,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
         float4 zv = make_float4(rv.x * dv[u].x, rv.y * dv[u].y, rv.z * dv[u].z, rv.w * dv[u].w);
         if (i < n4) {
           reinterpret_cast<float4*>(a.x)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (sl < G) rS[sl * kBlock] = rv;
+          if (sl < G) rS[sl * kPcgBlock] = rv;
           else r4[i] = rv;
           reinterpret_cast<float4*>(a.z)[i] = zv;
           arr += rv.x * rv.x + rv.y * rv.y + rv.z * rv.z + rv.w * rv.w;
@@ -116,57 +116,63 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
   bool done = !(rr0 > 0.f);
   int it = 0;
+  // x += alpha p of iteration i is applied in phase A of iteration i + 1 (from p before its
+  // update), or by the pass after the loop: phase B then writes z alone, so the ordered barrier
+  // after it waits for fewer outstanding stores.  Same operations on every x element.
+  float al_x = 0.f;   // alpha whose x update is pending (0: none)
+  float4* const x4 = reinterpret_cast<float4*>(a.x);
 
   for (int i = 0; i < a.max_it && !done; ++i) {
     const bool first = i == 0;
     const float fb = beta;
-    // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp (groups of 4 pitched nodes) ----------
+    // ---- A: x += alpha_{i-1} p; w = H z; p = z + beta p; Hp = w + beta Hp -----------------
     float acc = 0.f;
     for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
       const bool on = sl < G;
       float4 po = make_float4(0.f, 0.f, 0.f, 0.f), ho = po, pn, hn;
       if (!first) {
-        po = on ? pS[sl * kBlock] : p4[t];
-        ho = on ? hS[sl * kBlock] : h4[t];
+        po = on ? pS[sl * kPcgBlock] : p4[t];
+        ho = on ? hS[sl * kPcgBlock] : h4[t];
+        float4 X = i == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
+        X.x = fmaf(al_x, po.x, X.x); X.y = fmaf(al_x, po.y, X.y);
+        X.z = fmaf(al_x, po.z, X.z); X.w = fmaf(al_x, po.w, X.w);
+        x4[t] = X;
       }
       acc += hv_core<P, true>(g, t, a.z, a.dco, a.eco, fb, first, po, ho, pn, hn);
-      if (on) { pS[sl * kBlock] = pn; hS[sl * kBlock] = hn; }
+      if (on) { pS[sl * kPcgBlock] = pn; hS[sl * kPcgBlock] = hn; }
       else { p4[t] = pn; h4[t] = hn; }
     }
+    al_x = 0.f;
     {
       // only p.Hp crosses blocks here (phase B reads the thread's own groups)
       float t1[1] = {acc};
       if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd)) { timed_out(); return; }
       if (!(t1[0] > 0.f)) { done = true; break; }
       const float al = rho / t1[0];
-      // ---- B: x += alpha p, r -= alpha Hp, z = r / diag ----------------------------------
+      al_x = al;
+      // ---- B: r -= alpha Hp, z = r / diag --------------------------------------------------
       float arr = 0.f, arz = 0.f;
       for (int j0 = gtid, s0 = 0; j0 < n4; j0 += kPcgUnroll * T, s0 += kPcgUnroll) {
-        float4 pv[kPcgUnroll], hv[kPcgUnroll], dv[kPcgUnroll], rv[kPcgUnroll], xv[kPcgUnroll];
+        float4 hv[kPcgUnroll], dv[kPcgUnroll], rv[kPcgUnroll];
 #pragma unroll
         for (int u = 0; u < kPcgUnroll; ++u) {
           // out-of-range slots re-read this thread's own group j0 (never another thread's)
           const bool in = j0 + u * T < n4;
           const int j = in ? j0 + u * T : j0, sl = in ? s0 + u : s0;
           const bool on = sl < G;
-          pv[u] = on ? pS[sl * kBlock] : p4[j];
-          hv[u] = on ? hS[sl * kBlock] : h4[j];
-          rv[u] = on ? rS[sl * kBlock] : r4[j];
+          hv[u] = on ? hS[sl * kPcgBlock] : h4[j];
+          rv[u] = on ? rS[sl * kPcgBlock] : r4[j];
           dv[u] = __ldg(reinterpret_cast<const float4*>(a.invd) + j);
-          xv[u] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : reinterpret_cast<const float4*>(a.x)[j];
         }
 #pragma unroll
         for (int u = 0; u < kPcgUnroll; ++u) {
           const int j = j0 + u * T, sl = s0 + u;
-          float4 X = xv[u], R = rv[u];
-          X.x = fmaf(al, pv[u].x, X.x); X.y = fmaf(al, pv[u].y, X.y);
-          X.z = fmaf(al, pv[u].z, X.z); X.w = fmaf(al, pv[u].w, X.w);
+          float4 R = rv[u];
           R.x = fmaf(-al, hv[u].x, R.x); R.y = fmaf(-al, hv[u].y, R.y);
           R.z = fmaf(-al, hv[u].z, R.z); R.w = fmaf(-al, hv[u].w, R.w);
           float4 Z = make_float4(R.x * dv[u].x, R.y * dv[u].y, R.z * dv[u].z, R.w * dv[u].w);
           if (j < n4) {
-            reinterpret_cast<float4*>(a.x)[j] = X;
-            if (sl < G) rS[sl * kBlock] = R;
+            if (sl < G) rS[sl * kPcgBlock] = R;
             else r4[j] = R;
             reinterpret_cast<float4*>(a.z)[j] = Z;
             arr += R.x * R.x + R.y * R.y + R.z * R.z + R.w * R.w;
@@ -184,6 +190,16 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     } else {
       beta = tot[1] / rho;
       rho = tot[1];
+    }
+  }
+  // the last iteration's x += alpha p (each thread its own groups: no barrier needed)
+  if (al_x != 0.f) {
+    for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
+      const float4 pv = sl < G ? pS[sl * kPcgBlock] : p4[t];
+      float4 X = it == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
+      X.x = fmaf(al_x, pv.x, X.x); X.y = fmaf(al_x, pv.y, X.y);
+      X.z = fmaf(al_x, pv.z, X.z); X.w = fmaf(al_x, pv.w, X.w);
+      x4[t] = X;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -445,12 +461,14 @@ static PcgPlan plan_for(int device, int n4) {
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
       cudaSuccess)
     optin = 48 * 1024;
-  // blocks per SM as the registers allow, then as many on-chip slots as keep that occupancy
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kBlock, 0) !=
+  // blocks per SM as the registers allow (at most kPcgBlocksPerSm: the barriers' latency grows
+  // with the number of blocks), then as many on-chip slots as keep that occupancy
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<P>, kPcgBlock, 0) !=
           cudaSuccess || per_sm < 1)
     return pl;
+  per_sm = std::min(per_sm, kPcgBlocksPerSm);
   const int grid = std::min(sms * per_sm, 32 * kTagWordsPerLane);
-  const long long T = (long long)grid * kBlock;
+  const long long T = (long long)grid * kPcgBlock;
   // the launch limit is the device's opt-in maximum less the static shared memory (the same for
   // every handle); the occupancy test below takes each candidate size explicitly
   int G = 0;
@@ -464,7 +482,7 @@ static PcgPlan plan_for(int device, int n4) {
     G = (int)std::min<long long>((n4 + T - 1) / T, dyn_max / pcg_onchip_bytes(1));
     for (; G > 0; --G) {
       int got = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k_pcg_persistent<P>, kBlock,
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&got, k_pcg_persistent<P>, kPcgBlock,
                                                         pcg_onchip_bytes(G)) == cudaSuccess &&
           got * sms >= grid)
         break;
@@ -527,7 +545,7 @@ cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* 
   void* args[] = {&gg, &a};
   void* fn = g.p == 0 ? (void*)k_pcg_persistent<0>
                       : (g.p == 1 ? (void*)k_pcg_persistent<1> : (void*)k_pcg_persistent<2>);
-  return cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kBlock), args,
+  return cudaLaunchCooperativeKernel(fn, dim3(pl.grid), dim3(kPcgBlock), args,
                                      pcg_onchip_bytes(pl.onchip), s);
 }
 

@@ -200,8 +200,9 @@ class Hysco:
         return b, (st[:gn_iters] if st is not None else None)
 
     def pcg_plan(self):
-        """(cooperative grid, on-chip slots per thread, slots per thread) of the persistent PCG."""
-        out = (C.c_int32 * 3)()
+        """(cooperative grid, on-chip slots per thread, slots per thread, threads per block) of
+        the persistent PCG."""
+        out = (C.c_int32 * 4)()
         _lib.check(self.lib.hysco_pcg_plan(self._h, out), "hysco_pcg_plan")
         return tuple(out)
 

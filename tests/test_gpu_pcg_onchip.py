@@ -32,8 +32,8 @@ def host(t):
 def test_onchip_placement_is_bit_identical(H, name):
     pr = ph.make_pair(name)
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
-    grid, onchip, slots = h.pcg_plan()
-    assert grid > 0 and slots >= 1
+    grid, onchip, slots, block = h.pcg_plan()
+    assert grid > 0 and slots >= 1 and block >= 32
     assert onchip == slots, (grid, onchip, slots)
     Ip = torch.from_numpy(pr.Ip).cuda()
     Im = torch.from_numpy(pr.Im).cuda()
