@@ -218,8 +218,9 @@ int hysco_selftest_barrier(int grid, int missing_block, int64_t spin_cycles,
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):
  * per GN iteration the per-pair evaluation, Armijo and update kernels of different pairs run on
- * concurrent branches, and the Jacobi PCG of all pairs is one cooperative launch whose grid is
- * shared among the pairs (the device-wide barriers are paid once for the batch).  The fixed launch
+ * concurrent branches, and the Jacobi PCG of all pairs is either one cooperative launch whose grid
+ * is shared among the pairs (the device-wide barriers are paid once for the batch) or each pair's
+ * own persistent PCG in turn (its vectors on chip, see hysco_pcg_plan).  The fixed launch
  * sequence is captured in a CUDA graph (cached per argument set) unless opts->no_graph.  The batch
  * holds no reference count: destroy it before any of its handles. */
 typedef struct hysco_batch_ctx* hysco_batch_t;
@@ -239,14 +240,21 @@ int hysco_batch_solve(hysco_batch_t batch, const void* const* Ip, const void* co
 
 /* Autotuner: times short trial solves (OT + at most 2 GN iterations into scratch fields, the
  * caller's fields untouched) of each candidate schedule -- 1, 2, 4 or 8 concurrent branches for
- * the per-pair kernels, PCG blocks shared by field size with at least 1 or at least 2 blocks per
- * pair -- and keeps the fastest.  Synchronises `stream`. */
+ * the per-pair kernels; the shared PCG launch with blocks by field size and at least 1 or at least
+ * 2 blocks per pair, or the per-pair persistent PCG -- and keeps the fastest.  Synchronises
+ * `stream`. */
 int hysco_batch_tune(hysco_batch_t batch, const void* const* Ip, const void* const* Im,
                      const hysco_opts* opts, hysco_stream_t stream);
 
-/* The schedule in use: out[0] branches, out[1] block-share policy (0: by field size, 1: by field
- * size with >= 2 blocks per pair), out[2] blocks of the batched PCG grid. */
+/* The schedule in use: out[0] branches, out[1] PCG policy (0: shared launch, blocks by field size;
+ * 1: the same with >= 2 blocks per pair; 2: each pair's persistent PCG in turn), out[2] blocks of
+ * the shared PCG launch's grid. */
 int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
+
+/* Sets the schedule: branches 1 .. min(8, n), PCG policy 0 .. 2 as in hysco_batch_schedule.
+ * HYSCO_EINVAL when out of range or infeasible for this batch (then unchanged).  Drops the cached
+ * graph. */
+int hysco_batch_set_schedule(hysco_batch_t batch, int branches, int policy);
 
 /* The persistent PCG's launch plan (pcg_path 0 / 2): out[0] cooperative grid (0 when the device
  * cannot run it), out[1] slots per thread whose r, p and H p stay in shared memory for the whole

@@ -75,6 +75,7 @@ def load():
         "hysco_batch_solve": (I, [P, P, P, P, C.POINTER(Opts), P, P]),
         "hysco_batch_tune": (I, [P, P, P, C.POINTER(Opts), P]),
         "hysco_batch_schedule": (I, [P, C.POINTER(C.c_int32)]),
+        "hysco_batch_set_schedule": (I, [P, I, I]),
         "hysco_selftest_barrier": (I, [I, I, C.c_int64, P]),
         "hysco_pcg_plan": (I, [P, C.POINTER(C.c_int32)]),
         "hysco_set_pcg_onchip": (I, [P, I]),

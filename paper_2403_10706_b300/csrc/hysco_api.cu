@@ -648,7 +648,8 @@ struct hysco_batch_ctx {
   int* d_block_pair = nullptr;
   unsigned* sync = nullptr;
   int branches = 4;                   // schedule: concurrent branches of per-pair kernels
-  int policy = 0;                     // schedule: 0 blocks by field size, 1 the same with >= 2 each
+  int policy = 0;                     // schedule: 0 blocks by field size, 1 the same with >= 2 each,
+                                      // 2 each pair's own persistent PCG in turn
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> side;
   cudaEvent_t fork = nullptr;
@@ -710,6 +711,12 @@ bool batch_shares(const hysco_batch_ctx* B, int lo, std::vector<int>& out) {
 }
 
 int batch_layout(hysco_batch_ctx* B, int policy) {
+  if (policy == 2) {   // per-pair persistent PCG: every pair needs its cooperative plan
+    for (const hysco_ctx* h : B->hs)
+      if (h->pplan.grid <= 0) return HYSCO_EINVAL;
+    B->policy = policy;
+    return HYSCO_OK;
+  }
   std::vector<int> share;
   if (!batch_shares(B, policy == 1 ? 2 : 1, share)) return HYSCO_EINVAL;
   std::vector<BatchPair> pairs(B->n);
@@ -767,8 +774,16 @@ int enqueue_batch(hysco_batch_ctx* B, const void* const* Ip, const void* const* 
                             h->invd, it, h->work(), branch(i)));
     }
     HYSCO_TRY(batch_join(B, s));
-    HYSCO_TRY(launch_pcg_batched(B->grid, B->d_pairs, B->d_block_pair, o->pcg_max_iters,
-                                 o->pcg_rtol, B->sync, s));
+    if (B->policy == 2) {
+      // one pair at a time, each with its vectors on chip (a stopped pair's launch returns at once)
+      for (int i = 0; i < B->n; ++i)
+        if (int rc = run_pcg(B->hs[i], B->hs[i]->grad, -1.0f, B->hs[i]->x, HYSCO_PC_JACOBI,
+                             o->pcg_max_iters, o->pcg_rtol, kPcgPersistent, s))
+          return rc;
+    } else {
+      HYSCO_TRY(launch_pcg_batched(B->grid, B->d_pairs, B->d_block_pair, o->pcg_max_iters,
+                                   o->pcg_rtol, B->sync, s));
+    }
     HYSCO_TRY(batch_fork(B, s));
     for (int i = 0; i < B->n; ++i) {
       hysco_ctx* h = B->hs[i];
@@ -880,6 +895,21 @@ int hysco_batch_schedule(hysco_batch_t B, int32_t out[3]) {
   return HYSCO_OK;
 }
 
+int hysco_batch_set_schedule(hysco_batch_t B, int branches, int policy) {
+  if (!B || branches < 1 || branches > kMaxBranches || branches > B->n || policy < 0 ||
+      policy > 2)
+    return HYSCO_EINVAL;
+  const int old = B->policy;
+  if (int rc = batch_layout(B, policy)) {
+    batch_layout(B, old);
+    return rc;
+  }
+  B->branches = branches;
+  if (B->gexec) cudaGraphExecDestroy(B->gexec);   // the cached graph used the old schedule
+  B->gexec = nullptr;
+  return HYSCO_OK;
+}
+
 int hysco_batch_solve(hysco_batch_t B, const void* const* Ip, const void* const* Im,
                       float* const* b, const hysco_opts* o, double* const* stats,
                       hysco_stream_t stream) {
@@ -930,7 +960,7 @@ int hysco_batch_tune(hysco_batch_t B, const void* const* Ip, const void* const* 
     rc = HYSCO_ECUDA;
   float best = 1e30f;
   int best_br = B->branches, best_pol = B->policy;
-  for (int pol = 0; pol < 2 && rc == HYSCO_OK; ++pol) {
+  for (int pol = 0; pol < 3 && rc == HYSCO_OK; ++pol) {
     if (batch_layout(B, pol) != HYSCO_OK) continue;   // policy not feasible for this batch
     for (int br = 1; br <= kMaxBranches && br <= B->n && rc == HYSCO_OK; br *= 2) {
       B->branches = br;

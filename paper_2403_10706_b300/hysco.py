@@ -299,7 +299,13 @@ class HyscoBatch:
         return self.schedule()
 
     def schedule(self):
-        """(branches, block-share policy, PCG grid blocks) in use."""
+        """(branches, PCG policy, shared PCG grid blocks) in use; policy 0 / 1: one PCG launch
+        shared by all pairs (blocks by field size, >= 1 / >= 2 per pair), 2: each pair's
+        persistent PCG in turn."""
         out = (C.c_int32 * 3)()
         _lib.check(self.lib.hysco_batch_schedule(self._b, out), "hysco_batch_schedule")
         return tuple(out)
+
+    def set_schedule(self, branches, policy):
+        _lib.check(self.lib.hysco_batch_set_schedule(self._b, int(branches), int(policy)),
+                   "hysco_batch_set_schedule")

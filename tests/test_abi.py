@@ -95,6 +95,7 @@ def test_adjoint_and_batch_entry_points_reject_null_arguments(lib):
     assert lib.hysco_batch_schedule(None, (C.c_int32 * 3)()) == _lib.EINVAL
     lib.hysco_batch_destroy(None)
     assert lib.hysco_pcg_plan(None, (C.c_int32 * 4)()) == _lib.EINVAL
+    assert lib.hysco_batch_set_schedule(None, 1, 0) == _lib.EINVAL
     assert lib.hysco_set_pcg_onchip(None, 0) == _lib.EINVAL
 
 
