@@ -20,6 +20,9 @@ _SRC = os.path.join(_HERE, "hysco_oracle.c")
 _LIB = os.path.join(_HERE, "libhysco_oracle.so")
 
 ST_FIELDS = ["J", "D", "S", "P", "gnorm", "gq", "gamma", "pcg_iters", "pcg_relres", "ls_trials"]
+# per ADMM iteration (Problem.admm)
+ADMM_FIELDS = ["J", "F_c", "rho", "r_primal", "s_dual", "rel_db", "rel_dz", "rel_du",
+               "block_pcg_iters", "gamma"]
 
 
 def build(force: bool = False) -> str:
@@ -75,6 +78,14 @@ def lib():
         _lib.orc_pushforward_matrix.argtypes = [P, C.c_int64, C.c_double, P]
         _lib.orc_feasible_start.restype = C.c_double
         _lib.orc_feasible_start.argtypes = [P, P]
+        _lib.orc_admm_eval.restype = C.c_int64
+        _lib.orc_admm_eval.argtypes = [P, P, P, P, C.c_int, C.c_double, P, P, P]
+        _lib.orc_block_pcg.restype = C.c_int64
+        _lib.orc_block_pcg.argtypes = [P, P, P, P, C.c_int, C.c_double, P, C.c_int, C.c_double,
+                                       P]
+        _lib.orc_admm_column_block.argtypes = [P, P, P, P, C.c_int, C.c_double, C.c_int64, P, P]
+        _lib.orc_admm_bupdate.argtypes = [P, P, P, C.c_int, C.c_double, P, C.c_int, C.c_int,
+                                          C.c_double, C.c_int, C.c_double, P, P]
     return _lib
 
 
@@ -96,7 +107,124 @@ def field_dims(dims, p):
     return tuple(fd)
 
 
-class Problem:
+def _rel(d, ref):
+    """||d|| / ||ref|| with 0/0 = 0 and x/0 = inf (relative change of an ADMM iterate)."""
+    nd, nr = np.linalg.norm(d.ravel()), np.linalg.norm(ref.ravel())
+    if nr > 0.0:
+        return nd / nr
+    return 0.0 if nd == 0.0 else np.inf
+
+
+class AdmmMixin:
+    """ADMM of Sec. 2.3.2 (split F(b) = D + alpha S3 + beta P, G(z) = alpha (S1 + S2), constraint
+    b = z, scaled multiplier u), on top of the b-update in hysco_oracle.c."""
+
+    def inplane_axes(self):
+        return [a for a in range(3) if a != self.pe_dim]
+
+    def admm_eval(self, Ip, Im, b, rho, c, contract=True, grad=True):
+        """F_c(b) = D + alpha S3 + beta P + rho vol/2 ||b - c||^2: dict(F_c, D, S3, P, prox,
+        infeasible, grad?)."""
+        terms = np.zeros(5)
+        g = np.zeros(self.fdims) if grad else None
+        bad = lib().orc_admm_eval(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                  int(contract), float(rho), _p(_f64(c)), _p(terms), _p(g))
+        out = dict(F_c=terms[0], D=terms[1], S3=terms[2], P=terms[3], prox=terms[4],
+                   infeasible=int(bad))
+        if grad:
+            out["grad"] = g
+        return out
+
+    def admm_column_block(self, Ip, Im, b, rho, col, contract=True):
+        m = self.dims[self.pe_dim]
+        dia, off = np.zeros(m + 1), np.zeros(m)
+        lib().orc_admm_column_block(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                    int(contract), float(rho), int(col), _p(dia), _p(off))
+        return dia, off
+
+    def block_pcg(self, Ip, Im, b, rho, rhs, max_it=10, rtol=0.1, contract=True):
+        """BlockPCG on the b-subproblem's GN system about b: (q, iterations summed over
+        columns)."""
+        q = np.zeros(self.fdims)
+        it = lib().orc_block_pcg(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), _p(_f64(b)),
+                                 int(contract), float(rho), _p(_f64(rhs)), int(max_it),
+                                 float(rtol), _p(q))
+        return q, int(it)
+
+    def admm_bupdate(self, Ip, Im, b, rho, c, gn_iters=1, pcg_max_iters=10, pcg_rtol=0.1,
+                     ls_max_iters=10, armijo_c1=1e-4, contract=True):
+        """The b-update: returns (b_new, status, stats[gn_iters, 5])."""
+        bb = _f64(b).copy()
+        st = np.zeros((max(gn_iters, 1), 5))
+        rc = lib().orc_admm_bupdate(C.byref(self.g), _p(_f32(Ip)), _p(_f32(Im)), int(contract),
+                                    float(rho), _p(_f64(c)), int(gn_iters), int(pcg_max_iters),
+                                    float(pcg_rtol), int(ls_max_iters), float(armijo_c1),
+                                    _p(bb), _p(st))
+        return bb, rc, st[:gn_iters]
+
+    def admm_z_solve(self, rhs, rho):
+        """The z-update of Sec. 2.3.2: (alpha H_G + rho I) z = rhs, H_G the Hessian of
+        S1 + S2 with periodic ends (block circulant with circulant blocks per PE plane), solved
+        by the 2D DFT over the in-plane axes: the eigenvalue of frequency (j0, j1) is
+        rho + alpha sum_a (h_p / h_a)^2 (2 - 2 cos(2 pi j_a / n_a))."""
+        axes = self.inplane_axes()
+        hp = self.spacing[self.pe_dim]
+        lam = np.full(self.fdims, float(rho))
+        for a in axes:
+            n = self.fdims[a]
+            mu = 2.0 - 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)
+            shape = [1, 1, 1]
+            shape[a] = n
+            lam = lam + self.g.alpha * (hp / self.spacing[a]) ** 2 * mu.reshape(shape)
+        Z = np.fft.fftn(_f64(rhs), axes=axes) / lam
+        return np.real(np.fft.ifftn(Z, axes=axes))
+
+    def admm(self, Ip, Im, b=None, admm_iters=10, gn_iters=1, pcg_max_iters=10, pcg_rtol=0.1,
+             ls_max_iters=10, armijo_c1=1e-4, rho0=None, tol=1e-3, mu=10.0, tau=2.0,
+             init=True, ot_blur=True, ot_eps=1e-3, contract=False):
+        """ADMM of Sec. 2.3.2.  Start: b from OT (feasible-start rule, as the GN solve) or the
+        given b, z = b, u = 0, rho = rho0 (default alpha).  Iteration k:
+          c = z - u;  b <- gn_iters GN steps on F_c (BlockPCG directions, Armijo on F_c);
+          z <- (alpha H_G + rho I)^{-1} rho (b + u);  u <- u + b - z;
+          r = ||b - z||, s = rho ||z - z_prev||; rho <- tau rho, u <- u / tau when r > mu s,
+          rho <- rho / tau, u <- u tau when s > mu r (Boyd et al. 2011, Sec. 3.4.1);
+          stop after the iteration in which the relative changes of b, z and u are all < tol.
+        Returns (b, z, u, status, stats[admm_iters, len(ADMM_FIELDS)]), rows after the stop NaN."""
+        if init:
+            b = self.ot_init(Ip, Im, eps=ot_eps, contract=contract, blur=ot_blur)
+            b, _ = self.feasible_start(b)
+        else:
+            b = _f64(b).copy()
+        z, u = b.copy(), np.zeros(self.fdims)
+        rho = float(self.g.alpha if rho0 is None else rho0)
+        stats = np.full((max(admm_iters, 1), len(ADMM_FIELDS)), np.nan)
+        status = 0
+        for k in range(admm_iters):
+            c = z - u
+            b_prev, z_prev, u_prev = b, z, u
+            b, status, bst = self.admm_bupdate(Ip, Im, b, rho, c, gn_iters, pcg_max_iters,
+                                               pcg_rtol, ls_max_iters, armijo_c1, contract)
+            if status != 0:
+                break
+            z = self.admm_z_solve(rho * (b + u), rho)
+            u = u + b - z
+            r = np.linalg.norm((b - z).ravel())
+            s = rho * np.linalg.norm((z - z_prev).ravel())
+            rel_db, rel_dz, rel_du = _rel(b - b_prev, b_prev), _rel(z - z_prev, z_prev), \
+                _rel(u - u_prev, u_prev)
+            Fc = self.admm_eval(Ip, Im, b, rho, c, contract=contract, grad=False)["F_c"]
+            J = self.eval(Ip, Im, b, contract=contract, grad=False)["J"]
+            stats[k] = [J, Fc, rho, r, s, rel_db, rel_dz, rel_du, bst[:, 3].sum(), bst[-1, 1]]
+            if r > mu * s:
+                rho, u = rho * tau, u / tau
+            elif s > mu * r:
+                rho, u = rho / tau, u * tau
+            if rel_db < tol and rel_dz < tol and rel_du < tol:
+                break
+        return b, z, u, status, stats[:admm_iters]
+
+
+class Problem(AdmmMixin):
     """Geometry + weights of one correction problem: image dims, spacing (mm), PE axis,
     alpha (smoothness) and beta (barrier) of Eq. 4."""
 

@@ -1181,3 +1181,232 @@ int64_t orc_ls_correct(const orc_geom* g, const float* Ip, const float* Im, cons
 void orc_pushforward_matrix(const double* bcol, int64_t m, double s, double* P) {
   pushforward_column(bcol, 1, m, s, P);
 }
+
+/* ------------------------------------------------------------------------------------------ */
+/* ADMM (Sec. 2.3.2): the b-update                                                             */
+/* ------------------------------------------------------------------------------------------ */
+
+/* The splitting of Sec. 2.3.2 puts the PE-direction part S3 of the smoothness term into
+ *   F(b) = D(b) + alpha S3(b) + beta P(b),
+ * and the in-plane parts S1 + S2 into G(z).  In PE-voxel units S3 = vol/2 h_p^2 b^T (G_p^T G_p /
+ * h_p^2) b = vol/2 sum over columns of sum_k (b_{k+1} - b_k)^2.  With the scaled multiplier u the
+ * b-update minimises the column-separable
+ *   F_c(b) = F(b) + rho vol / 2 ||b - c||^2,   c = z - u,
+ * (the augmentation weight rho h^3 of Sec. 2.3.2 read as rho times the cell volume). */
+static double smooth_pe(const orc_geom* g, const double* b, double* Lpe /* nullable: L_pe b */) {
+  int64_t m = g->d[g->p];
+  int64_t sf[3]; fld_strides(g, sf);
+  int64_t stf = sf[g->p];
+  int64_t ncols = column_count(g);
+  double s = 0.0;
+  if (Lpe) memset(Lpe, 0, fld_count(g) * sizeof(double));
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    for (int64_t k = 0; k < m; ++k) {
+      double d = b[of + (k + 1) * stf] - b[of + k * stf];
+      s += d * d;
+      if (Lpe) {                       /* G_p^T G_p b, one edge at a time */
+        Lpe[of + (k + 1) * stf] += d;
+        Lpe[of + k * stf] -= d;
+      }
+    }
+  }
+  return 0.5 * cell_volume(g) * s;
+}
+
+/* F_c at b: terms = {F_c, D, S3, P, prox} with prox = vol/2 ||b - c||^2 (so F_c = D + alpha S3 +
+ * beta P + rho prox); gradient on request:
+ *   vol [Jr^T r + alpha G_p^T G_p b + beta/2 D^T phi'(delta) + rho (b - c)].
+ * Returns the number of barrier-infeasible cells. */
+int64_t orc_admm_eval(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                      int contract, double rho, const double* c, double* terms, double* grad) {
+  int64_t nc = img_count(g), nf = fld_count(g);
+  double vol = cell_volume(g);
+  orc_lin lin;
+  int want_lin = grad != NULL;
+  if (want_lin && !lin_alloc(&lin, nc)) return -1;
+  double D, P;
+  int64_t bad = residual_pass(g, Ip, Im, b, contract, &D, &P, want_lin ? &lin : NULL, NULL, NULL,
+                              NULL, NULL);
+  double* Lpe = malloc(nf * sizeof(double));
+  double S3 = smooth_pe(g, b, Lpe);
+  double prox = 0.0;
+  for (int64_t k = 0; k < nf; ++k) prox += (b[k] - c[k]) * (b[k] - c[k]);
+  prox *= 0.5 * vol;
+  terms[1] = D; terms[2] = S3; terms[3] = P; terms[4] = prox;
+  terms[0] = D + g->alpha * S3 + g->beta * P + rho * prox;
+  if (want_lin) {
+    double* t = calloc(nf, sizeof(double));
+    double* u = calloc(nf, sizeof(double));
+    jr_transpose_add(g, &lin, lin.r, t);
+    fd_transpose_add(g, lin.dphi, u);
+    for (int64_t k = 0; k < nf; ++k)
+      grad[k] = vol * (t[k] + g->alpha * Lpe[k] + 0.5 * g->beta * u[k] + rho * (b[k] - c[k]));
+    free(t); free(u);
+    lin_free(&lin);
+  }
+  free(Lpe);
+  return bad;
+}
+
+/* The GN Hessian of F_c restricted to one PE column (it is block diagonal: F_c has no in-plane
+ * coupling): vol [Jr^T Jr + alpha G_p^T G_p + beta/2 D^T diag(phi'') D + rho I], tridiagonal of
+ * order m+1. */
+static void admm_column_block(const orc_geom* g, const orc_lin* lin, int64_t col, double rho,
+                              double* dia, double* off) {
+  int64_t m = g->d[g->p];
+  int64_t si[3]; img_strides(g, si);
+  double vol = cell_volume(g);
+  int64_t oi, of, c0, c1;
+  column_offsets(g, col, &oi, &of, &c0, &c1);
+  for (int64_t k = 0; k <= m; ++k) dia[k] = g->alpha * (double)((k > 0) + (k < m)) + rho;
+  for (int64_t k = 0; k < m; ++k) off[k] = -g->alpha;
+  for (int64_t j = 0; j < m; ++j) {
+    int64_t c = oi + j * si[g->p];
+    double jl = lin->jl[c], jr = lin->jr[c], q = 0.5 * g->beta * lin->d2phi[c];
+    dia[j] += jl * jl + q;
+    dia[j + 1] += jr * jr + q;
+    off[j] += jl * jr - q;
+  }
+  for (int64_t k = 0; k <= m; ++k) dia[k] *= vol;
+  for (int64_t k = 0; k < m; ++k) off[k] *= vol;
+}
+
+/* symmetric tridiagonal product y = T x of order n */
+static void tridiag_apply(int64_t n, const double* dia, const double* off, const double* x,
+                          double* y) {
+  for (int64_t k = 0; k < n; ++k) {
+    double v = dia[k] * x[k];
+    if (k > 0) v += off[k - 1] * x[k - 1];
+    if (k < n - 1) v += off[k] * x[k + 1];
+    y[k] = v;
+  }
+}
+
+/* BlockPCG (Sec. 2.3.2): the Jacobi-preconditioned CG of Sec. 2.3.1 run on every column's block
+ * independently, with the column's own step sizes and its own stop (||r|| / ||r0|| < rtol after an
+ * update, p^T H p <= 0, or max_it iterations).  q = 0 where the column's right-hand side is 0.
+ * Returns the sum over columns of the iterations taken. */
+static int64_t block_pcg(const orc_geom* g, const orc_lin* lin, double rho, const double* rhs,
+                         int max_it, double rtol, double* q) {
+  int64_t m = g->d[g->p], n = m + 1;
+  int64_t sf[3]; fld_strides(g, sf);
+  int64_t stf = sf[g->p];
+  int64_t ncols = column_count(g), total = 0;
+  double *dia = malloc(n * sizeof(double)), *off = malloc(n * sizeof(double));
+  double *x = malloc(n * sizeof(double)), *r = malloc(n * sizeof(double));
+  double *z = malloc(n * sizeof(double)), *p = malloc(n * sizeof(double));
+  double *Hp = malloc(n * sizeof(double));
+  for (int64_t col = 0; col < ncols; ++col) {
+    int64_t oi, of, c0, c1;
+    column_offsets(g, col, &oi, &of, &c0, &c1);
+    admm_column_block(g, lin, col, rho, dia, off);
+    for (int64_t k = 0; k < n; ++k) { x[k] = 0.0; r[k] = rhs[of + k * stf]; }
+    double rr0 = 0.0;
+    for (int64_t k = 0; k < n; ++k) rr0 += r[k] * r[k];
+    if (rr0 > 0.0) {
+      jacobi_precond(n, dia, r, z);
+      for (int64_t k = 0; k < n; ++k) p[k] = z[k];
+      double rz = 0.0;
+      for (int64_t k = 0; k < n; ++k) rz += r[k] * z[k];
+      for (int i = 0; i < max_it; ++i) {
+        tridiag_apply(n, dia, off, p, Hp);
+        double pHp = 0.0;
+        for (int64_t k = 0; k < n; ++k) pHp += p[k] * Hp[k];
+        if (!(pHp > 0.0)) break;
+        double a = rz / pHp;
+        for (int64_t k = 0; k < n; ++k) { x[k] += a * p[k]; r[k] -= a * Hp[k]; }
+        ++total;
+        double rr = 0.0;
+        for (int64_t k = 0; k < n; ++k) rr += r[k] * r[k];
+        if (sqrt(rr) / sqrt(rr0) < rtol) break;
+        jacobi_precond(n, dia, r, z);
+        double rz_new = 0.0;
+        for (int64_t k = 0; k < n; ++k) rz_new += r[k] * z[k];
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t k = 0; k < n; ++k) p[k] = z[k] + beta * p[k];
+      }
+    }
+    for (int64_t k = 0; k < n; ++k) q[of + k * stf] = x[k];
+  }
+  free(dia); free(off); free(x); free(r); free(z); free(p); free(Hp);
+  return total;
+}
+
+/* BlockPCG alone on the b-subproblem about b (exported for tests): q ~= -H^{-1} grad F_c. */
+int64_t orc_block_pcg(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                      int contract, double rho, const double* rhs, int max_it, double rtol,
+                      double* q) {
+  orc_lin lin;
+  if (!lin_alloc(&lin, img_count(g))) return -1;
+  double D, P;
+  residual_pass(g, Ip, Im, b, contract, &D, &P, &lin, NULL, NULL, NULL, NULL);
+  int64_t it = block_pcg(g, &lin, rho, rhs, max_it, rtol, q);
+  lin_free(&lin);
+  return it;
+}
+
+/* The dense block of one column (exported for tests) */
+int orc_admm_column_block(const orc_geom* g, const float* Ip, const float* Im, const double* b,
+                          int contract, double rho, int64_t col, double* dia, double* off) {
+  orc_lin lin;
+  if (!lin_alloc(&lin, img_count(g))) return -1;
+  double D, P;
+  residual_pass(g, Ip, Im, b, contract, &D, &P, &lin, NULL, NULL, NULL, NULL);
+  admm_column_block(g, &lin, col, rho, dia, off);
+  lin_free(&lin);
+  return 0;
+}
+
+/* The b-update: gn_iters Gauss-Newton iterations on F_c (Sec. 2.3.2: the GN scheme of Sec. 2.3.1
+ * with the search direction from BlockPCG), Armijo backtracking on F_c as in orc_solve.  Stops
+ * early only when F_c is not finite (returns 1 for +inf, 2 for NaN).  stats (nullable):
+ * gn_iters x 5 doubles {F_c before the step, gamma, grad^T q, BlockPCG iterations summed over
+ * columns, line-search trials}. */
+int orc_admm_bupdate(const orc_geom* g, const float* Ip, const float* Im, int contract,
+                     double rho, const double* c, int gn_iters, int pcg_max_iters,
+                     double pcg_rtol, int ls_max_iters, double armijo_c1, double* b,
+                     double* stats) {
+  int64_t nf = fld_count(g);
+  double* grad = malloc(nf * sizeof(double));
+  double* rhs = malloc(nf * sizeof(double));
+  double* q = malloc(nf * sizeof(double));
+  double* bt = malloc(nf * sizeof(double));
+  orc_lin lin;
+  if (!lin_alloc(&lin, img_count(g))) return -1;
+  int status = 0;
+  if (stats) for (int64_t i = 0; i < (int64_t)gn_iters * 5; ++i) stats[i] = NAN;
+  for (int it = 0; it < gn_iters; ++it) {
+    double terms[5];
+    orc_admm_eval(g, Ip, Im, b, contract, rho, c, terms, grad);
+    double F = terms[0];
+    double* st = stats ? stats + (int64_t)it * 5 : NULL;
+    if (st) st[0] = F;
+    if (!isfinite(F)) { status = isnan(F) ? 2 : 1; break; }
+    double D, P;
+    residual_pass(g, Ip, Im, b, contract, &D, &P, &lin, NULL, NULL, NULL, NULL);
+    for (int64_t k = 0; k < nf; ++k) rhs[k] = -grad[k];
+    int64_t pit = block_pcg(g, &lin, rho, rhs, pcg_max_iters, pcg_rtol, q);
+    double gq = dot(grad, q, nf);
+    double gamma = 0.0;
+    int trials = 0;
+    if (gq < 0.0) {
+      double step = 1.0;
+      for (int t = 0; t < ls_max_iters; ++t) {
+        ++trials;
+        for (int64_t k = 0; k < nf; ++k) bt[k] = b[k] + step * q[k];
+        double tt[5];
+        orc_admm_eval(g, Ip, Im, bt, contract, rho, c, tt, NULL);
+        if (tt[0] <= F + armijo_c1 * step * gq) { gamma = step; break; }
+        step *= 0.5;
+      }
+    }
+    if (gamma > 0.0) for (int64_t k = 0; k < nf; ++k) b[k] += gamma * q[k];
+    if (st) { st[1] = gamma; st[2] = gq; st[3] = (double)pit; st[4] = trials; }
+  }
+  lin_free(&lin);
+  free(grad); free(rhs); free(q); free(bt);
+  return status;
+}
