@@ -214,6 +214,55 @@ int hysco_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout,
 int hysco_selftest_barrier(int grid, int missing_block, int64_t spin_cycles,
                            hysco_stream_t stream);
 
+/* ---- ADMM (Sec. 2.3.2) -----------------------------------------------------------------------
+ * The alternative optimiser of Sec. 2.3.2: the objective is split into F(b) = D + alpha S3 +
+ * beta P (S3 the smoothness along PE) and G(z) = alpha (S1 + S2) (the in-plane smoothness) with
+ * the constraint b = z; with the scaled multiplier u every iteration
+ *   b <- argmin F(b) + rho vol/2 ||b - z + u||^2   by gn_iters Gauss-Newton steps whose
+ *        directions come from BlockPCG (the Jacobi CG of Sec. 2.3.1 run on every PE column
+ *        independently, with the column's own step sizes and stop) and Armijo backtracking on
+ *        that subproblem's objective;
+ *   z <- argmin G(z) + rho vol/2 ||b - z + u||^2   solved directly per PE plane with periodic
+ *        in-plane ends (the 2D Fourier transform diagonalises it);
+ *   u <- u + b - z;
+ * then rho is balanced (Boyd et al. 2011, Sec. 3.4.1): r = ||b - z||, s = rho ||z - z_prev||,
+ * rho <- tau rho (u <- u / tau) when r > mu s, rho <- rho / tau (u <- tau u) when s > mu r; the
+ * run stops after the iteration in which the relative changes of b, z and u are all below tol.
+ * (Readings where the paper is silent: the augmentation weight rho h^3 is rho times the cell
+ * volume; rho starts at alpha unless rho0 > 0; the relative change of a vector that was zero is
+ * infinite.) */
+typedef struct {
+  int32_t admm_iters;     /* maximum ADMM iterations (default 20) */
+  int32_t gn_iters;       /* Gauss-Newton steps per b-update (default 2) */
+  int32_t pcg_max_iters;  /* BlockPCG iterations per column and GN step, <= 64 (default 10) */
+  int32_t ls_max_iters;   /* Armijo trials per GN step, <= 16 (default 10) */
+  int32_t init;           /* 1 = OT initialisation with the feasible-start rule, 0 = from b_inout */
+  int32_t ot_blur;        /* as in hysco_opts */
+  int32_t no_graph;       /* as in hysco_opts */
+  int32_t pad_;
+  double pcg_rtol;        /* per-column relative residual stop (default 0.1) */
+  double armijo_c1;       /* default 1e-4 */
+  double ot_eps;          /* default 1e-3 */
+  double rho0;            /* initial rho; <= 0: alpha (default 0) */
+  double tol;             /* stop tolerance on the relative changes (default 1e-3) */
+  double mu, tau;         /* rho rule (defaults 10 and 2) */
+} hysco_admm_opts;
+
+void hysco_default_admm_opts(hysco_admm_opts* opts);
+
+#define HYSCO_ADMM_NSTATS 10   /* per iteration: J(b), (unused, NaN), rho, r, s, relative
+                                  changes of b, z and u, BlockPCG iterations summed over columns
+                                  and GN steps, the last GN step's gamma */
+
+/* Runs ADMM on the pair (images as in hysco_solve) from b_inout (or OT) and writes the final b
+ * into b_inout.  stats: NULL or an admm_iters x HYSCO_ADMM_NSTATS device array of doubles (rows
+ * after the stop NaN).  The PE extent must be at most 255 cells (BlockPCG keeps a column's 256
+ * nodes in one warp's registers), else HYSCO_EINVAL.  Stream-ordered; hysco_last_status reports
+ * HYSCO_INFEASIBLE / HYSCO_ENONFINITE when a b-update met a non-finite objective (the run stops
+ * there).  Uses the handle's workspace plus five field-sized arrays allocated at the first call. */
+int hysco_admm(hysco_t h, const void* Ip, const void* Im, float* b_inout,
+               const hysco_admm_opts* opts, double* stats, hysco_stream_t stream);
+
 /* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):

@@ -179,7 +179,7 @@ class AdmmMixin:
         Z = np.fft.fftn(_f64(rhs), axes=axes) / lam
         return np.real(np.fft.ifftn(Z, axes=axes))
 
-    def admm(self, Ip, Im, b=None, admm_iters=10, gn_iters=1, pcg_max_iters=10, pcg_rtol=0.1,
+    def admm(self, Ip, Im, b=None, admm_iters=20, gn_iters=2, pcg_max_iters=10, pcg_rtol=0.1,
              ls_max_iters=10, armijo_c1=1e-4, rho0=None, tol=1e-3, mu=10.0, tau=2.0,
              init=True, ot_blur=True, ot_eps=1e-3, contract=False):
         """ADMM of Sec. 2.3.2.  Start: b from OT (feasible-start rule, as the GN solve) or the

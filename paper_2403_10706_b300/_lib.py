@@ -28,6 +28,18 @@ class Opts(C.Structure):
                 ("ot_eps", C.c_double), ("pcg_path", C.c_int32), ("no_graph", C.c_int32)]
 
 
+class AdmmOpts(C.Structure):
+    _fields_ = [("admm_iters", C.c_int32), ("gn_iters", C.c_int32),
+                ("pcg_max_iters", C.c_int32), ("ls_max_iters", C.c_int32), ("init", C.c_int32),
+                ("ot_blur", C.c_int32), ("no_graph", C.c_int32), ("pad_", C.c_int32),
+                ("pcg_rtol", C.c_double), ("armijo_c1", C.c_double), ("ot_eps", C.c_double),
+                ("rho0", C.c_double), ("tol", C.c_double), ("mu", C.c_double),
+                ("tau", C.c_double)]
+
+
+ADMM_NSTATS = 10
+
+
 class HyscoError(RuntimeError):
     def __init__(self, status, what):
         super().__init__(f"{what}: {strerror(status)} (status {status})")
@@ -51,6 +63,8 @@ def load():
         "hysco_version": (C.c_char_p, []),
         "hysco_strerror": (C.c_char_p, [I]),
         "hysco_default_opts": (None, [C.POINTER(Opts)]),
+        "hysco_default_admm_opts": (None, [C.POINTER(AdmmOpts)]),
+        "hysco_admm": (I, [P, P, P, P, C.POINTER(AdmmOpts), P, P]),
         "hysco_create": (I, [I64P, C.POINTER(C.c_double), I, D, D, I, C.POINTER(P)]),
         "hysco_destroy": (None, [P]),
         "hysco_field_dims": (I, [P, I64P]),
@@ -108,4 +122,10 @@ def declared_functions(header: str = HEADER):
 def default_opts() -> Opts:
     o = Opts()
     load().hysco_default_opts(C.byref(o))
+    return o
+
+
+def default_admm_opts() -> AdmmOpts:
+    o = AdmmOpts()
+    load().hysco_default_admm_opts(C.byref(o))
     return o

@@ -43,6 +43,15 @@ struct hysco_ctx {
   float* g_b;
   double* g_stats;
   hysco_opts g_opts;
+  // ADMM workspace (allocated at the first hysco_admm call): z (two buffers, alternating by
+  // iteration), u, c = z - u and the b of the iteration's start, pitched; the in-plane bases
+  float *az[2], *au, *ac, *abprev;
+  float *aQA, *aQB, *amuA, *amuB;
+  cudaGraphExec_t agexec;
+  const void *ag_Ip, *ag_Im;
+  float* ag_b;
+  double* ag_stats;
+  hysco_admm_opts ag_opts;
   Work work() const { return Work{partials, counter, st}; }
 };
 
@@ -76,6 +85,10 @@ void free_all(hysco_ctx* h) {
   if (h->counter) cudaFree(h->counter);
   if (h->psync) cudaFree(h->psync);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  float* abufs[] = {h->az[0], h->az[1], h->au, h->ac, h->abprev, h->aQA, h->aQB, h->amuA, h->amuB};
+  for (float* b : abufs)
+    if (b) cudaFree(b);
+  if (h->agexec) cudaGraphExecDestroy(h->agexec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->st) cudaFree(h->st);
 }
@@ -270,7 +283,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   // partials: the largest grid of any reducing kernel times its reduction width
   long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, kSeg);
   long long flat_blocks = (long long)ceil_div(g.nf, kBlock) + 1;
-  long long nparts = march_blocks * (3 * kLsBatch + 1) + flat_blocks * 2 + 148 * 8 * 2 +
+  long long nparts = march_blocks * (4 * kLsBatch + 1) + flat_blocks * 2 + 148 * 8 * 2 +
                      (long long)g.ncols * 2 + 64;
   if (cudaMalloc((void**)&h->partials, nparts * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
@@ -626,6 +639,182 @@ int hysco_last_status(hysco_t h, hysco_stream_t stream) {
   if (cudaMemcpy(&st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess)
     return HYSCO_ECUDA;
   return st.status;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// ADMM (Sec. 2.3.2): see include/hysco.h and k_admm.cu
+// ------------------------------------------------------------------------------------------
+
+namespace {
+
+// real orthonormal Fourier basis of length n (row = position x, column = basis function) and the
+// eigenvalue 2 - 2 cos(2 pi j / n) of the periodic second difference on each column: the
+// constant, then cos / sin pairs of frequencies j = 1 .. (n - 1) / 2, then (-1)^x for even n
+void real_fourier_basis(int n, std::vector<float>& Q, std::vector<float>& mu) {
+  const double pi = 3.14159265358979323846;
+  Q.assign((size_t)n * n, 0.f);
+  mu.assign(n, 0.f);
+  const double c0 = 1.0 / std::sqrt((double)n), c1 = std::sqrt(2.0 / n);
+  for (int x = 0; x < n; ++x) Q[(size_t)x * n] = (float)c0;
+  int col = 1;
+  for (int j = 1; 2 * j < n; ++j, col += 2) {
+    for (int x = 0; x < n; ++x) {
+      const double t = 2.0 * pi * (double)((long long)j * x % n) / n;
+      Q[(size_t)x * n + col] = (float)(c1 * std::cos(t));
+      Q[(size_t)x * n + col + 1] = (float)(c1 * std::sin(t));
+    }
+    mu[col] = mu[col + 1] = (float)(2.0 - 2.0 * std::cos(2.0 * pi * j / n));
+  }
+  if (n % 2 == 0) {
+    for (int x = 0; x < n; ++x) Q[(size_t)x * n + col] = (float)((x % 2 ? -1.0 : 1.0) * c0);
+    mu[col] = 4.f;
+  }
+}
+
+int admm_setup(hysco_ctx* h) {
+  if (h->au) return HYSCO_OK;
+  const size_t fbytes = (size_t)std::max<long long>(h->g.nfp, h->nfld) * sizeof(float);
+  float** bufs[] = {&h->az[0], &h->az[1], &h->au, &h->ac, &h->abprev};
+  for (float** b : bufs)
+    if (cudaMalloc((void**)b, fbytes) != cudaSuccess || cudaMemset(*b, 0, fbytes) != cudaSuccess)
+      return HYSCO_ENOMEM;
+  std::vector<float> QA, QB, muA, muB;
+  real_fourier_basis(h->g.nA, QA, muA);
+  real_fourier_basis(h->g.nB, QB, muB);
+  struct { float** d; const std::vector<float>* v; } up[] = {
+      {&h->aQA, &QA}, {&h->aQB, &QB}, {&h->amuA, &muA}, {&h->amuB, &muB}};
+  for (auto& u : up)
+    if (cudaMalloc((void**)u.d, u.v->size() * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(*u.d, u.v->data(), u.v->size() * sizeof(float), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return HYSCO_ENOMEM;
+  return HYSCO_OK;
+}
+
+int check_admm_opts(const hysco_ctx* h, const hysco_admm_opts* o) {
+  if (!o) return HYSCO_EINVAL;
+  if (o->admm_iters < 0 || o->admm_iters > 100000 || o->gn_iters < 1 || o->gn_iters > 100 ||
+      o->pcg_max_iters < 1 || o->pcg_max_iters > 64 || o->ls_max_iters < 1 ||
+      o->ls_max_iters > kMaxTrials)
+    return HYSCO_EINVAL;
+  if (!(o->pcg_rtol >= 0.0) || !(o->armijo_c1 >= 0.0) || !(o->ot_eps >= 0.0) ||
+      !(o->tol >= 0.0) || !(o->mu >= 1.0) || !(o->tau > 1.0) || !std::isfinite(o->rho0) ||
+      !std::isfinite(o->mu) || !std::isfinite(o->tau))
+    return HYSCO_EINVAL;
+  if (o->init < 0 || o->init > 1 || o->no_graph < 0 || o->no_graph > 1) return HYSCO_EINVAL;
+  if (h->g.E > kAdmmMaxNodes) return HYSCO_EINVAL;
+  return HYSCO_OK;
+}
+
+int enqueue_admm(hysco_ctx* h, const void* Ip, const void* Im, float* b, const hysco_admm_opts* o,
+                 double* stats, cudaStream_t s) {
+  const Geo& g = h->g;
+  Geo gs = g;   // the b-subproblem's geometry: no in-plane smoothness (S3 alone)
+  gs.wA = 0.f;
+  gs.wB = 0.f;
+  for (int a = 0; a < 3; ++a)
+    if (a != g.p) gs.w[a] = 0.f;
+  Work w = h->work();
+  if (int rc = reset_state(h, s)) return rc;
+  if (o->init) {
+    if (int rc = init_ot_impl(h, Ip, Im, b, o->ot_blur, o->ot_eps, nullptr, nullptr, s)) return rc;
+    HYSCO_TRY(launch_feasible_start(g, b, w, s));
+  }
+  const float rho0 = o->rho0 > 0.0 ? (float)o->rho0 : g.alpha;
+  HYSCO_TRY(launch_admm_init(h->st, rho0, stats, o->admm_iters, s));
+  HYSCO_TRY(launch_to_pitched(g, b, h->az[0], s));
+  HYSCO_TRY(cudaMemsetAsync(h->au, 0, (size_t)g.nfp * sizeof(float), s));
+  const AdmmBasis basis{h->aQA, h->aQB, h->amuA, h->amuB};
+  for (int k = 0; k < o->admm_iters; ++k) {
+    float* zc = h->az[k & 1];
+    float* zn = h->az[(k + 1) & 1];
+    HYSCO_TRY(launch_admm_prep(g, b, zc, h->au, h->ac, h->abprev, w, s));
+    for (int i = 0; i < o->gn_iters; ++i) {
+      HYSCO_TRY(launch_eval(gs, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd,
+                            i, w, s, h->ac));
+      HYSCO_TRY(launch_block_pcg(gs, h->grad, h->dco, h->eco, h->invd, h->x, o->pcg_max_iters,
+                                 o->pcg_rtol, h->st, s));
+      HYSCO_TRY(launch_eval_trial(gs, h->dtype, Ip, Im, b, h->x, h->grad, h->dco, h->eco,
+                                  h->invd, o->ls_max_iters, o->armijo_c1, w, s, h->ac));
+      for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
+        HYSCO_TRY(launch_linesearch(gs, h->dtype, Ip, Im, b, h->x, h->grad, t0, o->ls_max_iters,
+                                    o->armijo_c1, w, s, h->ac));
+      HYSCO_TRY(launch_update(gs, b, h->x, i, nullptr, w, s));
+    }
+    // J(b) for the statistics (a fresh full evaluation unless the run has stopped)
+    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd, -2,
+                          w, s));
+    HYSCO_TRY(launch_admm_zsolve(g, b, h->au, basis, h->tmp, h->q0, zn, h->st, s));
+    HYSCO_TRY(launch_admm_post(g, b, zn, zc, h->au, h->abprev, k, o->tol, o->mu, o->tau, stats,
+                               w, s));
+  }
+  return HYSCO_OK;
+}
+
+bool same_admm_opts(const hysco_admm_opts& a, const hysco_admm_opts& b) {
+  return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+void hysco_default_admm_opts(hysco_admm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->admm_iters = 20;
+  o->gn_iters = 2;
+  o->pcg_max_iters = 10;
+  o->ls_max_iters = 10;
+  o->init = 1;
+  o->ot_blur = 1;
+  o->no_graph = 0;
+  o->pcg_rtol = 0.1;
+  o->armijo_c1 = 1e-4;
+  o->ot_eps = 1e-3;
+  o->rho0 = 0.0;
+  o->tol = 1e-3;
+  o->mu = 10.0;
+  o->tau = 2.0;
+}
+
+int hysco_admm(hysco_t h, const void* Ip, const void* Im, float* b_inout,
+               const hysco_admm_opts* o, double* stats, hysco_stream_t stream) {
+  if (!h || check_admm_opts(h, o) || check_img(h, Ip) || check_img(h, Im) || check_f32(b_inout))
+    return HYSCO_EINVAL;
+  if (stats && !aligned(stats, 8)) return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->have_lin = false;
+  h->have_factor = false;
+  if (o->no_graph) return enqueue_admm(h, Ip, Im, b_inout, o, stats, s);
+  const bool cached = h->agexec && h->ag_Ip == Ip && h->ag_Im == Im && h->ag_b == b_inout &&
+                      h->ag_stats == stats && same_admm_opts(h->ag_opts, *o);
+  if (!cached) {
+    if (h->agexec) cudaGraphExecDestroy(h->agexec);
+    h->agexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = ok ? enqueue_admm(h, Ip, Im, b_inout, o, stats, h->cap) : HYSCO_ECUDA;
+    cudaError_t ec = cudaStreamEndCapture(h->cap, &graph);
+    ok = ok && rc == HYSCO_OK && ec == cudaSuccess && graph != nullptr;
+    if (ok) ok = cudaGraphInstantiate(&h->agexec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      h->agexec = nullptr;
+      cudaGetLastError();
+      return enqueue_admm(h, Ip, Im, b_inout, o, stats, s);
+    }
+    h->ag_Ip = Ip;
+    h->ag_Im = Im;
+    h->ag_b = b_inout;
+    h->ag_stats = stats;
+    h->ag_opts = *o;
+  }
+  HYSCO_TRY(cudaGraphLaunch(h->agexec, s));
+  return HYSCO_OK;
 }
 
 }  // extern "C"

@@ -77,6 +77,13 @@ struct DevState {
   int coef_fresh, status_n;
   double Jn, Dn, Sn, Pn, gnorm_n;
   float start_scale;          // factor applied to the OT start by the feasible-start rule
+  // ADMM (Sec. 2.3.2)
+  float admm_rho;             // augmentation weight of the current b-update (prox rho vol/2 ||b-c||^2)
+  float admm_scale;           // factor on u pending from the last rho change
+  int admm_iter;              // ADMM iterations completed
+  int blk_iters;              // BlockPCG iterations summed over columns (this ADMM iteration)
+  double prox;                // vol/2 ||b - c||^2 at the last evaluation with the prox term
+  double nb_prev, nz_prev, nu_prev;   // ||b||^2, ||z||^2, ||u||^2 at the iteration's start
 };
 
 constexpr int kBlock = 256;   // threads per block of every kernel
@@ -349,20 +356,22 @@ struct Work {        // device buffers the launchers need
 
 // k_eval.cu
 // grad: caller layout (nullable); grad_p: pitched solver copy (nullable); dco, eco, invd pitched
+// cpx (nullable): the ADMM prox centre c (pitched), see k_eval's PROX
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
-                        const Work& w, cudaStream_t s);
+                        const Work& w, cudaStream_t s, const float* cpx = nullptr);
 // The gamma = 1 Armijo trial as a full evaluation at b + q (q pitched): J, grad, d, e, 1/diag at
 // b + q overwrite the solver arrays (grad_p is read first for grad^T q), and the Armijo decision
 // for gamma = 1 is taken; on acceptance the next launch_eval only promotes the stashed terms.
 cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, float* grad_p, float* dco,
                               float* eco, float* invd, int ls_max, double c1, const Work& w,
-                              cudaStream_t s);
+                              cudaStream_t s, const float* cpx = nullptr);
 // trials t0 .. t0 + kLsBatch - 1 (J only); the gamma = 1 trial is launch_eval_trial
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
-                              int ls_max, double c1, const Work& w, cudaStream_t s);
+                              int ls_max, double c1, const Work& w, cudaStream_t s,
+                              const float* cpx = nullptr);
 cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
                           const Work& w, cudaStream_t s);
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
@@ -408,6 +417,29 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const float* p, const float* Hp, float* z, const float* invD,
                              const float* lco, int first, double rtol, float sign,
                              const Work& w, cudaStream_t s);
+
+// k_admm.cu: ADMM of Sec. 2.3.2 (BlockPCG b-update directions, z-update, multiplier / rho)
+constexpr int kAdmmNStats = 10;     // statistics per ADMM iteration
+constexpr int kAdmmMaxNodes = 256;  // PE nodes per column that BlockPCG holds in registers
+struct AdmmBasis {                  // real orthonormal Fourier bases of the in-plane axes
+  const float* QA;                  // nA x nA, row = position, column = basis function
+  const float* QB;                  // nB x nB
+  const float* muA;                 // 2 - 2 cos(2 pi j / nA) of each column of QA
+  const float* muB;
+};
+cudaError_t launch_block_pcg(const Geo& g, const float* grad, const float* dco, const float* eco,
+                             const float* invd, float* x, int max_it, double rtol, DevState* st,
+                             cudaStream_t s);
+cudaError_t launch_admm_init(DevState* st, float rho0, double* stats, int nrows, cudaStream_t s);
+cudaError_t launch_admm_prep(const Geo& g, const float* b, const float* z, float* u, float* c,
+                             float* bprev, const Work& w, cudaStream_t s);
+// T0, T1: dense scratch of E * nB * nA floats each; z pitched
+cudaError_t launch_admm_zsolve(const Geo& g, const float* b, const float* u, const AdmmBasis& q,
+                               float* T0, float* T1, float* z, const DevState* st,
+                               cudaStream_t s);
+cudaError_t launch_admm_post(const Geo& g, const float* b, const float* z, const float* zprev,
+                             float* u, const float* bprev, int it, double tol, double mu,
+                             double tau, double* stats, const Work& w, cudaStream_t s);
 
 // k_pcg_persistent.cu: cooperative grid size on `device` (0 if not possible) for a field of n4
 // float4 groups, and the slots per thread whose r, p, Hp stay in shared memory; the number of

@@ -27,19 +27,24 @@ namespace hysco {
 // J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
 // ------------------------------------------------------------------------------------------
 
-// TRIAL = false: evaluation at b (GN iteration `it`, or it < 0 for a single hysco_eval call).  In a
+// TRIAL = false: evaluation at b (GN iteration `it`, or it = -1 for a single hysco_eval call, or
+// it = -2 for a fresh evaluation that a stopped run skips).  In a
 // solve, when the previous gamma = 1 trial was accepted the coefficients at this iterate are
 // already in place: one thread promotes the stashed terms and every block returns at once (no
 // block enters the reduction, so the ticket counter is untouched).
 // TRIAL = true: the gamma = 1 Armijo trial, an evaluation at b + q.
 // Each thread keeps only the previous cell (rolling window); the in-plane neighbours along the
 // column index's fast axis A are the adjacent lanes (warp shuffle; an edge lane loads).
-template <typename TI, int SEG, bool TRIAL>
+// PROX (the ADMM b-subproblem of Sec. 2.3.2): J gains rho vol/2 ||b - c||^2 (c pitched, rho the
+// device state's admm_rho), the gradient rho vol (b - c) and the GN coefficient d the constant rho;
+// with the split geometry (in-plane Laplacian weights 0) S is the PE part S3 alone.
+template <typename TI, int SEG, bool TRIAL, bool PROX>
 __global__ void __launch_bounds__(kBlock)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-       const float* __restrict__ q, float* __restrict__ grad, float* __restrict__ grad_p,
-       float* __restrict__ dco, float* __restrict__ eco, float* __restrict__ invd, int it,
-       int ls_max, double c1, float* partials, unsigned* counter, DevState* st) {
+       const float* __restrict__ q, const float* __restrict__ cpx, float* __restrict__ grad,
+       float* __restrict__ grad_p, float* __restrict__ dco, float* __restrict__ eco,
+       float* __restrict__ invd, int it, int ls_max, double c1, float* partials,
+       unsigned* counter, DevState* st) {
   if (TRIAL) {
     if (st->stop || st->ls_done) return;
   } else if (it >= 0) {
@@ -54,11 +59,14 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
       }
       return;
     }
+  } else if (it < -1 && st->stop) {
+    return;   // it = -2: a fresh evaluation unless the run has stopped
   }
   const int inner = g.inner, m = g.m;
   const int lane = threadIdx.x & 31;
   const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
-  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f, accGQ = 0.f;
+  const float rho = PROX ? st->admm_rho : 0.f;
+  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f, accGQ = 0.f, accR = 0.f;
   // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
   int c = (item % ncb) * kBlock + threadIdx.x;
@@ -133,12 +141,20 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
       accS += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
       accD += cr * cr;
       accP += cphi;
-      float gk = g.vol * (pjr * pr + cjl * cr + g.alpha * lap + g.half_beta * (pdphi - cdphi));
+      const int pi = pb + k * g.psP;   // solver arrays are pitched
+      float prx = 0.f;
+      if (PROX) {
+        prx = bk - __ldg(cpx + pi);
+        accR += prx * prx;
+      }
+      float gsum = pjr * pr + cjl * cr + g.alpha * lap + g.half_beta * (pdphi - cdphi);
+      if (PROX) gsum += rho * prx;
+      float gk = g.vol * gsum;
       float dk = pjr * pjr + cjl * cjl + ppsi + cpsi;
+      if (PROX) dk += rho;
       float ek = cjl * cjr - cpsi;
       float npe = (float)((k > 0) + (k < m));
       float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
-      const int pi = pb + k * g.psP;   // solver arrays are pitched
       if (grad) grad[fb + k * inner] = gk;
       if (grad_p) grad_p[pi] = gk;
       dco[pi] = dk;
@@ -149,12 +165,19 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     pr = cr; pjr = cjr; pdphi = cdphi; ppsi = cpsi;
   }
   }   // work items
-  float v[5] = {accD, accS, accP, accG, accGQ};
-  double tot[5];
-  if (grid_sum<5>(v, partials, counter, tot)) {
+  constexpr int NV = PROX ? 6 : 5;
+  float v[NV];
+  v[0] = accD; v[1] = accS; v[2] = accP; v[3] = accG; v[4] = accGQ;
+  if (PROX) v[NV - 1] = accR;
+  double tot[NV];
+  if (grid_sum<NV>(v, partials, counter, tot)) {
     double hv = 0.5 * (double)g.vol;
     double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
     double J = D + g.alpha_d * S + g.beta_d * P;
+    if (PROX) {
+      st->prox = hv * tot[NV - 1];
+      J += (double)rho * st->prox;
+    }
     if (!TRIAL) {
       st->J = J; st->D = D; st->S = S; st->P = P;
       st->gnorm = sqrt(tot[3]);
@@ -191,18 +214,18 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
 // gamma = 1 trial is a full evaluation (launch_eval_trial); this kernel tries the halvings.
 // ------------------------------------------------------------------------------------------
 
-template <typename TI, int SEG, int T>
+template <typename TI, int SEG, int T, bool PROX>
 __global__ void __launch_bounds__(kBlock)
 k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
              const float* __restrict__ b, const float* __restrict__ q,
-             const float* __restrict__ grad, int t0, int ls_max, double c1,
-             float* partials, unsigned* counter, DevState* st) {
+             const float* __restrict__ cpx, const float* __restrict__ grad, int t0, int ls_max,
+             double c1, float* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->ls_done) return;
   const int inner = g.inner, m = g.m;
   const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
-  float aD[T], aS[T], aP[T], agq = 0.f;
+  float aD[T], aS[T], aP[T], aR[T], agq = 0.f;
 #pragma unroll
-  for (int t = 0; t < T; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; }
+  for (int t = 0; t < T; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; aR[t] = 0.f; }
   // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
   for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
   int c = (item % ncb) * kBlock + threadIdx.x;
@@ -215,12 +238,13 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
   const ColNbrs nb = col_nbrs(g, c, fb);
   const int pb = col_pbase(g, c);
   const ColNbrs nq = col_nbrs_pitched(g, c, pb);   // q and grad are pitched solver arrays
-  float bw[SEG + 1], qw[SEG + 1], bAp[SEG], qAp[SEG], bBp[SEG], qBp[SEG];
+  float bw[SEG + 1], qw[SEG + 1], bAp[SEG], qAp[SEG], bBp[SEG], qBp[SEG], cw[SEG];
 #pragma unroll
   for (int j = 0; j <= SEG; ++j) {
     int kk = min(k0 + j, m);
     bw[j] = __ldg(b + fb + kk * inner);
     qw[j] = __ldg(q + pb + kk * g.psP);
+    if (PROX && j < SEG) cw[j] = __ldg(cpx + pb + kk * g.psP);
   }
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
@@ -250,21 +274,27 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
       float dPE = x[j + 1] - x[j];
       float dA = fmaf(gam, qAp[j], bAp[j]) - x[j], dB = fmaf(gam, qBp[j], bBp[j]) - x[j];
       aS[t] += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
+      if (PROX) aR[t] += (x[j] - cw[j]) * (x[j] - cw[j]);
     }
   }
   }   // work items
-  float v[3 * T + 1];
-  double tot[3 * T + 1];
+  constexpr int NV = (PROX ? 4 : 3) * T + 1;
+  float v[NV];
+  double tot[NV];
 #pragma unroll
-  for (int t = 0; t < T; ++t) { v[3 * t] = aD[t]; v[3 * t + 1] = aS[t]; v[3 * t + 2] = aP[t]; }
+  for (int t = 0; t < T; ++t) {
+    v[3 * t] = aD[t]; v[3 * t + 1] = aS[t]; v[3 * t + 2] = aP[t];
+    if (PROX) v[3 * T + 1 + t] = aR[t];
+  }
   v[3 * T] = agq;
-  if (grid_sum<3 * T + 1>(v, partials, counter, tot)) {
+  if (grid_sum<NV>(v, partials, counter, tot)) {
     if (t0 == 0) st->gq = tot[3 * T];
     double gq = st->gq, J = st->J, hv = 0.5 * (double)g.vol;
     if (!(gq < 0.0)) { st->ls_done = 1; st->gamma = 0.0; st->ls_trials = 0; return; }
     for (int t = 0; t < T && t0 + t < ls_max; ++t) {
       double gm = ldexp(1.0, -(t0 + t));
       double Jt = hv * tot[3 * t] + g.alpha_d * hv * tot[3 * t + 1] + g.beta_d * hv * tot[3 * t + 2];
+      if (PROX) Jt += (double)st->admm_rho * hv * tot[3 * T + 1 + t];
       st->ls_trials = t0 + t + 1;
       if (Jt <= J + c1 * gm * gq) { st->ls_done = 1; st->gamma = gm; return; }
     }
@@ -394,39 +424,62 @@ static dim3 resident_grid(const Geo& g, int per_sm = 4) {
 
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
-                        const Work& w, cudaStream_t s) {
-  HYSCO_DISPATCH(dtype, T,
-    (k_eval<T, kSeg, false><<<resident_grid(g), kBlock, 0, s>>>(
-        g, (const T*)Ip, (const T*)Im, b, nullptr, grad, grad_p, dco, eco, invd, it, 0, 0.0,
-        w.partials, w.counter, w.st)))
+                        const Work& w, cudaStream_t s, const float* cpx) {
+  if (cpx) {
+    HYSCO_DISPATCH(dtype, T,
+      (k_eval<T, kSeg, false, true><<<resident_grid(g), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, nullptr, cpx, grad, grad_p, dco, eco, invd, it, 0,
+          0.0, w.partials, w.counter, w.st)))
+  } else {
+    HYSCO_DISPATCH(dtype, T,
+      (k_eval<T, kSeg, false, false><<<resident_grid(g), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, nullptr, nullptr, grad, grad_p, dco, eco, invd, it,
+          0, 0.0, w.partials, w.counter, w.st)))
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, float* grad_p, float* dco,
                               float* eco, float* invd, int ls_max, double c1, const Work& w,
-                              cudaStream_t s) {
-  HYSCO_DISPATCH(dtype, T,
-    (k_eval<T, kSeg, true><<<resident_grid(g), kBlock, 0, s>>>(
-        g, (const T*)Ip, (const T*)Im, b, q, nullptr, grad_p, dco, eco, invd, 0, ls_max, c1,
-        w.partials, w.counter, w.st)))
+                              cudaStream_t s, const float* cpx) {
+  if (cpx) {
+    HYSCO_DISPATCH(dtype, T,
+      (k_eval<T, kSeg, true, true><<<resident_grid(g), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, cpx, nullptr, grad_p, dco, eco, invd, 0, ls_max,
+          c1, w.partials, w.counter, w.st)))
+  } else {
+    HYSCO_DISPATCH(dtype, T,
+      (k_eval<T, kSeg, true, false><<<resident_grid(g), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, nullptr, nullptr, grad_p, dco, eco, invd, 0,
+          ls_max, c1, w.partials, w.counter, w.st)))
+  }
   return cudaGetLastError();
+}
+
+template <bool PROX>
+static void linesearch_impl(const Geo& g, int dtype, const void* Ip, const void* Im,
+                            const float* b, const float* q, const float* cpx, const float* grad,
+                            int t0, int ls_max, double c1, const Work& w, cudaStream_t s) {
+  if (t0 == 0) {
+    HYSCO_DISPATCH(dtype, T,
+      (k_linesearch<T, kSeg, 1, PROX><<<resident_grid(g), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, cpx, grad, t0, ls_max, c1, w.partials,
+          w.counter, w.st)))
+  } else {
+    HYSCO_DISPATCH(dtype, T,
+      (k_linesearch<T, kSeg, kLsBatch, PROX><<<resident_grid(g, 2), kBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, q, cpx, grad, t0, ls_max, c1, w.partials,
+          w.counter, w.st)))
+  }
 }
 
 cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, const float* q, const float* grad, int t0,
-                              int ls_max, double c1, const Work& w, cudaStream_t s) {
-  if (t0 == 0) {
-    HYSCO_DISPATCH(dtype, T,
-      (k_linesearch<T, kSeg, 1><<<resident_grid(g), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
-          w.st)))
-  } else {
-    HYSCO_DISPATCH(dtype, T,
-      (k_linesearch<T, kSeg, kLsBatch><<<resident_grid(g, 2), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, q, grad, t0, ls_max, c1, w.partials, w.counter,
-          w.st)))
-  }
+                              int ls_max, double c1, const Work& w, cudaStream_t s,
+                              const float* cpx) {
+  if (cpx) linesearch_impl<true>(g, dtype, Ip, Im, b, q, cpx, grad, t0, ls_max, c1, w, s);
+  else linesearch_impl<false>(g, dtype, Ip, Im, b, q, nullptr, grad, t0, ls_max, c1, w, s);
   return cudaGetLastError();
 }
 

@@ -199,6 +199,25 @@ class Hysco:
                                         _stream(self.device)), "hysco_solve")
         return b, (st[:gn_iters] if st is not None else None)
 
+    def admm(self, Ip, Im, b=None, stats=True, **kw):
+        """ADMM of Sec. 2.3.2 (hysco_admm).  Keyword options are the fields of hysco_admm_opts
+        (defaults from hysco_default_admm_opts; init defaults to OT when b is None).  Returns
+        (b, stats [admm_iters, ADMM_NSTATS] float64 or None)."""
+        o = _lib.default_admm_opts()
+        kw.setdefault("init", int(b is None))
+        for k, v in kw.items():
+            if not hasattr(o, k) or k == "pad_":
+                raise TypeError(f"unknown ADMM option {k}")
+            setattr(o, k, type(getattr(o, k))(v))
+        b = self._new_fld() if b is None else b
+        st = (torch.full((max(o.admm_iters, 1), _lib.ADMM_NSTATS), float("nan"),
+                         dtype=torch.float64, device=self.device) if stats else None)
+        _lib.check(self.lib.hysco_admm(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                       self._fld(b, "b"), C.byref(o),
+                                       None if st is None else C.c_void_p(st.data_ptr()),
+                                       _stream(self.device)), "hysco_admm")
+        return b, (st[:o.admm_iters] if st is not None else None)
+
     def pcg_plan(self):
         """(cooperative grid, on-chip slots per thread, slots per thread, threads per block) of
         the persistent PCG."""

@@ -1,0 +1,127 @@
+"""ADMM (Sec. 2.3.2, hysco_admm) against the double-precision oracle's ADMM on the same inputs.
+
+Every decision of a run is compared first: the rho sequence (the residual-balancing rule) and
+the stopping iteration must be identical, and the BlockPCG iteration counts (summed over
+columns) may differ only where a column's relative residual sits at the 0.1 threshold (within
+1%).  Values: J at every iterate relative 1e-4 and the final field relative 1e-3 in the 2-norm
+(single-precision arithmetic through the same iterations, as for the GN solve); the residuals
+r, s and the relative changes, whose single-precision values are differences of nearby fields,
+relative 1e-2.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2403_10706_b300 import _lib  # noqa: E402
+from paper_2403_10706_b300 import phantom as ph  # noqa: E402
+
+ALPHA, BETA = 300.0, 1e4
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2403_10706_b300 import build
+    build.build()
+    from paper_2403_10706_b300.hysco import Hysco
+    return Hysco
+
+
+def rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300)
+
+
+def run_both(H, orc, pr, iters, gn_iters=2, **kw):
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    b, st = h.admm(torch.from_numpy(pr.Ip).cuda(), torch.from_numpy(pr.Im).cuda(),
+                   admm_iters=iters, gn_iters=gn_iters, **kw)
+    torch.cuda.synchronize()
+    assert h.last_status() == 0
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    okw = {k: v for k, v in kw.items() if k in ("tol", "mu", "tau", "rho0")}
+    rb, rz, ru, status, rst = P.admm(pr.Ip, pr.Im, admm_iters=iters, gn_iters=gn_iters,
+                                     contract=True, **okw)
+    assert status == 0
+    return b.cpu().numpy(), st.cpu().numpy(), rb, rst, orc.ADMM_FIELDS
+
+
+def check(gs, rs, fields, gb, rb, what):
+    F = {f: i for i, f in enumerate(fields)}
+    done_g = ~np.isnan(gs[:, F["J"]])
+    done_r = ~np.isnan(rs[:, F["J"]])
+    assert np.array_equal(done_g, done_r), (what, done_g, done_r)
+    gs, rs = gs[done_g], rs[done_r]
+    assert np.array_equal(gs[:, F["rho"]], rs[:, F["rho"]]), (what, gs[:, F["rho"]], rs[:, F["rho"]])
+    np.testing.assert_allclose(gs[:, F["J"]], rs[:, F["J"]], rtol=1e-4, err_msg=what)
+    np.testing.assert_allclose(gs[:, F["block_pcg_iters"]], rs[:, F["block_pcg_iters"]],
+                               rtol=1e-2, err_msg=what)
+    for f in ("r_primal", "s_dual", "rel_db", "rel_dz"):
+        np.testing.assert_allclose(gs[:, F[f]], rs[:, F[f]], rtol=1e-2, err_msg=f"{what} {f}")
+    assert rel(gb, rb) <= 1e-3, (what, rel(gb, rb))
+
+
+def test_one_iteration_matches_oracle(H, orc):
+    pr = ph.make_pair("tiny")
+    gb, gs, rb, rs, fields = run_both(H, orc, pr, 1, gn_iters=1)
+    check(gs, rs, fields, gb, rb, "tiny, 1 iteration")
+
+
+def test_tiny_run_matches_oracle(H, orc):
+    pr = ph.make_pair("tiny")
+    gb, gs, rb, rs, fields = run_both(H, orc, pr, 10)
+    check(gs, rs, fields, gb, rb, "tiny, 10 iterations")
+
+
+@pytest.mark.parametrize("name", ["small", "7t"])
+def test_larger_volumes_match_oracle(H, orc, name):
+    """96x96x60 (PE axis 1) and 130x130x85 (PE axis 0), 4 iterations."""
+    pr = ph.make_pair(name)
+    gb, gs, rb, rs, fields = run_both(H, orc, pr, 4)
+    check(gs, rs, fields, gb, rb, name)
+
+
+def test_pe_axis_2_and_ragged_planes(H, orc):
+    recipe = dict(dims=(21, 19, 40), spacing=(1.1, 0.9, 1.0), pe_dim=2, seed=7001, n_ellipsoids=3,
+                  n_blobs=2, semi_axes=(3.0, 8.0), smooth=0.5, n_gauss=3, sigma=(4.0, 6.0),
+                  bmax=2.5, noise=0.01)
+    pr = ph.make_pair(recipe)
+    gb, gs, rb, rs, fields = run_both(H, orc, pr, 5)
+    check(gs, rs, fields, gb, rb, "pe 2")
+
+
+def test_stop_rule_matches_oracle(H, orc):
+    pr = ph.make_pair("tiny")
+    gb, gs, rb, rs, fields = run_both(H, orc, pr, 30, tol=0.05)
+    assert np.isnan(gs[-1, 0])   # stopped before the cap
+    check(gs, rs, fields, gb, rb, "tol 0.05")
+
+
+def test_graph_replay_equals_direct_launches(H):
+    pr = ph.make_pair("tiny")
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    Ip, Im = torch.from_numpy(pr.Ip).cuda(), torch.from_numpy(pr.Im).cuda()
+    outs = []
+    b = h._new_fld()
+    for no_graph in (1, 0, 0):
+        b, st = h.admm(Ip, Im, b=b, init=1, admm_iters=6, no_graph=no_graph)
+        torch.cuda.synchronize()
+        outs.append((b.cpu().numpy().copy(), st.cpu().numpy().copy()))
+    for k in (1, 2):
+        assert np.array_equal(outs[0][0], outs[k][0])
+        assert np.array_equal(outs[0][1], outs[k][1], equal_nan=True)
+
+
+def test_rejects_long_columns_and_bad_options(H):
+    h = H((4, 300, 3), (1.0, 1.0, 1.0), 1, ALPHA, BETA)   # 301 PE nodes > 256
+    Ip = torch.zeros((4, 300, 3), device="cuda")
+    with pytest.raises(_lib.HyscoError):
+        h.admm(Ip, Ip, admm_iters=1)
+    h2 = H((8, 8, 8), (1.0, 1.0, 1.0), 1, ALPHA, BETA)
+    I2 = torch.zeros((8, 8, 8), device="cuda")
+    for bad in (dict(tau=1.0), dict(mu=0.5), dict(gn_iters=0), dict(pcg_max_iters=65),
+                dict(tol=-1.0)):
+        with pytest.raises(_lib.HyscoError):
+            h2.admm(I2, I2, admm_iters=1, **bad)
