@@ -23,14 +23,13 @@ __device__ __forceinline__ int cell_index(float t, int m, float& w) {
   return (int)f;
 }
 
+// the two taps are loaded only where they lie inside the column (predicated loads), 0 outside
 template <typename TI>
 __device__ __forceinline__ void interp(const TI* col, int inner, int m, int i, float w,
                                        float& val, float& slope) {
-  int i0 = min(max(i, 0), m - 1), i1 = min(max(i + 1, 0), m - 1);
-  float I0 = ldf(col + i0 * inner);
-  float I1 = ldf(col + i1 * inner);
-  I0 = (i >= 0 && i < m) ? I0 : 0.0f;
-  I1 = (i >= -1 && i + 1 < m) ? I1 : 0.0f;
+  const bool in0 = (unsigned)i < (unsigned)m, in1 = (unsigned)(i + 1) < (unsigned)m;
+  const float I0 = in0 ? ldf(col + i * inner) : 0.0f;
+  const float I1 = in1 ? ldf(col + (i + 1) * inner) : 0.0f;
   slope = I1 - I0;
   val = fmaf(w, slope, I0);
 }

@@ -4,10 +4,10 @@
 //
 // Thread mapping ("column march"): thread = (PE column c, segment of kSeg nodes along PE).
 // Consecutive threads own consecutive columns, so for pe_dim != 2 every PE step is a coalesced
-// row access.  The segment loop is fully unrolled and every load is unconditional: indices are
+// row access.  The segment loop is fully unrolled with no serialising branches: field indices are
 // clamped into range and absent neighbours are read at the node itself (zero Laplacian
-// difference), out-of-image interpolation taps are selected to zero after the load.  So a thread
-// issues all of its field loads, then all of its image gathers, with no serialising branches.
+// difference); an interpolation tap outside the image is a predicated-off load that reads 0.  So
+// a thread issues all of its field loads, then all of its image gathers.
 // Per cell j (nodes j, j+1):
 //   bc = (b_j + b_{j+1}) / 2, delta = b_{j+1} - b_j, t+- = j +- bc      (averaging / FD operators)
 //   I(t) = I[i] + w (I[i+1] - I[i]), i = floor(t), w = t - i, I = 0 outside 0..m-1
