@@ -388,6 +388,7 @@ def batch_bench(dev, stream, flush, reps=2):
 def run_ours(args):
     import torch
 
+    from paper_2403_10706_b300 import _lib
     from paper_2403_10706_b300 import build as b
     from paper_2403_10706_b300.hysco import Hysco
 
@@ -589,6 +590,27 @@ def run_ours(args):
     ls = {"launch_ms": ls_ms, "alg_bytes_per_launch": alg_ls,
           "achieved": alg_ls / (ls_ms / 1e3) / 1e9, "unit": "GB/s", "kernel": "k_ls_correct",
           "columns_skipped": int(nbad.item())}
+    # the other hot-path entry points, each timed alone (L2 flushed before every call) with its
+    # minimal algorithmic bytes per node (4-byte floats; images 4 B per voxel and image):
+    #   hysco_init_ot   read I+, I- (8 per voxel), write b (4 per node)         [shift, OT, blur]
+    #   hysco_hessvec   read v, d, e (12), write Hv (4)                        [to / from pitched]
+    #   hysco_precond   read r, d, e (12), write z (4): per-column tridiagonal factor and solve
+    def table_row(ms, alg, launches):
+        return {"launch_ms": ms, "alg_bytes_per_call": alg, "launches": launches,
+                "achieved": alg / (ms / 1e3) / 1e9, "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak}
+    bt = torch.empty_like(b_out)
+    vv = torch.randn_like(b_out)
+    hv_out, pc_out = torch.empty_like(b_out), torch.empty_like(b_out)
+    kernels = {
+        "hysco_init_ot": table_row(time_launches(lambda: h.init_ot(Ip, Im, out=bt)),
+                                   8 * nimg + 4 * nfld, "k_ot_shift, k_ot, k_blur"),
+    }
+    h.eval(Ip, Im, b_out, grad=g, terms=terms)   # the linearisation the next two calls use
+    kernels["hysco_hessvec"] = table_row(time_launches(lambda: h.hessvec(vv, out=hv_out)),
+                                         16 * nfld, "k_to_pitched, k_hv, k_from_pitched")
+    kernels["hysco_precond_column"] = table_row(
+        time_launches(lambda: h.precond(vv, kind=_lib.PC_COLUMN, out=pc_out)), 16 * nfld,
+        "k_to_pitched, k_col_factor, k_col_solve, k_from_pitched")
     # ADMM (Sec. 2.3.2) on the same pair: OT + 20 iterations of 2 GN steps (BlockPCG directions)
     # each, against the GN solve's 20 iterations; the z-update's four per-plane products move
     # 2 * E * nB * nA * (nB + nA) flops each way (forward and inverse transform)
@@ -645,7 +667,7 @@ def run_ours(args):
                 "config": config(args, world), "status": status,
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "eval_roofline": eval_roof, "adjoint": adjoint,
-                "ls_correct": ls, "admm": admm}
+                "ls_correct": ls, "admm": admm, "kernel_table": kernels}
         if prec is not None:
             line["precision"] = prec
         if batch is not None:

@@ -66,16 +66,35 @@ k_ot_shift(const TI* __restrict__ Ip, const TI* __restrict__ Im, int n, float ep
   __syncthreads();
   if (!is_last) return;
   __threadfence();
-  if (tid == 0) {
+  // warp 0 of the last block: lane l takes blocks l, l + 32, ... (eight loads in flight), then a
+  // shuffle tree; min and max are exact in any order
+  if (tid < 32) {
     float gmn = __int_as_float(0x7f800000), gmx = 0.f;
-    for (unsigned b = 0; b < gridDim.x; ++b) {
-      gmn = fminf(gmn, __ldcg(partials + 2 * b));
-      gmx = fmaxf(gmx, __ldcg(partials + 2 * b + 1));
+    const int nblk = gridDim.x;
+    for (int b0 = tid; b0 < nblk; b0 += 32 * 8) {
+      float lo[8], hi[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + 32 * u;
+        lo[u] = b < nblk ? __ldcg(partials + 2 * b) : __int_as_float(0x7f800000);
+        hi[u] = b < nblk ? __ldcg(partials + 2 * b + 1) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        gmn = fminf(gmn, lo[u]);
+        gmx = fmaxf(gmx, hi[u]);
+      }
     }
-    float neg = -gmn > 0.f ? -gmn : 0.f;
-    float s = __fadd_rn(neg, __fmul_rn(eps, gmx));
-    st->ot_shift = (double)s;
-    *counter = 0u;
+    for (int off = 16; off > 0; off >>= 1) {
+      gmn = fminf(gmn, __shfl_down_sync(0xffffffffu, gmn, off));
+      gmx = fmaxf(gmx, __shfl_down_sync(0xffffffffu, gmx, off));
+    }
+    if (tid == 0) {
+      float neg = -gmn > 0.f ? -gmn : 0.f;
+      float s = __fadd_rn(neg, __fmul_rn(eps, gmx));
+      st->ot_shift = (double)s;
+      *counter = 0u;
+    }
   }
 }
 
