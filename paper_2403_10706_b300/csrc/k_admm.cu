@@ -144,18 +144,21 @@ k_block_pcg(Geo g, const float* __restrict__ grad, const float* __restrict__ dco
 // z-update: dense plane layout [E][nB][nA] for the transforms
 // ------------------------------------------------------------------------------------------
 
+// The node-wise ADMM kernels run over (block of kBlock PE columns) x (segment of kAdmmSeg nodes):
+// a thread finds its column's bases once and walks the segment.
+constexpr int kAdmmSeg = 8;
+
 // T0[k][cB][cA] = b + u at node k of column c = cB nA + cA (b in the caller's layout, u pitched)
 __global__ void __launch_bounds__(kBlock)
 k_zrhs(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* __restrict__ T0,
        const DevState* st) {
   if (st->stop) return;
-  const long long n = (long long)g.E * g.ncols;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(i / g.ncols), c = (int)(i - (long long)k * g.ncols);
-    const float bv = __ldg(b + col_base(c, g.inner, g.fld_ostride) + k * g.inner);
-    T0[i] = bv + __ldg(u + col_pbase(g, c) + k * g.psP);
-  }
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncols) return;
+  const int fb = col_base(c, g.inner, g.fld_ostride), pb = col_pbase(g, c);
+  const int k0 = blockIdx.y * kAdmmSeg, k1 = min(k0 + kAdmmSeg, g.E);
+  for (int k = k0; k < k1; ++k)
+    T0[(long long)k * g.ncols + c] = __ldg(b + fb + k * g.inner) + __ldg(u + pb + k * g.psP);
 }
 
 // Batched C_z = A_z B_z (M x N, inner dimension K) over planes z = blockIdx.z, each operand
@@ -242,20 +245,22 @@ k_admm_prep(Geo g, const float* __restrict__ b, const float* __restrict__ zc,
   if (st->stop) return;
   const float s = st->admm_scale;
   float nb = 0.f, nz = 0.f, nu = 0.f;
-  const long long n = (long long)g.E * g.ncols;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(i / g.ncols), cc = (int)(i - (long long)k * g.ncols);
-    const int pi = col_pbase(g, cc) + k * g.psP;
-    const float bv = __ldg(b + col_base(cc, g.inner, g.fld_ostride) + k * g.inner);
-    const float zv = zc[pi];
-    const float uv = s * u[pi];
-    u[pi] = uv;
-    c[pi] = zv - uv;
-    bprev[pi] = bv;
-    nb += bv * bv;
-    nz += zv * zv;
-    nu += uv * uv;
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc < g.ncols) {
+    const int fb = col_base(cc, g.inner, g.fld_ostride), pb = col_pbase(g, cc);
+    const int k0 = blockIdx.y * kAdmmSeg, k1 = min(k0 + kAdmmSeg, g.E);
+    for (int k = k0; k < k1; ++k) {
+      const int pi = pb + k * g.psP;
+      const float bv = __ldg(b + fb + k * g.inner);
+      const float zv = zc[pi];
+      const float uv = s * u[pi];
+      u[pi] = uv;
+      c[pi] = zv - uv;
+      bprev[pi] = bv;
+      nb += bv * bv;
+      nz += zv * zv;
+      nu += uv * uv;
+    }
   }
   float v[3] = {nb, nz, nu};
   double tot[3];
@@ -286,19 +291,21 @@ k_admm_post(Geo g, const float* __restrict__ b, const float* __restrict__ z,
             double* stats, float* partials, unsigned* counter, DevState* st) {
   if (st->stop) return;
   float r2 = 0.f, s2 = 0.f, db2 = 0.f;
-  const long long n = (long long)g.E * g.ncols;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k = (int)(i / g.ncols), cc = (int)(i - (long long)k * g.ncols);
-    const int pi = col_pbase(g, cc) + k * g.psP;
-    const float bv = __ldg(b + col_base(cc, g.inner, g.fld_ostride) + k * g.inner);
-    const float zv = z[pi];
-    const float dv = bv - zv;
-    u[pi] += dv;
-    const float dz = zv - zprev[pi], db = bv - bprev[pi];
-    r2 += dv * dv;
-    s2 += dz * dz;
-    db2 += db * db;
+  const int cc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cc < g.ncols) {
+    const int fb = col_base(cc, g.inner, g.fld_ostride), pb = col_pbase(g, cc);
+    const int k0 = blockIdx.y * kAdmmSeg, k1 = min(k0 + kAdmmSeg, g.E);
+    for (int k = k0; k < k1; ++k) {
+      const int pi = pb + k * g.psP;
+      const float bv = __ldg(b + fb + k * g.inner);
+      const float zv = z[pi];
+      const float dv = bv - zv;
+      u[pi] += dv;
+      const float dz = zv - zprev[pi], db = bv - bprev[pi];
+      r2 += dv * dv;
+      s2 += dz * dz;
+      db2 += db * db;
+    }
   }
   float v[3] = {r2, s2, db2};
   double tot[3];
@@ -350,9 +357,8 @@ __global__ void k_admm_init(DevState* st, float rho0, double* stats, int nrows) 
 
 // ------------------------------------------------------------------------------------------
 
-static int flat_grid(long long n) {
-  long long b = (n + kBlock - 1) / kBlock;
-  return (int)std::min<long long>(b, 148 * 8);
+static dim3 node_grid(const Geo& g) {
+  return dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, kAdmmSeg));
 }
 
 cudaError_t launch_block_pcg(const Geo& g, const float* grad, const float* dco, const float* eco,
@@ -381,7 +387,7 @@ cudaError_t launch_admm_init(DevState* st, float rho0, double* stats, int nrows,
 
 cudaError_t launch_admm_prep(const Geo& g, const float* b, const float* z, float* u, float* c,
                              float* bprev, const Work& w, cudaStream_t s) {
-  k_admm_prep<<<flat_grid((long long)g.E * g.ncols), kBlock, 0, s>>>(g, b, z, u, c, bprev,
+  k_admm_prep<<<node_grid(g), kBlock, 0, s>>>(g, b, z, u, c, bprev,
                                                                     w.partials, w.counter, w.st);
   return cudaGetLastError();
 }
@@ -391,7 +397,7 @@ cudaError_t launch_admm_zsolve(const Geo& g, const float* b, const float* u, con
                                cudaStream_t s) {
   const int nA = g.nA, nB = g.nB, E = g.E;
   const long long P = (long long)nA * nB;
-  k_zrhs<<<flat_grid((long long)E * g.ncols), kBlock, 0, s>>>(g, b, u, T0, st);
+  k_zrhs<<<node_grid(g), kBlock, 0, s>>>(g, b, u, T0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const dim3 grid(ceil_div(nA, kMmTile), ceil_div(nB, kMmTile), E);
@@ -417,7 +423,7 @@ cudaError_t launch_admm_zsolve(const Geo& g, const float* b, const float* u, con
 cudaError_t launch_admm_post(const Geo& g, const float* b, const float* z, const float* zprev,
                              float* u, const float* bprev, int it, double tol, double mu,
                              double tau, double* stats, const Work& w, cudaStream_t s) {
-  k_admm_post<<<flat_grid((long long)g.E * g.ncols), kBlock, 0, s>>>(
+  k_admm_post<<<node_grid(g), kBlock, 0, s>>>(
       g, b, z, zprev, u, bprev, it, (float)tol, (float)mu, (float)tau, stats, w.partials,
       w.counter, w.st);
   return cudaGetLastError();
