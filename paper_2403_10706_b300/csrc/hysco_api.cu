@@ -673,23 +673,40 @@ void real_fourier_basis(int n, std::vector<float>& Q, std::vector<float>& mu) {
   }
 }
 
+// allocates what is still missing (a failed earlier call leaves no leak: every buffer lives in
+// the handle and is freed with it); the bases are uploaded once
 int admm_setup(hysco_ctx* h) {
-  if (h->au) return HYSCO_OK;
+  if (h->amuB) return HYSCO_OK;
   const size_t fbytes = (size_t)std::max<long long>(h->g.nfp, h->nfld) * sizeof(float);
   float** bufs[] = {&h->az[0], &h->az[1], &h->au, &h->ac, &h->abprev};
-  for (float** b : bufs)
-    if (cudaMalloc((void**)b, fbytes) != cudaSuccess || cudaMemset(*b, 0, fbytes) != cudaSuccess)
+  for (float** b : bufs) {
+    if (*b) continue;
+    if (cudaMalloc((void**)b, fbytes) != cudaSuccess) {
+      *b = nullptr;
+      cudaGetLastError();
       return HYSCO_ENOMEM;
+    }
+    if (cudaMemset(*b, 0, fbytes) != cudaSuccess) return HYSCO_ECUDA;
+  }
   std::vector<float> QA, QB, muA, muB;
   real_fourier_basis(h->g.nA, QA, muA);
   real_fourier_basis(h->g.nB, QB, muB);
   struct { float** d; const std::vector<float>* v; } up[] = {
       {&h->aQA, &QA}, {&h->aQB, &QB}, {&h->amuA, &muA}, {&h->amuB, &muB}};
-  for (auto& u : up)
-    if (cudaMalloc((void**)u.d, u.v->size() * sizeof(float)) != cudaSuccess ||
-        cudaMemcpy(*u.d, u.v->data(), u.v->size() * sizeof(float), cudaMemcpyHostToDevice) !=
-            cudaSuccess)
+  for (auto& u : up) {
+    if (*u.d) continue;
+    float* d = nullptr;
+    if (cudaMalloc((void**)&d, u.v->size() * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
       return HYSCO_ENOMEM;
+    }
+    if (cudaMemcpy(d, u.v->data(), u.v->size() * sizeof(float), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      cudaFree(d);
+      return HYSCO_ECUDA;
+    }
+    *u.d = d;   // set only once uploaded: amuB marks a complete setup
+  }
   return HYSCO_OK;
 }
 

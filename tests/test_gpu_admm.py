@@ -125,3 +125,40 @@ def test_rejects_long_columns_and_bad_options(H):
                 dict(tol=-1.0)):
         with pytest.raises(_lib.HyscoError):
             h2.admm(I2, I2, admm_iters=1, **bad)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+def test_half_precision_images_match_oracle_on_the_same_values(H, orc, dtype):
+    """Images stored in bf16 / f16 (the prox evaluation kernels are templated on the storage
+    type): against the oracle's ADMM on the same quantised values."""
+    td = {"bf16": torch.bfloat16, "f16": torch.float16}[dtype]
+    pr = ph.make_pair("tiny")
+    Ipq = torch.from_numpy(pr.Ip).cuda().to(td)
+    Imq = torch.from_numpy(pr.Im).cuda().to(td)
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA, dtype=td)
+    b, st = h.admm(Ipq, Imq, admm_iters=6)
+    torch.cuda.synchronize()
+    assert h.last_status() == 0
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    rb, rz, ru, status, rst = P.admm(Ipq.float().cpu().numpy(), Imq.float().cpu().numpy(),
+                                     admm_iters=6, contract=True)
+    check(st.cpu().numpy(), rst, orc.ADMM_FIELDS, b.cpu().numpy(), rb, dtype)
+
+
+def test_start_from_a_given_field(H, orc):
+    """init = 0: the run starts from the caller's b (here the oracle's 3-iteration GN field)."""
+    pr = ph.make_pair("tiny")
+    P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    b0, status, _ = P.solve(pr.Ip, pr.Im, gn_iters=3)
+    assert status == 0
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    b = torch.from_numpy(b0.astype(np.float32)).cuda()
+    b, st = h.admm(torch.from_numpy(pr.Ip).cuda(), torch.from_numpy(pr.Im).cuda(), b=b, init=0,
+                   admm_iters=5, rho0=50.0)
+    torch.cuda.synchronize()
+    assert h.last_status() == 0
+    rb, rz, ru, status, rst = P.admm(pr.Ip, pr.Im, b=b0.astype(np.float32).astype(np.float64),
+                                     init=False, admm_iters=5, rho0=50.0, contract=True)
+    assert status == 0
+    assert st.cpu().numpy()[0, 2] == 50.0
+    check(st.cpu().numpy(), rst, orc.ADMM_FIELDS, b.cpu().numpy(), rb, "init 0, rho0 50")
