@@ -622,6 +622,12 @@ def run_ours(args):
     fe = h.field_dims
     plane = [fe[a] for a in range(3) if a != pr.pe_dim]
     zflop = 2 * 2 * fe[pr.pe_dim] * plane[0] * plane[1] * (plane[0] + plane[1])
+    # the work the timed solves do (deterministic: the same trajectory as this solve's)
+    gs = gst.cpu().numpy()
+    work = {"gn_iters": int(gn), "pcg_iterations": int(np.nansum(gs[:, 7])),
+            "ls_trials": int(np.nansum(gs[:, 9])),
+            "gamma_1_accepted": int(np.sum(gs[:, 6] == 1.0)),
+            "J_at_first_gn_iter": float(gs[0, 0]), "J_at_last_gn_iter": float(gs[-1, 0])}
     admm = {"iters": 20, "gn_steps_per_b_update": 2, "ms_per_run": admm_ms,
             "pairs_per_s": 1e3 / admm_ms, "J_final": float(ast[-1, 0].item()),
             "J_gn_solve": float(gst[-1, 0].item()), "rho_final": float(ast[-1, 2].item()),
@@ -667,7 +673,7 @@ def run_ours(args):
                 "config": config(args, world), "status": status,
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "eval_roofline": eval_roof, "adjoint": adjoint,
-                "ls_correct": ls, "admm": admm, "kernel_table": kernels}
+                "ls_correct": ls, "admm": admm, "kernel_table": kernels, "work": work}
         if prec is not None:
             line["precision"] = prec
         if batch is not None:
