@@ -263,6 +263,21 @@ void hysco_default_admm_opts(hysco_admm_opts* opts);
 int hysco_admm(hysco_t h, const void* Ip, const void* Im, float* b_inout,
                const hysco_admm_opts* opts, double* stats, hysco_stream_t stream);
 
+/* The ADMM b-update's direction solver alone (BlockPCG, Sec. 2.3.2): linearises the b-subproblem
+ * F(b) + rho vol/2 ||b - c||^2 at b (its GN Hessian does not depend on c) and solves
+ * H_col q = rhs on every PE column independently by Jacobi CG with the column's own step sizes
+ * and stop (||r|| / ||r0|| < rtol after an update, p^T H p <= 0, or max_iters <= 1000).  b, rhs,
+ * q: field-shaped float32 (device); iters: NULL or one device int32 receiving the iterations
+ * summed over columns.  PE extent at most 255 cells, rho >= 0, else HYSCO_EINVAL. */
+int hysco_block_pcg(hysco_t h, const void* Ip, const void* Im, const float* b, double rho,
+                    const float* rhs, float* q, int max_iters, double rtol, int32_t* iters,
+                    hysco_stream_t stream);
+
+/* The ADMM z-update alone (Sec. 2.3.2): z = argmin alpha (S1 + S2)(z) + rho vol/2 ||v - z||^2
+ * with periodic in-plane ends, i.e. z = rho (alpha H_G + rho I)^{-1} v, per PE plane through the
+ * real Fourier bases of the in-plane axes.  v, z: field-shaped float32 (device); rho > 0. */
+int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_stream_t stream);
+
 /* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):

@@ -65,6 +65,8 @@ def load():
         "hysco_default_opts": (None, [C.POINTER(Opts)]),
         "hysco_default_admm_opts": (None, [C.POINTER(AdmmOpts)]),
         "hysco_admm": (I, [P, P, P, P, C.POINTER(AdmmOpts), P, P]),
+        "hysco_block_pcg": (I, [P, P, P, P, D, P, P, I, D, P, P]),
+        "hysco_admm_zsolve": (I, [P, P, D, P, P]),
         "hysco_create": (I, [I64P, C.POINTER(C.c_double), I, D, D, I, C.POINTER(P)]),
         "hysco_destroy": (None, [P]),
         "hysco_field_dims": (I, [P, I64P]),

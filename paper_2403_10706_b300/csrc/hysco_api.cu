@@ -751,8 +751,8 @@ int enqueue_admm(hysco_ctx* h, const void* Ip, const void* Im, float* b, const h
     for (int i = 0; i < o->gn_iters; ++i) {
       HYSCO_TRY(launch_eval(gs, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd,
                             i, w, s, h->ac));
-      HYSCO_TRY(launch_block_pcg(gs, h->grad, h->dco, h->eco, h->invd, h->x, o->pcg_max_iters,
-                                 o->pcg_rtol, h->st, s));
+      HYSCO_TRY(launch_block_pcg(gs, h->grad, -1.0f, h->dco, h->eco, h->invd, h->x,
+                                 o->pcg_max_iters, o->pcg_rtol, h->st, s));
       HYSCO_TRY(launch_eval_trial(gs, h->dtype, Ip, Im, b, h->x, h->grad, h->dco, h->eco,
                                   h->invd, o->ls_max_iters, o->armijo_c1, w, s, h->ac));
       for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
@@ -795,6 +795,58 @@ void hysco_default_admm_opts(hysco_admm_opts* o) {
   o->tol = 1e-3;
   o->mu = 10.0;
   o->tau = 2.0;
+}
+
+int hysco_block_pcg(hysco_t h, const void* Ip, const void* Im, const float* b, double rho,
+                    const float* rhs, float* q, int max_iters, double rtol, int32_t* iters,
+                    hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(rhs) ||
+      check_f32(q))
+    return HYSCO_EINVAL;
+  if (iters && !aligned(iters, 4)) return HYSCO_EINVAL;
+  if (!(rho >= 0.0) || !std::isfinite(rho) || max_iters < 1 || max_iters > 1000 ||
+      !(rtol >= 0.0) || h->g.E > kAdmmMaxNodes)
+    return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  const Geo& g = h->g;
+  Geo gs = g;   // the b-subproblem's geometry: no in-plane smoothness
+  gs.wA = 0.f;
+  gs.wB = 0.f;
+  for (int a = 0; a < 3; ++a)
+    if (a != g.p) gs.w[a] = 0.f;
+  cudaStream_t s = (cudaStream_t)stream;
+  Work w = h->work();
+  h->have_lin = false;
+  h->have_factor = false;
+  if (int rc = reset_state(h, s)) return rc;
+  HYSCO_TRY(launch_admm_init(h->st, (float)rho, nullptr, 0, s));
+  // the linearisation at b with the prox centre c = b (the coefficients do not depend on c)
+  HYSCO_TRY(launch_to_pitched(g, b, h->ac, s));
+  HYSCO_TRY(launch_eval(gs, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd, -1, w,
+                        s, h->ac));
+  HYSCO_TRY(launch_to_pitched(g, rhs, h->tmp, s));
+  HYSCO_TRY(launch_block_pcg(gs, h->tmp, 1.0f, h->dco, h->eco, h->invd, h->x, max_iters, rtol,
+                             h->st, s));
+  HYSCO_TRY(launch_from_pitched(g, h->x, q, s));
+  if (iters)
+    HYSCO_TRY(cudaMemcpyAsync(iters, &h->st->blk_iters, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                              s));
+  return HYSCO_OK;
+}
+
+int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_stream_t stream) {
+  if (!h || check_f32(v) || check_f32(z) || !(rho > 0.0) || !std::isfinite(rho))
+    return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  const Geo& g = h->g;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  HYSCO_TRY(launch_admm_init(h->st, (float)rho, nullptr, 0, s));
+  HYSCO_TRY(cudaMemsetAsync(h->ac, 0, (size_t)g.nfp * sizeof(float), s));   // u = 0
+  const AdmmBasis basis{h->aQA, h->aQB, h->amuA, h->amuB};
+  HYSCO_TRY(launch_admm_zsolve(g, v, h->ac, basis, h->tmp, h->q0, h->az[0], h->st, s));
+  HYSCO_TRY(launch_from_pitched(g, h->az[0], z, s));
+  return HYSCO_OK;
 }
 
 int hysco_admm(hysco_t h, const void* Ip, const void* Im, float* b_inout,

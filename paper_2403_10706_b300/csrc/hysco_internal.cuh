@@ -427,9 +427,9 @@ struct AdmmBasis {                  // real orthonormal Fourier bases of the in-
   const float* muA;                 // 2 - 2 cos(2 pi j / nA) of each column of QA
   const float* muB;
 };
-cudaError_t launch_block_pcg(const Geo& g, const float* grad, const float* dco, const float* eco,
-                             const float* invd, float* x, int max_it, double rtol, DevState* st,
-                             cudaStream_t s);
+cudaError_t launch_block_pcg(const Geo& g, const float* rhs, float rhs_sign, const float* dco,
+                             const float* eco, const float* invd, float* x, int max_it,
+                             double rtol, DevState* st, cudaStream_t s);
 cudaError_t launch_admm_init(DevState* st, float rho0, double* stats, int nrows, cudaStream_t s);
 cudaError_t launch_admm_prep(const Geo& g, const float* b, const float* z, float* u, float* c,
                              float* bprev, const Work& w, cudaStream_t s);

@@ -47,7 +47,8 @@ __device__ __forceinline__ void neighbours(const float (&v)[J], int lane, float 
   }
 }
 
-// x = the per-column Jacobi CG solution of H_c x = -grad, H_c = vol [tridiag(e_{k-1}, d_k, e_k)
+// x = the per-column Jacobi CG solution of H_c x = rhs_sign * rhs (rhs_sign = -1 with the
+// gradient as rhs for a GN direction), H_c = vol [tridiag(e_{k-1}, d_k, e_k)
 // + alpha L_pe] (d carries rho, L_pe the 1D Neumann second difference along PE), as in Sec. 2.3.1
 // per column: x0 = 0, stop after an update when ||r|| / ||r0|| < rtol, or when p^T H p <= 0, or
 // after max_it iterations.  Dot products: each lane sums its nodes in j order, then a fixed
@@ -55,7 +56,7 @@ __device__ __forceinline__ void neighbours(const float (&v)[J], int lane, float 
 // uniform).  The iterations taken are added to st->blk_iters.
 template <int J>
 __global__ void __launch_bounds__(kBlock)
-k_block_pcg(Geo g, const float* __restrict__ grad, const float* __restrict__ dco,
+k_block_pcg(Geo g, const float* __restrict__ rhs, float rhs_sign, const float* __restrict__ dco,
             const float* __restrict__ eco, const float* __restrict__ invd,
             float* __restrict__ x, int max_it, float rtol, DevState* st) {
   if (st->stop) return;
@@ -76,7 +77,7 @@ k_block_pcg(Geo g, const float* __restrict__ grad, const float* __restrict__ dco
     d[j] = ok[j] ? __ldg(dco + pi) : 0.f;
     e[j] = ok[j] ? __ldg(eco + pi) : 0.f;
     di[j] = ok[j] ? __ldg(invd + pi) : 0.f;
-    r[j] = ok[j] ? -__ldg(grad + pi) : 0.f;
+    r[j] = ok[j] ? rhs_sign * __ldg(rhs + pi) : 0.f;
     npe[j] = (float)((k > 0) + (k < m));
     xv[j] = 0.f;
   }
@@ -361,22 +362,21 @@ static dim3 node_grid(const Geo& g) {
   return dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, kAdmmSeg));
 }
 
-cudaError_t launch_block_pcg(const Geo& g, const float* grad, const float* dco, const float* eco,
-                             const float* invd, float* x, int max_it, double rtol, DevState* st,
-                             cudaStream_t s) {
+cudaError_t launch_block_pcg(const Geo& g, const float* rhs, float rhs_sign, const float* dco,
+                             const float* eco, const float* invd, float* x, int max_it,
+                             double rtol, DevState* st, cudaStream_t s) {
   const int grid = ceil_div(g.ncols, kBlock / 32);
   const float rt = (float)rtol;
+#define HYSCO_BPCG(J)                                                                        \
+  case J:                                                                                    \
+    k_block_pcg<J><<<grid, kBlock, 0, s>>>(g, rhs, rhs_sign, dco, eco, invd, x, max_it, rt, st); \
+    break;
   switch (ceil_div(g.E, 32)) {
-    case 1: k_block_pcg<1><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 2: k_block_pcg<2><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 3: k_block_pcg<3><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 4: k_block_pcg<4><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 5: k_block_pcg<5><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 6: k_block_pcg<6><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 7: k_block_pcg<7><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
-    case 8: k_block_pcg<8><<<grid, kBlock, 0, s>>>(g, grad, dco, eco, invd, x, max_it, rt, st); break;
+    HYSCO_BPCG(1) HYSCO_BPCG(2) HYSCO_BPCG(3) HYSCO_BPCG(4)
+    HYSCO_BPCG(5) HYSCO_BPCG(6) HYSCO_BPCG(7) HYSCO_BPCG(8)
     default: return cudaErrorInvalidValue;   // the caller limits the column length
   }
+#undef HYSCO_BPCG
   return cudaGetLastError();
 }
 

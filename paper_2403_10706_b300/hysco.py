@@ -218,6 +218,26 @@ class Hysco:
                                        _stream(self.device)), "hysco_admm")
         return b, (st[:o.admm_iters] if st is not None else None)
 
+    def block_pcg(self, Ip, Im, b, rho, rhs, max_iters=10, rtol=0.1, out=None):
+        """BlockPCG on the ADMM b-subproblem linearised at b (hysco_block_pcg): returns
+        (q, iterations summed over columns as a 1-element int32 CUDA tensor)."""
+        out = self._new_fld() if out is None else out
+        it = torch.zeros(1, dtype=torch.int32, device=self.device)
+        _lib.check(self.lib.hysco_block_pcg(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                            self._fld(b, "b"), float(rho), self._fld(rhs, "rhs"),
+                                            self._fld(out, "q"), int(max_iters), float(rtol),
+                                            C.c_void_p(it.data_ptr()), _stream(self.device)),
+                   "hysco_block_pcg")
+        return out, it
+
+    def admm_zsolve(self, v, rho, out=None):
+        """The ADMM z-update alone: rho (alpha H_G + rho I)^{-1} v (hysco_admm_zsolve)."""
+        out = self._new_fld() if out is None else out
+        _lib.check(self.lib.hysco_admm_zsolve(self._h, self._fld(v, "v"), float(rho),
+                                              self._fld(out, "z"), _stream(self.device)),
+                   "hysco_admm_zsolve")
+        return out
+
     def pcg_plan(self):
         """(cooperative grid, on-chip slots per thread, slots per thread, threads per block) of
         the persistent PCG."""

@@ -96,6 +96,8 @@ def test_adjoint_and_batch_entry_points_reject_null_arguments(lib):
     lib.hysco_batch_destroy(None)
     assert lib.hysco_pcg_plan(None, (C.c_int32 * 4)()) == _lib.EINVAL
     assert lib.hysco_batch_set_schedule(None, 1, 0) == _lib.EINVAL
+    assert lib.hysco_block_pcg(None, f, f, f, 1.0, f, f, 10, 0.1, None, None) == _lib.EINVAL
+    assert lib.hysco_admm_zsolve(None, f, 1.0, f, None) == _lib.EINVAL
     assert lib.hysco_set_pcg_onchip(None, 0) == _lib.EINVAL
 
 

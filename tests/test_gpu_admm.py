@@ -162,3 +162,48 @@ def test_start_from_a_given_field(H, orc):
     assert status == 0
     assert st.cpu().numpy()[0, 2] == 50.0
     check(st.cpu().numpy(), rst, orc.ADMM_FIELDS, b.cpu().numpy(), rb, "init 0, rho0 50")
+
+
+@pytest.mark.parametrize("name,p", [("tiny", None), ("pe0", 0), ("pe2", 2)])
+def test_block_pcg_matches_oracle(H, orc, name, p):
+    """BlockPCG alone (hysco_block_pcg) against the oracle's per-column CG on the same
+    linearisation: q relative 1e-4 (single-precision CG through <= 10 iterations per column, as
+    for the global PCG step), iterations summed over columns within 1% (a column whose relative
+    residual sits at 0.1 may stop one iteration apart)."""
+    if p is None:
+        pr = ph.make_pair("tiny")
+        dims, spacing, pe, Ip, Im = pr.dims, pr.spacing, pr.pe_dim, pr.Ip, pr.Im
+    else:
+        dims, spacing, pe = ((9, 6, 11), (1.1, 1.0, 1.2), 0) if p == 0 else \
+            ((5, 4, 17), (0.9, 1.3, 1.0), 2)
+        Ip, Im = ph.random_images(dims, 801, 0.1, 1.0)
+    b = ph.random_field(dims, pe, 802, scale=1.2, smooth=1.0)
+    P = orc.Problem(dims, spacing, pe, ALPHA, BETA)
+    rng = np.random.default_rng(803)
+    rhs = rng.standard_normal(P.fdims).astype(np.float32)
+    rho = 40.0
+    h = H(dims, spacing, pe, ALPHA, BETA)
+    q, it = h.block_pcg(torch.from_numpy(Ip).cuda(), torch.from_numpy(Im).cuda(),
+                        torch.from_numpy(b).cuda(), rho, torch.from_numpy(rhs).cuda())
+    torch.cuda.synchronize()
+    qref, itref = P.block_pcg(Ip, Im, b.astype(np.float64), rho, rhs.astype(np.float64))
+    assert rel(q.cpu().numpy(), qref) <= 1e-4, rel(q.cpu().numpy(), qref)
+    assert abs(int(it.item()) - itref) <= 0.01 * itref, (int(it.item()), itref)
+
+
+@pytest.mark.parametrize("dims,spacing,p", [((32, 32, 16), (1.0, 1.0, 1.0), 1),
+                                            ((9, 6, 11), (1.1, 1.0, 1.2), 0),
+                                            ((5, 4, 17), (0.9, 1.3, 1.0), 2),
+                                            ((1, 7, 6), (1.0, 1.0, 1.0), 1)])
+def test_z_update_matches_the_oracles_fft(H, orc, dims, spacing, p):
+    """The z-update alone (hysco_admm_zsolve, real Fourier bases, single precision) against the
+    oracle's numpy 2D FFT inversion: relative 2e-5 (four transforms of length <= 32)."""
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    rng = np.random.default_rng(901)
+    v = rng.standard_normal(P.fdims).astype(np.float32)
+    rho = 7.5
+    h = H(dims, spacing, p, ALPHA, BETA)
+    z = h.admm_zsolve(torch.from_numpy(v).cuda(), rho)
+    torch.cuda.synchronize()
+    zref = P.admm_z_solve(rho * v.astype(np.float64), rho)
+    assert rel(z.cpu().numpy(), zref) <= 2e-5, rel(z.cpu().numpy(), zref)
