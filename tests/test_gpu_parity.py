@@ -27,6 +27,8 @@ SHAPES = [  # (dims, spacing, pe): ragged sizes, every PE axis, single columns
     ((1, 33, 1), (1.0, 1.0, 1.0), 1),
     ((40, 3, 37), (1.0, 1.5, 1.0), 1),
     ((2, 2, 2), (1.0, 1.0, 1.0), 0),
+    ((4, 2, 5), (1.0, 1.2, 0.9), 1),    # the shortest PE extent the handle accepts (m = 2)
+    ((3, 4, 2), (1.1, 1.0, 0.8), 2),    # PE innermost, m = 2: three nodes in a 4-wide pitch
 ]
 
 
@@ -131,7 +133,7 @@ def test_corrected_images_match_oracle(H, orc, dims, spacing, p):
     assert np.abs(host(Tm) - e["Tm"]).max() <= 1e-5 * np.abs(e["Tm"]).max()
 
 
-@pytest.mark.parametrize("dims,spacing,p", SHAPES[:5])
+@pytest.mark.parametrize("dims,spacing,p", SHAPES[:5] + SHAPES[6:])
 @pytest.mark.parametrize("blur", [False, True])
 def test_ot_init_matches_oracle(H, orc, dims, spacing, p, blur):
     pr_I = ph.random_images(dims, 500, -0.05, 1.0)
