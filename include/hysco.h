@@ -250,9 +250,10 @@ typedef struct {
 
 void hysco_default_admm_opts(hysco_admm_opts* opts);
 
-#define HYSCO_ADMM_NSTATS 10   /* per iteration: J(b), (unused, NaN), rho, r, s, relative
-                                  changes of b, z and u, BlockPCG iterations summed over columns
-                                  and GN steps, the last GN step's gamma */
+#define HYSCO_ADMM_NSTATS 10   /* per iteration: J(b), the b-subproblem's objective
+                                  F(b) + rho vol/2 ||b - z + u||^2 at the new b, rho, r, s,
+                                  relative changes of b, z and u, BlockPCG iterations summed over
+                                  columns and GN steps, the last GN step's gamma */
 
 /* Runs ADMM on the pair (images as in hysco_solve) from b_inout (or OT) and writes the final b
  * into b_inout.  stats: NULL or an admm_iters x HYSCO_ADMM_NSTATS device array of doubles (rows

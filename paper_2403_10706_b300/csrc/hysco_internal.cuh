@@ -83,6 +83,7 @@ struct DevState {
   int admm_iter;              // ADMM iterations completed
   int blk_iters;              // BlockPCG iterations summed over columns (this ADMM iteration)
   double prox;                // vol/2 ||b - c||^2 at the last evaluation with the prox term
+  double Jacc;                // the prox objective at the iterate the last b-update step kept
   double nb_prev, nz_prev, nu_prev;   // ||b||^2, ||z||^2, ||u||^2 at the iteration's start
 };
 

@@ -319,7 +319,7 @@ k_admm_post(Geo g, const float* __restrict__ b, const float* __restrict__ z,
     if (stats) {
       double* row = stats + (long long)it * kAdmmNStats;
       row[0] = st->J;                                          // J at b (evaluated before)
-      row[1] = __longlong_as_double(0x7ff8000000000000LL);     // F_c: not recorded here
+      row[1] = st->Jacc;                                       // F_c at the b-update's result
       row[2] = rho;
       row[3] = r;
       row[4] = s;

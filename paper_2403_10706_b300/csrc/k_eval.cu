@@ -52,6 +52,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     if (st->coef_fresh) {
       if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         st->J = st->Jn; st->D = st->Dn; st->S = st->Sn; st->P = st->Pn;
+        if (PROX) st->Jacc = st->Jn;
         st->gnorm = st->gnorm_n;
         st->status = st->status_n;
         st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
@@ -180,6 +181,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
     }
     if (!TRIAL) {
       st->J = J; st->D = D; st->S = S; st->P = P;
+      if (PROX) st->Jacc = J;
       st->gnorm = sqrt(tot[3]);
       st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
       st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
@@ -196,6 +198,7 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
         st->ls_trials = 1;
         if (J <= st->J + c1 * gq) {  // Armijo with gamma = 1
           st->ls_done = 1; st->gamma = 1.0;
+          if (PROX) st->Jacc = J;
           st->coef_fresh = 1;
           st->Jn = J; st->Dn = D; st->Sn = S; st->Pn = P;
           st->gnorm_n = sqrt(tot[3]);
@@ -296,7 +299,11 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
       double Jt = hv * tot[3 * t] + g.alpha_d * hv * tot[3 * t + 1] + g.beta_d * hv * tot[3 * t + 2];
       if (PROX) Jt += (double)st->admm_rho * hv * tot[3 * T + 1 + t];
       st->ls_trials = t0 + t + 1;
-      if (Jt <= J + c1 * gm * gq) { st->ls_done = 1; st->gamma = gm; return; }
+      if (Jt <= J + c1 * gm * gq) {
+        st->ls_done = 1; st->gamma = gm;
+        if (PROX) st->Jacc = Jt;
+        return;
+      }
     }
     if (t0 + T >= ls_max) { st->ls_done = 1; st->gamma = 0.0; }
   }

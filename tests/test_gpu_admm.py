@@ -3,7 +3,8 @@
 Every decision of a run is compared first: the rho sequence (the residual-balancing rule) and
 the stopping iteration must be identical, and the BlockPCG iteration counts (summed over
 columns) may differ only where a column's relative residual sits at the 0.1 threshold (within
-1%).  Values: J at every iterate relative 1e-4 and the final field relative 1e-3 in the 2-norm
+1%).  Values: J and the b-subproblem's objective at every iterate relative 1e-4 and the final
+field relative 1e-3 in the 2-norm
 (single-precision arithmetic through the same iterations, as for the GN solve); the residuals
 r, s and the relative changes, whose single-precision values are differences of nearby fields,
 relative 1e-2.
@@ -56,6 +57,7 @@ def check(gs, rs, fields, gb, rb, what):
     gs, rs = gs[done_g], rs[done_r]
     assert np.array_equal(gs[:, F["rho"]], rs[:, F["rho"]]), (what, gs[:, F["rho"]], rs[:, F["rho"]])
     np.testing.assert_allclose(gs[:, F["J"]], rs[:, F["J"]], rtol=1e-4, err_msg=what)
+    np.testing.assert_allclose(gs[:, F["F_c"]], rs[:, F["F_c"]], rtol=1e-4, err_msg=what)
     np.testing.assert_allclose(gs[:, F["block_pcg_iters"]], rs[:, F["block_pcg_iters"]],
                                rtol=1e-2, err_msg=what)
     for f in ("r_primal", "s_dual", "rel_db", "rel_dz"):
