@@ -31,7 +31,7 @@ from paper_2403_10706_b300 import phantom as ph  # noqa: E402
 
 METRIC = "corrected 3T-shaped volume pairs/sec (fixed GN iters); eval-kernel HBM GB/s vs peak"
 UNIT = "pairs/s"
-GN_ITERS = {"3t": 20, "7t": 20, "small": 20, "tiny": 10}
+GN_ITERS = {"3t": 20, "7t": 20, "small": 20, "tiny": 10, "7t_paper": 20}
 ALPHA, BETA = 300.0, 1e4
 
 
@@ -611,6 +611,22 @@ def run_ours(args):
     kernels["hysco_precond_column"] = table_row(
         time_launches(lambda: h.precond(vv, kind=_lib.PC_COLUMN, out=pc_out)), 16 * nfld,
         "k_to_pitched, k_col_factor, k_col_solve, k_from_pitched")
+    # the paper's 7T acquisition size (200 x 200 x 132, PE axis 0): a field of 5.3 M nodes, twice
+    # what the persistent PCG keeps on chip, so half its slots keep r, p, Hp in global memory
+    extra = None
+    if args.workload == "3t":
+        px = ph.make_pair("7t_paper")
+        hx = Hysco(px.dims, px.spacing, px.pe_dim, ALPHA, BETA, device=dev)
+        Ipx, Imx = torch.from_numpy(px.Ip).to(dev), torch.from_numpy(px.Im).to(dev)
+        bx = hx._new_fld()
+        x_ms = time_launches(lambda: hx.solve(Ipx, Imx, b=bx, gn_iters=20, init=True,
+                                              stats=False), n=5)
+        gridx, onx, slotsx, _ = hx.pcg_plan()
+        extra = {"7t_paper": {"dims": list(px.dims), "pe_dim": px.pe_dim, "gn_iters": 20,
+                              "ms_per_solve": x_ms, "pairs_per_s": 1e3 / x_ms,
+                              "status": hx.last_status(),
+                              "pcg_onchip_slots": [onx, slotsx]}}
+        del hx, Ipx, Imx, bx
     # ADMM (Sec. 2.3.2) on the same pair: OT + 20 iterations of 2 GN steps (BlockPCG directions)
     # each, against the GN solve's 20 iterations; the z-update's four per-plane products move
     # 2 * E * nB * nA * (nB + nA) flops each way (forward and inverse transform)
@@ -673,7 +689,8 @@ def run_ours(args):
                 "config": config(args, world), "status": status,
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roof, "eval_roofline": eval_roof, "adjoint": adjoint,
-                "ls_correct": ls, "admm": admm, "kernel_table": kernels, "work": work}
+                "ls_correct": ls, "admm": admm, "kernel_table": kernels, "work": work,
+                "extra_shapes": extra}
         if prec is not None:
             line["precision"] = prec
         if batch is not None:

@@ -37,6 +37,11 @@ RECIPES = {
     "small": dict(dims=(96, 96, 60), spacing=(1.5, 1.5, 1.5), pe_dim=1, seed=1004,
                   n_ellipsoids=12, n_blobs=8, semi_axes=None, smooth=1.0,
                   n_gauss=20, sigma=(5.0, 15.0), bmax=6.0, noise=0.02),
+    # the size of the paper's 7T acquisitions (an extra timing row; the 7T recipe above keeps the
+    # smaller shape of the parity and adjoint cases)
+    "7t_paper": dict(dims=(200, 200, 132), spacing=(1.05, 1.05, 1.05), pe_dim=0, seed=1005,
+                     n_ellipsoids=12, n_blobs=8, semi_axes=None, smooth=1.0,
+                     n_gauss=20, sigma=(10.0, 20.0), bmax=8.0, noise=0.02),
 }
 
 # the generator redraws b* (next seed) until its largest PE difference is at most this
