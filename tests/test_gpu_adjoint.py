@@ -89,6 +89,30 @@ def test_correct_adjoint_with_folding_field(H, orc, dims, spacing, p):
     check(host(db), rb, "db")
 
 
+@pytest.mark.parametrize("compress", [False, True])
+def test_correct_adjoint_long_columns(H, orc, compress):
+    """Columns of the 3T length (168 cells: eight segments of 21 per column and image) with a
+    smooth field, and with a stretch of PE slope -0.95 in some columns that squeezes ~20 cells of
+    the + image into one voxel (a voxel shared by three segments: those columns take the
+    single-thread path, the others the segmented one)."""
+    dims, spacing, p = (6, 168, 5), (1.25, 1.25, 1.25), 1
+    Ip, Im, b, gp, gm = case(dims, p, 650, bscale=3.0)
+    if compress:
+        b = b.copy()
+        for i0, i2 in ((1, 2), (4, 0), (5, 4)):
+            ramp = np.zeros(dims[p] + 1)
+            ramp[40:70] = -0.95
+            b[i0, :, i2] = np.cumsum(ramp) - np.cumsum(ramp).mean()
+        assert np.abs(np.diff(b, axis=p)).max() < 1.0
+    h = H(dims, spacing, p, ALPHA, BETA)
+    dIp, dIm, db = h.correct_adjoint(dev(Ip), dev(Im), dev(b), dev(gp), dev(gm))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    rp, rm, rb = P.correct_adjoint(Ip, Im, b, gp, gm, contract=True)
+    check(host(dIp), rp, "dIp")
+    check(host(dIm), rm, "dIm")
+    check(host(db), rb, "db")
+
+
 def test_correct_adjoint_optional_arguments(H, orc):
     dims, spacing, p = SHAPES[0]
     Ip, Im, b, gp, gm = case(dims, p, 700)
