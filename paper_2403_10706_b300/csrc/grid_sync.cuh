@@ -30,11 +30,17 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // first + l + 32, ... in turn, then a fixed shuffle tree), in double-float.  On return v holds
 // those totals, identical in every thread of every block that passed the same range.
 // Returns false in every thread of the block when the spin budget (clock cycles) ran out.
-template <int K>
-__device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
-                                               float* shf, df32* shd, int first = 0,
-                                               int count = -1,
-                                               long long budget = kBarrierSpinCycles) {
+// grid_allreduce_then runs `work()` in every thread after the block's arrival and before the
+// wait: block-local work that the barrier neither orders nor waits for (its writes are not
+// released to other blocks), overlapped with the barrier's latency.
+struct NoWork {
+  __device__ void operator()() const {}
+};
+template <int K, typename F>
+__device__ __forceinline__ bool grid_allreduce_then(float (&v)[K], unsigned* sync, unsigned gen,
+                                                    float* shf, df32* shd, F&& work,
+                                                    int first = 0, int count = -1,
+                                                    long long budget = kBarrierSpinCycles) {
   static_assert(K >= 1 && K <= kSyncMaxK, "grid_allreduce: K exceeds the slot width");
   const int tid = threadIdx.x, nb = gridDim.x;
   if (count < 0) count = nb;
@@ -46,6 +52,9 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
 #pragma unroll
     for (int i = 0; i < K; ++i) __stcg(slot + blockIdx.x * K + i, v[i]);
     red_release_add(counter, 1u);
+  }
+  work();
+  if (tid == 0) {
     const unsigned target = gen * (unsigned)nb;
     const long long t0 = clock64();
     int ok = 1;
@@ -87,6 +96,13 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
 #pragma unroll
   for (int i = 0; i < K; ++i) v[i] = shd[i].hi + shd[i].lo;
   return true;
+}
+template <int K>
+__device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
+                                               float* shf, df32* shd, int first = 0,
+                                               int count = -1,
+                                               long long budget = kBarrierSpinCycles) {
+  return grid_allreduce_then<K>(v, sync, gen, shf, shd, NoWork{}, first, count, budget);
 }
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {

@@ -116,16 +116,16 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
   bool done = !(rr0 > 0.f);
   int it = 0;
-  // x += alpha p of iteration i is applied in phase A of iteration i + 1 (from p before its
-  // update), or by the pass after the loop: phase B then writes z alone, so the ordered barrier
-  // after it waits for fewer outstanding stores.  Same operations on every x element.
-  float al_x = 0.f;   // alpha whose x update is pending (0: none)
+  // x += alpha p runs inside the barrier after phase B, between the block's arrival and its wait
+  // (x is read and written only at the thread's own groups, so the barrier need not order it):
+  // its traffic overlaps the barrier's latency, and phase B's release waits for the z stores
+  // alone.
   float4* const x4 = reinterpret_cast<float4*>(a.x);
 
   for (int i = 0; i < a.max_it && !done; ++i) {
     const bool first = i == 0;
     const float fb = beta;
-    // ---- A: x += alpha_{i-1} p; w = H z; p = z + beta p; Hp = w + beta Hp -----------------
+    // ---- A: w = H z; p = z + beta p; Hp = w + beta Hp ----------------------------------------
     float acc = 0.f;
     for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
       const bool on = sl < G;
@@ -133,23 +133,18 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       if (!first) {
         po = on ? pS[sl * kPcgBlock] : p4[t];
         ho = on ? hS[sl * kPcgBlock] : h4[t];
-        float4 X = i == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
-        X.x = fmaf(al_x, po.x, X.x); X.y = fmaf(al_x, po.y, X.y);
-        X.z = fmaf(al_x, po.z, X.z); X.w = fmaf(al_x, po.w, X.w);
-        x4[t] = X;
       }
       acc += hv_core<P, true>(g, t, a.z, a.dco, a.eco, fb, first, po, ho, pn, hn);
       if (on) { pS[sl * kPcgBlock] = pn; hS[sl * kPcgBlock] = hn; }
       else { p4[t] = pn; h4[t] = hn; }
     }
-    al_x = 0.f;
+    float al;
     {
       // only p.Hp crosses blocks here (phase B reads the thread's own groups)
       float t1[1] = {acc};
       if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd)) { timed_out(); return; }
       if (!(t1[0] > 0.f)) { done = true; break; }
-      const float al = rho / t1[0];
-      al_x = al;
+      al = rho / t1[0];
       // ---- B: r -= alpha Hp, z = r / diag --------------------------------------------------
       float arr = 0.f, arz = 0.f;
       for (int j0 = gtid, s0 = 0; j0 < n4; j0 += kPcgUnroll * T, s0 += kPcgUnroll) {
@@ -182,7 +177,17 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       }
       tot[0] = arr; tot[1] = arz;
     }
-    if (!grid_allreduce<2>(tot, a.sync, ++gen, shf, shd)) { timed_out(); return; }
+    // x += alpha p (x = 0 before the first update) while the barrier completes
+    auto x_update = [&]() {
+      for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
+        const float4 pv = sl < G ? pS[sl * kPcgBlock] : p4[t];
+        float4 X = first ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
+        X.x = fmaf(al, pv.x, X.x); X.y = fmaf(al, pv.y, X.y);
+        X.z = fmaf(al, pv.z, X.z); X.w = fmaf(al, pv.w, X.w);
+        x4[t] = X;
+      }
+    };
+    if (!grid_allreduce_then<2>(tot, a.sync, ++gen, shf, shd, x_update)) { timed_out(); return; }
     it = i + 1;
     relres = sqrtf(tot[0]) / sqrtf(rr0);
     if (relres < (float)a.rtol) {
@@ -190,16 +195,6 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     } else {
       beta = tot[1] / rho;
       rho = tot[1];
-    }
-  }
-  // the last iteration's x += alpha p (each thread its own groups: no barrier needed)
-  if (al_x != 0.f) {
-    for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
-      const float4 pv = sl < G ? pS[sl * kPcgBlock] : p4[t];
-      float4 X = it == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
-      X.x = fmaf(al_x, pv.x, X.x); X.y = fmaf(al_x, pv.y, X.y);
-      X.z = fmaf(al_x, pv.z, X.z); X.w = fmaf(al_x, pv.w, X.w);
-      x4[t] = X;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
