@@ -116,10 +116,12 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
   bool done = !(rr0 > 0.f);
   int it = 0;
-  // x += alpha p runs inside the barrier after phase B, between the block's arrival and its wait
-  // (x is read and written only at the thread's own groups, so the barrier need not order it):
-  // its traffic overlaps the barrier's latency, and phase B's release waits for the z stores
-  // alone.
+  // x += alpha p.  x is read and written only at the thread's own groups, so no barrier orders
+  // it.  On-chip slots: inside the barrier after phase B, between the block's arrival and its
+  // wait, where its traffic overlaps the barrier's latency.  Slots in global memory: in phase A
+  // of the next iteration, where p is read anyway (x += alpha_{i-1} p_{i-1} before p's update),
+  // or by the pass after the loop.  Same operations on every x element either way.
+  float al_x = 0.f;   // alpha whose update of the global-memory slots is pending (0: none)
   float4* const x4 = reinterpret_cast<float4*>(a.x);
 
   for (int i = 0; i < a.max_it && !done; ++i) {
@@ -133,11 +135,18 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       if (!first) {
         po = on ? pS[sl * kPcgBlock] : p4[t];
         ho = on ? hS[sl * kPcgBlock] : h4[t];
+        if (!on) {
+          float4 X = i == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
+          X.x = fmaf(al_x, po.x, X.x); X.y = fmaf(al_x, po.y, X.y);
+          X.z = fmaf(al_x, po.z, X.z); X.w = fmaf(al_x, po.w, X.w);
+          x4[t] = X;
+        }
       }
       acc += hv_core<P, true>(g, t, a.z, a.dco, a.eco, fb, first, po, ho, pn, hn);
       if (on) { pS[sl * kPcgBlock] = pn; hS[sl * kPcgBlock] = hn; }
       else { p4[t] = pn; h4[t] = hn; }
     }
+    al_x = 0.f;
     float al;
     {
       // only p.Hp crosses blocks here (phase B reads the thread's own groups)
@@ -145,6 +154,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd)) { timed_out(); return; }
       if (!(t1[0] > 0.f)) { done = true; break; }
       al = rho / t1[0];
+      al_x = al;
       // ---- B: r -= alpha Hp, z = r / diag --------------------------------------------------
       float arr = 0.f, arz = 0.f;
       for (int j0 = gtid, s0 = 0; j0 < n4; j0 += kPcgUnroll * T, s0 += kPcgUnroll) {
@@ -177,14 +187,27 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       }
       tot[0] = arr; tot[1] = arz;
     }
-    // x += alpha p (x = 0 before the first update) while the barrier completes
+    // on-chip slots: x += alpha p (x = 0 before the first update) while the barrier completes,
+    // kPcgUnroll groups' loads in flight at a time so that it fits in the barrier's latency
     auto x_update = [&]() {
-      for (int t = gtid, sl = 0; t < n4; t += T, ++sl) {
-        const float4 pv = sl < G ? pS[sl * kPcgBlock] : p4[t];
-        float4 X = first ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
-        X.x = fmaf(al, pv.x, X.x); X.y = fmaf(al, pv.y, X.y);
-        X.z = fmaf(al, pv.z, X.z); X.w = fmaf(al, pv.w, X.w);
-        x4[t] = X;
+      for (int j0 = gtid, s0 = 0; j0 < n4 && s0 < G; j0 += kPcgUnroll * T, s0 += kPcgUnroll) {
+        float4 pv[kPcgUnroll], xv[kPcgUnroll];
+#pragma unroll
+        for (int u = 0; u < kPcgUnroll; ++u) {
+          // slots past the range or off chip re-read this thread's own group j0 (slot s0 < G)
+          const bool in = j0 + u * T < n4 && s0 + u < G;
+          const int j = in ? j0 + u * T : j0, sl = in ? s0 + u : s0;
+          pv[u] = pS[sl * kPcgBlock];
+          xv[u] = first ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[j];
+        }
+#pragma unroll
+        for (int u = 0; u < kPcgUnroll; ++u) {
+          const int j = j0 + u * T;
+          float4 X = xv[u];
+          X.x = fmaf(al, pv[u].x, X.x); X.y = fmaf(al, pv[u].y, X.y);
+          X.z = fmaf(al, pv[u].z, X.z); X.w = fmaf(al, pv[u].w, X.w);
+          if (j < n4 && s0 + u < G) x4[j] = X;
+        }
       }
     };
     if (!grid_allreduce_then<2>(tot, a.sync, ++gen, shf, shd, x_update)) { timed_out(); return; }
@@ -195,6 +218,16 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     } else {
       beta = tot[1] / rho;
       rho = tot[1];
+    }
+  }
+  // the last iteration's update of the global-memory slots
+  if (al_x != 0.f) {
+    for (int t = gtid + G * T, sl = G; t < n4; t += T, ++sl) {
+      const float4 pv = p4[t];
+      float4 X = it == 1 ? make_float4(0.f, 0.f, 0.f, 0.f) : x4[t];
+      X.x = fmaf(al_x, pv.x, X.x); X.y = fmaf(al_x, pv.y, X.y);
+      X.z = fmaf(al_x, pv.z, X.z); X.w = fmaf(al_x, pv.w, X.w);
+      x4[t] = X;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
