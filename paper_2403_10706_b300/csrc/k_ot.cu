@@ -137,6 +137,8 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
   bool act = c < g.ncols;
   float s = (float)st->ot_shift;
   int ib = act ? col_base(c, g.inner, g.img_ostride) : 0;
+  // four rows' loads in flight per thread
+#pragma unroll 4
   for (int k = ty; k < m; k += blockDim.y) {
     float a = 0.f, b = 0.f;
     if (act) {
@@ -203,17 +205,30 @@ k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, f
       int a = min(max(cA + da, 0), g.nA - 1), bb = min(max(cB + db, 0), g.nB - 1);
       base[db + 1][da + 1] = col_base(bb * g.nA + a, g.inner, g.fld_ostride);
     }
+  // rolling window along the column: win[db][da][dk] holds the neighbour column's value at
+  // node clamp(k - 1 + dk), so each node loads the nine values at k + 1 only (same sums)
+  float win[3][3][3];
+#pragma unroll
+  for (int db = 0; db < 3; ++db)
+#pragma unroll
+    for (int da = 0; da < 3; ++da) {
+      win[db][da][1] = __ldg(in + base[db][da] + max(k0 - 1, 0) * g.inner);
+      win[db][da][2] = __ldg(in + base[db][da] + k0 * g.inner);
+    }
   for (int k = k0; k < k1; ++k) {
-    int kk[3] = {max(k - 1, 0), k, min(k + 1, g.E - 1)};
+    const int kn = min(k + 1, g.E - 1);
     float acc = 0.f;
 #pragma unroll
     for (int db = 0; db < 3; ++db) {
       float accb = 0.f;
 #pragma unroll
       for (int da = 0; da < 3; ++da) {
+        win[db][da][0] = win[db][da][1];
+        win[db][da][1] = win[db][da][2];
+        win[db][da][2] = __ldg(in + base[db][da] + kn * g.inner);
         float acca = 0.f;
 #pragma unroll
-        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * __ldg(in + base[db][da] + kk[dk] * g.inner);
+        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * win[db][da][dk];
         accb += wt[da] * acca;
       }
       acc += wt[db] * accb;
