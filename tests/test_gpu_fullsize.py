@@ -7,7 +7,9 @@ same seeded phantom.  Same tolerances as the small-size parity tests:
     within 2e-4 of the largest magnitude; OT field: 2e-4 voxel;
   - one PCG solve of a GN step: relative 1e-4 (ten single-precision iterations);
   - two GN iterations from the OT start: the same accepted steps and PCG iteration counts,
-    J within 1e-4, field relative 1e-3.
+    J within 1e-4, field relative 1e-3;
+  - a property that holds at any size: reversing the phase-encoding direction (Eq. 1) negates
+    the OT field exactly and the gradient and the 20-iteration solve within those tolerances.
 """
 import numpy as np
 import pytest
@@ -112,3 +114,26 @@ def test_3t_two_gn_iterations_match_oracle(H, orc, pair):
     assert np.array_equal(gs[:, 7], rst[:, 7]), (gs[:, 7], rst[:, 7])        # PCG iterations
     assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4), (gs[:, 0], rst[:, 0])
     assert rel(host(b), ref) <= 1e-3, rel(host(b), ref)
+
+
+def test_3t_polarity_swap_symmetry(H, pair):
+    """Reversing the phase-encoding direction (swapping the images, negating the field) maps T+ to
+    T- and back (Eq. 1): J and its terms are unchanged, the gradient and the solved field change
+    sign.  The OT field is exactly antisymmetric (its operations only exchange operands); the
+    objective holds the symmetry up to single-precision rounding, because fused multiply-adds
+    round the two images' products in the other order on the swapped pair, so the tolerances are
+    the parity ones: terms 1e-5, gradient 1e-5 / 2e-4, the 20-iteration solve 1e-3 with the
+    objective history 1e-4 and the same accepted steps and PCG iteration counts."""
+    h = H(pair.dims, pair.spacing, pair.pe_dim, ALPHA, BETA)
+    Ip, Im = dev(pair.Ip), dev(pair.Im)
+    b0 = host(h.init_ot(Ip, Im))
+    assert np.array_equal(host(h.init_ot(Im, Ip)), -b0)
+    t1, g1 = (host(x).copy() for x in h.eval(Ip, Im, dev(b0)))
+    t2, g2 = (host(x).copy() for x in h.eval(Im, Ip, dev(-b0)))
+    assert np.all(np.abs(t2 - t1) <= 1e-5 * np.abs(t1)), (t1, t2)
+    check_field(-g2, g1, "swapped gradient")
+    b1, st1 = (host(x).copy() for x in h.solve(Ip, Im, gn_iters=20))
+    b2, st2 = (host(x).copy() for x in h.solve(Im, Ip, gn_iters=20))
+    assert np.array_equal(st2[:, 6], st1[:, 6]) and np.array_equal(st2[:, 7], st1[:, 7])
+    assert np.allclose(st2[:, 0], st1[:, 0], rtol=1e-4), (st1[:, 0], st2[:, 0])
+    assert rel(-b2, b1) <= 1e-3, rel(-b2, b1)

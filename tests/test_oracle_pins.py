@@ -24,6 +24,37 @@ def smooth_case(dims, p, seed, bscale=1.5):
 
 
 # --------------------------------------------------------------------------------------------
+# reversing the phase-encoding direction (Eq. 1): the two acquisitions trade places
+# --------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [0, 1, 2])
+def test_polarity_swap_symmetry(orc, p):
+    """Swapping the two images and negating the field maps T+ to T- and back (Eq. 1): the
+    residual changes sign, the smoothness and barrier terms are even in b, so J, D, S, P are
+    unchanged, the gradient changes sign and the Gauss-Newton Hessian is unchanged.  A wrong sign
+    of b or of the modulation in either image's term breaks this."""
+    dims = (5, 9, 6)
+    P = problem(orc, dims, (1.0, 1.25, 0.8), p)
+    Ip, Im, b = smooth_case(dims, p, 40)
+    v = np.random.default_rng(41).normal(size=b.shape)
+    for contract in (True, False):
+        e1 = P.eval(Ip, Im, b, contract=contract)
+        e2 = P.eval(Im, Ip, -b, contract=contract)
+        for k in "JDSP":
+            assert abs(e2[k] - e1[k]) <= 1e-13 * abs(e1[k]), (k, contract)
+        assert np.abs(e2["grad"] + e1["grad"]).max() <= 1e-13 * np.abs(e1["grad"]).max()
+        h1 = P.hessvec(Ip, Im, b, v, contract=contract)
+        h2 = P.hessvec(Im, Ip, -b, v, contract=contract)
+        assert np.abs(h2 - h1).max() <= 1e-13 * np.abs(h1).max()
+    # the whole GN solve from the OT start: the swapped pair's field is the negated field
+    b1, s1, st1 = P.solve(Ip, Im, gn_iters=3)
+    b2, s2, st2 = P.solve(Im, Ip, gn_iters=3)
+    assert s1 == 0 and s2 == 0
+    assert np.abs(b2 + b1).max() <= 1e-12 * np.abs(b1).max()
+    assert np.allclose(st2[:, 0], st1[:, 0], rtol=1e-12)
+
+
+# --------------------------------------------------------------------------------------------
 # the barrier function (Eq. 3)
 # --------------------------------------------------------------------------------------------
 
