@@ -29,8 +29,17 @@ def build(force: bool = False) -> str:
     """Compile the oracle with plain gcc (IEEE semantics: no fast-math, no FP contraction)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
+                               "-fopenmp", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"])
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops (the results do not depend on it)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
 
 
 class Geom(C.Structure):
@@ -64,6 +73,8 @@ def lib():
         _lib.orc_ot_init.argtypes = [P, P, P, C.c_double, C.c_int, C.c_int, P, P, P]
         _lib.orc_blur.argtypes = [P, P]
         _lib.orc_solve.argtypes = [P, P, P, P, P, P]
+        _lib.orc_set_threads.argtypes = [C.c_int]
+        _lib.orc_max_threads.restype = C.c_int
         _lib.orc_pcg.argtypes = [P, P, P, P, C.c_int, C.c_int, P, C.c_int, C.c_double, P, P]
         _lib.orc_phi.argtypes = [C.c_double, P, P, P]
         _lib.orc_correct_adjoint.argtypes = [P, P, P, P, C.c_int, P, P, P, P, P]

@@ -7,6 +7,10 @@
  * CPU-baseline leg may load this library.  It shares no code, header, table or constant with
  * the CUDA library and never calls it.  Every loop below is one formula of the paper, written
  * for a reader who checks it against the paper by eye: no blocking, no fusion, no reordering.
+ * Loops over columns, nodes and cells run on OpenMP threads where each iteration writes its own
+ * elements; every sum has a fixed order (a sum over cells is a sum of per-column sums taken in
+ * column order, an inner product a sum of fixed 4096-term chunks taken in chunk order), so the
+ * number of threads never changes a result.
  *
  * Notation (Sec. 2.1: Eq. 1 transform model, Eq. 2 distance, Eq. 3 barrier, Eq. 5 smoothness,
  * and the discretisation paragraph between them):
@@ -43,6 +47,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int64_t d[3];    /* image dims, C order */
@@ -74,6 +81,22 @@ enum { ST_J, ST_D, ST_S, ST_P, ST_GNORM, ST_GQ, ST_GAMMA, ST_PCG_IT, ST_PCG_RELR
 /* ------------------------------------------------------------------------------------------ */
 /* geometry helpers                                                                            */
 /* ------------------------------------------------------------------------------------------ */
+
+/* Threads of the OpenMP loops (columns, nodes, fixed chunks): results do not depend on it. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 static int64_t img_count(const orc_geom* g) { return g->d[0] * g->d[1] * g->d[2]; }
 static int64_t fld_dim(const orc_geom* g, int ax) { return ax == g->p ? g->d[ax] + 1 : g->d[ax]; }
@@ -171,6 +194,7 @@ static void interp1(const float* col, int64_t st, int64_t m, double t,
 void orc_laplacian(const orc_geom* g, const double* x, double* y) {
   int64_t n[3] = {fld_dim(g, 0), fld_dim(g, 1), fld_dim(g, 2)};
   int64_t s[3]; fld_strides(g, s);
+#pragma omp parallel for schedule(static)
   for (int64_t i0 = 0; i0 < n[0]; ++i0)
     for (int64_t i1 = 0; i1 < n[1]; ++i1)
       for (int64_t i2 = 0; i2 < n[2]; ++i2) {
@@ -190,6 +214,7 @@ void orc_laplacian(const orc_geom* g, const double* x, double* y) {
 static void laplacian_diag(const orc_geom* g, double* y) {
   int64_t n[3] = {fld_dim(g, 0), fld_dim(g, 1), fld_dim(g, 2)};
   int64_t s[3]; fld_strides(g, s);
+#pragma omp parallel for schedule(static)
   for (int64_t i0 = 0; i0 < n[0]; ++i0)
     for (int64_t i1 = 0; i1 < n[1]; ++i1)
       for (int64_t i2 = 0; i2 < n[2]; ++i2) {
@@ -203,9 +228,22 @@ static void laplacian_diag(const orc_geom* g, double* y) {
       }
 }
 
+/* Inner product as sums of fixed chunks of ORC_CHUNK terms, added in chunk order: the order of
+ * every addition is fixed, whatever the number of threads. */
+#define ORC_CHUNK 4096
 static double dot(const double* a, const double* b, int64_t n) {
+  int64_t nch = (n + ORC_CHUNK - 1) / ORC_CHUNK;
+  double* part = malloc((nch > 0 ? nch : 1) * sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nch; ++c) {
+    double s = 0.0;
+    int64_t end = (c + 1) * ORC_CHUNK < n ? (c + 1) * ORC_CHUNK : n;
+    for (int64_t i = c * ORC_CHUNK; i < end; ++i) s += a[i] * b[i];
+    part[c] = s;
+  }
   double s = 0.0;
-  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  for (int64_t c = 0; c < nch; ++c) s += part[c];
+  free(part);
   return s;
 }
 
@@ -231,10 +269,14 @@ static int64_t residual_pass(const orc_geom* g, const float* Ip, const float* Im
   int64_t sti = si[g->p], stf = sf[g->p];
   int64_t ncols = column_count(g);
   int64_t bad = 0;
-  double dsum = 0.0, psum = 0.0;
+  /* per-column sums, added in column order below */
+  double* dcol = malloc(ncols * sizeof(double));
+  double* pcol = malloc(ncols * sizeof(double));
+#pragma omp parallel for schedule(static) reduction(+ : bad)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
+    double dsum = 0.0, psum = 0.0;
     for (int64_t j = 0; j < m; ++j) {
       double bj = b[of + j * stf], bj1 = b[of + (j + 1) * stf];
       double tp, tm, delta;
@@ -266,7 +308,15 @@ static int64_t residual_pass(const orc_geom* g, const float* Ip, const float* Im
       if (cell_p) cell_p[cidx] = (int32_t)ip;
       if (cell_m) cell_m[cidx] = (int32_t)im;
     }
+    dcol[col] = dsum;
+    pcol[col] = psum;
   }
+  double dsum = 0.0, psum = 0.0;
+  for (int64_t col = 0; col < ncols; ++col) {
+    dsum += dcol[col];
+    psum += pcol[col];
+  }
+  free(dcol); free(pcol);
   double vol = cell_volume(g);
   *Dsum = 0.5 * vol * dsum;
   *Psum = 0.5 * vol * psum;
@@ -284,6 +334,7 @@ static void jr_transpose_add(const orc_geom* g, const orc_lin* lin, const double
   int64_t m = g->d[g->p];
   int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
   int64_t ncols = column_count(g);
+#pragma omp parallel for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -300,6 +351,7 @@ static void jr_apply(const orc_geom* g, const orc_lin* lin, const double* v, dou
   int64_t m = g->d[g->p];
   int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
   int64_t ncols = column_count(g);
+#pragma omp parallel for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -315,6 +367,7 @@ static void fd_apply(const orc_geom* g, const double* v, double* u) {
   int64_t m = g->d[g->p];
   int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
   int64_t ncols = column_count(g);
+#pragma omp parallel for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -328,6 +381,7 @@ static void fd_transpose_add(const orc_geom* g, const double* s, double* y) {
   int64_t m = g->d[g->p];
   int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
   int64_t ncols = column_count(g);
+#pragma omp parallel for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -361,6 +415,7 @@ static void gradient_from_lin(const orc_geom* g, const orc_lin* lin, const doubl
   orc_laplacian(g, b, Lb);
   jr_transpose_add(g, lin, lin->r, t);
   fd_transpose_add(g, lin->dphi, u);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < nf; ++k)
     grad[k] = vol * (t[k] + g->alpha * hp * hp * Lb[k] + 0.5 * g->beta * u[k]);
   free(Lb); free(t); free(u);
@@ -379,9 +434,11 @@ static void hessvec_from_lin(const orc_geom* g, const orc_lin* lin, const double
   jr_apply(g, lin, v, Jv);
   jr_transpose_add(g, lin, Jv, t);
   fd_apply(g, v, Dv);
+#pragma omp parallel for schedule(static)
   for (int64_t c = 0; c < nc; ++c) Dv[c] *= lin->d2phi[c];
   fd_transpose_add(g, Dv, u);
   orc_laplacian(g, v, Lv);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < nf; ++k)
     Hv[k] = vol * (t[k] + g->alpha * hp * hp * Lv[k] + 0.5 * g->beta * u[k]);
   free(Jv); free(Dv); free(Lv); free(t); free(u);
@@ -396,6 +453,7 @@ static void hessdiag_from_lin(const orc_geom* g, const orc_lin* lin, double* dia
   double* pp = calloc(nf, sizeof(double));   /* sum_j D_{jk}^2 phi''_j */
   double* Ld = malloc(nf * sizeof(double));
   int64_t ncols = column_count(g);
+#pragma omp parallel for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -409,6 +467,7 @@ static void hessdiag_from_lin(const orc_geom* g, const orc_lin* lin, double* dia
     }
   }
   laplacian_diag(g, Ld);
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < nf; ++k)
     diag[k] = vol * (jj[k] + g->alpha * hp * hp * Ld[k] + 0.5 * g->beta * pp[k]);
   free(jj); free(pp); free(Ld);
@@ -759,6 +818,7 @@ static void blur_axis(const orc_geom* g, int ax, const double* x, double* y) {
   int64_t n[3] = {fld_dim(g, 0), fld_dim(g, 1), fld_dim(g, 2)};
   int64_t s[3]; fld_strides(g, s);
   double w = exp(-0.5), norm = 1.0 + 2.0 * w;
+#pragma omp parallel for schedule(static)
   for (int64_t i0 = 0; i0 < n[0]; ++i0)
     for (int64_t i1 = 0; i1 < n[1]; ++i1)
       for (int64_t i2 = 0; i2 < n[2]; ++i2) {
@@ -792,9 +852,12 @@ void orc_ot_init(const orc_geom* g, const float* Ip, const float* Im, double eps
   int64_t m = g->d[g->p];
   int64_t si[3], sf[3]; img_strides(g, si); fld_strides(g, sf);
   double shift = ot_shift(Ip, Im, img_count(g), eps, contract);
+  int64_t ncols = column_count(g);
+#pragma omp parallel
+  {
   double* Cp = malloc((m + 1) * sizeof(double));
   double* Cm = malloc((m + 1) * sizeof(double));
-  int64_t ncols = column_count(g);
+#pragma omp for schedule(static)
   for (int64_t col = 0; col < ncols; ++col) {
     int64_t oi, of, c0, c1;
     column_offsets(g, col, &oi, &of, &c0, &c1);
@@ -817,6 +880,7 @@ void orc_ot_init(const orc_geom* g, const float* Ip, const float* Im, double eps
     }
   }
   free(Cp); free(Cm);
+  }
   if (blur) orc_blur(g, b0);
 }
 
@@ -833,6 +897,7 @@ static int pcg(const orc_geom* g, const orc_lin* lin, const double* diag, int pr
   double* z = malloc(n * sizeof(double));
   double* p = malloc(n * sizeof(double));
   double* Hp = malloc(n * sizeof(double));
+#pragma omp parallel for schedule(static)
   for (int64_t k = 0; k < n; ++k) { q[k] = 0.0; r[k] = rhs[k]; }
   double rr0 = dot(r, r, n);
   int it = 0;
@@ -840,6 +905,7 @@ static int pcg(const orc_geom* g, const orc_lin* lin, const double* diag, int pr
   if (rr0 > 0.0) {
     if (precond == 0) jacobi_precond(n, diag, r, z);
     else column_precond_from_lin(g, lin, r, z);
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < n; ++k) p[k] = z[k];
     double rho = dot(r, z, n);
     for (int i = 0; i < max_it; ++i) {
@@ -847,6 +913,7 @@ static int pcg(const orc_geom* g, const orc_lin* lin, const double* diag, int pr
       double pHp = dot(p, Hp, n);
       if (!(pHp > 0.0)) break;
       double a = rho / pHp;
+#pragma omp parallel for schedule(static)
       for (int64_t k = 0; k < n; ++k) { q[k] += a * p[k]; r[k] -= a * Hp[k]; }
       it = i + 1;
       double rr = dot(r, r, n);
@@ -857,6 +924,7 @@ static int pcg(const orc_geom* g, const orc_lin* lin, const double* diag, int pr
       double rho_new = dot(r, z, n);
       double beta = rho_new / rho;
       rho = rho_new;
+#pragma omp parallel for schedule(static)
       for (int64_t k = 0; k < n; ++k) p[k] = z[k] + beta * p[k];
     }
   }
@@ -930,6 +998,7 @@ int orc_solve(const orc_geom* g, const float* Ip, const float* Im, const orc_opt
     if (!isfinite(J)) { status = isnan(J) ? 2 : 1; break; }
     gradient_from_lin(g, &lin, b, grad);
     if (o->precond == 0) hessdiag_from_lin(g, &lin, diag);
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < nf; ++k) rhs[k] = -grad[k];
     double relres;
     int pit = pcg(g, &lin, diag, o->precond, rhs, o->pcg_max_iters, o->pcg_rtol, q, &relres);
@@ -940,13 +1009,17 @@ int orc_solve(const orc_geom* g, const float* Ip, const float* Im, const orc_opt
       double step = 1.0;
       for (int t = 0; t < o->ls_max_iters; ++t) {
         ++trials;
+#pragma omp parallel for schedule(static)
         for (int64_t k = 0; k < nf; ++k) bt[k] = b[k] + step * q[k];
         double Jt = objective_only(g, Ip, Im, bt, o->contract, Lb);
         if (Jt <= J + o->armijo_c1 * step * gq) { gamma = step; break; }
         step *= 0.5;
       }
     }
-    if (gamma > 0.0) for (int64_t k = 0; k < nf; ++k) b[k] += gamma * q[k];
+    if (gamma > 0.0) {
+#pragma omp parallel for schedule(static)
+      for (int64_t k = 0; k < nf; ++k) b[k] += gamma * q[k];
+    }
     if (st) {
       st[ST_GNORM] = sqrt(dot(grad, grad, nf));
       st[ST_GQ] = gq;
