@@ -1,15 +1,22 @@
-"""Builds libhysco.so in-tree with nvcc for sm_103a (B300)."""
+"""Builds libhysco.so in-tree with nvcc for sm_103a (B300).
+
+Each translation unit compiles to an object under `_build/` in parallel (they share no device
+code: no relocatable device code is needed), then one nvcc call links the shared library.
+"""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhysco.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
 
 def sources():
@@ -21,6 +28,10 @@ def headers():
         os.path.join(os.path.dirname(HERE), "include", "hysco.h")]
 
 
+def _obj(src):
+    return os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
+
+
 def stale() -> bool:
     if not os.path.exists(LIB):
         return True
@@ -28,16 +39,37 @@ def stale() -> bool:
     return any(os.path.getmtime(f) > t for f in sources() + headers())
 
 
+def _compile(src, nvcc, verbose, hdr_time):
+    obj = _obj(src)
+    if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_time):
+        return obj, ""
+    cmd = [nvcc, *ARCH, *FLAGS, "-c", "-o", obj, src]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stdout}{r.stderr}")
+    return obj, r.stdout + r.stderr
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-Xlinker", "--no-undefined",
-           "-o", LIB, *sources()]
+    os.makedirs(OBJ, exist_ok=True)
+    hdr_time = 0.0 if force else max(os.path.getmtime(h) for h in headers())
+    if force:
+        for s in sources():
+            if os.path.exists(_obj(s)):
+                os.remove(_obj(s))
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 4)) as ex:
+        results = list(ex.map(lambda s: _compile(s, nvcc, verbose, hdr_time), sources()))
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        for _, log in results:
+            if log:
+                print(log, end="")
+    objs = [o for o, _ in results]
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", LIB, *objs])
     return LIB
 
 
