@@ -6,9 +6,12 @@
 // the process exits.
 //
 // Host code must not pass the array's name to a kernel: on the host that name is a stand-in, not
-// a device address.  The first call on each device, with that device current, looks up the
-// array's device address with cudaGetSymbolAddress and remembers it for that device; every call
-// then passes that address to the kernel.
+// a device address.  The first call in each CUDA context (the device's primary context, with that
+// device current) looks up the array's device address with cudaGetSymbolAddress and remembers it
+// under the context's unique id; every call then passes that address to the kernel.  A context
+// that is destroyed and re-created (cudaDeviceReset) gets a new id, and so a fresh lookup.
+#include <cuda.h>
+
 #include <cmath>
 #include <mutex>
 
@@ -18,32 +21,70 @@
 namespace hysco {
 namespace {
 
-constexpr int kStaticMaxBlocks = 32768;   // largest reduction grid served (512 KiB of partials)
-constexpr int kStaticTerms = 4;           // D, S, P and sum of squared gradient entries
+constexpr int kStaticMaxBlocks = 32768;   // largest reduction grid served (384 KiB of partials)
+constexpr int kStaticTerms = 3;           // D, S and P
 constexpr size_t kCounterBytes = 256;     // ticket counter, padded to keep the partials aligned
 constexpr size_t kStaticScratchBytes =
     kCounterBytes + sizeof(float) * (size_t)kStaticMaxBlocks * kStaticTerms;
 
 static __device__ __align__(256) unsigned char g_eval_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
+constexpr int kMaxContexts = 64;
+struct ScratchEntry {
+  unsigned long long ctx_id;
+  void* addr;
+};
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+ScratchEntry g_scratch[kMaxContexts] = {};
+int g_nscratch = 0;
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrent g_ctx_current = nullptr;
+CtxGetId g_ctx_id = nullptr;
 
-// device address of g_eval_scratch on the current device (looked up once per device)
+// unique id of the calling thread's current context (the driver entry points are looked up once)
+cudaError_t current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* f0 = nullptr;
+    void* f1 = nullptr;
+    cudaDriverEntryPointQueryResult q0, q1;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) !=
+            cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) !=
+            cudaSuccess ||
+        q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess)
+      return cudaErrorNotSupported;
+    g_ctx_current = reinterpret_cast<CtxGetCurrent>(f0);
+    g_ctx_id = reinterpret_cast<CtxGetId>(f1);
+  }
+  CUcontext ctx = nullptr;
+  if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  return g_ctx_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// device address of g_eval_scratch in the current context (looked up once per context)
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  e = cudaSetDevice(dev);   // makes the device's primary context current, initialised
+  if (e != cudaSuccess) return e;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_eval_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  unsigned long long id = 0;
+  e = current_context_id(&id);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < g_nscratch; ++i)
+    if (g_scratch[i].ctx_id == id) {
+      *out = g_scratch[i].addr;
+      return cudaSuccess;
+    }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_eval_scratch);
+  if (e != cudaSuccess) return e;
+  ScratchEntry ent{id, p};
+  if (g_nscratch < kMaxContexts) g_scratch[g_nscratch++] = ent;
+  else g_scratch[id % kMaxContexts] = ent;   // many re-created contexts: reuse a slot
+  *out = p;
   return cudaSuccess;
 }
 
@@ -86,7 +127,7 @@ k_eval_static(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     cdphi[j] = cv ? q.dphi : 0.f;
     cphi[j] = cv ? q.phi : 0.f;
   }
-  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f;
+  float accD = 0.f, accS = 0.f, accP = 0.f;
 #pragma unroll
   for (int j = 0; j < SEG; ++j) {
     int k = k0 + j;
@@ -101,9 +142,8 @@ k_eval_static(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     float gk = g.vol * (cjr[j] * cr[j] + cjl[j + 1] * cr[j + 1] + g.alpha * lap +
                         g.half_beta * (cdphi[j] - cdphi[j + 1]));
     if (grad) grad[fb + k * inner] = gk;
-    accG += gk * gk;
   }
-  float v[kStaticTerms] = {accD, accS, accP, accG};
+  float v[kStaticTerms] = {accD, accS, accP};
   double tot[kStaticTerms];
   if (grid_sum<kStaticTerms>(v, partials, counter, tot)) {
     double hv = 0.5 * (double)g.vol;

@@ -5,8 +5,10 @@ memory manager that owns the whole device budget, or latency-critical code that 
 cudaMalloc's implicit synchronisation.  It keeps its reduction scratch in a static device array
 shared by every call, so this test calls it twice in a row on the same stream (the second call
 must not see stale partial sums or a stale ticket counter) and compares both results with
-hysco_eval, called through the C ABI, within the parity tolerances of the other GPU tests:
-relative 1e-5 on J, D, S, P and on the gradient's 2-norm, 2e-4 of the largest entry elementwise.
+hysco_eval, called through the C ABI, and with the double-precision oracle, within the parity
+tolerances of the other GPU tests: relative 1e-5 on J, D, S, P and on the gradient's 2-norm,
+2e-4 of the largest entry elementwise.  A third call without a gradient output must give the
+same terms bit for bit (the same reduction in the same order).
 
 This file is collected last on purpose: a failure here leaves every other test already run.
 """
@@ -39,7 +41,8 @@ def stream():
 
 
 @pytest.mark.parametrize("dims,spacing,p,alpha,beta,dtype", CASES)
-def test_static_eval_matches_handle_eval_twice_in_a_row(dims, spacing, p, alpha, beta, dtype):
+def test_static_eval_matches_handle_eval_twice_in_a_row(orc, dims, spacing, p, alpha, beta,
+                                                        dtype):
     build.build()
     lib = _lib.load()
     Ipn, Imn = ph.random_images(dims, 4242, 0.1, 1.0)
@@ -56,6 +59,12 @@ def test_static_eval_matches_handle_eval_twice_in_a_row(dims, spacing, p, alpha,
         t_ref = torch.empty(4, dtype=torch.float64, device="cuda")
         g_ref = torch.empty_like(b)
         assert lib.hysco_eval(h, ptr(Ip), ptr(Im), ptr(b), ptr(t_ref), ptr(g_ref), stream()) == 0
+        # the oracle on the values the GPU sees (bf16 images rounded, then widened exactly)
+        P = orc.Problem(dims, spacing, p, alpha, beta)
+        ev = P.eval(Ip.float().cpu().numpy(), Im.float().cpu().numpy(),
+                    bn.astype(np.float64), contract=True)
+        t_orc = np.array([ev["J"], ev["D"], ev["S"], ev["P"]])
+        terms = []
         for call in range(2):
             t = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
             g = torch.full_like(b, float("nan"))
@@ -63,11 +72,21 @@ def test_static_eval_matches_handle_eval_twice_in_a_row(dims, spacing, p, alpha,
                                        ptr(b), ptr(t), ptr(g), stream())
             assert rc == 0, (call, _lib.strerror(rc))
             torch.cuda.synchronize()
-            tr, tn = t_ref.cpu().numpy(), t.cpu().numpy()
-            assert np.all(np.abs(tn - tr) <= 1e-5 * np.abs(tr)), (call, tn, tr)
-            gr, gn = g_ref.cpu().numpy(), g.cpu().numpy()
-            assert np.linalg.norm(gn - gr) <= 1e-5 * np.linalg.norm(gr), call
-            assert np.abs(gn - gr).max() <= 2e-4 * np.abs(gr).max(), call
+            tn = t.cpu().numpy()
+            terms.append(tn)
+            gn = g.cpu().numpy()
+            for tr, gr in ((t_ref.cpu().numpy(), g_ref.cpu().numpy()), (t_orc, ev["grad"])):
+                assert np.all(np.abs(tn - tr) <= 1e-5 * np.abs(tr)), (call, tn, tr)
+                assert np.linalg.norm(gn - gr) <= 1e-5 * np.linalg.norm(gr), call
+                assert np.abs(gn - gr).max() <= 2e-4 * np.abs(gr).max(), call
+        # without a gradient output: the same reduction, so the same terms bit for bit
+        t = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
+        rc = lib.hysco_eval_static(cdims, cspac, p, alpha, beta, DT[dtype], ptr(Ip), ptr(Im),
+                                   ptr(b), ptr(t), None, stream())
+        assert rc == 0, _lib.strerror(rc)
+        torch.cuda.synchronize()
+        assert np.array_equal(t.cpu().numpy(), terms[-1])
+        assert np.array_equal(terms[0], terms[1])
     finally:
         lib.hysco_destroy(h)
 
