@@ -154,6 +154,18 @@ int hysco_correct_adjoint(hysco_t h, const void* Ip, const void* Im, const float
                           const float* gTp, const float* gTm, float* dIp, float* dIm, float* db,
                           hysco_stream_t stream);
 
+/* The corrected image of Sec. 2.4 ("Image Correction"): the average of the two corrected images
+ * of Eq. 1, T = 1/2 (Tp + Tm), image-shaped float32 -- the image PyHySCO returns. */
+int hysco_correct_mean(hysco_t h, const void* Ip, const void* Im, const float* b, float* T,
+                       hysco_stream_t stream);
+
+/* Adjoint of hysco_correct_mean at b: for the sensitivity gT of a scalar loss to T (image-shaped
+ * float32, device, not NULL) it writes dIp, dIm and db as hysco_correct_adjoint does for
+ * gTp = gTm = gT / 2 (each output nullable; same layout, determinism and aliasing rules). */
+int hysco_correct_mean_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                               const float* gT, float* dIp, float* dIm, float* db,
+                               hysco_stream_t stream);
+
 /* Implicit differentiation through a solve (the Gauss-Newton system of Sec. 2.3.1 at a solution):
  * at a stationary point b of J the gradient g(b; theta) = 0 defines b as a function of every input
  * theta, and for a loss L(b), with H the Gauss-Newton Hessian at b standing in for J's Hessian,
@@ -189,9 +201,10 @@ int hysco_image_grad(hysco_t h, const void* Ip, const void* Im, const float* b, 
  * [j - 1/2 +- b_j, j + 1/2 +- b_{j+1}] (cell-index coordinates, b in PE voxels) and distorted cell i
  * collects the part inside [i - 1/2, i + 1/2].  lambda > 0 (1e-6 is negligible at single precision)
  * sets cells whose mass leaves the column in both images to 0.  out: image-shaped float32.  A column
- * whose field has |d_v b| >= 1 somewhere, or whose normal matrix is wider than a band of 4 (|d_v b|
- * above about 0.75), is set to 0 and counted in *nbad (device int32, nullable).  Uses the handle's
- * PCG scratch arrays (not the GN linearisation). */
+ * whose field has |d_v b| >= 1 somewhere, or whose normal matrix is wider than a band of half-width
+ * 16 (compression |d_v b| above about 0.94 over many cells), is set to 0 and counted in *nbad
+ * (device int32, nullable).  The first call allocates the handle's least-squares workspace (17
+ * image-shaped arrays): HYSCO_ENOMEM if that fails. */
 int hysco_ls_correct(hysco_t h, const void* Ip, const void* Im, const float* b, double lambda,
                      float* out, int32_t* nbad, hysco_stream_t stream);
 
@@ -284,8 +297,13 @@ int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_str
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):
  * per GN iteration the per-pair evaluation, Armijo and update kernels of different pairs run on
  * concurrent branches, and the Jacobi PCG of all pairs is either one cooperative launch whose grid
- * is shared among the pairs (the device-wide barriers are paid once for the batch) or each pair's
- * own persistent PCG in turn (its vectors on chip, see hysco_pcg_plan).  The fixed launch
+ * is shared among the pairs (the device-wide barriers are paid once for the batch), each pair's
+ * own persistent PCG in turn (its vectors on chip, see hysco_pcg_plan), or waves: the pairs are
+ * packed, largest first, into waves whose PCG vectors fit the device together (on chip, or with up
+ * to 1.25 or 1.5 times as many vector slots per thread as shared memory holds, the excess in
+ * global memory); a wave's pairs go through their whole GN loop together and their PCGs share one
+ * cooperative launch per GN step, each pair on its own block range with barriers among those
+ * blocks only.  The fixed launch
  * sequence is captured in a CUDA graph (cached per argument set) unless opts->no_graph.  The batch
  * holds no reference count: destroy it before any of its handles. */
 typedef struct hysco_batch_ctx* hysco_batch_t;
@@ -306,17 +324,18 @@ int hysco_batch_solve(hysco_batch_t batch, const void* const* Ip, const void* co
 /* Autotuner: times short trial solves (OT + at most 2 GN iterations into scratch fields, the
  * caller's fields untouched) of each candidate schedule -- 1, 2, 4 or 8 concurrent branches for
  * the per-pair kernels; the shared PCG launch with blocks by field size and at least 1 or at least
- * 2 blocks per pair, or the per-pair persistent PCG -- and keeps the fastest.  Synchronises
+ * 2 blocks per pair, the per-pair persistent PCG, or waves -- and keeps the fastest.  Synchronises
  * `stream`. */
 int hysco_batch_tune(hysco_batch_t batch, const void* const* Ip, const void* const* Im,
                      const hysco_opts* opts, hysco_stream_t stream);
 
 /* The schedule in use: out[0] branches, out[1] PCG policy (0: shared launch, blocks by field size;
- * 1: the same with >= 2 blocks per pair; 2: each pair's persistent PCG in turn), out[2] blocks of
- * the shared PCG launch's grid. */
+ * 1: the same with >= 2 blocks per pair; 2: each pair's persistent PCG in turn; 3, 4, 5: waves
+ * packed to 1, 1.25 and 1.5 times the on-chip vector capacity), out[2] blocks of the shared PCG
+ * launch's grid. */
 int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
 
-/* Sets the schedule: branches 1 .. min(8, n), PCG policy 0 .. 2 as in hysco_batch_schedule.
+/* Sets the schedule: branches 1 .. min(8, n), PCG policy 0 .. 5 as in hysco_batch_schedule.
  * HYSCO_EINVAL when out of range or infeasible for this batch (then unchanged).  Drops the cached
  * graph. */
 int hysco_batch_set_schedule(hysco_batch_t batch, int branches, int policy);
@@ -354,10 +373,11 @@ int hysco_ot_indices(hysco_t h, const void* Ip, const void* Im, double eps, int3
  * for which cudaMalloc's implicit synchronisation is unacceptable.  The paper has no counterpart:
  * this is a library convenience around the same per-cell arithmetic as hysco_eval.
  * Takes the geometry of hysco_create by value and needs no handle.  Its only scratch (the
- * per-block partial sums of the reduction and a ticket counter, 512 KiB plus 256 bytes) lives in a
+ * per-block partial sums of the reduction and a ticket counter, 384 KiB plus 256 bytes) lives in a
  * static device array that every GPU loading this library holds until the process exits; the
- * call allocates nothing.  The first call on each device (with that device current) looks up the
- * array's device address, so make that first call before any stream capture.  All calls share the
+ * call allocates nothing.  The first call in each CUDA context (on each device, with that device
+ * current, and again after cudaDeviceReset re-creates the context) looks up the array's device
+ * address, so make that first call before any stream capture.  All calls share the
  * array: calls whose work overlaps on the GPU (two streams, or two host threads) race and give
  * wrong results; calls ordered on one stream are safe.  Volumes whose reduction grid exceeds
  * 32768 blocks (ceil(columns / 256) * ceil((m + 1) / 4)) return HYSCO_EINVAL.  No status word is

@@ -78,6 +78,8 @@ def load():
         "hysco_correct": (I, [P, P, P, P, P, P, P]),
         "hysco_ls_correct": (I, [P, P, P, P, D, P, P, P]),
         "hysco_correct_adjoint": (I, [P, P, P, P, P, P, P, P, P, P]),
+        "hysco_correct_mean": (I, [P, P, P, P, P, P]),
+        "hysco_correct_mean_adjoint": (I, [P, P, P, P, P, P, P, P, P]),
         "hysco_image_grad": (I, [P, P, P, P, D, P, P, P]),
         "hysco_implicit_parts": (I, [P, P, P, P, P, P, P, P, P]),
         "hysco_solve_adjoint": (I, [P, P, P, P, P, I, D, P, P, P, P, P]),

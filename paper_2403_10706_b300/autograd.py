@@ -35,6 +35,28 @@ class CorrectedImages(torch.autograd.Function):
                 None if dIm is None else dIm.to(Im.dtype), db)
 
 
+class CorrectedImage(torch.autograd.Function):
+    """(Ip, Im, b) -> T = 1/2 (Tp + Tm), the corrected image, on handle h."""
+
+    @staticmethod
+    def forward(ctx, h, Ip, Im, b):
+        T = h.correct_mean(Ip, Im, b)
+        ctx.h = h
+        ctx.save_for_backward(Ip, Im, b)
+        return T
+
+    @staticmethod
+    def backward(ctx, gT):
+        Ip, Im, b = ctx.saved_tensors
+        need = ctx.needs_input_grad
+        if not any(need[1:4]):
+            return None, None, None, None
+        dIp, dIm, db = ctx.h.correct_mean_adjoint(Ip, Im, b, gT.float().contiguous(),
+                                                  want=need[1:4])
+        return (None, None if dIp is None else dIp.to(Ip.dtype),
+                None if dIm is None else dIm.to(Im.dtype), db)
+
+
 class Objective(torch.autograd.Function):
     """(Ip, Im, b, alpha, beta) -> J (float64 scalar) = D + alpha S + beta P on handle h, whose
     weights alpha and beta the arguments must equal (dJ/dalpha = S, dJ/dbeta = P)."""
@@ -77,8 +99,7 @@ def corrected_images(h, Ip, Im, b):
 
 def corrected_image(h, Ip, Im, b):
     """Differentiable 1/2 (Tp + Tm), the corrected image."""
-    Tp, Tm = CorrectedImages.apply(h, Ip, Im, b)
-    return 0.5 * (Tp + Tm)
+    return CorrectedImage.apply(h, Ip, Im, b)
 
 
 def objective(h, Ip, Im, b, alpha=None, beta=None):

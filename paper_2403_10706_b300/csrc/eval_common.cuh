@@ -53,19 +53,18 @@ __device__ __forceinline__ void barrier(float z, float& f, float& df, float& d2f
 }
 
 struct CellLin {
-  float r, jl, jr, dphi, psi, phi;
+  float r, jl, jr, dphi, psi, phi, dlt;   // dlt = delta = b_{j+1} - b_j
 };
 
-template <typename TI>
-__device__ __forceinline__ CellLin cell_lin(const TI* Ipc, const TI* Imc, int inner, int m, int j,
-                                            float bj, float bj1, float half_beta) {
-  float tp, tm, wp, wm;
-  cell_positions(bj, bj1, j, tp, tm);
-  int ip = cell_index(tp, m, wp), im = cell_index(tm, m, wm);
-  float vp, sp, vm, sm;
-  interp(Ipc, inner, m, ip, wp, vp, sp);
-  interp(Imc, inner, m, im, wm, vm, sm);
-  float delta = bj1 - bj;
+// the absent cells left of node 0 and right of node m: no residual, no barrier, delta = 0
+__device__ __forceinline__ CellLin cell_zero() { return CellLin{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; }
+
+// cell arithmetic from the two images' taps at the cell's positions: I(t) = I0 + w (I1 - I0)
+__device__ __forceinline__ CellLin cell_from_taps(float Ip0, float Ip1, float wp, float Im0,
+                                                  float Im1, float wm, float delta,
+                                                  float half_beta) {
+  const float sp = Ip1 - Ip0, vp = fmaf(wp, sp, Ip0);
+  const float sm = Im1 - Im0, vm = fmaf(wm, sm, Im0);
   float op = 1.0f + delta, om = 1.0f - delta;
   CellLin q;
   q.r = vp * op - vm * om;
@@ -76,7 +75,21 @@ __device__ __forceinline__ CellLin cell_lin(const TI* Ipc, const TI* Imc, int in
   float d2;
   barrier(delta, q.phi, q.dphi, d2);
   q.psi = half_beta * d2;
+  q.dlt = delta;
   return q;
+}
+
+template <typename TI>
+__device__ __forceinline__ CellLin cell_lin(const TI* Ipc, const TI* Imc, int inner, int m, int j,
+                                            float bj, float bj1, float half_beta) {
+  float tp, tm, wp, wm;
+  cell_positions(bj, bj1, j, tp, tm);
+  int ip = cell_index(tp, m, wp), im = cell_index(tm, m, wm);
+  const bool p0 = (unsigned)ip < (unsigned)m, p1 = (unsigned)(ip + 1) < (unsigned)m;
+  const bool m0 = (unsigned)im < (unsigned)m, m1 = (unsigned)(im + 1) < (unsigned)m;
+  const float Ip0 = p0 ? ldf(Ipc + ip * inner) : 0.0f, Ip1 = p1 ? ldf(Ipc + (ip + 1) * inner) : 0.0f;
+  const float Im0 = m0 ? ldf(Imc + im * inner) : 0.0f, Im1 = m1 ? ldf(Imc + (im + 1) * inner) : 0.0f;
+  return cell_from_taps(Ip0, Ip1, wp, Im0, Im1, wm, bj1 - bj, half_beta);
 }
 
 // r and phi only (line-search trials)

@@ -33,16 +33,26 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // grid_allreduce_then runs `work()` in every thread after the block's arrival and before the
 // wait: block-local work that the barrier neither orders nor waits for (its writes are not
 // released to other blocks), overlapped with the barrier's latency.
+// A barrier group is the whole grid by default; `grp` names a subset of the grid instead (a block
+// range that works on one problem): the block's rank within it and its size.  The group's sync
+// words (a counter and slots for grp.size blocks) are its own.
 struct NoWork {
   __device__ void operator()() const {}
 };
+struct BarrierGroup {
+  int rank, size;
+};
+__device__ __forceinline__ BarrierGroup whole_grid() {
+  return BarrierGroup{(int)blockIdx.x, (int)gridDim.x};
+}
 template <int K, typename F>
 __device__ __forceinline__ bool grid_allreduce_then(float (&v)[K], unsigned* sync, unsigned gen,
                                                     float* shf, df32* shd, F&& work,
                                                     int first = 0, int count = -1,
-                                                    long long budget = kBarrierSpinCycles) {
+                                                    long long budget = kBarrierSpinCycles,
+                                                    BarrierGroup grp = whole_grid()) {
   static_assert(K >= 1 && K <= kSyncMaxK, "grid_allreduce: K exceeds the slot width");
-  const int tid = threadIdx.x, nb = gridDim.x;
+  const int tid = threadIdx.x, nb = grp.size;
   if (count < 0) count = nb;
   unsigned* counter = sync;
   float* slot = reinterpret_cast<float*>(sync + kSyncHeader) + (size_t)(gen & 1u) * nb * kSyncMaxK;
@@ -50,7 +60,7 @@ __device__ __forceinline__ bool grid_allreduce_then(float (&v)[K], unsigned* syn
   block_sum<K, float>(v, shf);   // its barrier orders this block's phase writes before the release
   if (tid == 0) {
 #pragma unroll
-    for (int i = 0; i < K; ++i) __stcg(slot + blockIdx.x * K + i, v[i]);
+    for (int i = 0; i < K; ++i) __stcg(slot + grp.rank * K + i, v[i]);
     red_release_add(counter, 1u);
   }
   work();
@@ -101,8 +111,9 @@ template <int K>
 __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, unsigned gen,
                                                float* shf, df32* shd, int first = 0,
                                                int count = -1,
-                                               long long budget = kBarrierSpinCycles) {
-  return grid_allreduce_then<K>(v, sync, gen, shf, shd, NoWork{}, first, count, budget);
+                                               long long budget = kBarrierSpinCycles,
+                                               BarrierGroup grp = whole_grid()) {
+  return grid_allreduce_then<K>(v, sync, gen, shf, shd, NoWork{}, first, count, budget, grp);
 }
 
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
@@ -136,8 +147,9 @@ constexpr int kTagWordsPerLane = kTagWordsPerLaneHost;   // block ranges of up t
 __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* sync, unsigned gen,
                                                          float* shf, df32* shd, int first = 0,
                                                          int count = -1,
-                                                         long long budget = kBarrierSpinCycles) {
-  const int tid = threadIdx.x, nb = gridDim.x;
+                                                         long long budget = kBarrierSpinCycles,
+                                                         BarrierGroup grp = whole_grid()) {
+  const int tid = threadIdx.x, nb = grp.size;
   if (count < 0) count = nb;
   unsigned* counter = sync;
   unsigned long long* words = reinterpret_cast<unsigned long long*>(
@@ -146,7 +158,7 @@ __device__ __forceinline__ bool grid_allreduce_unordered(float& v, unsigned* syn
   float vv[1] = {v};
   block_sum<1, float>(vv, shf);
   if (tid == 0) {
-    st_relaxed_u64(words + blockIdx.x, ((unsigned long long)gen << 32) | __float_as_uint(vv[0]));
+    st_relaxed_u64(words + grp.rank, ((unsigned long long)gen << 32) | __float_as_uint(vv[0]));
     red_relaxed_add(counter, 1u);
     const unsigned target = gen * (unsigned)nb;
     const long long t0 = clock64();

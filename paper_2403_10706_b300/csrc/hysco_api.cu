@@ -47,6 +47,9 @@ struct hysco_ctx {
   // iteration), u, c = z - u and the b of the iteration's start, pitched; the in-plane bases
   float *az[2], *au, *ac, *abprev;
   float *aQA, *aQB, *amuA, *amuB;
+  // least-squares correction workspace (allocated at the first hysco_ls_correct call): the
+  // normal matrix's band (kLsBandWide image-shaped arrays), its right-hand side, column flags
+  float* lsw;
   cudaGraphExec_t agexec;
   const void *ag_Ip, *ag_Im;
   float* ag_b;
@@ -85,6 +88,7 @@ void free_all(hysco_ctx* h) {
   if (h->counter) cudaFree(h->counter);
   if (h->psync) cudaFree(h->psync);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->lsw) cudaFree(h->lsw);
   float* abufs[] = {h->az[0], h->az[1], h->au, h->ac, h->abprev, h->aQA, h->aQB, h->amuA, h->amuB};
   for (float* b : abufs)
     if (b) cudaFree(b);
@@ -261,6 +265,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   g.divG4 = make_fastdiv((unsigned)g.G4);
   g.divfe1 = make_fastdiv((unsigned)g.fe[1]);
   g.divfe2 = make_fastdiv((unsigned)g.fe[2]);
+  set_march(g, h->device);
   long long nfp = (long long)g.fe[0] * g.fe[1] * g.P2;
   if (nfp >= (1LL << 31)) {
     delete h;
@@ -284,6 +289,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   long long march_blocks = (long long)ceil_div(g.ncols, kBlock) * ceil_div(g.E, kSeg);
   long long flat_blocks = (long long)ceil_div(g.nf, kBlock) + 1;
   long long nparts = march_blocks * (4 * kLsBatch + 1) + flat_blocks * 2 + 148 * 8 * 2 +
+                     (long long)eval_blocks(g) * 8 +
                      (long long)g.ncols * 2 + 64;
   if (cudaMalloc((void**)&h->partials, nparts * sizeof(float)) != cudaSuccess ||
       cudaMalloc((void**)&h->counter, 64 * sizeof(unsigned)) != cudaSuccess ||
@@ -365,11 +371,10 @@ int hysco_eval(hysco_t h, const void* Ip, const void* Im, const float* b, double
   if (!terms_dev || !aligned(terms_dev, 8)) return HYSCO_EINVAL;
   if (grad && !aligned(grad, 4)) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (int rc = reset_state(h, s)) return rc;
+  // one launch: the evaluation's last block writes J, D, S, P and the state itself
   Work w = h->work();
   HYSCO_TRY(launch_eval(h->g, h->dtype, Ip, Im, b, grad, nullptr, h->dco, h->eco, h->invd, -1, w,
-                        s));
-  HYSCO_TRY(launch_publish_terms(terms_dev, w, s));
+                        s, nullptr, terms_dev));
   h->have_lin = true;
   h->have_factor = false;
   return HYSCO_OK;
@@ -429,6 +434,27 @@ int hysco_correct(hysco_t h, const void* Ip, const void* Im, const float* b, flo
       check_f32(Tm))
     return HYSCO_EINVAL;
   HYSCO_TRY(launch_correct(h->g, h->dtype, Ip, Im, b, Tp, Tm, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_correct_mean(hysco_t h, const void* Ip, const void* Im, const float* b, float* T,
+                       hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(T))
+    return HYSCO_EINVAL;
+  HYSCO_TRY(launch_correct(h->g, h->dtype, Ip, Im, b, T, nullptr, (cudaStream_t)stream));
+  return HYSCO_OK;
+}
+
+int hysco_correct_mean_adjoint(hysco_t h, const void* Ip, const void* Im, const float* b,
+                               const float* gT, float* dIp, float* dIm, float* db,
+                               hysco_stream_t stream) {
+  if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(gT))
+    return HYSCO_EINVAL;
+  if ((dIp && !aligned(dIp, 4)) || (dIm && !aligned(dIm, 4)) || (db && !aligned(db, 4)))
+    return HYSCO_EINVAL;
+  // T = 1/2 (T+ + T-): the adjoint of hysco_correct with both upstream sensitivities gT / 2
+  HYSCO_TRY(launch_correct_adjoint(h->g, h->dtype, Ip, Im, b, gT, gT, dIp, dIm, db,
+                                   (size_t)h->nimg * sizeof(float), (cudaStream_t)stream, 0.5f));
   return HYSCO_OK;
 }
 
@@ -496,12 +522,20 @@ int hysco_ls_correct(hysco_t h, const void* Ip, const void* Im, const float* b, 
   if (!h || check_img(h, Ip) || check_img(h, Im) || check_f32(b) || check_f32(out)) return HYSCO_EINVAL;
   if (!(lambda > 0.0) || !std::isfinite(lambda) || (nbad && !aligned(nbad, 4))) return HYSCO_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  // scratch: five band arrays and the right-hand side in solver arrays the GN linearisation
-  // (grad, d, e, 1/diag) and the column factors do not use
-  LsBand band{{h->r, h->z, h->p0, h->p1, h->Hp}};
+  const size_t nimg = (size_t)h->nimg;
+  if (!h->lsw &&
+      cudaMalloc((void**)&h->lsw, ((kLsBandWide + 1) * nimg + (size_t)h->g.ncols) * sizeof(float)) !=
+          cudaSuccess) {
+    h->lsw = nullptr;
+    return HYSCO_ENOMEM;
+  }
+  float* band = h->lsw;
+  float* rhs = h->lsw + kLsBandWide * nimg;
+  int* wide = reinterpret_cast<int*>(h->lsw + (kLsBandWide + 1) * nimg);
   int* bad = reinterpret_cast<int*>(h->counter + 48);
   HYSCO_TRY(cudaMemsetAsync(bad, 0, sizeof(int), s));
-  HYSCO_TRY(launch_ls_correct(h->g, h->dtype, Ip, Im, b, (float)lambda, band, h->q0, out, bad, s));
+  HYSCO_TRY(launch_ls_correct(h->g, h->dtype, Ip, Im, b, (float)lambda, band, (long long)nimg, rhs,
+                              out, bad, wide, s));
   if (nbad) HYSCO_TRY(cudaMemcpyAsync(nbad, bad, sizeof(int), cudaMemcpyDeviceToDevice, s));
   return HYSCO_OK;
 }
@@ -907,7 +941,15 @@ struct hysco_batch_ctx {
   unsigned* sync = nullptr;
   int branches = 4;                   // schedule: concurrent branches of per-pair kernels
   int policy = 0;                     // schedule: 0 blocks by field size, 1 the same with >= 2 each,
-                                      // 2 each pair's own persistent PCG in turn
+                                      // 2 each pair's own persistent PCG in turn, 3 waves
+  // policy 3: the pairs in waves whose PCGs share one cooperative launch (each pair on its own
+  // block range with its vectors on chip); a wave runs its whole GN loop before the next
+  int wgrid = 0;                      // co-resident blocks of the wave kernel
+  std::vector<std::vector<int>> waves;          // pair indices of each wave
+  std::vector<std::vector<int>> wave_nblk;      // their block shares
+  std::vector<int> wave_onchip;                 // largest on-chip slot count in each wave
+  unsigned* wsync = nullptr;                    // sync words of the running wave
+  size_t wsync_words = 0;
   cudaStream_t cap = nullptr;
   std::vector<cudaStream_t> side;
   cudaEvent_t fork = nullptr;
@@ -922,9 +964,12 @@ struct hysco_batch_ctx {
 namespace {
 
 constexpr int kMaxBranches = 8;
+constexpr int kMaxPolicy = 5;
+constexpr double kWavePack[3] = {1.0, 1.25, 1.5};   // policies 3, 4, 5
 
 void batch_free(hysco_batch_ctx* B) {
   if (B->gexec) cudaGraphExecDestroy(B->gexec);
+  if (B->wsync) cudaFree(B->wsync);
   if (B->d_pairs) cudaFree(B->d_pairs);
   if (B->d_block_pair) cudaFree(B->d_block_pair);
   if (B->sync) cudaFree(B->sync);
@@ -968,10 +1013,76 @@ bool batch_shares(const hysco_batch_ctx* B, int lo, std::vector<int>& out) {
   return true;
 }
 
+// policy 3: pairs sorted by field size, largest first, placed first-fit into waves; a pair needs
+// enough blocks to keep its r, p, Hp on chip (kWaveSlots slots per thread) and a wave holds at
+// most wgrid blocks and kWaveMax pairs.  A wave's spare blocks go to its pairs in proportion to
+// their sizes (fewer groups per block: a shorter stencil phase).
+int batch_waves(hysco_batch_ctx* B, double pack) {
+  if (B->wgrid <= 0) return HYSCO_EINVAL;
+  const int n = B->n;
+  // float4 groups a block takes: kWaveSlots on chip per thread, times `pack` (> 1: the slots past
+  // kWaveSlots keep r, p, Hp in global memory, so that more pairs share a wave)
+  const long long per_block = (long long)(kPcgBlock * kWaveSlots * pack);
+  std::vector<long long> n4(n);
+  std::vector<int> need(n), order(n);
+  for (int i = 0; i < n; ++i) {
+    n4[i] = B->hs[i]->g.nfp / 4;
+    need[i] = (int)std::min<long long>((n4[i] + per_block - 1) / per_block, B->wgrid);
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n4[a] > n4[b]; });
+  std::vector<std::vector<int>> waves;
+  std::vector<int> used;
+  for (int i : order) {
+    size_t w = 0;
+    while (w < waves.size() && (used[w] + need[i] > B->wgrid || (int)waves[w].size() >= kWaveMax))
+      ++w;
+    if (w == waves.size()) {
+      waves.emplace_back();
+      used.push_back(0);
+    }
+    waves[w].push_back(i);
+    used[w] += need[i];
+  }
+  B->waves = waves;
+  B->wave_nblk.assign(waves.size(), {});
+  B->wave_onchip.assign(waves.size(), 0);
+  size_t words = 0;
+  for (size_t w = 0; w < waves.size(); ++w) {
+    long long tot = 0;
+    for (int i : waves[w]) tot += n4[i];
+    const int spare = B->wgrid - used[w];
+    std::vector<int>& nb = B->wave_nblk[w];
+    size_t ww = 0;
+    for (int i : waves[w]) {
+      const int k = need[i] + (int)((long long)spare * n4[i] / tot);
+      nb.push_back(k);
+      const long long G = (n4[i] + (long long)k * kPcgBlock - 1) / ((long long)k * kPcgBlock);
+      B->wave_onchip[w] = std::max(B->wave_onchip[w], (int)std::min<long long>(G, kWaveSlots));
+      ww += pcg_sync_words(k);
+    }
+    words = std::max(words, ww);
+  }
+  if (words > B->wsync_words) {
+    if (B->wsync) cudaFree(B->wsync);
+    B->wsync = nullptr;
+    B->wsync_words = 0;
+    if (cudaMalloc((void**)&B->wsync, words * sizeof(unsigned)) != cudaSuccess)
+      return HYSCO_ENOMEM;
+    B->wsync_words = words;
+  }
+  return HYSCO_OK;
+}
+
 int batch_layout(hysco_batch_ctx* B, int policy) {
   if (policy == 2) {   // per-pair persistent PCG: every pair needs its cooperative plan
     for (const hysco_ctx* h : B->hs)
       if (h->pplan.grid <= 0) return HYSCO_EINVAL;
+    B->policy = policy;
+    return HYSCO_OK;
+  }
+  if (policy >= 3 && policy <= 5) {
+    if (int rc = batch_waves(B, kWavePack[policy - 3])) return rc;
     B->policy = policy;
     return HYSCO_OK;
   }
@@ -1011,8 +1122,76 @@ cudaError_t batch_join(hysco_batch_ctx* B, cudaStream_t s) {
   return e;
 }
 
+// policy 3: wave after wave, each wave's pairs through their whole GN loop together, their per-
+// pair kernels on concurrent branches and their PCGs in one cooperative launch per GN step
+int enqueue_waves(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
+                  float* const* b, const hysco_opts* o, double* const* stats, cudaStream_t s) {
+  for (size_t w = 0; w < B->waves.size(); ++w) {
+    const std::vector<int>& pw = B->waves[w];
+    auto branch = [&](int j) { return B->side[j % B->branches]; };
+    HYSCO_TRY(batch_fork(B, s));
+    for (size_t j = 0; j < pw.size(); ++j) {
+      const int i = pw[j];
+      hysco_ctx* h = B->hs[i];
+      if (int rc = reset_state(h, branch(j))) return rc;
+      if (o->init) {
+        if (int rc = init_ot_impl(h, Ip[i], Im[i], b[i], o->ot_blur, o->ot_eps, nullptr, nullptr,
+                                  branch(j)))
+          return rc;
+        HYSCO_TRY(launch_feasible_start(h->g, b[i], h->work(), branch(j)));
+      }
+    }
+    // the wave's PCG arguments (fixed for the whole loop)
+    PcgWave wv{};
+    wv.n = (int)pw.size();
+    int blk = 0;
+    size_t off = 0;
+    for (size_t j = 0; j < pw.size(); ++j) {
+      hysco_ctx* h = B->hs[pw[j]];
+      const int nb = B->wave_nblk[w][j];
+      const long long n4 = h->g.nfp / 4;
+      const int G = (int)std::min<long long>((n4 + (long long)nb * kPcgBlock - 1) /
+                                                 ((long long)nb * kPcgBlock), kWaveSlots);
+      wv.blk0[j] = blk;
+      wv.nblk[j] = nb;
+      wv.g[j] = h->g;
+      wv.a[j] = PcgArgs{h->grad, -1.0f, h->x, h->r, h->z, h->p0, h->p1, h->Hp, h->dco, h->eco,
+                        h->invd, B->wsync + off, h->st, o->pcg_max_iters, o->pcg_rtol, G};
+      blk += nb;
+      off += pcg_sync_words(nb);
+    }
+    for (int it = 0; it < o->gn_iters; ++it) {
+      for (size_t j = 0; j < pw.size(); ++j) {
+        hysco_ctx* h = B->hs[pw[j]];
+        const int i = pw[j];
+        HYSCO_TRY(launch_eval(h->g, h->dtype, Ip[i], Im[i], b[i], nullptr, h->grad, h->dco,
+                              h->eco, h->invd, it, h->work(), branch(j)));
+      }
+      HYSCO_TRY(batch_join(B, s));
+      HYSCO_TRY(launch_pcg_wave(wv, blk, B->wave_onchip[w], B->wsync, off, s));
+      HYSCO_TRY(batch_fork(B, s));
+      for (size_t j = 0; j < pw.size(); ++j) {
+        const int i = pw[j];
+        hysco_ctx* h = B->hs[i];
+        const Geo& g = h->g;
+        Work wk = h->work();
+        cudaStream_t bs = branch(j);
+        HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip[i], Im[i], b[i], h->x, h->grad, h->dco,
+                                    h->eco, h->invd, o->ls_max_iters, o->armijo_c1, wk, bs));
+        for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
+          HYSCO_TRY(launch_linesearch(g, h->dtype, Ip[i], Im[i], b[i], h->x, h->grad, t0,
+                                      o->ls_max_iters, o->armijo_c1, wk, bs));
+        HYSCO_TRY(launch_update(g, b[i], h->x, it, stats ? stats[i] : nullptr, wk, bs));
+      }
+    }
+    HYSCO_TRY(batch_join(B, s));
+  }
+  return HYSCO_OK;
+}
+
 int enqueue_batch(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
                   float* const* b, const hysco_opts* o, double* const* stats, cudaStream_t s) {
+  if (B->policy >= 3) return enqueue_waves(B, Ip, Im, b, o, stats, s);
   auto branch = [&](int i) { return B->side[i % B->branches]; };
   HYSCO_TRY(batch_fork(B, s));
   for (int i = 0; i < B->n; ++i) {
@@ -1114,6 +1293,7 @@ int hysco_batch_create(int n, const hysco_t* handles, hysco_batch_t* out) {
   B->device = handles[0]->device;
   B->hs.assign(handles, handles + n);
   B->grid = grid;
+  B->wgrid = pcg_wave_setup(B->device);
   bool ok = cudaMalloc((void**)&B->d_pairs, sizeof(BatchPair) * n) == cudaSuccess &&
             cudaMalloc((void**)&B->d_block_pair, sizeof(int) * B->grid) == cudaSuccess &&
             cudaMalloc((void**)&B->sync, pcg_sync_words(B->grid) * sizeof(unsigned)) ==
@@ -1155,7 +1335,7 @@ int hysco_batch_schedule(hysco_batch_t B, int32_t out[3]) {
 
 int hysco_batch_set_schedule(hysco_batch_t B, int branches, int policy) {
   if (!B || branches < 1 || branches > kMaxBranches || branches > B->n || policy < 0 ||
-      policy > 2)
+      policy > kMaxPolicy)
     return HYSCO_EINVAL;
   const int old = B->policy;
   if (int rc = batch_layout(B, policy)) {
@@ -1218,7 +1398,7 @@ int hysco_batch_tune(hysco_batch_t B, const void* const* Ip, const void* const* 
     rc = HYSCO_ECUDA;
   float best = 1e30f;
   int best_br = B->branches, best_pol = B->policy;
-  for (int pol = 0; pol < 3 && rc == HYSCO_OK; ++pol) {
+  for (int pol = 0; pol <= kMaxPolicy && rc == HYSCO_OK; ++pol) {
     if (batch_layout(B, pol) != HYSCO_OK) continue;   // policy not feasible for this batch
     for (int br = 1; br <= kMaxBranches && br <= B->n && rc == HYSCO_OK; br *= 2) {
       B->branches = br;

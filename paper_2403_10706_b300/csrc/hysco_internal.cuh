@@ -58,6 +58,11 @@ struct Geo {
   int ps[3];             // pitched strides (ps[2] = 1)
   int psA, psB, psP;     // pitched strides of the in-plane axes A, B and of the PE axis
   FastDiv divG4, divfe1, divfe2;
+  // Column march of the objective kernels: a warp owns 32 consecutive columns (a "tile") and one
+  // segment of mseg consecutive nodes of each; nseg segments cover the E nodes.  Chosen at
+  // handle creation so that ntile * nseg warps fit in one wave of resident blocks.
+  FastDiv divIn, divA;   // dividers by inner and by nA
+  int ntile, nseg, mseg;
 };
 
 // Device-resident scalar state of a solve (and of single hysco_eval calls).
@@ -89,7 +94,8 @@ struct DevState {
 
 constexpr int kBlock = 256;   // threads per block of every kernel
 constexpr int kMaxTrials = 16;
-constexpr int kSeg = 4;       // PE nodes per thread in the column-march kernels
+constexpr int kSeg = 4;       // PE nodes per thread in the short column-march kernels
+constexpr int kMinMarch = 4;  // fewest PE nodes per segment of the objective's column march
 constexpr int kNpt = 2;       // nodes per thread in the flat stencil kernels
 constexpr int kLsBatch = 9;   // Armijo trials per line-search launch after the first (gamma = 1)
 
@@ -356,11 +362,16 @@ struct Work {        // device buffers the launchers need
 };
 
 // k_eval.cu
+// the column-march decomposition of g (divIn, divA, ntile, nseg, mseg) for `device`
+void set_march(Geo& g, int device);
+int eval_blocks(const Geo& g);   // blocks of an objective launch (one warp per tile and segment)
 // grad: caller layout (nullable); grad_p: pitched solver copy (nullable); dco, eco, invd pitched
-// cpx (nullable): the ADMM prox centre c (pitched), see k_eval's PROX
+// cpx (nullable): the ADMM prox centre c (pitched), see k_eval's PROX; terms (nullable, device):
+// a single evaluation (it = -1) also writes J, D, S, P there
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
-                        const Work& w, cudaStream_t s, const float* cpx = nullptr);
+                        const Work& w, cudaStream_t s, const float* cpx = nullptr,
+                        double* terms = nullptr);
 // The gamma = 1 Armijo trial as a full evaluation at b + q (q pitched): J, grad, d, e, 1/diag at
 // b + q overwrite the solver arrays (grad_p is read first for grad^T q), and the Armijo decision
 // for gamma = 1 is taken; on acceptance the next launch_eval only promotes the stashed terms.
@@ -375,13 +386,14 @@ cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const voi
                               const float* cpx = nullptr);
 cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
                           const Work& w, cudaStream_t s);
+// Tm == nullptr: Tp receives the corrected image 1/2 (T+ + T-)
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s);
 // k_adjoint.cu: adjoints of the corrected images and of J's distance term at fixed b
 cudaError_t launch_correct_adjoint(const Geo& g, int dtype, const void* Ip, const void* Im,
                                    const float* b, const float* gTp, const float* gTm,
                                    float* dIp, float* dIm, float* db, size_t img_bytes,
-                                   cudaStream_t s);
+                                   cudaStream_t s, float scale = 1.0f);
 cudaError_t launch_image_grad(const Geo& g, int dtype, const void* Ip, const void* Im,
                               const float* b, float svol, float* dIp, float* dIm,
                               cudaStream_t s);
@@ -393,7 +405,6 @@ cudaError_t launch_mixed_image_adjoint(const Geo& g, int dtype, const void* Ip, 
                                        const float* b, const float* v, float svol, float* dIp,
                                        float* dIm, cudaStream_t s);
 cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s);
-cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s);
 
 // k_pcg.cu
 cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
@@ -410,7 +421,6 @@ cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const fl
 // caller layout <-> pitched layout of a field-shaped array
 cudaError_t launch_to_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_from_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s);
-int column_tile_width(int E);
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
                               float* lco, cudaStream_t s);
 // mode 0 = apply z = M^{-1} r;  1 = PCG init (r = sign * grad, x = 0);  2 = PCG update
@@ -450,6 +460,7 @@ struct PcgPlan {
 };
 PcgPlan pcg_persistent_plan(int device, int pe_axis, int n4);
 constexpr int kPcgBlock = 768;        // threads per block of the persistent PCG
+constexpr int kWaveMax = 8;           // problems per launch of the batched (wave) PCG
 constexpr int kPcgBlocksPerSm = 1;    // its blocks per SM at most
 inline size_t pcg_onchip_bytes(int slots) { return (size_t)slots * 3 * kPcgBlock * 16; }   // r, p, Hp
 constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arrival counter's line)
@@ -457,6 +468,39 @@ constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused red
 constexpr int kTagWordsPerLaneHost = 16;   // grid_allreduce_unordered's block-range limit / 32
 // counter line, two float slots of kSyncMaxK per block, two slots of one tagged 64-bit word per block
 inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid + 4ull * (size_t)grid; }
+// arguments of one problem's persistent PCG
+struct PcgArgs {
+  const float* grad;     // right-hand side is rhs_sign * grad
+  float rhs_sign;
+  float* x;
+  float* r;
+  float* z;
+  float* p0;
+  float* p1;
+  float* Hp;
+  const float* dco;
+  const float* eco;
+  const float* invd;
+  unsigned* sync;        // arrival counter + 2 slots of partial sums; zeroed before every launch
+  DevState* st;
+  int max_it;
+  double rtol;
+  int onchip;            // slots per thread whose r, p, Hp are in shared memory
+};
+constexpr int kWaveSlots = 6;   // on-chip slots per thread a wave plans for (221 KB per block)
+// a wave: up to kWaveMax problems, each with its block range and arguments
+struct PcgWave {
+  int n;
+  int blk0[kWaveMax], nblk[kWaveMax];
+  Geo g[kWaveMax];
+  PcgArgs a[kWaveMax];
+};
+// co-resident blocks of the wave kernel on `device` (0 if it cannot run); sets its attributes
+int pcg_wave_setup(int device);
+// one cooperative launch for the problems of w (grid = their block total); sync: the problems'
+// sync words, sync_words of them, zeroed first
+cudaError_t launch_pcg_wave(const PcgWave& w, int grid, int onchip_max, unsigned* sync,
+                            size_t sync_words, cudaStream_t s);
 cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,
@@ -492,16 +536,15 @@ cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void*
 int ot_tile_width(int E);
 cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
                       int* kp, int* km, const Work& w, cudaStream_t s);
-cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s);
-// k_ls.cu: least-squares correction; the normal matrix's band (half-width kLsBand) lives in
-// kLsBand + 1 image-layout scratch arrays
+cudaError_t launch_blur(const Geo& g, float* in, float* out, cudaStream_t s);   // in: scratch
+// k_ls.cu: least-squares correction; the normal matrix's band lives in kLsBandWide + 1
+// image-layout scratch arrays (band + d * bstride), its right-hand side in rhs; wide: one int per
+// column (the columns the narrow first pass hands to the wide second pass)
 constexpr int kLsBand = 4;
-struct LsBand {
-  float* d[kLsBand + 1];
-};
+constexpr int kLsBandWide = 16;
 cudaError_t launch_ls_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
-                              const float* b, float lambda, LsBand band, float* rhs, float* out,
-                              int* nbad, cudaStream_t s);
+                              const float* b, float lambda, float* band, long long bstride,
+                              float* rhs, float* out, int* nbad, int* wide, cudaStream_t s);
 
 // the GN loop's feasible start: b (caller layout) halved until max |delta| < 1
 cudaError_t launch_feasible_start(const Geo& g, float* b, const Work& w, cudaStream_t s);

@@ -49,7 +49,7 @@ __device__ __forceinline__ int adj_cell(int m, int inner, const TI* Ipc, const T
   float w;
   const int i = cell_index(plus ? tp : tm, m, w);
   if (MODE == 0) {
-    const float coef = gj * mod;
+    const float coef = svol * gj * mod;   // svol: a factor on the upstream sensitivity
     c0 = (1.0f - w) * coef;
     c1 = w * coef;
   } else if (MODE == 1) {
@@ -256,7 +256,7 @@ template <typename TI>
 __global__ void __launch_bounds__(kBlock)
 k_field_adjoint(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
                 const float* __restrict__ b, const float* __restrict__ gTp,
-                const float* __restrict__ gTm, float* __restrict__ db) {
+                const float* __restrict__ gTm, float scale, float* __restrict__ db) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncols) return;
   const int inner = g.inner, m = g.m;
@@ -273,8 +273,8 @@ k_field_adjoint(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     interp(Ip + ib, inner, m, ip, wp, vp, sp);
     interp(Im + ib, inner, m, im, wm, vm, sm);
     const float delta = bn - bj;
-    const float gp = gTp ? __ldg(gTp + ib + j * inner) : 0.f;
-    const float gm = gTm ? __ldg(gTm + ib + j * inner) : 0.f;
+    const float gp = gTp ? scale * __ldg(gTp + ib + j * inner) : 0.f;
+    const float gm = gTm ? scale * __ldg(gTm + ib + j * inner) : 0.f;
     const float ap = 0.5f * sp * (1.0f + delta), am = 0.5f * sm * (1.0f - delta);
     lo = gp * (ap - vp) + gm * (vm - am);
     hi = gp * (ap + vp) - gm * (am + vm);
@@ -360,7 +360,7 @@ cudaError_t launch_mixed_image_adjoint(const Geo& g, int dtype, const void* Ip, 
 cudaError_t launch_correct_adjoint(const Geo& g, int dtype, const void* Ip, const void* Im,
                                    const float* b, const float* gTp, const float* gTm,
                                    float* dIp, float* dIm, float* db, size_t img_bytes,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, float scale) {
   const dim3 cols(ceil_div(g.ncols, kAdjBlock / kAdjLanes), 2);
   const dim3 march(ceil_div(g.ncols, kBlock), ceil_div(g.E, kSeg));
   // an image without an upstream sensitivity has a zero adjoint
@@ -374,8 +374,8 @@ cudaError_t launch_correct_adjoint(const Geo& g, int dtype, const void* Ip, cons
     using T = decltype(tag);
     const T* P = (const T*)Ip;
     const T* M = (const T*)Im;
-    if (dp || dm) k_image_adjoint<T, 0><<<cols, kAdjBlock, 0, s>>>(g, P, M, b, gTp, gTm, 0.f, dp, dm);
-    if (db) k_field_adjoint<T><<<march, kBlock, 0, s>>>(g, P, M, b, gTp, gTm, db);
+    if (dp || dm) k_image_adjoint<T, 0><<<cols, kAdjBlock, 0, s>>>(g, P, M, b, gTp, gTm, scale, dp, dm);
+    if (db) k_field_adjoint<T><<<march, kBlock, 0, s>>>(g, P, M, b, gTp, gTm, scale, db);
     return cudaGetLastError();
   };
   switch (dtype) {

@@ -178,8 +178,8 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
            long long cz, long long ci, long long cj, const float* __restrict__ muB,
            const float* __restrict__ muA, float alpha, float wB, float wA, const DevState* st) {
   if (st->stop) return;
-  __shared__ float As[kMmDepth][kMmTile + 4];
-  __shared__ float Bs[kMmDepth][kMmTile + 4];
+  __shared__ __align__(16) float As[kMmDepth][kMmTile + 4];
+  __shared__ __align__(16) float Bs[kMmDepth][kMmTile + 4];
   const int z = blockIdx.z;
   const int i0 = blockIdx.y * kMmTile, j0 = blockIdx.x * kMmTile;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -202,13 +202,13 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
       Bs[e >> 6][e & 63] = (lb < K && jb < N) ? __ldg(Bp + lb * B.si + jb * B.sj) : 0.f;
     }
     __syncthreads();
+    // thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the tile: its
+    // operands of each depth step are two 16-byte shared loads
 #pragma unroll
     for (int l = 0; l < kMmDepth; ++l) {
-      float av[4], bv[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) av[a] = As[l][ty + 16 * a];
-#pragma unroll
-      for (int bb = 0; bb < 4; ++bb) bv[bb] = Bs[l][tx + 16 * bb];
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[l][4 * ty]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[l][4 * tx]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -219,11 +219,11 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
   const float rho = SCALE ? st->admm_rho : 0.f;
 #pragma unroll
   for (int a = 0; a < 4; ++a) {
-    const int i = i0 + ty + 16 * a;
+    const int i = i0 + 4 * ty + a;
     if (i >= M) continue;
 #pragma unroll
     for (int bb = 0; bb < 4; ++bb) {
-      const int j = j0 + tx + 16 * bb;
+      const int j = j0 + 4 * tx + bb;
       if (j >= N) continue;
       float v = acc[a][bb];
       if (SCALE) v *= rho / (rho + alpha * (wB * __ldg(muB + i) + wA * __ldg(muA + j)));

@@ -2,12 +2,10 @@
 // (Sec. 2.1 Eq. 1-5, Sec. 2.3.1), the Armijo line search, the GN update, the corrected images
 // (Sec. 2.4) and the interpolation cell indices.
 //
-// Thread mapping ("column march"): thread = (PE column c, segment of kSeg nodes along PE).
+// Thread mapping ("column march"): thread = (PE column c, segment of nodes along PE).
 // Consecutive threads own consecutive columns, so for pe_dim != 2 every PE step is a coalesced
-// row access.  The segment loop is fully unrolled with no serialising branches: field indices are
-// clamped into range and absent neighbours are read at the node itself (zero Laplacian
-// difference); an interpolation tap outside the image is a predicated-off load that reads 0.  So
-// a thread issues all of its field loads, then all of its image gathers.
+// row access.  Absent neighbours are read at the node itself (zero Laplacian difference); an
+// interpolation tap outside the image is a predicated-off load that reads 0.
 // Per cell j (nodes j, j+1):
 //   bc = (b_j + b_{j+1}) / 2, delta = b_{j+1} - b_j, t+- = j +- bc      (averaging / FD operators)
 //   I(t) = I[i] + w (I[i+1] - I[i]), i = floor(t), w = t - i, I = 0 outside 0..m-1
@@ -27,30 +25,21 @@ namespace hysco {
 // J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
 // ------------------------------------------------------------------------------------------
 
-// TRIAL = false: evaluation at b (GN iteration `it`, or it = -1 for a single hysco_eval call, or
-// it = -2 for a fresh evaluation that a stopped run skips).  In a
-// solve, when the previous gamma = 1 trial was accepted the coefficients at this iterate are
-// already in place: one thread promotes the stashed terms and every block returns at once (no
-// block enters the reduction, so the ticket counter is untouched).
-// TRIAL = true: the gamma = 1 Armijo trial, an evaluation at b + q.
-// Each thread keeps only the previous cell (rolling window); the in-plane neighbours along the
-// column index's fast axis A are the adjacent lanes (warp shuffle; an edge lane loads).
-// PROX (the ADMM b-subproblem of Sec. 2.3.2): J gains rho vol/2 ||b - c||^2 (c pitched, rho the
-// device state's admm_rho), the gradient rho vol (b - c) and the GN coefficient d the constant rho;
-// with the split geometry (in-plane Laplacian weights 0) S is the PE part S3 alone.
-template <typename TI, int SEG, bool TRIAL, bool PROX>
-__global__ void __launch_bounds__(kBlock)
-k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
-       const float* __restrict__ q, const float* __restrict__ cpx, float* __restrict__ grad,
-       float* __restrict__ grad_p, float* __restrict__ dco, float* __restrict__ eco,
-       float* __restrict__ invd, int it, int ls_max, double c1, float* partials,
-       unsigned* counter, DevState* st) {
-  if (TRIAL) {
-    if (st->stop || st->ls_done) return;
-  } else if (it >= 0) {
-    if (st->stop) return;
+constexpr int kEvalU = 4;           // nodes whose loads are issued together (evaluation)
+constexpr int kEvalUTrial = 2;      // the same for the trial and the prox variants
+constexpr int kEvalMinBlocks = 3;   // resident blocks per SM the registers must allow (80 regs)
+
+// Whether an objective launch has nothing to do: a stopped run, a line search already decided,
+// or (in a solve, when the previous gamma = 1 trial was accepted) coefficients already in place,
+// whose stashed terms one thread promotes.  The same for every block, so no block enters the
+// reduction and the ticket counter is untouched.
+template <bool TRIAL, bool PROX>
+__device__ __forceinline__ bool eval_skip(int it, DevState* st) {
+  if (TRIAL) return st->stop || st->ls_done;
+  if (it >= 0) {
+    if (st->stop) return true;
     if (st->coef_fresh) {
-      if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->J = st->Jn; st->D = st->Dn; st->S = st->Sn; st->P = st->Pn;
         if (PROX) st->Jacc = st->Jn;
         st->gnorm = st->gnorm_n;
@@ -58,157 +47,214 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
         st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
         st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
       }
-      return;
+      return true;
     }
-  } else if (it < -1 && st->stop) {
-    return;   // it = -2: a fresh evaluation unless the run has stopped
+    return false;
   }
-  const int inner = g.inner, m = g.m;
-  const int lane = threadIdx.x & 31;
-  const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
+  return it < -1 && st->stop;   // it = -2: a fresh evaluation unless the run has stopped
+}
+
+// The finisher of an objective launch (the last block, after the grid sum of D, S, P, sum g^2,
+// grad^T q and, with PROX, ||b - c||^2): J and its terms into the device state, and for the
+// trial the Armijo decision for gamma = 1.
+template <bool TRIAL, bool PROX, int NV>
+__device__ __forceinline__ void eval_finish(const Geo& g, const double (&tot)[NV], float rho,
+                                            int it, int ls_max, double c1, DevState* st,
+                                            double* terms) {
+  double hv = 0.5 * (double)g.vol;
+  double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
+  double J = D + g.alpha_d * S + g.beta_d * P;
+  if (PROX) {
+    st->prox = hv * tot[NV - 1];
+    J += (double)rho * st->prox;
+  }
+  if (!TRIAL) {
+    st->J = J; st->D = D; st->S = S; st->P = P;
+    if (PROX) st->Jacc = J;
+    st->gnorm = sqrt(tot[3]);
+    st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
+    st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
+    st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
+    st->coef_fresh = 0;
+    if (it >= 0 && !isfinite(J)) { st->stop = 1; st->stop_iter = it; }
+    if (it == -1) st->stop = 0;   // a single evaluation starts no run
+    if (terms) {                  // a single evaluation's J, D, S, P for the caller
+      terms[0] = J; terms[1] = D; terms[2] = S; terms[3] = P;
+    }
+  } else {
+    double gq = tot[4];
+    st->gq = gq;
+    st->coef_fresh = 0;
+    if (!(gq < 0.0)) {             // not a descent direction: keep the iterate
+      st->ls_done = 1; st->gamma = 0.0; st->ls_trials = 0;
+    } else {
+      st->ls_trials = 1;
+      if (J <= st->J + c1 * gq) {  // Armijo with gamma = 1
+        st->ls_done = 1; st->gamma = 1.0;
+        if (PROX) st->Jacc = J;
+        st->coef_fresh = 1;
+        st->Jn = J; st->Dn = D; st->Sn = S; st->Pn = P;
+        st->gnorm_n = sqrt(tot[3]);
+        st->status_n = 0;
+      } else if (ls_max <= 1) {
+        st->ls_done = 1; st->gamma = 0.0;
+      }
+    }
+  }
+}
+
+// TRIAL = false: evaluation at b (GN iteration `it`, or it = -1 for a single hysco_eval call, or
+// it = -2 for a fresh evaluation that a stopped run skips).  In a solve, when the previous
+// gamma = 1 trial was accepted the coefficients at this iterate are already in place: one thread
+// promotes the stashed terms and every block returns at once (no block enters the reduction, so
+// the ticket counter is untouched).
+// TRIAL = true: the gamma = 1 Armijo trial, an evaluation at b + q.
+// PROX (the ADMM b-subproblem of Sec. 2.3.2): J gains rho vol/2 ||b - c||^2 (c pitched, rho the
+// device state's admm_rho), the gradient rho vol (b - c) and the GN coefficient d the constant rho;
+// with the split geometry (in-plane Laplacian weights 0) S is the PE part S3 alone.
+//
+// Column march: warp w owns the 32 consecutive columns of tile w % ntile (lane = column) and the
+// nodes of segment w / ntile; each thread walks its segment node by node with a rolling window
+// of one cell (the cell right of node k is evaluated once and reused as the cell left of node
+// k + 1), so the column's geometry, its neighbours' offsets and the constant part of the Jacobi
+// diagonal are set up once per segment.  Loads of U nodes are issued together before their
+// arithmetic.  A lane past the last column repeats the last column (identical values stored to
+// identical addresses) and adds nothing to the sums.
+template <typename TI, bool TRIAL, bool PROX, int U, int OUT>
+__global__ void __launch_bounds__(kBlock, kEvalMinBlocks)
+k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
+       const float* __restrict__ q, const float* __restrict__ cpx, float* __restrict__ grad,
+       float* __restrict__ grad_p, float* __restrict__ dco, float* __restrict__ eco,
+       float* __restrict__ invd, int it, int ls_max, double c1, float* partials,
+       unsigned* counter, DevState* st, double* terms) {
+  if (eval_skip<TRIAL, PROX>(it, st)) return;
+  const int inner = g.inner, m = g.m, psP = g.psP;
+  const float wA = g.wA, wB = g.wB, alpha = g.alpha, hbeta = g.half_beta, vol = g.vol;
   const float rho = PROX ? st->admm_rho : 0.f;
   float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f, accGQ = 0.f, accR = 0.f;
-  // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-  int c = (item % ncb) * kBlock + threadIdx.x;
-  const bool act = c < g.ncols;
-  c = act ? c : g.ncols - 1;
-  const int k0 = (item / ncb) * SEG;
-  const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-  const TI* Ipc = Ip + ib;
-  const TI* Imc = Im + ib;
-  const ColNbrs nb = col_nbrs(g, c, fb);
-  const int pb = col_pbase(g, c);
-  const ColNbrs nq = col_nbrs_pitched(g, c, pb);
-  const int cA = c % g.nA;
-  const bool hasAm = cA > 0, hasAp = cA < g.nA - 1;
-  // field value at user offset uo / pitched offset po (b, or b + q in the trial)
-  auto fld = [&](int uo, int po) {
-    float v = __ldg(b + uo);
-    return TRIAL ? fmaf(1.0f, __ldg(q + po), v) : v;
-  };
-
-  // column nodes k0-1 .. k0+SEG (clamped to [0, m]); B neighbours of k0 .. k0+SEG-1 by loads,
-  // A neighbours from the lanes beside (edge lanes load)
-  float bw[SEG + 2], bBm[SEG], bBp[SEG], eAm[SEG], eAp[SEG];
-#pragma unroll
-  for (int j = 0; j < SEG + 2; ++j) {
-    int kk = min(max(k0 - 1 + j, 0), m);
-    bw[j] = fld(fb + kk * inner, pb + kk * g.psP);
-  }
-#pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    int kk = min(k0 + j, m);
-    int o = kk * inner, op = kk * g.psP;
-    bBm[j] = fld(nb.Bm + o, nq.Bm + op);
-    bBp[j] = fld(nb.Bp + o, nq.Bp + op);
-    eAm[j] = (lane == 0 && hasAm) ? fld(nb.Am + o, nq.Am + op) : 0.f;
-    eAp[j] = (lane == 31 && hasAp) ? fld(nb.Ap + o, nq.Ap + op) : 0.f;
-  }
-  // grad^T q with the gradient at b (trial only), loaded before this thread overwrites it
-  if (TRIAL) {
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      int kk = min(k0 + j, m);
-      float gv = grad_p[pb + kk * g.psP], qv = __ldg(q + pb + kk * g.psP);
-      accGQ += (act && k0 + j <= m) ? gv * qv : 0.f;
-    }
-  }
-  // the cell left of node k0 (cell k0 - 1)
-  float pr, pjr, pdphi, ppsi;
-  {
-    CellLin cl = cell_lin(Ipc, Imc, inner, m, k0 - 1, bw[0], bw[1], g.half_beta);
-    bool cv = k0 >= 1;
-    pr = cv ? cl.r : 0.f; pjr = cv ? cl.jr : 0.f;
-    pdphi = cv ? cl.dphi : 0.f; ppsi = cv ? cl.psi : 0.f;
-  }
-#pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    const int k = k0 + j;
-    // the cell right of node k (cell k)
-    CellLin cl = cell_lin(Ipc, Imc, inner, m, k, bw[j + 1], bw[j + 2], g.half_beta);
-    const bool cv = k < m;
-    const float cr = cv ? cl.r : 0.f, cjl = cv ? cl.jl : 0.f, cjr = cv ? cl.jr : 0.f;
-    const float cdphi = cv ? cl.dphi : 0.f, cpsi = cv ? cl.psi : 0.f, cphi = cv ? cl.phi : 0.f;
-    const float bk = bw[j + 1], bn = bw[j + 2];
-    const float fromL = __shfl_up_sync(0xffffffffu, bk, 1);
-    const float fromR = __shfl_down_sync(0xffffffffu, bk, 1);
-    const float bAm = hasAm ? (lane > 0 ? fromL : eAm[j]) : bk;
-    const float bAp = hasAp ? (lane < 31 ? fromR : eAp[j]) : bk;
-    if (act && k <= m) {
-      float lap = (bk - bw[j]) + (bk - bn) + g.wA * ((bk - bAm) + (bk - bAp)) +
-                  g.wB * ((bk - bBm[j]) + (bk - bBp[j]));
-      float dPE = bn - bk, dA = bAp - bk, dB = bBp[j] - bk;
-      accS += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
-      accD += cr * cr;
-      accP += cphi;
-      const int pi = pb + k * g.psP;   // solver arrays are pitched
+  const int wid = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
+  const int seg = wid / g.ntile;
+  if (seg < g.nseg) {
+    int c = (wid - seg * g.ntile) * 32 + (threadIdx.x & 31);
+    const bool act = c < g.ncols;
+    c = act ? c : g.ncols - 1;
+    const int k0 = seg * g.mseg, k1 = min(k0 + g.mseg, g.E);
+    // column geometry: caller-layout bases (image, field), pitched base, in-plane neighbours
+    const int o = (int)fdiv((unsigned)c, g.divIn), ci = c - o * inner;
+    const int ib = o * (int)g.img_ostride + ci, fb = o * (int)g.fld_ostride + ci;
+    const int cB = (int)fdiv((unsigned)c, g.divA), cA = c - cB * g.nA;
+    const bool hAm = cA > 0, hAp = cA < g.nA - 1, hBm = cB > 0, hBp = cB < g.nB - 1;
+    auto fbase = [&](int cc) {
+      const int oo = (int)fdiv((unsigned)cc, g.divIn);
+      return oo * (int)g.fld_ostride + (cc - oo * inner);
+    };
+    // offsets of the neighbour columns from this one (0: absent, the node itself, so that its
+    // Laplacian difference vanishes)
+    const int uAm = hAm ? fbase(c - 1) - fb : 0, uAp = hAp ? fbase(c + 1) - fb : 0;
+    const int uBm = hBm ? fbase(c - g.nA) - fb : 0, uBp = hBp ? fbase(c + g.nA) - fb : 0;
+    const int pAm = hAm ? -g.psA : 0, pAp = hAp ? g.psA : 0;
+    const int pBm = hBm ? -g.psB : 0, pBp = hBp ? g.psB : 0;
+    const float nin = g.wA * (float)((int)hAm + (int)hAp) + g.wB * (float)((int)hBm + (int)hBp);
+    const float dg2 = g.alpha * (2.0f + nin), dg1 = g.alpha * (1.0f + nin);
+    const TI* Ipc = Ip + ib;
+    const TI* Imc = Im + ib;
+    // field value (b, or b + q in the trial) at caller offset uo / pitched offset po
+    auto fld = [&](int uo, int po) {
+      const float v = __ldg(b + uo);
+      return TRIAL ? v + __ldg(q + po) : v;
+    };
+    auto cell = [&](int j, float bj, float bj1) {
+      return cell_lin(Ipc, Imc, inner, m, j, bj, bj1, hbeta);
+    };
+    // node k from the cells left (P) and right (C) of it: gradient, GN coefficients, sums
+    auto node = [&](int k, const CellLin& P, const CellLin& C, float bk, float bAm, float bAp,
+                    float bBm, float bBp, float qk, float gpk, float ck, int uo, int po,
+                    float dgk) {
+      const float dAm = bk - bAm, dAp = bAp - bk, dBm = bk - bBm, dBp = bBp - bk;
+      const float lap = (P.dlt - C.dlt) + wA * (dAm - dAp) + wB * (dBm - dBp);
+      accS += C.dlt * C.dlt + wA * dAp * dAp + wB * dBp * dBp;
+      accD += C.r * C.r;
+      accP += C.phi;
       float prx = 0.f;
       if (PROX) {
-        prx = bk - __ldg(cpx + pi);
+        prx = bk - ck;
         accR += prx * prx;
       }
-      float gsum = pjr * pr + cjl * cr + g.alpha * lap + g.half_beta * (pdphi - cdphi);
+      float gsum = P.jr * P.r + C.jl * C.r + alpha * lap + hbeta * (P.dphi - C.dphi);
       if (PROX) gsum += rho * prx;
-      float gk = g.vol * gsum;
-      float dk = pjr * pjr + cjl * cjl + ppsi + cpsi;
+      const float gk = vol * gsum;
+      float dk = P.jr * P.jr + C.jl * C.jl + P.psi + C.psi;
       if (PROX) dk += rho;
-      float ek = cjl * cjr - cpsi;
-      float npe = (float)((k > 0) + (k < m));
-      float diag = g.vol * (dk + g.alpha * (npe + nb.nin));
-      if (grad) grad[fb + k * inner] = gk;
-      if (grad_p) grad_p[pi] = gk;
-      dco[pi] = dk;
-      eco[pi] = ek;
-      invd[pi] = diag > 0.f ? __fdividef(1.0f, diag) : 1.0f;
+      const float ek = C.jl * C.jr - C.psi;
+      const float diag = vol * (dk + dgk);
+      if (TRIAL) accGQ += gpk * qk;
+      if (OUT & 1) grad[uo] = gk;
+      if (OUT & 2) grad_p[po] = gk;
+      dco[po] = dk;
+      eco[po] = ek;
+      invd[po] = diag > 0.f ? __fdividef(1.0f, diag) : 1.0f;
       accG += gk * gk;
+    };
+
+    int uo = fb + k0 * inner, po = col_pbase(g, c) + k0 * psP;
+    float bk = fld(uo, po);
+    float qk = TRIAL ? __ldg(q + po) : 0.f;
+    CellLin P = cell_zero();
+    if (k0 > 0) P = cell(k0 - 1, fld(uo - inner, po - psP), bk);
+    const int kend = min(k1, m);   // nodes below kend have a cell on their right
+    int k = k0;
+    for (; k + U <= kend; k += U) {
+      float bn[U], qn[U], bAm[U], bAp[U], bBm[U], bBp[U], gp[U], cc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int uk = uo + u * inner, pk = po + u * psP;
+        bn[u] = fld(uk + inner, pk + psP);
+        qn[u] = TRIAL ? __ldg(q + pk + psP) : 0.f;
+        bAm[u] = fld(uk + uAm, pk + pAm);
+        bAp[u] = fld(uk + uAp, pk + pAp);
+        bBm[u] = fld(uk + uBm, pk + pBm);
+        bBp[u] = fld(uk + uBp, pk + pBp);
+        gp[u] = TRIAL ? grad_p[pk] : 0.f;
+        cc[u] = PROX ? __ldg(cpx + pk) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const CellLin C = cell(k + u, bk, bn[u]);
+        node(k + u, P, C, bk, bAm[u], bAp[u], bBm[u], bBp[u], qk, gp[u], cc[u],
+             uo + u * inner, po + u * psP, (k + u > 0) ? dg2 : dg1);
+        P = C;
+        bk = bn[u];
+        qk = qn[u];
+      }
+      uo += U * inner;
+      po += U * psP;
     }
-    pr = cr; pjr = cjr; pdphi = cdphi; ppsi = cpsi;
+    for (; k < k1; ++k) {   // the rest of the segment, and node m (no cell on its right)
+      const bool cv = k < m;
+      const float bn = cv ? fld(uo + inner, po + psP) : bk;
+      const float qnx = (TRIAL && cv) ? __ldg(q + po + psP) : 0.f;
+      const float gpk = TRIAL ? grad_p[po] : 0.f;
+      const float ck = PROX ? __ldg(cpx + po) : 0.f;
+      const CellLin C = cv ? cell(k, bk, bn) : cell_zero();
+      node(k, P, C, bk, fld(uo + uAm, po + pAm), fld(uo + uAp, po + pAp),
+           fld(uo + uBm, po + pBm), fld(uo + uBp, po + pBp), qk, gpk, ck, uo, po,
+           (k > 0 && k < m) ? dg2 : dg1);
+      P = C;
+      bk = bn;
+      qk = qnx;
+      uo += inner;
+      po += psP;
+    }
+    if (!act) {
+      accD = 0.f; accS = 0.f; accP = 0.f; accG = 0.f; accGQ = 0.f; accR = 0.f;
+    }
   }
-  }   // work items
   constexpr int NV = PROX ? 6 : 5;
   float v[NV];
   v[0] = accD; v[1] = accS; v[2] = accP; v[3] = accG; v[4] = accGQ;
   if (PROX) v[NV - 1] = accR;
   double tot[NV];
-  if (grid_sum<NV>(v, partials, counter, tot)) {
-    double hv = 0.5 * (double)g.vol;
-    double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
-    double J = D + g.alpha_d * S + g.beta_d * P;
-    if (PROX) {
-      st->prox = hv * tot[NV - 1];
-      J += (double)rho * st->prox;
-    }
-    if (!TRIAL) {
-      st->J = J; st->D = D; st->S = S; st->P = P;
-      if (PROX) st->Jacc = J;
-      st->gnorm = sqrt(tot[3]);
-      st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
-      st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
-      st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
-      st->coef_fresh = 0;
-      if (it >= 0 && !isfinite(J)) { st->stop = 1; st->stop_iter = it; }
-    } else {
-      double gq = tot[4];
-      st->gq = gq;
-      st->coef_fresh = 0;
-      if (!(gq < 0.0)) {             // not a descent direction: keep the iterate
-        st->ls_done = 1; st->gamma = 0.0; st->ls_trials = 0;
-      } else {
-        st->ls_trials = 1;
-        if (J <= st->J + c1 * gq) {  // Armijo with gamma = 1
-          st->ls_done = 1; st->gamma = 1.0;
-          if (PROX) st->Jacc = J;
-          st->coef_fresh = 1;
-          st->Jn = J; st->Dn = D; st->Sn = S; st->Pn = P;
-          st->gnorm_n = sqrt(tot[3]);
-          st->status_n = 0;
-        } else if (ls_max <= 1) {
-          st->ls_done = 1; st->gamma = 0.0;
-        }
-      }
-    }
-  }
+  if (grid_sum<NV>(v, partials, counter, tot)) eval_finish<TRIAL, PROX, NV>(g, tot, rho, it, ls_max, c1, st, terms);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -355,8 +401,9 @@ k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, doub
   }
 }
 
-// corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta)
-template <typename TI>
+// corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta); MEAN: their average
+// 1/2 (T+ + T-) into Tp
+template <typename TI, bool MEAN>
 __global__ void __launch_bounds__(kBlock)
 k_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
           float* __restrict__ Tp, float* __restrict__ Tm) {
@@ -375,8 +422,13 @@ k_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const flo
     interp(Ip + ib, inner, m, ip, wp, vp, sp);
     interp(Im + ib, inner, m, im, wm, vm, sm);
     float delta = bn - bj;
-    Tp[ib + j * inner] = vp * (1.0f + delta);
-    Tm[ib + j * inner] = vm * (1.0f - delta);
+    const float tpv = vp * (1.0f + delta), tmv = vm * (1.0f - delta);
+    if (MEAN) {
+      Tp[ib + j * inner] = 0.5f * (tpv + tmv);
+    } else {
+      Tp[ib + j * inner] = tpv;
+      Tm[ib + j * inner] = tmv;
+    }
     bj = bn;
   }
 }
@@ -397,9 +449,6 @@ k_cells(Geo g, const float* __restrict__ b, int* __restrict__ cp, int* __restric
   }
 }
 
-__global__ void k_publish_terms(double* terms, const DevState* st) {
-  terms[0] = st->J; terms[1] = st->D; terms[2] = st->S; terms[3] = st->P;
-}
 
 // ------------------------------------------------------------------------------------------
 
@@ -429,19 +478,59 @@ static dim3 resident_grid(const Geo& g, int per_sm = 4) {
     default: { using T = __half; __VA_ARGS__; break; }                                 \
   }
 
+void set_march(Geo& g, int device) {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      sms <= 0)
+    sms = 148;
+  g.divIn = make_fastdiv((unsigned)g.inner);
+  g.divA = make_fastdiv((unsigned)g.nA);
+  g.ntile = ceil_div(g.ncols, 32);
+  // resident warps: the fewest blocks per SM of any objective kernel, 8 warps each
+  int per_sm = 64;
+  auto occ = [&](const void* f) {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, kBlock, 0) == cudaSuccess && n > 0)
+      per_sm = std::min(per_sm, n);
+  };
+  occ((const void*)k_eval<float, false, false, kEvalU, 2>);
+  occ((const void*)k_eval<float, true, false, kEvalUTrial, 2>);
+  occ((const void*)k_eval<__nv_bfloat16, false, false, kEvalU, 2>);
+  occ((const void*)k_eval<__nv_bfloat16, true, false, kEvalUTrial, 2>);
+  occ((const void*)k_eval<__half, false, false, kEvalU, 2>);
+  occ((const void*)k_eval<__half, true, false, kEvalUTrial, 2>);
+  if (per_sm == 64) per_sm = kEvalMinBlocks;
+  const int slots = sms * per_sm * (kBlock / 32);
+  const int most = ceil_div(g.E, kMinMarch);     // segments of at least kMinMarch nodes
+  int nseg = std::max(1, std::min(slots / g.ntile, most));
+  g.mseg = ceil_div(g.E, nseg);
+  g.nseg = ceil_div(g.E, g.mseg);
+}
+
+int eval_blocks(const Geo& g) { return ceil_div(g.ntile * g.nseg, kBlock / 32); }
+
+#define HYSCO_EVAL_LAUNCH(TRIAL, PROX, U, OUT)                                                  \
+  HYSCO_DISPATCH(dtype, T,                                                                      \
+    (k_eval<T, TRIAL, PROX, U, OUT><<<eval_blocks(g), kBlock, 0, s>>>(                          \
+        g, (const T*)Ip, (const T*)Im, b, q, cpx, grad, grad_p, dco, eco, invd, it, ls_max, c1,  \
+        w.partials, w.counter, w.st, terms)))
+
 cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im, const float* b,
                         float* grad, float* grad_p, float* dco, float* eco, float* invd, int it,
-                        const Work& w, cudaStream_t s, const float* cpx) {
+                        const Work& w, cudaStream_t s, const float* cpx, double* terms) {
+  const float* q = nullptr;
+  const int ls_max = 0;
+  const double c1 = 0.0;
   if (cpx) {
-    HYSCO_DISPATCH(dtype, T,
-      (k_eval<T, kSeg, false, true><<<resident_grid(g), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, nullptr, cpx, grad, grad_p, dco, eco, invd, it, 0,
-          0.0, w.partials, w.counter, w.st)))
+    HYSCO_EVAL_LAUNCH(false, true, kEvalUTrial, 2)
+  } else if (grad && !grad_p) {
+    HYSCO_EVAL_LAUNCH(false, false, kEvalU, 1)
+  } else if (!grad && grad_p) {
+    HYSCO_EVAL_LAUNCH(false, false, kEvalU, 2)
+  } else if (!grad && !grad_p) {
+    HYSCO_EVAL_LAUNCH(false, false, kEvalU, 0)
   } else {
-    HYSCO_DISPATCH(dtype, T,
-      (k_eval<T, kSeg, false, false><<<resident_grid(g), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, nullptr, nullptr, grad, grad_p, dco, eco, invd, it,
-          0, 0.0, w.partials, w.counter, w.st)))
+    HYSCO_EVAL_LAUNCH(false, false, kEvalU, 3)
   }
   return cudaGetLastError();
 }
@@ -450,16 +539,13 @@ cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const voi
                               const float* b, const float* q, float* grad_p, float* dco,
                               float* eco, float* invd, int ls_max, double c1, const Work& w,
                               cudaStream_t s, const float* cpx) {
+  float* grad = nullptr;
+  double* terms = nullptr;
+  const int it = 0;
   if (cpx) {
-    HYSCO_DISPATCH(dtype, T,
-      (k_eval<T, kSeg, true, true><<<resident_grid(g), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, q, cpx, nullptr, grad_p, dco, eco, invd, 0, ls_max,
-          c1, w.partials, w.counter, w.st)))
+    HYSCO_EVAL_LAUNCH(true, true, kEvalUTrial, 2)
   } else {
-    HYSCO_DISPATCH(dtype, T,
-      (k_eval<T, kSeg, true, false><<<resident_grid(g), kBlock, 0, s>>>(
-          g, (const T*)Ip, (const T*)Im, b, q, nullptr, nullptr, grad_p, dco, eco, invd, 0,
-          ls_max, c1, w.partials, w.counter, w.st)))
+    HYSCO_EVAL_LAUNCH(true, false, kEvalUTrial, 2)
   }
   return cudaGetLastError();
 }
@@ -500,9 +586,15 @@ cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double
 
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s) {
-  HYSCO_DISPATCH(dtype, T,
-    (k_correct<T><<<march_grid(g, g.m), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, Tp,
-                                                         Tm)))
+  if (Tm) {
+    HYSCO_DISPATCH(dtype, T,
+      (k_correct<T, false><<<march_grid(g, g.m), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b,
+                                                                  Tp, Tm)))
+  } else {
+    HYSCO_DISPATCH(dtype, T,
+      (k_correct<T, true><<<march_grid(g, g.m), kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b,
+                                                                 Tp, nullptr)))
+  }
   return cudaGetLastError();
 }
 
@@ -511,9 +603,5 @@ cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_publish_terms(double* terms, const Work& w, cudaStream_t s) {
-  k_publish_terms<<<1, 1, 0, s>>>(terms, w.st);
-  return cudaGetLastError();
-}
 
 }  // namespace hysco

@@ -10,8 +10,12 @@
 // (the band; edges kept in a rolling register window) and rhs_j += P_ij I[i].  Each row goes
 // straight into one step of a banded LDL^T factorisation with the forward substitution L y = rhs
 // fused in (the last four columns of L and D in registers); L and D^{-1} y go to scratch for the
-// back substitution L^T x = D^{-1} y into the output.  A column whose field has |delta| >= 1, or
-// whose band would be wider than kLsBand (|delta| above about 0.75), is set to 0 and counted.
+// back substitution L^T x = D^{-1} y into the output.  A column whose field has |delta| >= 1 is
+// set to 0 and counted.  The band a column needs grows with its compression (true cells j and
+// j + d share a distorted cell when the d - 1 cells between them shrink by more than d - 2 in
+// total): a first pass with half-width 4 (|delta| up to about 0.75) serves most columns and flags
+// the others, which a second pass with half-width 16 (|delta| up to about 0.94) redoes; a column
+// wider still is set to 0 and counted.
 #include "eval_common.cuh"
 
 namespace hysco {
@@ -23,18 +27,43 @@ __device__ __forceinline__ float overlap(int i, float e0, float e1) {
   return fmaxf(0.f, fminf(e1, (float)i + 0.5f) - fmaxf(e0, (float)i - 0.5f));
 }
 
-template <typename TI>
+// PASS 0: every column, half-width kLsBand, columns whose band is too narrow flagged in `wide`
+// (their output left to pass 1).  PASS 1: the flagged columns only, half-width BAND.  STAGED: the
+// block's two image columns are first copied to shared memory (rows of kLsColBlock consecutive
+// columns, coalesced), so the per-row gathers of the sequential factorisation are shared loads.
+template <typename TI, int BAND, int PASS, bool STAGED>
 __global__ void __launch_bounds__(kLsColBlock)
 k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
-             const float* __restrict__ b, float lambda, LsBand band, float* __restrict__ rhs,
-             float* __restrict__ out, int* __restrict__ nbad) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= g.ncols) return;
+             const float* __restrict__ b, float lambda, float* __restrict__ band,
+             long long bstride, float* __restrict__ rhs, float* __restrict__ out,
+             int* __restrict__ nbad, int* __restrict__ wide) {
+  constexpr int kLsBand = BAND;
+  extern __shared__ float simg[];   // STAGED: [2][m][kLsColBlock]
+  const int c0 = blockIdx.x * blockDim.x, tid = threadIdx.x;
+  const int c = c0 + tid;
+  bool live = c < g.ncols && (PASS == 0 || wide[c]);
+  if (PASS == 1 && !__syncthreads_or(live)) return;   // no flagged column in this block
   const int inner = g.inner, m = g.m;
+  if (STAGED) {
+    // row i of both images for the block's columns (a lane per column; absent columns read 0)
+    const int nw = blockDim.x >> 5, lane = tid & 31, w = tid >> 5;
+    for (int s = 0; s < 2; ++s) {
+      const TI* img = s == 0 ? Ip : Im;
+      float* dst = simg + (size_t)s * m * kLsColBlock;
+      for (int cc = lane; cc < kLsColBlock; cc += 32) {
+        const int col = c0 + cc;
+        const int cb = col < g.ncols ? col_base(col, inner, g.img_ostride) : 0;
+        for (int i = w; i < m; i += nw)
+          dst[i * kLsColBlock + cc] = col < g.ncols ? ldf(img + cb + i * inner) : 0.f;
+      }
+    }
+    __syncthreads();
+  }
+  if (!live) return;
   const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-  auto Lst = [&](int d, int j) -> float& { return band.d[d][ib + j * inner]; };   // L[j+1+d][j]
+  auto Lst = [&](int d, int j) -> float& { return band[d * bstride + ib + j * inner]; };   // L[j+1+d][j]
   auto Z = [&](int j) -> float& { return rhs[ib + j * inner]; };                 // D^-1 y
-  bool ok = true;
+  bool ok = true, narrow = false;
   // rolling field window: bw[u] = b at node j + u, u = 0 .. kLsBand + 1; and the reciprocal
   // lengths 1 / (e_{j+u+1} - e_{j+u}) of the mapped cells for both directions
   float bw[kLsBand + 2], ilp[kLsBand + 1], ilm[kLsBand + 1];
@@ -58,7 +87,7 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     float N[kLsBand + 1], r = 0.f;
 #pragma unroll
     for (int d = 0; d <= kLsBand; ++d) N[d] = d == 0 ? lambda : 0.f;
-    if (!(fabsf(bw[1] - bw[0]) < 1.0f)) ok = false;
+    if (!(fabsf(bw[1] - bw[0]) < 1.0f)) { ok = false; narrow = false; }
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       const float sg = s == 0 ? 1.0f : -1.0f;
@@ -68,11 +97,15 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
       const float* il = s == 0 ? ilp : ilm;
       const int ilo = max((int)floorf(e[0] + 0.5f), 0), ihi = min((int)floorf(e[1] + 0.5f), m - 1);
       // cells past j + kLsBand must not reach the last distorted cell of this row
-      if (j + kLsBand + 1 < m && (float)ihi + 0.5f > e[kLsBand + 1]) ok = false;
+      if (ok && j + kLsBand + 1 < m && (float)ihi + 0.5f > e[kLsBand + 1]) {
+        ok = false;
+        narrow = true;
+      }
       const TI* img = (s == 0 ? Ip : Im) + ib;
+      const float* simgc = simg + (size_t)s * m * kLsColBlock + tid;
       for (int i = ilo; i <= ihi; ++i) {
         const float pij = overlap(i, e[0], e[1]) * il[0];
-        r += pij * ldf(img + i * inner);
+        r += pij * (STAGED ? simgc[i * kLsColBlock] : ldf(img + i * inner));
 #pragma unroll
         for (int d = 0; d <= kLsBand; ++d)
           if (j + d < m) N[d] += pij * overlap(i, e[d], e[d + 1]) * il[d];
@@ -120,45 +153,78 @@ k_ls_correct(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     ilm[kLsBand] = 1.0f / (1.0f - (bw[kLsBand + 1] - bw[kLsBand]));
   }
   if (!ok) {
+    // a band too narrow in pass 0 (the field itself feasible so far): pass 1 redoes the column
+    // (an infeasible cell further on is found there); otherwise the column is set to 0, counted
+    if (PASS == 0 && narrow) {
+      wide[c] = 1;
+      return;
+    }
     for (int j = 0; j < m; ++j) out[ib + j * inner] = 0.f;
     atomicAdd(nbad, 1);
     return;
   }
-  // ---- L^T x = D^{-1} y -----------------------------------------------------------------------
+  // ---- L^T x = D^{-1} y (rows of L and D^{-1} y loaded ahead of the recurrence) --------------
+  constexpr int kAhead = BAND <= 4 ? 8 : 2;
   float xw[kLsBand];
 #pragma unroll
   for (int t = 0; t < kLsBand; ++t) xw[t] = 0.f;   // x_{j+1+t}
-  for (int j = m - 1; j >= 0; --j) {
-    float x = Z(j);
+  for (int j1 = m - 1; j1 >= 0; j1 -= kAhead) {
+    float zv[kAhead], lv[kAhead][kLsBand];
 #pragma unroll
-    for (int d = 0; d < kLsBand; ++d) x -= Lst(d, j) * xw[d];
+    for (int u = 0; u < kAhead; ++u) {
+      const int j = max(j1 - u, 0);
+      zv[u] = Z(j);
 #pragma unroll
-    for (int t = kLsBand - 1; t > 0; --t) xw[t] = xw[t - 1];
-    xw[0] = x;
-    out[ib + j * inner] = x;
+      for (int d = 0; d < kLsBand; ++d) lv[u][d] = Lst(d, j);
+    }
+#pragma unroll
+    for (int u = 0; u < kAhead; ++u) {
+      if (j1 - u < 0) break;
+      float x = zv[u];
+#pragma unroll
+      for (int d = 0; d < kLsBand; ++d) x -= lv[u][d] * xw[d];
+#pragma unroll
+      for (int t = kLsBand - 1; t > 0; --t) xw[t] = xw[t - 1];
+      xw[0] = x;
+      out[ib + (j1 - u) * inner] = x;
+    }
   }
 }
 
 cudaError_t launch_ls_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
-                              const float* b, float lambda, LsBand band, float* rhs, float* out,
-                              int* nbad, cudaStream_t s) {
+                              const float* b, float lambda, float* band, long long bstride,
+                              float* rhs, float* out, int* nbad, int* wide, cudaStream_t s) {
   const dim3 grid(ceil_div(g.ncols, kLsColBlock));
+  cudaError_t e = cudaMemsetAsync(wide, 0, sizeof(int) * (size_t)g.ncols, s);
+  if (e != cudaSuccess) return e;
+  // stage the images in shared memory when a block's two image columns fit
+  const size_t smem = 2ull * g.m * kLsColBlock * sizeof(float);
+  const bool staged = smem <= 160 * 1024;
+  auto run = [&](auto tag) -> cudaError_t {
+    using T = decltype(tag);
+    if (staged) {
+      for (const void* f : {(const void*)k_ls_correct<T, kLsBand, 0, true>,
+                            (const void*)k_ls_correct<T, kLsBandWide, 1, true>})
+        if (cudaError_t ea = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)smem))
+          return ea;
+      k_ls_correct<T, kLsBand, 0, true><<<grid, kLsColBlock, smem, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, lambda, band, bstride, rhs, out, nbad, wide);
+      k_ls_correct<T, kLsBandWide, 1, true><<<grid, kLsColBlock, smem, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, lambda, band, bstride, rhs, out, nbad, wide);
+    } else {
+      k_ls_correct<T, kLsBand, 0, false><<<grid, kLsColBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, lambda, band, bstride, rhs, out, nbad, wide);
+      k_ls_correct<T, kLsBandWide, 1, false><<<grid, kLsColBlock, 0, s>>>(
+          g, (const T*)Ip, (const T*)Im, b, lambda, band, bstride, rhs, out, nbad, wide);
+    }
+    return cudaGetLastError();
+  };
   switch (dtype) {
-    case 0:
-      k_ls_correct<float><<<grid, kLsColBlock, 0, s>>>(g, (const float*)Ip, (const float*)Im, b,
-                                                      lambda, band, rhs, out, nbad);
-      break;
-    case 1:
-      k_ls_correct<__nv_bfloat16><<<grid, kLsColBlock, 0, s>>>(
-          g, (const __nv_bfloat16*)Ip, (const __nv_bfloat16*)Im, b, lambda, band, rhs, out,
-          nbad);
-      break;
-    default:
-      k_ls_correct<__half><<<grid, kLsColBlock, 0, s>>>(g, (const __half*)Ip, (const __half*)Im,
-                                                       b, lambda, band, rhs, out, nbad);
-      break;
+    case 0: return run(float{});
+    case 1: return run(__nv_bfloat16{});
+    default: return run(__half{});
   }
-  return cudaGetLastError();
 }
 
 }  // namespace hysco

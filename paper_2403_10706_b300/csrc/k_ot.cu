@@ -9,8 +9,9 @@
 //     k* = min{j in [0, m-1] : C(j+1) >= r}    (binary search on the other image's CDF)
 //   and C^{-1}(r) = k* + (r - C(k*)) / (C(k*+1) - C(k*)), capped at m.  Then
 //     b0_k = 1/4 [ (C+^{-1}(C-(k)) - k) - (C-^{-1}(C+(k)) - k) ].
-// k_blur: separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
-//   voxel), replicate boundary, evaluated as one 27-point pass.
+// k_blur_axis: separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
+//   voxel), replicate boundary, one pass per axis.
+#include <algorithm>
 #include <cmath>
 
 #include "hysco_internal.cuh"
@@ -124,6 +125,19 @@ __device__ __forceinline__ float cdf_inverse(const float* C, int CW, int m, floa
   return fminf(x, (float)m);
 }
 
+// the same lookup with the bracket search started at kstar (a bracket of a smaller or equal r);
+// kstar is updated in place
+__device__ __forceinline__ float cdf_inverse_from(const float* C, int CW, int m, float r,
+                                                  int& kstar) {
+  if (r <= 0.f) { kstar = 0; return 0.f; }
+  int k = kstar;
+  while (k < m - 1 && !(C[(k + 1) * CW] >= r)) ++k;
+  kstar = k;
+  float c0 = C[k * CW], c1 = C[(k + 1) * CW];
+  float x = (float)k + (r - c0) / (c1 - c0);
+  return fminf(x, (float)m);
+}
+
 template <typename TI, bool INDICES>
 __global__ void __launch_bounds__(kBlock)
 k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restrict__ b0,
@@ -149,15 +163,26 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
     Cm[(k + 1) * CW + tx] = b;
   }
   __syncthreads();
-  if (ty == 0) {
-    float ap = 0.f, am = 0.f;
-    Cp[tx] = 0.f;
-    Cm[tx] = 0.f;
-    for (int k = 1; k <= m; ++k) {
-      ap = __fadd_rn(ap, Cp[k * CW + tx]);
-      am = __fadd_rn(am, Cm[k * CW + tx]);
-      Cp[k * CW + tx] = ap;
-      Cm[k * CW + tx] = am;
+  // cumulative sums, single precision, left to right: row 0 of threads scans I+, row 1 I-
+  // (eight rows loaded ahead of their dependent additions)
+  if (ty < 2) {
+    float* C = ty == 0 ? Cp : Cm;
+    float acc = 0.f;
+    C[tx] = 0.f;
+    int k = 1;
+    for (; k + 7 <= m; k += 8) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = C[(k + u) * CW + tx];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        acc = __fadd_rn(acc, v[u]);
+        C[(k + u) * CW + tx] = acc;
+      }
+    }
+    for (; k <= m; ++k) {
+      acc = __fadd_rn(acc, C[k * CW + tx]);
+      C[k * CW + tx] = acc;
     }
   }
   __syncthreads();
@@ -172,68 +197,53 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
   __syncthreads();
   if (!act) return;
   int fb = col_base(c, g.inner, g.fld_ostride);
-  for (int k = ty; k <= m; k += blockDim.y) {
+  // thread row ty takes the nodes [ka, kb): C+(k) and C-(k) do not decrease with k, so each
+  // bracket min{j : C(j+1) >= r} is found from the previous node's by walking forward (the same
+  // index a binary search finds), after one binary search at the run's first node
+  const int L = ceil_div(E, (int)blockDim.y), ka = ty * L, kb = min(ka + L, E);
+  int jp = -1, jm = -1;
+  for (int k = ka; k < kb; ++k) {
     int i = fb + k * g.inner;
     if (!ok) {
       b0[i] = 0.f;
       if (INDICES) { kp[i] = 0; km[i] = 0; }
       continue;
     }
-    int jp, jm;
-    float xp = cdf_inverse(Cm + tx, CW, m, Cp[k * CW + tx], jp);   // C-^{-1}(C+(k))
-    float xm = cdf_inverse(Cp + tx, CW, m, Cm[k * CW + tx], jm);   // C+^{-1}(C-(k))
+    const float rp = Cp[k * CW + tx], rm = Cm[k * CW + tx];
+    float xp, xm;
+    if (jp < 0) {
+      xp = cdf_inverse(Cm + tx, CW, m, rp, jp);   // C-^{-1}(C+(k))
+      xm = cdf_inverse(Cp + tx, CW, m, rm, jm);   // C+^{-1}(C-(k))
+    } else {
+      xp = cdf_inverse_from(Cm + tx, CW, m, rp, jp);
+      xm = cdf_inverse_from(Cp + tx, CW, m, rm, jm);
+    }
     float kf = (float)k;
     b0[i] = 0.25f * ((xm - kf) - (xp - kf));
     if (INDICES) { kp[i] = jp; km[i] = jm; }
   }
 }
 
-// 27-point separable Gaussian with replicate boundary on the field grid
+// one axis of the separable Gaussian: out_k = w1 x_{k-s} + w0 x_k + w1 x_{k+s} along axis AX of
+// the field (caller's layout), replicate boundary; one node per thread
+template <int AX>
 __global__ void __launch_bounds__(kBlock)
-k_blur(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
-  const int seg = kSeg;
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  int k0 = blockIdx.y * seg, k1 = min(k0 + seg, g.E);
-  if (c >= g.ncols) return;
-  int cA = c % g.nA, cB = c / g.nA;
-  int base[3][3];
-  float wt[3] = {w1, w0, w1};
-#pragma unroll
-  for (int db = -1; db <= 1; ++db)
-#pragma unroll
-    for (int da = -1; da <= 1; ++da) {
-      int a = min(max(cA + da, 0), g.nA - 1), bb = min(max(cB + db, 0), g.nB - 1);
-      base[db + 1][da + 1] = col_base(bb * g.nA + a, g.inner, g.fld_ostride);
+k_blur_axis(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
+  const int T = gridDim.x * blockDim.x;
+  const int s = g.fs[AX], ext = g.fe[AX];
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nf; n += T) {
+    int i;
+    if (AX == 0) {
+      i = (int)fdiv((unsigned)n, g.div0);
+    } else if (AX == 1) {
+      const unsigned row = fdiv((unsigned)n, g.divfe2);
+      i = (int)(row - fdiv(row, g.divfe1) * (unsigned)g.fe[1]);
+    } else {
+      i = n - (int)fdiv((unsigned)n, g.divfe2) * g.fe[2];
     }
-  // rolling window along the column: win[db][da][dk] holds the neighbour column's value at
-  // node clamp(k - 1 + dk), so each node loads the nine values at k + 1 only (same sums)
-  float win[3][3][3];
-#pragma unroll
-  for (int db = 0; db < 3; ++db)
-#pragma unroll
-    for (int da = 0; da < 3; ++da) {
-      win[db][da][1] = __ldg(in + base[db][da] + max(k0 - 1, 0) * g.inner);
-      win[db][da][2] = __ldg(in + base[db][da] + k0 * g.inner);
-    }
-  for (int k = k0; k < k1; ++k) {
-    const int kn = min(k + 1, g.E - 1);
-    float acc = 0.f;
-#pragma unroll
-    for (int db = 0; db < 3; ++db) {
-      float accb = 0.f;
-#pragma unroll
-      for (int da = 0; da < 3; ++da) {
-        win[db][da][0] = win[db][da][1];
-        win[db][da][1] = win[db][da][2];
-        win[db][da][2] = __ldg(in + base[db][da] + kn * g.inner);
-        float acca = 0.f;
-#pragma unroll
-        for (int dk = 0; dk < 3; ++dk) acca += wt[dk] * win[db][da][dk];
-        accb += wt[da] * acca;
-      }
-      acc += wt[db] * accb;
-    }
-    out[col_base(c, g.inner, g.fld_ostride) + k * g.inner] = acc;
+    const float xm = __ldg(in + (i > 0 ? n - s : n));
+    const float xp = __ldg(in + (i < ext - 1 ? n + s : n));
+    out[n] = w1 * xm + w0 * __ldg(in + n) + w1 * xp;
   }
 }
 
@@ -281,11 +291,14 @@ cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, f
              : ot_one<__half, false>(g, Ip, Im, b0, kp, km, w, s);
 }
 
-cudaError_t launch_blur(const Geo& g, const float* in, float* out, cudaStream_t s) {
+// three one-axis passes (axis 0, 1, 2): in -> out -> in -> out (in is scratch afterwards)
+cudaError_t launch_blur(const Geo& g, float* in, float* out, cudaStream_t s) {
   double e = std::exp(-0.5);   // the sigma = 1 Gaussian at distance 1 voxel
   float w0 = (float)(1.0 / (1.0 + 2.0 * e)), w1 = (float)(e / (1.0 + 2.0 * e));
-  k_blur<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(g.E, kSeg)), kBlock, 0, s>>>(g, in, out, w0,
-                                                                                 w1);
+  const int blocks = std::min(ceil_div(g.nf, kBlock), 148 * 8);
+  k_blur_axis<0><<<blocks, kBlock, 0, s>>>(g, in, out, w0, w1);
+  k_blur_axis<1><<<blocks, kBlock, 0, s>>>(g, out, in, w0, w1);
+  k_blur_axis<2><<<blocks, kBlock, 0, s>>>(g, in, out, w0, w1);
   return cudaGetLastError();
 }
 

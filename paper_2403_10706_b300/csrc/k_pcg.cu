@@ -170,96 +170,79 @@ k_from_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// per-column block preconditioner: the exact tridiagonal diagonal block of H per PE column,
-//   dia_k = vol [d_k + alpha (npe_k + nin)],  off_k = vol [e_k - alpha],
-// factored once per GN iteration (LDL^T, l_k = off_k / D_k, D_{k+1} = dia_{k+1} - l_k off_k)
-// and applied per PCG iteration by a forward and a backward sweep.
-// Tile: CW consecutive columns (lanes) x (kBlock / CW) rows; the tile is staged through shared
-// memory with coalesced row accesses and one thread per column runs the sequential sweep.
-// ------------------------------------------------------------------------------------------
+// Per-column block preconditioner (end of Sec. 2.3.1): one thread per PE column marches along it
+// in registers (coalesced row loads across the warp, eight nodes loaded ahead of their sequential
+// recurrence), so every thread of the grid does useful work and no shared memory is needed.
+//   M = tridiag(vol (e_k - alpha), vol (d_k + alpha (npe_k + nin)), vol (e_k - alpha)), M = L D L^T:
+//   D_0 = dia_0, l_k = off_k / D_k, D_{k+1} = dia_{k+1} - l_k off_k; stored 1 / D_k and l_k.
+constexpr int kColAhead = 8;
 
-int column_tile_width(int E) {
-  // three E x CW float arrays must fit in shared memory
-  if (12LL * E * 32 <= 200 * 1024) return 32;
-  if (12LL * E * 16 <= 200 * 1024) return 16;
-  return 8;
+struct ColPos {
+  int base;     // pitched offset of node 0
+  float nin;    // in-plane part of L_kk
+};
+__device__ __forceinline__ ColPos col_pos(const Geo& g, int c) {
+  const int cB = c / g.nA, cA = c - cB * g.nA;
+  ColPos q;
+  q.base = cB * g.psB + cA * g.psA;
+  q.nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
+  return q;
 }
 
 __global__ void __launch_bounds__(kBlock)
 k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco,
              float* __restrict__ invD, float* __restrict__ lco) {
-  extern __shared__ float sm[];
-  const int CW = blockDim.x, E = g.E;
-  float* dia = sm;            // [E][CW]
-  float* off = sm + E * CW;   // [E][CW]
-  int tx = threadIdx.x, ty = threadIdx.y;
-  int c = blockIdx.x * CW + tx;
-  bool act = c < g.ncols;
-  int fb = act ? col_pbase(g, c) : 0;
-  float nin = 0.f;
-  if (act) {
-    int cA = c % g.nA, cB = c / g.nA;
-    nin = g.wA * (float)((cA > 0) + (cA < g.nA - 1)) + g.wB * (float)((cB > 0) + (cB < g.nB - 1));
-  }
-  for (int k = ty; k < E; k += blockDim.y) {
-    float dv = 1.f, ov = 0.f;
-    if (act) {
-      int i = fb + k * g.psP;
-      float npe = (float)((k > 0) + (k < g.m));
-      dv = g.vol * (__ldg(dco + i) + g.alpha * (npe + nin));
-      ov = k < g.m ? g.vol * (__ldg(eco + i) - g.alpha) : 0.f;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.ncols) return;
+  const ColPos cp = col_pos(g, c);
+  const int E = g.E, m = g.m, ps = g.psP, fb = cp.base;
+  // dia_0 (npe = 1: node 0 has one PE neighbour)
+  float D = g.vol * (__ldg(dco + fb) + g.alpha * (1.0f + cp.nin));
+  for (int k0 = 0; k0 < E - 1; k0 += kColAhead) {
+    float ev[kColAhead], dv[kColAhead];
+#pragma unroll
+    for (int u = 0; u < kColAhead; ++u) {
+      const int kk = min(k0 + u, E - 2);
+      ev[u] = __ldg(eco + fb + kk * ps);
+      dv[u] = __ldg(dco + fb + (kk + 1) * ps);
     }
-    dia[k * CW + tx] = dv;
-    off[k * CW + tx] = ov;
-  }
-  __syncthreads();
-  if (ty == 0) {
-    float D = dia[tx];
-    for (int k = 0; k < E - 1; ++k) {
-      float iD = 1.0f / D;
-      float ok = off[k * CW + tx];
-      float l = ok * iD;
-      dia[k * CW + tx] = iD;
-      off[k * CW + tx] = l;
-      D = fmaf(-l, ok, dia[(k + 1) * CW + tx]);   // D_{k+1} = dia_{k+1} - l_k off_k
+#pragma unroll
+    for (int u = 0; u < kColAhead; ++u) {
+      const int kk = k0 + u;
+      if (kk < E - 1) {
+        const float ok = g.vol * (ev[u] - g.alpha);
+        const float iD = 1.0f / D;
+        const float l = ok * iD;
+        invD[fb + kk * ps] = iD;
+        lco[fb + kk * ps] = l;
+        const float npe = (float)(1 + (kk + 1 < m));
+        D = fmaf(-l, ok, g.vol * (dv[u] + g.alpha * (npe + cp.nin)));
+      }
     }
-    dia[(E - 1) * CW + tx] = 1.0f / D;
-    off[(E - 1) * CW + tx] = 0.f;
   }
-  __syncthreads();
-  if (act)
-    for (int k = ty; k < E; k += blockDim.y) {
-      int i = fb + k * g.psP;
-      invD[i] = dia[k * CW + tx];
-      lco[i] = off[k * CW + tx];
-    }
+  invD[fb + (E - 1) * ps] = 1.0f / D;
+  lco[fb + (E - 1) * ps] = 0.f;
 }
 
-// mode 0: z = M^{-1} r.  mode 1: PCG init (r = sign * grad, x = 0).  mode 2: PCG update.
+// z = M^{-1} r per column (forward L y = r, backward L^T z = D^{-1} y; y kept in z).  MODE 0:
+// apply to r; MODE 1: PCG init (r = sign * grad, x = 0); MODE 2: PCG update (x += alpha p,
+// r -= alpha Hp) first.  MODE 1 / 2 reduce r.r and r.z and take the PCG decisions.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float* r,
             const float* __restrict__ p, const float* __restrict__ Hp, float* __restrict__ z,
             const float* __restrict__ invD, const float* __restrict__ lco, int first,
             double rtol, float sign, float* partials, unsigned* counter, DevState* st) {
-  extern __shared__ float sm[];
   if (MODE != 0 && st->stop) return;
   if (MODE == 2 && st->pcg_done) return;
-  const int CW = blockDim.x, E = g.E;
-  float* R = sm;               // r, then y, then z
-  float* L = sm + E * CW;
-  float* ID = sm + 2 * E * CW;
-  int tx = threadIdx.x, ty = threadIdx.y;
-  int c = blockIdx.x * CW + tx;
-  bool act = c < g.ncols;
-  int fb = act ? col_pbase(g, c) : 0;
-  float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
   float arr = 0.f, arz = 0.f;
-  for (int k = ty; k < E; k += blockDim.y) {
-    float rk = 0.f, lk = 0.f, idk = 1.f;
-    if (act) {
-      int i = fb + k * g.psP;
+  if (c < g.ncols) {
+    const int E = g.E, ps = g.psP, fb = col_pos(g, c).base;
+    const float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
+    // the residual at pitched offset i (MODE 1 / 2 also update x and r there)
+    auto resid = [&](int i) {
+      float rk;
       if (MODE == 0) {
         rk = r[i];
       } else if (MODE == 1) {
@@ -267,41 +250,56 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
         x[i] = 0.f;
         r[i] = rk;
       } else {
-        float pk = __ldg(p + i);
+        const float pk = __ldg(p + i);
         x[i] = first ? a * pk : fmaf(a, pk, x[i]);
         rk = fmaf(-a, __ldg(Hp + i), r[i]);
         r[i] = rk;
       }
-      lk = __ldg(lco + i);
-      idk = __ldg(invD + i);
-      arr += rk * rk;
+      return rk;
+    };
+    // forward: y_0 = r_0, y_k = r_k - l_{k-1} y_{k-1}
+    float y = resid(fb);
+    arr += y * y;
+    z[fb] = y;
+    for (int k0 = 1; k0 < E; k0 += kColAhead) {
+      float rv[kColAhead], lv[kColAhead];
+#pragma unroll
+      for (int u = 0; u < kColAhead; ++u) {
+        const int kk = min(k0 + u, E - 1);
+        lv[u] = __ldg(lco + fb + (kk - 1) * ps);
+        rv[u] = k0 + u < E ? resid(fb + kk * ps) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kColAhead; ++u)
+        if (k0 + u < E) {
+          arr += rv[u] * rv[u];
+          y = fmaf(-lv[u], y, rv[u]);
+          z[fb + (k0 + u) * ps] = y;
+        }
     }
-    R[k * CW + tx] = rk;
-    L[k * CW + tx] = lk;
-    ID[k * CW + tx] = idk;
+    // backward: z_{E-1} = y_{E-1} / D_{E-1}, z_k = y_k / D_k - l_k z_{k+1}
+    float zz = y * __ldg(invD + fb + (E - 1) * ps);
+    z[fb + (E - 1) * ps] = zz;
+    if (MODE != 0) arz += r[fb + (E - 1) * ps] * zz;
+    for (int k1 = E - 2; k1 >= 0; k1 -= kColAhead) {
+      float yv[kColAhead], lv[kColAhead], iv[kColAhead], rv[kColAhead];
+#pragma unroll
+      for (int u = 0; u < kColAhead; ++u) {
+        const int kk = max(k1 - u, 0);
+        yv[u] = z[fb + kk * ps];
+        lv[u] = __ldg(lco + fb + kk * ps);
+        iv[u] = __ldg(invD + fb + kk * ps);
+        rv[u] = MODE != 0 ? r[fb + kk * ps] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < kColAhead; ++u)
+        if (k1 - u >= 0) {
+          zz = fmaf(-lv[u], zz, yv[u] * iv[u]);
+          z[fb + (k1 - u) * ps] = zz;
+          if (MODE != 0) arz += rv[u] * zz;
+        }
+    }
   }
-  __syncthreads();
-  if (ty == 0) {
-    float y = R[tx];
-    for (int k = 1; k < E; ++k) {            // forward: y_k = r_k - l_{k-1} y_{k-1}
-      y = fmaf(-L[(k - 1) * CW + tx], y, R[k * CW + tx]);
-      R[k * CW + tx] = y;
-    }
-    float zz = y * ID[(E - 1) * CW + tx];    // backward: z_k = y_k / D_k - l_k z_{k+1}
-    R[(E - 1) * CW + tx] = zz;
-    for (int k = E - 2; k >= 0; --k) {
-      zz = fmaf(-L[k * CW + tx], zz, R[k * CW + tx] * ID[k * CW + tx]);
-      R[k * CW + tx] = zz;
-    }
-  }
-  __syncthreads();
-  if (act)
-    for (int k = ty; k < E; k += blockDim.y) {
-      int i = fb + k * g.psP;
-      float zk = R[k * CW + tx];
-      z[i] = zk;
-      if (MODE != 0) arz += r[i] * zk;
-    }
   if (MODE == 0) return;
   float v[2] = {arr, arz};
   double tot[2];
@@ -315,6 +313,27 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
       pcg_finish(st, tot[0], tot[1], rtol);
     }
   }
+}
+
+cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
+                              float* lco, cudaStream_t s) {
+  k_col_factor<<<ceil_div(g.ncols, kBlock), kBlock, 0, s>>>(g, dco, eco, invD, lco);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
+                             const float* p, const float* Hp, float* z, const float* invD,
+                             const float* lco, int first, double rtol, float sign,
+                             const Work& w, cudaStream_t s) {
+  const dim3 grid(ceil_div(g.ncols, kBlock));
+#define HYSCO_COLSOLVE(M)                                                                       \
+  k_col_solve<M><<<grid, kBlock, 0, s>>>(g, grad, x, r, p, Hp, z, invD, lco, first, rtol, sign, \
+                                         w.partials, w.counter, w.st);
+  if (mode == 0) { HYSCO_COLSOLVE(0) }
+  else if (mode == 1) { HYSCO_COLSOLVE(1) }
+  else { HYSCO_COLSOLVE(2) }
+#undef HYSCO_COLSOLVE
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -376,36 +395,5 @@ cudaError_t launch_from_pitched(const Geo& g, const float* src, float* dst, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
-                              float* lco, cudaStream_t s) {
-  int CW = column_tile_width(g.E);
-  size_t smem = 2ull * g.E * CW * sizeof(float);
-  cudaError_t e = cudaFuncSetAttribute(k_col_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_col_factor<<<ceil_div(g.ncols, CW), dim3(CW, kBlock / CW), smem, s>>>(g, dco, eco, invD, lco);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
-                             const float* p, const float* Hp, float* z, const float* invD,
-                             const float* lco, int first, double rtol, float sign,
-                             const Work& w, cudaStream_t s) {
-  int CW = column_tile_width(g.E);
-  size_t smem = 3ull * g.E * CW * sizeof(float);
-  dim3 grid(ceil_div(g.ncols, CW)), block(CW, kBlock / CW);
-  cudaError_t e;
-#define HYSCO_COLSOLVE(M)                                                                    \
-  e = cudaFuncSetAttribute(k_col_solve<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                           (int)smem);                                                       \
-  if (e != cudaSuccess) return e;                                                            \
-  k_col_solve<M><<<grid, block, smem, s>>>(g, grad, x, r, p, Hp, z, invD, lco, first, rtol,  \
-                                           sign, w.partials, w.counter, w.st);
-  if (mode == 0) { HYSCO_COLSOLVE(0) }
-  else if (mode == 1) { HYSCO_COLSOLVE(1) }
-  else { HYSCO_COLSOLVE(2) }
-#undef HYSCO_COLSOLVE
-  return cudaGetLastError();
-}
 
 }  // namespace hysco

@@ -40,35 +40,20 @@ namespace hysco {
 
 constexpr int kPcgUnroll = 4;
 
-struct PcgArgs {
-  const float* grad;     // right-hand side is rhs_sign * grad
-  float rhs_sign;
-  float* x;
-  float* r;
-  float* z;
-  float* p0;
-  float* p1;
-  float* Hp;
-  const float* dco;
-  const float* eco;
-  const float* invd;
-  unsigned* sync;        // arrival counter + 2 slots of partial sums; zeroed before every launch
-  DevState* st;
-  int max_it;
-  double rtol;
-  int onchip;            // slots per thread whose r, p, Hp are in shared memory
-};
+
+
+// The PCG of one problem on a group of blocks (the whole grid, or a block range of a batched
+// launch): grp.rank is this block's rank in the group, grp.size the group's block count; the
+// barriers span the group alone, with the problem's own sync words.
+
 
 template <int P>
-__global__ void __launch_bounds__(kPcgBlock)
-k_pcg_persistent(Geo g, PcgArgs a) {
-  __shared__ float shf[32 * 2];
-  __shared__ df32 shd[32 * 2];
-  extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kPcgBlock]
+__device__ __forceinline__ void pcg_run(const Geo& g, const PcgArgs& a, BarrierGroup grp,
+                                        float* shf, df32* shd, float4* slots) {
   DevState* st = a.st;
   if (st->stop) return;
-  const int T = gridDim.x * blockDim.x;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int T = grp.size * blockDim.x;
+  const int gtid = grp.rank * blockDim.x + threadIdx.x;
   const int n4 = g.nfp >> 2;   // float4 groups of the pitched field (padding is zero)
   const int G = a.onchip;
   float4* const rS = slots + threadIdx.x;
@@ -110,7 +95,10 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     }
     tot[0] = arr; tot[1] = arz;
   }
-  if (!grid_allreduce<2>(tot, a.sync, ++gen, shf, shd)) { timed_out(); return; }
+  if (!grid_allreduce<2>(tot, a.sync, ++gen, shf, shd, 0, -1, kBarrierSpinCycles, grp)) {
+    timed_out();
+    return;
+  }
   // scalars in single precision (the sums themselves are double-float accurate)
   const float rr0 = tot[0];
   float rho = tot[1], beta = 0.f, relres = rr0 > 0.f ? 1.f : 0.f;
@@ -151,7 +139,11 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     {
       // only p.Hp crosses blocks here (phase B reads the thread's own groups)
       float t1[1] = {acc};
-      if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd)) { timed_out(); return; }
+      if (!grid_allreduce_unordered(t1[0], a.sync, ++gen, shf, shd, 0, -1, kBarrierSpinCycles,
+                                    grp)) {
+        timed_out();
+        return;
+      }
       if (!(t1[0] > 0.f)) { done = true; break; }
       al = rho / t1[0];
       al_x = al;
@@ -210,7 +202,11 @@ k_pcg_persistent(Geo g, PcgArgs a) {
         }
       }
     };
-    if (!grid_allreduce_then<2>(tot, a.sync, ++gen, shf, shd, x_update)) { timed_out(); return; }
+    if (!grid_allreduce_then<2>(tot, a.sync, ++gen, shf, shd, x_update, 0, -1,
+                                kBarrierSpinCycles, grp)) {
+      timed_out();
+      return;
+    }
     it = i + 1;
     relres = sqrtf(tot[0]) / sqrtf(rr0);
     if (relres < (float)a.rtol) {
@@ -230,7 +226,7 @@ k_pcg_persistent(Geo g, PcgArgs a) {
       x4[t] = X;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (grp.rank == 0 && threadIdx.x == 0) {
     st->rr0 = rr0;
     st->rho = rho;
     st->beta_cg = beta;
@@ -238,6 +234,33 @@ k_pcg_persistent(Geo g, PcgArgs a) {
     st->relres = relres;
     st->pcg_done = 1;
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kPcgBlock)
+k_pcg_persistent(Geo g, PcgArgs a) {
+  __shared__ float shf[32 * 2];
+  __shared__ df32 shd[32 * 2];
+  extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kPcgBlock]
+  pcg_run<P>(g, a, whole_grid(), shf, shd, slots);
+}
+
+// Several problems' PCGs in one cooperative launch (a wave of a batch): problem i is worked on by
+// blocks w.blk0[i] .. w.blk0[i] + w.nblk[i] - 1 with its own arguments (its on-chip slots, its
+// sync words) and barriers among those blocks only, so the problems proceed independently.
+__global__ void __launch_bounds__(kPcgBlock)
+k_pcg_wave(const PcgWave wv) {
+  __shared__ float shf[32 * 2];
+  __shared__ df32 shd[32 * 2];
+  extern __shared__ float4 slots[];
+  int i = 0;
+  while (i + 1 < wv.n && (int)blockIdx.x >= wv.blk0[i + 1]) ++i;
+  if ((int)blockIdx.x >= wv.blk0[i] + wv.nblk[i]) return;   // spare blocks of the launch
+  const BarrierGroup grp{(int)blockIdx.x - wv.blk0[i], wv.nblk[i]};
+  const Geo& g = wv.g[i];
+  if (g.p == 0) pcg_run<0>(g, wv.a[i], grp, shf, shd, slots);
+  else if (g.p == 1) pcg_run<1>(g, wv.a[i], grp, shf, shd, slots);
+  else pcg_run<2>(g, wv.a[i], grp, shf, shd, slots);
 }
 
 // ==========================================================================================
@@ -553,6 +576,37 @@ cudaError_t launch_pcg_fused(const Geo& g, int grid, const float* grad, float rh
   void* fn = g.p == 0 ? (void*)k_pcg_fused<0>
                       : (g.p == 1 ? (void*)k_pcg_fused<1> : (void*)k_pcg_fused<2>);
   return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+}
+
+int pcg_wave_setup(int device) {
+  int sms = 0, coop = 0, optin = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess ||
+      !coop ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+          cudaSuccess)
+    return 0;
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, k_pcg_wave) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pcg_wave, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_wave, kPcgBlock,
+                                                    pcg_onchip_bytes(kWaveSlots)) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return std::min(sms, 32 * kTagWordsPerLane);   // one block per SM
+}
+
+cudaError_t launch_pcg_wave(const PcgWave& w, int grid, int onchip_max, unsigned* sync,
+                            size_t sync_words, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sync, 0, sync_words * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  PcgWave copy = w;
+  void* args[] = {&copy};
+  return cudaLaunchCooperativeKernel((void*)k_pcg_wave, dim3(grid), dim3(kPcgBlock), args,
+                                     pcg_onchip_bytes(onchip_max), s);
 }
 
 PcgPlan pcg_persistent_plan(int device, int pe_axis, int n4) {

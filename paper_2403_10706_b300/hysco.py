@@ -115,6 +115,27 @@ class Hysco:
                    "hysco_correct")
         return Tp, Tm
 
+    def correct_mean(self, Ip, Im, b):
+        """The corrected image 1/2 (Tp + Tm) (hysco_correct_mean)."""
+        T = torch.empty(self.dims, dtype=torch.float32, device=self.device)
+        _lib.check(self.lib.hysco_correct_mean(self._h, self._img(Ip, "Ip"), self._img(Im, "Im"),
+                                               self._fld(b, "b"), C.c_void_p(T.data_ptr()),
+                                               _stream(self.device)), "hysco_correct_mean")
+        return T
+
+    def correct_mean_adjoint(self, Ip, Im, b, gT, want=(True, True, True)):
+        """Adjoint of correct_mean for the upstream sensitivity gT: (dIp, dIm, db), each None when
+        not wanted."""
+        dIp = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[0] else None
+        dIm = torch.empty(self.dims, dtype=torch.float32, device=self.device) if want[1] else None
+        db = self._new_fld() if want[2] else None
+        p = lambda t: None if t is None else C.c_void_p(t.data_ptr())  # noqa: E731
+        _lib.check(self.lib.hysco_correct_mean_adjoint(
+            self._h, self._img(Ip, "Ip"), self._img(Im, "Im"), self._fld(b, "b"),
+            self._img_f32(gT, "gT"), p(dIp), p(dIm), p(db), _stream(self.device)),
+            "hysco_correct_mean_adjoint")
+        return dIp, dIm, db
+
     def ls_correct(self, Ip, Im, b, lam=1e-6):
         """Least-squares corrected image at b and the number of skipped columns."""
         out = torch.empty(self.dims, dtype=torch.float32, device=self.device)
@@ -340,7 +361,8 @@ class HyscoBatch:
     def schedule(self):
         """(branches, PCG policy, shared PCG grid blocks) in use; policy 0 / 1: one PCG launch
         shared by all pairs (blocks by field size, >= 1 / >= 2 per pair), 2: each pair's
-        persistent PCG in turn."""
+        persistent PCG in turn, 3 / 4 / 5: waves of pairs whose PCGs share one launch per GN step
+        (vectors packed to 1, 1.25, 1.5 times the on-chip capacity)."""
         out = (C.c_int32 * 3)()
         _lib.check(self.lib.hysco_batch_schedule(self._b, out), "hysco_batch_schedule")
         return tuple(out)

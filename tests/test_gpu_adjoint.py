@@ -275,3 +275,26 @@ def test_autograd_bf16_images_return_bf16_gradients(H):
     C.square().sum().backward()
     assert tIp.grad.dtype == torch.bfloat16 and tIm.grad.dtype == torch.bfloat16
     assert torch.isfinite(tIp.grad.float()).all()
+
+
+@pytest.mark.parametrize("dims,spacing,p", SHAPES)
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+def test_corrected_mean_and_its_adjoint(H, orc, dims, spacing, p, dt):
+    """hysco_correct_mean against the oracle's 1/2 (T+ + T-) (1e-5 of the largest intensity), and
+    its adjoint against hysco_correct_adjoint with both sensitivities gT / 2: halving is exact, so
+    the two adjoints agree bit for bit."""
+    Ip, Im, b, gT, _ = case(dims, p, 8100 + 7 * p)
+    h = H(dims, spacing, p, ALPHA, BETA, dtype=DT[dt])
+    tIp, tIm = dev(Ip, DT[dt]), dev(Im, DT[dt])
+    T = host(h.correct_mean(tIp, tIm, dev(b)))
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    ev = P.eval(host(tIp).astype(np.float32), host(tIm).astype(np.float32), b.astype(np.float64),
+                contract=True, grad=False, corrected=True)
+    ref = 0.5 * (ev["Tp"] + ev["Tm"])
+    assert np.abs(T - ref).max() <= 1e-5 * np.abs(ref).max()
+    tgT = dev(gT)
+    a = h.correct_mean_adjoint(tIp, tIm, dev(b), tgT)
+    half = (0.5 * tgT).contiguous()
+    r = h.correct_adjoint(tIp, tIm, dev(b), half, half)
+    for x, y in zip(a, r):
+        assert torch.equal(x, y)

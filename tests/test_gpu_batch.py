@@ -76,7 +76,7 @@ def test_batch_matches_oracle_per_pair(mods, problem):
     torch.cuda.synchronize()
     check_against_oracle(bs, sts, refs, hs, "default schedule")
     branches, policy, grid = batch.schedule()
-    assert 1 <= branches <= 8 and policy in (0, 1, 2) and grid >= len(hs)
+    assert 1 <= branches <= 8 and policy in (0, 1, 2, 3, 4, 5) and grid >= len(hs)
 
 
 def test_batch_graph_replay_equals_direct_launches(mods, problem):
@@ -95,10 +95,13 @@ def test_batch_graph_replay_equals_direct_launches(mods, problem):
             assert np.array_equal(outs[0][1][i], outs[k][1][i], equal_nan=True)
 
 
-@pytest.mark.parametrize("branches,policy", [(1, 0), (4, 1), (2, 2), (5, 2)])
+@pytest.mark.parametrize("branches,policy",
+                         [(1, 0), (4, 1), (2, 2), (5, 2), (1, 3), (4, 3), (2, 4), (3, 5)])
 def test_every_schedule_matches_oracle(mods, problem, branches, policy):
-    """Each PCG policy (shared launch with either block share, or the pairs' own persistent
-    kernels one after another) and branch count gives every pair the oracle's trajectory."""
+    """Each PCG policy (shared launch with either block share, the pairs' own persistent kernels
+    one after another, or waves of pairs sharing one launch per GN step with barriers per pair)
+    and branch count gives every pair the oracle's trajectory.  The five small pairs of this batch
+    fit one wave, so with policy 3 all five PCGs run in the same cooperative launch."""
     _, HyscoBatch = mods
     pairs, refs, hs, Ips, Ims = problem
     batch = HyscoBatch(hs)
@@ -115,7 +118,7 @@ def test_batch_tuner_picks_a_schedule_that_still_matches(mods, problem):
     batch = HyscoBatch(hs)
     sched = batch.tune(Ips, Ims, gn_iters=GN)
     assert sched == batch.schedule()
-    assert 1 <= sched[0] <= 8 and sched[1] in (0, 1, 2)
+    assert 1 <= sched[0] <= 8 and sched[1] in (0, 1, 2, 3, 4, 5)
     bs, sts = batch.solve(Ips, Ims, gn_iters=GN)
     torch.cuda.synchronize()
     check_against_oracle(bs, sts, refs, hs, f"tuned {sched}")
@@ -137,5 +140,5 @@ def test_batch_rejects_bad_arguments(mods, problem):
     assert rc == _lib.EINVAL   # the batched PCG is Jacobi only
     with pytest.raises(ValueError):
         batch.solve(Ips[:2], Ims[::-1][:2])   # pair 1's images have the wrong shape
-    for br, pol in ((0, 0), (3, 0), (1, 3), (1, -1)):   # 3 branches exceed the 2 pairs
+    for br, pol in ((0, 0), (3, 0), (1, 6), (1, -1)):   # 3 branches exceed the 2 pairs
         assert lib.hysco_batch_set_schedule(batch._b, br, pol) == _lib.EINVAL
