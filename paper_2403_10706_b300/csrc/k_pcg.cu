@@ -171,11 +171,13 @@ k_from_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
 }
 
 // Per-column block preconditioner (end of Sec. 2.3.1): one thread per PE column marches along it
-// in registers (coalesced row loads across the warp, eight nodes loaded ahead of their sequential
-// recurrence), so every thread of the grid does useful work and no shared memory is needed.
+// in registers (coalesced row loads across the warp), the loads of the next kColAhead nodes
+// issued before the sequential recurrence of the current ones (two register buffers), so that
+// every thread of the grid does useful work, no shared memory is needed, and the memory latency
+// of a column's march overlaps its arithmetic.
 //   M = tridiag(vol (e_k - alpha), vol (d_k + alpha (npe_k + nin)), vol (e_k - alpha)), M = L D L^T:
 //   D_0 = dia_0, l_k = off_k / D_k, D_{k+1} = dia_{k+1} - l_k off_k; stored 1 / D_k and l_k.
-constexpr int kColAhead = 8;
+constexpr int kColAhead = 16;
 
 struct ColPos {
   int base;     // pitched offset of node 0
@@ -189,6 +191,23 @@ __device__ __forceinline__ ColPos col_pos(const Geo& g, int c) {
   return q;
 }
 
+// Runs body(k0, buf) over blocks of kColAhead steps k0 = first, first + step, ... (n blocks),
+// with load(k0, buf) for block i + 1 issued before body of block i (two buffers).
+template <typename Buf, typename Load, typename Body>
+__device__ __forceinline__ void col_pipeline(int first, int step, int n, Load&& load,
+                                             Body&& body) {
+  Buf A, B;
+  if (n > 0) load(first, A);
+  for (int i = 0; i < n; i += 2) {
+    if (i + 1 < n) load(first + (i + 1) * step, B);
+    body(first + i * step, A);
+    if (i + 1 < n) {
+      if (i + 2 < n) load(first + (i + 2) * step, A);
+      body(first + (i + 1) * step, B);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kBlock)
 k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco,
              float* __restrict__ invD, float* __restrict__ lco) {
@@ -198,28 +217,31 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
   const int E = g.E, m = g.m, ps = g.psP, fb = cp.base;
   // dia_0 (npe = 1: node 0 has one PE neighbour)
   float D = g.vol * (__ldg(dco + fb) + g.alpha * (1.0f + cp.nin));
-  for (int k0 = 0; k0 < E - 1; k0 += kColAhead) {
-    float ev[kColAhead], dv[kColAhead];
+  struct Buf { float ev[kColAhead], dv[kColAhead]; };
+  auto load = [&](int k0, Buf& x) {
 #pragma unroll
     for (int u = 0; u < kColAhead; ++u) {
       const int kk = min(k0 + u, E - 2);
-      ev[u] = __ldg(eco + fb + kk * ps);
-      dv[u] = __ldg(dco + fb + (kk + 1) * ps);
+      x.ev[u] = __ldg(eco + fb + kk * ps);
+      x.dv[u] = __ldg(dco + fb + (kk + 1) * ps);
     }
+  };
+  auto body = [&](int k0, const Buf& x) {
 #pragma unroll
     for (int u = 0; u < kColAhead; ++u) {
       const int kk = k0 + u;
       if (kk < E - 1) {
-        const float ok = g.vol * (ev[u] - g.alpha);
+        const float ok = g.vol * (x.ev[u] - g.alpha);
         const float iD = 1.0f / D;
         const float l = ok * iD;
         invD[fb + kk * ps] = iD;
         lco[fb + kk * ps] = l;
         const float npe = (float)(1 + (kk + 1 < m));
-        D = fmaf(-l, ok, g.vol * (dv[u] + g.alpha * (npe + cp.nin)));
+        D = fmaf(-l, ok, g.vol * (x.dv[u] + g.alpha * (npe + cp.nin)));
       }
     }
-  }
+  };
+  col_pipeline<Buf>(0, kColAhead, ceil_div(E - 1, kColAhead), load, body);
   invD[fb + (E - 1) * ps] = 1.0f / D;
   lco[fb + (E - 1) * ps] = 0.f;
 }
@@ -261,44 +283,51 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
     float y = resid(fb);
     arr += y * y;
     z[fb] = y;
-    for (int k0 = 1; k0 < E; k0 += kColAhead) {
-      float rv[kColAhead], lv[kColAhead];
+    struct Fwd { float rv[kColAhead], lv[kColAhead]; };
+    auto fload = [&](int k0, Fwd& f) {
 #pragma unroll
       for (int u = 0; u < kColAhead; ++u) {
         const int kk = min(k0 + u, E - 1);
-        lv[u] = __ldg(lco + fb + (kk - 1) * ps);
-        rv[u] = k0 + u < E ? resid(fb + kk * ps) : 0.f;
+        f.lv[u] = __ldg(lco + fb + (kk - 1) * ps);
+        f.rv[u] = k0 + u < E ? resid(fb + kk * ps) : 0.f;
       }
+    };
+    auto fbody = [&](int k0, const Fwd& f) {
 #pragma unroll
       for (int u = 0; u < kColAhead; ++u)
         if (k0 + u < E) {
-          arr += rv[u] * rv[u];
-          y = fmaf(-lv[u], y, rv[u]);
+          arr += f.rv[u] * f.rv[u];
+          y = fmaf(-f.lv[u], y, f.rv[u]);
           z[fb + (k0 + u) * ps] = y;
         }
-    }
+    };
+    col_pipeline<Fwd>(1, kColAhead, ceil_div(E - 1, kColAhead), fload, fbody);
     // backward: z_{E-1} = y_{E-1} / D_{E-1}, z_k = y_k / D_k - l_k z_{k+1}
     float zz = y * __ldg(invD + fb + (E - 1) * ps);
     z[fb + (E - 1) * ps] = zz;
     if (MODE != 0) arz += r[fb + (E - 1) * ps] * zz;
-    for (int k1 = E - 2; k1 >= 0; k1 -= kColAhead) {
-      float yv[kColAhead], lv[kColAhead], iv[kColAhead], rv[kColAhead];
+    constexpr int kB = kColAhead / 2;
+    struct Bwd { float yv[kB], lv[kB], iv[kB], rv[kB]; };
+    auto bload = [&](int k1, Bwd& q) {
 #pragma unroll
-      for (int u = 0; u < kColAhead; ++u) {
+      for (int u = 0; u < kB; ++u) {
         const int kk = max(k1 - u, 0);
-        yv[u] = z[fb + kk * ps];
-        lv[u] = __ldg(lco + fb + kk * ps);
-        iv[u] = __ldg(invD + fb + kk * ps);
-        rv[u] = MODE != 0 ? r[fb + kk * ps] : 0.f;
+        q.yv[u] = z[fb + kk * ps];
+        q.lv[u] = __ldg(lco + fb + kk * ps);
+        q.iv[u] = __ldg(invD + fb + kk * ps);
+        q.rv[u] = MODE != 0 ? r[fb + kk * ps] : 0.f;
       }
+    };
+    auto bbody = [&](int k1, const Bwd& q) {
 #pragma unroll
-      for (int u = 0; u < kColAhead; ++u)
+      for (int u = 0; u < kB; ++u)
         if (k1 - u >= 0) {
-          zz = fmaf(-lv[u], zz, yv[u] * iv[u]);
+          zz = fmaf(-q.lv[u], zz, q.yv[u] * q.iv[u]);
           z[fb + (k1 - u) * ps] = zz;
-          if (MODE != 0) arz += rv[u] * zz;
+          if (MODE != 0) arz += q.rv[u] * zz;
         }
-    }
+    };
+    col_pipeline<Bwd>(E - 2, -kB, ceil_div(E - 1, kB), bload, bbody);
   }
   if (MODE == 0) return;
   float v[2] = {arr, arz};
