@@ -69,7 +69,11 @@ typedef struct {
                              barrier per iteration (the direction product p.Hp taken from its
                              bilinear expansion in H z, see k_pcg_persistent.cu), or HYSCO_EINVAL.
                              1 and 2 have the same arithmetic; 3 gives the same iterates in exact
-                             arithmetic.  The column preconditioner always uses 1. */
+                             arithmetic; 4 = hysco_solve only: the whole GN loop (evaluation,
+                             PCG as in 2, the gamma = 1 trial, halvings, update) in one persistent
+                             cooperative launch, every scalar decision on the device (hysco_pcg
+                             takes it as 2), or HYSCO_EINVAL.  4 gives the iterates of 2 up to the
+                             rounding of J's sums.  The column preconditioner always uses 1. */
   int32_t no_graph;       /* 0 (default): the solve's fixed launch sequence is captured once in a
                              CUDA graph per (images, field, stats, options) and replayed; 1: launch
                              the kernels directly every call.  Same kernels either way. */
@@ -324,18 +328,20 @@ int hysco_batch_solve(hysco_batch_t batch, const void* const* Ip, const void* co
 /* Autotuner: times short trial solves (OT + at most 2 GN iterations into scratch fields, the
  * caller's fields untouched) of each candidate schedule -- 1, 2, 4 or 8 concurrent branches for
  * the per-pair kernels; the shared PCG launch with blocks by field size and at least 1 or at least
- * 2 blocks per pair, the per-pair persistent PCG, or waves -- and keeps the fastest.  Synchronises
+ * 2 blocks per pair, the per-pair persistent PCG, waves of PCG launches, or waves of whole GN
+ * loops, each wave packing at 1, 1.25 or 1.5 -- and keeps the fastest.  Synchronises
  * `stream`. */
 int hysco_batch_tune(hysco_batch_t batch, const void* const* Ip, const void* const* Im,
                      const hysco_opts* opts, hysco_stream_t stream);
 
 /* The schedule in use: out[0] branches, out[1] PCG policy (0: shared launch, blocks by field size;
  * 1: the same with >= 2 blocks per pair; 2: each pair's persistent PCG in turn; 3, 4, 5: waves
- * packed to 1, 1.25 and 1.5 times the on-chip vector capacity), out[2] blocks of the shared PCG
- * launch's grid. */
+ * packed to 1, 1.25 and 1.5 times the on-chip vector capacity, one PCG launch per wave and GN
+ * step; 6, 7, 8: the same waves, each wave's whole GN loops in one persistent launch as in
+ * pcg_path 4, waves of one image type), out[2] blocks of the shared PCG launch's grid. */
 int hysco_batch_schedule(hysco_batch_t batch, int32_t out[3]);
 
-/* Sets the schedule: branches 1 .. min(8, n), PCG policy 0 .. 5 as in hysco_batch_schedule.
+/* Sets the schedule: branches 1 .. min(8, n), PCG policy 0 .. 8 as in hysco_batch_schedule.
  * HYSCO_EINVAL when out of range or infeasible for this batch (then unchanged).  Drops the cached
  * graph. */
 int hysco_batch_set_schedule(hysco_batch_t batch, int branches, int policy);

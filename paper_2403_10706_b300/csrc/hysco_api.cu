@@ -34,6 +34,7 @@ struct hysco_ctx {
   PcgPlan pplan;      // persistent PCG grid (0: not available on this device), on-chip slots
   int onchip_max;     // the plan's on-chip slots before any hysco_set_pcg_onchip
   int fgrid;          // one-barrier persistent PCG grid (0: not available)
+  bool gn_ok;         // the persistent GN loop (pcg_path 4) can run with the plan's grid
   unsigned* psync;    // their barrier / reduction words
   bool have_lin, have_factor;
   // CUDA graph of the last solve's launch sequence and the arguments it was captured with
@@ -102,8 +103,9 @@ int reset_state(hysco_ctx* h, cudaStream_t s) {
 }
 
 // How a Jacobi or column PCG runs: separate kernels per phase, one persistent kernel with two
-// barriers per iteration, or one persistent kernel with one barrier per iteration.
-enum PcgMode { kPcgSeparate = 0, kPcgPersistent = 1, kPcgFused = 2 };
+// barriers per iteration, or one persistent kernel with one barrier per iteration; in a solve,
+// kGnLoop runs the whole GN loop (PCG included) in one persistent kernel.
+enum PcgMode { kPcgSeparate = 0, kPcgPersistent = 1, kPcgFused = 2, kGnLoop = 3 };
 
 // pcg_path (hysco_opts) -> mode; HYSCO_EINVAL when the requested kernel cannot run here
 int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
@@ -115,6 +117,7 @@ int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
     case 1: *mode = kPcgSeparate; return HYSCO_OK;
     case 2: *mode = kPcgPersistent; return jac && h->pplan.grid > 0 ? HYSCO_OK : HYSCO_EINVAL;
     case 3: *mode = kPcgFused; return jac && h->fgrid > 0 ? HYSCO_OK : HYSCO_EINVAL;
+    case 4: *mode = kGnLoop; return jac && h->gn_ok ? HYSCO_OK : HYSCO_EINVAL;
     default: return HYSCO_EINVAL;
   }
 }
@@ -301,6 +304,7 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   h->pplan = pcg_persistent_plan(h->device, pe_dim, (int)(nfp >> 2));
   h->onchip_max = h->pplan.onchip;
   h->fgrid = pcg_fused_grid(h->device, pe_dim);
+  h->gn_ok = h->pplan.grid > 0 && gn_setup(h->device, h->dtype, h->onchip_max) >= 1;
   const int sync_grid = h->pplan.grid > h->fgrid ? h->pplan.grid : h->fgrid;
   if (sync_grid > 0 &&
       cudaMalloc((void**)&h->psync, pcg_sync_words(sync_grid) * sizeof(unsigned)) !=
@@ -419,6 +423,7 @@ int hysco_pcg(hysco_t h, const float* rhs, float* q, int precond, int max_iters,
   if (max_iters < 1 || max_iters > 64 || !(rtol >= 0.0)) return HYSCO_EINVAL;
   PcgMode mode;
   if (pcg_mode(h, precond, pcg_path, &mode)) return HYSCO_EINVAL;
+  if (mode == kGnLoop) mode = kPcgPersistent;   // the GN loop's PCG is the persistent kernel's
   if (!h->have_lin) return HYSCO_ENOTREADY;
   cudaStream_t s = (cudaStream_t)stream;
   if (int rc = reset_state(h, s)) return rc;
@@ -562,6 +567,23 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
     if (int rc = init_ot_impl(h, Ip, Im, b_inout, o->ot_blur, o->ot_eps, nullptr, nullptr, s))
       return rc;
     HYSCO_TRY(launch_feasible_start(g, b_inout, w, s));
+  }
+  if (mode == kGnLoop) {   // the whole GN loop in one persistent launch on the PCG plan's grid
+    if (o->gn_iters == 0) return HYSCO_OK;
+    GnWave wv{};
+    wv.n = 1;
+    wv.blk0[0] = 0;
+    wv.nblk[0] = h->pplan.grid;
+    wv.g[0] = g;
+    set_march_warps(wv.g[0], h->pplan.grid * (kPcgBlock / 32));
+    wv.a[0] = GnArgs{Ip, Im, b_inout, h->p1, h->grad, stats,
+                     PcgArgs{h->grad, -1.0f, h->x, h->r, h->z, h->p0, h->p1, h->Hp, h->dco,
+                             h->eco, h->invd, h->psync, h->st, o->pcg_max_iters, o->pcg_rtol,
+                             h->pplan.onchip},
+                     o->gn_iters, o->ls_max_iters, o->armijo_c1};
+    HYSCO_TRY(launch_gn_wave(wv, h->dtype, h->pplan.grid, h->pplan.onchip, h->psync,
+                             pcg_sync_words(h->pplan.grid), s));
+    return HYSCO_OK;
   }
   for (int it = 0; it < o->gn_iters; ++it) {
     HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, nullptr, h->grad, h->dco, h->eco, h->invd,
@@ -964,8 +986,8 @@ struct hysco_batch_ctx {
 namespace {
 
 constexpr int kMaxBranches = 8;
-constexpr int kMaxPolicy = 5;
-constexpr double kWavePack[3] = {1.0, 1.25, 1.5};   // policies 3, 4, 5
+constexpr int kMaxPolicy = 8;
+constexpr double kWavePack[3] = {1.0, 1.25, 1.5};   // policies 3, 4, 5 and 6, 7, 8
 
 void batch_free(hysco_batch_ctx* B) {
   if (B->gexec) cudaGraphExecDestroy(B->gexec);
@@ -1017,7 +1039,8 @@ bool batch_shares(const hysco_batch_ctx* B, int lo, std::vector<int>& out) {
 // enough blocks to keep its r, p, Hp on chip (kWaveSlots slots per thread) and a wave holds at
 // most wgrid blocks and kWaveMax pairs.  A wave's spare blocks go to its pairs in proportion to
 // their sizes (fewer groups per block: a shorter stencil phase).
-int batch_waves(hysco_batch_ctx* B, double pack) {
+// by_dtype: a wave holds pairs of one image type only (the GN-loop kernel is compiled per type)
+int batch_waves(hysco_batch_ctx* B, double pack, bool by_dtype) {
   if (B->wgrid <= 0) return HYSCO_EINVAL;
   const int n = B->n;
   // float4 groups a block takes: kWaveSlots on chip per thread, times `pack` (> 1: the slots past
@@ -1035,7 +1058,9 @@ int batch_waves(hysco_batch_ctx* B, double pack) {
   std::vector<int> used;
   for (int i : order) {
     size_t w = 0;
-    while (w < waves.size() && (used[w] + need[i] > B->wgrid || (int)waves[w].size() >= kWaveMax))
+    while (w < waves.size() &&
+           (used[w] + need[i] > B->wgrid || (int)waves[w].size() >= kWaveMax ||
+            (by_dtype && B->hs[waves[w][0]]->dtype != B->hs[i]->dtype)))
       ++w;
     if (w == waves.size()) {
       waves.emplace_back();
@@ -1082,7 +1107,15 @@ int batch_layout(hysco_batch_ctx* B, int policy) {
     return HYSCO_OK;
   }
   if (policy >= 3 && policy <= 5) {
-    if (int rc = batch_waves(B, kWavePack[policy - 3])) return rc;
+    if (int rc = batch_waves(B, kWavePack[policy - 3], false)) return rc;
+    B->policy = policy;
+    return HYSCO_OK;
+  }
+  if (policy >= 6 && policy <= 8) {   // whole GN loops per wave: the kernel must fit each wave
+    if (int rc = batch_waves(B, kWavePack[policy - 6], true)) return rc;
+    for (size_t w = 0; w < B->waves.size(); ++w)
+      if (gn_setup(B->device, B->hs[B->waves[w][0]]->dtype, B->wave_onchip[w]) < 1)
+        return HYSCO_EINVAL;
     B->policy = policy;
     return HYSCO_OK;
   }
@@ -1189,8 +1222,58 @@ int enqueue_waves(hysco_batch_ctx* B, const void* const* Ip, const void* const* 
   return HYSCO_OK;
 }
 
+// policies 6-8: wave after wave, each wave's pairs started (OT) on concurrent branches, then
+// their whole GN loops in one persistent cooperative launch, each pair on its own block range
+int enqueue_gn_waves(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
+                     float* const* b, const hysco_opts* o, double* const* stats, cudaStream_t s) {
+  for (size_t w = 0; w < B->waves.size(); ++w) {
+    const std::vector<int>& pw = B->waves[w];
+    auto branch = [&](int j) { return B->side[j % B->branches]; };
+    HYSCO_TRY(batch_fork(B, s));
+    for (size_t j = 0; j < pw.size(); ++j) {
+      const int i = pw[j];
+      hysco_ctx* h = B->hs[i];
+      if (int rc = reset_state(h, branch(j))) return rc;
+      if (o->init) {
+        if (int rc = init_ot_impl(h, Ip[i], Im[i], b[i], o->ot_blur, o->ot_eps, nullptr, nullptr,
+                                  branch(j)))
+          return rc;
+        HYSCO_TRY(launch_feasible_start(h->g, b[i], h->work(), branch(j)));
+      }
+    }
+    HYSCO_TRY(batch_join(B, s));
+    if (o->gn_iters == 0) continue;
+    GnWave wv{};
+    wv.n = (int)pw.size();
+    int blk = 0;
+    size_t off = 0;
+    for (size_t j = 0; j < pw.size(); ++j) {
+      const int i = pw[j];
+      hysco_ctx* h = B->hs[i];
+      const int nb = B->wave_nblk[w][j];
+      const long long n4 = h->g.nfp / 4;
+      const int G = (int)std::min<long long>((n4 + (long long)nb * kPcgBlock - 1) /
+                                                 ((long long)nb * kPcgBlock), kWaveSlots);
+      wv.blk0[j] = blk;
+      wv.nblk[j] = nb;
+      wv.g[j] = h->g;
+      set_march_warps(wv.g[j], nb * (kPcgBlock / 32));
+      wv.a[j] = GnArgs{Ip[i], Im[i], b[i], h->p1, h->grad, stats ? stats[i] : nullptr,
+                       PcgArgs{h->grad, -1.0f, h->x, h->r, h->z, h->p0, h->p1, h->Hp, h->dco,
+                               h->eco, h->invd, B->wsync + off, h->st, o->pcg_max_iters,
+                               o->pcg_rtol, G},
+                       o->gn_iters, o->ls_max_iters, o->armijo_c1};
+      blk += nb;
+      off += pcg_sync_words(nb);
+    }
+    HYSCO_TRY(launch_gn_wave(wv, B->hs[pw[0]]->dtype, blk, B->wave_onchip[w], B->wsync, off, s));
+  }
+  return HYSCO_OK;
+}
+
 int enqueue_batch(hysco_batch_ctx* B, const void* const* Ip, const void* const* Im,
                   float* const* b, const hysco_opts* o, double* const* stats, cudaStream_t s) {
+  if (B->policy >= 6) return enqueue_gn_waves(B, Ip, Im, b, o, stats, s);
   if (B->policy >= 3) return enqueue_waves(B, Ip, Im, b, o, stats, s);
   auto branch = [&](int i) { return B->side[i % B->branches]; };
   HYSCO_TRY(batch_fork(B, s));

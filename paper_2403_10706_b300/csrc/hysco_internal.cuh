@@ -111,6 +111,14 @@ __device__ __forceinline__ float ldf(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
 __device__ __forceinline__ float ldf(const __half* p) { return __half2float(__ldg(p)); }
 
+// A load of an array that the launch reads only (RO: the read-only path) or that the same launch
+// also writes, before a device-wide barrier (!RO: an ordinary, coherent load).
+template <bool RO, typename T>
+__device__ __forceinline__ T ld_in(const T* p) {
+  if constexpr (RO) return __ldg(p);
+  else return *p;
+}
+
 // ------------------------------------------------------------------------------------------
 // deterministic reductions: per-thread and per-block partial sums in single precision (a warp
 // shuffle tree, then one warp over the block's warp sums); the last block to finish (atomic
@@ -278,12 +286,13 @@ __device__ __forceinline__ float f4get(const float4& v, int u) {
 // H z at the four nodes of group t (pitched layout), with the PCG direction update
 // p = z + beta p_old, Hp = H z + beta Hp_old (PCG; p_old, Hp_old given, ignored when first) or
 // Hv = H z (plain, into hn).  P is the PE axis.  z, which a persistent kernel writes, is read
-// with ordinary loads; d, e with the read-only path.  Padding lanes produce zeros.  Returns the
+// with ordinary loads; d, e with the read-only path (RO), or with ordinary loads when the same
+// launch has written them (the persistent GN loop).  Padding lanes produce zeros.  Returns the
 // sum over the group of p * Hp (PCG).
-template <int P, bool PCG>
+template <int P, bool PCG, bool RO = true>
 __device__ __forceinline__ float hv_core(const Geo& g, int t, const float* z,
-                                         const float* __restrict__ dco,
-                                         const float* __restrict__ eco, float beta, bool first,
+                                         const float* dco, const float* eco, float beta,
+                                         bool first,
                                          const float4& po, const float4& ho, float4& pn,
                                          float4& hn) {
   const GroupPos q = group_pos(g, t);
@@ -295,13 +304,13 @@ __device__ __forceinline__ float hv_core(const Geo& g, int t, const float* z,
   const float4 z0m = q.i0 > 0 ? z4p[t - s0] : zc, z0p = q.i0 < g.fe[0] - 1 ? z4p[t + s0] : zc;
   const float zl = q.x0 > 0 ? z[n - 1] : 0.f;
   const float zr = q.x0 + 4 < g.P2 ? z[n + 4] : 0.f;
-  const float4 d4 = __ldg(reinterpret_cast<const float4*>(dco) + t);
-  const float4 e4 = __ldg(reinterpret_cast<const float4*>(eco) + t);
+  const float4 d4 = ld_in<RO>(reinterpret_cast<const float4*>(dco) + t);
+  const float4 e4 = ld_in<RO>(reinterpret_cast<const float4*>(eco) + t);
   float4 em4 = make_float4(0.f, 0.f, 0.f, 0.f);
   float el = 0.f;
-  if (P == 0 && q.i0 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s0);
-  if (P == 1 && q.i1 > 0) em4 = __ldg(reinterpret_cast<const float4*>(eco) + t - s1);
-  if (P == 2 && q.x0 > 0) el = __ldg(eco + n - 1);
+  if (P == 0 && q.i0 > 0) em4 = ld_in<RO>(reinterpret_cast<const float4*>(eco) + t - s0);
+  if (P == 1 && q.i1 > 0) em4 = ld_in<RO>(reinterpret_cast<const float4*>(eco) + t - s1);
+  if (P == 2 && q.x0 > 0) el = ld_in<RO>(eco + n - 1);
   float outp[4], outh[4], acc = 0.f;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
@@ -501,6 +510,36 @@ int pcg_wave_setup(int device);
 // sync words, sync_words of them, zeroed first
 cudaError_t launch_pcg_wave(const PcgWave& w, int grid, int onchip_max, unsigned* sync,
                             size_t sync_words, cudaStream_t s);
+// k_gn.cu: the whole Gauss-Newton loop of a problem (Sec. 2.3.1) in one persistent launch on a
+// group of blocks: evaluation, Jacobi PCG, the gamma = 1 trial, Armijo halvings and the update,
+// every scalar decision taken identically by every block from the same reduced sums.
+struct GnArgs {
+  const void* Ip;        // images (the wave's dtype), caller layout
+  const void* Im;
+  float* b;              // field, caller layout: the start on entry, the result on exit
+  float* bscr;           // a second field buffer (>= the field's nodes): the gamma = 1 trial
+                         // writes b + q there, and an accepted trial swaps the two buffers
+  float* grad_p;         // pitched gradient (the PCG's right-hand side is -grad_p)
+  double* stats;         // gn_iters rows of 10 (hysco_solve's statistics) or null
+  PcgArgs pcg;           // x = q, the work vectors, d, e, 1/diag, the sync words, the state
+  int gn_iters, ls_max;
+  double c1;
+};
+struct GnWave {
+  int n;
+  int blk0[kWaveMax], nblk[kWaveMax];
+  Geo g[kWaveMax];       // each with the column march sized for its block range
+  GnArgs a[kWaveMax];
+};
+// co-resident 768-thread blocks per SM of the GN kernel for images of `dtype` with `onchip`
+// slots (0: it cannot run); sets its attributes
+int gn_setup(int device, int dtype, int onchip);
+// the column march of g for `warps` resident warps (k_eval.cu)
+void set_march_warps(Geo& g, int warps);
+// one cooperative launch for the problems of w (grid = their block total), images of `dtype`;
+// sync: the problems' sync words, sync_words of them, zeroed first
+cudaError_t launch_gn_wave(const GnWave& w, int dtype, int grid, int onchip_max, unsigned* sync,
+                           size_t sync_words, cudaStream_t s);
 cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,

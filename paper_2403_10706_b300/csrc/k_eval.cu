@@ -17,7 +17,7 @@
 // and the Jacobi preconditioner is 1 / (vol [d_k + alpha L_kk]).
 #include <algorithm>
 
-#include "eval_common.cuh"
+#include "eval_march.cuh"
 
 namespace hysco {
 
@@ -25,8 +25,6 @@ namespace hysco {
 // J, grad J, the tridiagonal GN coefficients (d, e) and the inverse Jacobi diagonal
 // ------------------------------------------------------------------------------------------
 
-constexpr int kEvalU = 4;           // nodes whose loads are issued together (evaluation)
-constexpr int kEvalUTrial = 2;      // the same for the trial and the prox variants
 constexpr int kEvalMinBlocks = 3;   // resident blocks per SM the registers must allow (80 regs)
 
 // Whether an objective launch has nothing to do: a stopped run, a line search already decided,
@@ -112,14 +110,7 @@ __device__ __forceinline__ void eval_finish(const Geo& g, const double (&tot)[NV
 // PROX (the ADMM b-subproblem of Sec. 2.3.2): J gains rho vol/2 ||b - c||^2 (c pitched, rho the
 // device state's admm_rho), the gradient rho vol (b - c) and the GN coefficient d the constant rho;
 // with the split geometry (in-plane Laplacian weights 0) S is the PE part S3 alone.
-//
-// Column march: warp w owns the 32 consecutive columns of tile w % ntile (lane = column) and the
-// nodes of segment w / ntile; each thread walks its segment node by node with a rolling window
-// of one cell (the cell right of node k is evaluated once and reused as the cell left of node
-// k + 1), so the column's geometry, its neighbours' offsets and the constant part of the Jacobi
-// diagonal are set up once per segment.  Loads of U nodes are issued together before their
-// arithmetic.  A lane past the last column repeats the last column (identical values stored to
-// identical addresses) and adds nothing to the sums.
+// One warp per work item of the column march (eval_item): the grid is ntile * nseg warps.
 template <typename TI, bool TRIAL, bool PROX, int U, int OUT>
 __global__ void __launch_bounds__(kBlock, kEvalMinBlocks)
 k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float* __restrict__ b,
@@ -128,131 +119,16 @@ k_eval(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, const float*
        float* __restrict__ invd, int it, int ls_max, double c1, float* partials,
        unsigned* counter, DevState* st, double* terms) {
   if (eval_skip<TRIAL, PROX>(it, st)) return;
-  const int inner = g.inner, m = g.m, psP = g.psP;
-  const float wA = g.wA, wB = g.wB, alpha = g.alpha, hbeta = g.half_beta, vol = g.vol;
   const float rho = PROX ? st->admm_rho : 0.f;
-  float accD = 0.f, accS = 0.f, accP = 0.f, accG = 0.f, accGQ = 0.f, accR = 0.f;
+  EvalAcc acc;
   const int wid = blockIdx.x * (kBlock / 32) + (threadIdx.x >> 5);
-  const int seg = wid / g.ntile;
-  if (seg < g.nseg) {
-    int c = (wid - seg * g.ntile) * 32 + (threadIdx.x & 31);
-    const bool act = c < g.ncols;
-    c = act ? c : g.ncols - 1;
-    const int k0 = seg * g.mseg, k1 = min(k0 + g.mseg, g.E);
-    // column geometry: caller-layout bases (image, field), pitched base, in-plane neighbours
-    const int o = (int)fdiv((unsigned)c, g.divIn), ci = c - o * inner;
-    const int ib = o * (int)g.img_ostride + ci, fb = o * (int)g.fld_ostride + ci;
-    const int cB = (int)fdiv((unsigned)c, g.divA), cA = c - cB * g.nA;
-    const bool hAm = cA > 0, hAp = cA < g.nA - 1, hBm = cB > 0, hBp = cB < g.nB - 1;
-    auto fbase = [&](int cc) {
-      const int oo = (int)fdiv((unsigned)cc, g.divIn);
-      return oo * (int)g.fld_ostride + (cc - oo * inner);
-    };
-    // offsets of the neighbour columns from this one (0: absent, the node itself, so that its
-    // Laplacian difference vanishes)
-    const int uAm = hAm ? fbase(c - 1) - fb : 0, uAp = hAp ? fbase(c + 1) - fb : 0;
-    const int uBm = hBm ? fbase(c - g.nA) - fb : 0, uBp = hBp ? fbase(c + g.nA) - fb : 0;
-    const int pAm = hAm ? -g.psA : 0, pAp = hAp ? g.psA : 0;
-    const int pBm = hBm ? -g.psB : 0, pBp = hBp ? g.psB : 0;
-    const float nin = g.wA * (float)((int)hAm + (int)hAp) + g.wB * (float)((int)hBm + (int)hBp);
-    const float dg2 = g.alpha * (2.0f + nin), dg1 = g.alpha * (1.0f + nin);
-    const TI* Ipc = Ip + ib;
-    const TI* Imc = Im + ib;
-    // field value (b, or b + q in the trial) at caller offset uo / pitched offset po
-    auto fld = [&](int uo, int po) {
-      const float v = __ldg(b + uo);
-      return TRIAL ? v + __ldg(q + po) : v;
-    };
-    auto cell = [&](int j, float bj, float bj1) {
-      return cell_lin(Ipc, Imc, inner, m, j, bj, bj1, hbeta);
-    };
-    // node k from the cells left (P) and right (C) of it: gradient, GN coefficients, sums
-    auto node = [&](int k, const CellLin& P, const CellLin& C, float bk, float bAm, float bAp,
-                    float bBm, float bBp, float qk, float gpk, float ck, int uo, int po,
-                    float dgk) {
-      const float dAm = bk - bAm, dAp = bAp - bk, dBm = bk - bBm, dBp = bBp - bk;
-      const float lap = (P.dlt - C.dlt) + wA * (dAm - dAp) + wB * (dBm - dBp);
-      accS += C.dlt * C.dlt + wA * dAp * dAp + wB * dBp * dBp;
-      accD += C.r * C.r;
-      accP += C.phi;
-      float prx = 0.f;
-      if (PROX) {
-        prx = bk - ck;
-        accR += prx * prx;
-      }
-      float gsum = P.jr * P.r + C.jl * C.r + alpha * lap + hbeta * (P.dphi - C.dphi);
-      if (PROX) gsum += rho * prx;
-      const float gk = vol * gsum;
-      float dk = P.jr * P.jr + C.jl * C.jl + P.psi + C.psi;
-      if (PROX) dk += rho;
-      const float ek = C.jl * C.jr - C.psi;
-      const float diag = vol * (dk + dgk);
-      if (TRIAL) accGQ += gpk * qk;
-      if (OUT & 1) grad[uo] = gk;
-      if (OUT & 2) grad_p[po] = gk;
-      dco[po] = dk;
-      eco[po] = ek;
-      invd[po] = diag > 0.f ? __fdividef(1.0f, diag) : 1.0f;
-      accG += gk * gk;
-    };
-
-    int uo = fb + k0 * inner, po = col_pbase(g, c) + k0 * psP;
-    float bk = fld(uo, po);
-    float qk = TRIAL ? __ldg(q + po) : 0.f;
-    CellLin P = cell_zero();
-    if (k0 > 0) P = cell(k0 - 1, fld(uo - inner, po - psP), bk);
-    const int kend = min(k1, m);   // nodes below kend have a cell on their right
-    int k = k0;
-    for (; k + U <= kend; k += U) {
-      float bn[U], qn[U], bAm[U], bAp[U], bBm[U], bBp[U], gp[U], cc[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int uk = uo + u * inner, pk = po + u * psP;
-        bn[u] = fld(uk + inner, pk + psP);
-        qn[u] = TRIAL ? __ldg(q + pk + psP) : 0.f;
-        bAm[u] = fld(uk + uAm, pk + pAm);
-        bAp[u] = fld(uk + uAp, pk + pAp);
-        bBm[u] = fld(uk + uBm, pk + pBm);
-        bBp[u] = fld(uk + uBp, pk + pBp);
-        gp[u] = TRIAL ? grad_p[pk] : 0.f;
-        cc[u] = PROX ? __ldg(cpx + pk) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const CellLin C = cell(k + u, bk, bn[u]);
-        node(k + u, P, C, bk, bAm[u], bAp[u], bBm[u], bBp[u], qk, gp[u], cc[u],
-             uo + u * inner, po + u * psP, (k + u > 0) ? dg2 : dg1);
-        P = C;
-        bk = bn[u];
-        qk = qn[u];
-      }
-      uo += U * inner;
-      po += U * psP;
-    }
-    for (; k < k1; ++k) {   // the rest of the segment, and node m (no cell on its right)
-      const bool cv = k < m;
-      const float bn = cv ? fld(uo + inner, po + psP) : bk;
-      const float qnx = (TRIAL && cv) ? __ldg(q + po + psP) : 0.f;
-      const float gpk = TRIAL ? grad_p[po] : 0.f;
-      const float ck = PROX ? __ldg(cpx + po) : 0.f;
-      const CellLin C = cv ? cell(k, bk, bn) : cell_zero();
-      node(k, P, C, bk, fld(uo + uAm, po + pAm), fld(uo + uAp, po + pAp),
-           fld(uo + uBm, po + pBm), fld(uo + uBp, po + pBp), qk, gpk, ck, uo, po,
-           (k > 0 && k < m) ? dg2 : dg1);
-      P = C;
-      bk = bn;
-      qk = qnx;
-      uo += inner;
-      po += psP;
-    }
-    if (!act) {
-      accD = 0.f; accS = 0.f; accP = 0.f; accG = 0.f; accGQ = 0.f; accR = 0.f;
-    }
-  }
+  if (wid < g.ntile * g.nseg)
+    eval_item<TI, TRIAL, PROX, U, OUT, true>(g, Ip, Im, b, q, cpx, grad, grad_p, dco, eco, invd,
+                                             rho, wid, threadIdx.x & 31, acc);
   constexpr int NV = PROX ? 6 : 5;
   float v[NV];
-  v[0] = accD; v[1] = accS; v[2] = accP; v[3] = accG; v[4] = accGQ;
-  if (PROX) v[NV - 1] = accR;
+  v[0] = acc.D; v[1] = acc.S; v[2] = acc.P; v[3] = acc.G; v[4] = acc.GQ;
+  if (PROX) v[NV - 1] = acc.R;
   double tot[NV];
   if (grid_sum<NV>(v, partials, counter, tot)) eval_finish<TRIAL, PROX, NV>(g, tot, rho, it, ls_max, c1, st, terms);
 }
@@ -270,63 +146,12 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
              const float* __restrict__ cpx, const float* __restrict__ grad, int t0, int ls_max,
              double c1, float* partials, unsigned* counter, DevState* st) {
   if (st->stop || st->ls_done) return;
-  const int inner = g.inner, m = g.m;
-  const int ncb = ceil_div(g.ncols, kBlock), nitems = ncb * ceil_div(g.E, SEG);
   float aD[T], aS[T], aP[T], aR[T], agq = 0.f;
 #pragma unroll
   for (int t = 0; t < T; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; aR[t] = 0.f; }
-  // grid-stride over work items (256 columns x SEG nodes); accumulators carry across items
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-  int c = (item % ncb) * kBlock + threadIdx.x;
-  const bool act = c < g.ncols;
-  c = act ? c : g.ncols - 1;
-  const int k0 = (item / ncb) * SEG;
-  const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
-  const TI* Ipc = Ip + ib;
-  const TI* Imc = Im + ib;
-  const ColNbrs nb = col_nbrs(g, c, fb);
-  const int pb = col_pbase(g, c);
-  const ColNbrs nq = col_nbrs_pitched(g, c, pb);   // q and grad are pitched solver arrays
-  float bw[SEG + 1], qw[SEG + 1], bAp[SEG], qAp[SEG], bBp[SEG], qBp[SEG], cw[SEG];
-#pragma unroll
-  for (int j = 0; j <= SEG; ++j) {
-    int kk = min(k0 + j, m);
-    bw[j] = __ldg(b + fb + kk * inner);
-    qw[j] = __ldg(q + pb + kk * g.psP);
-    if (PROX && j < SEG) cw[j] = __ldg(cpx + pb + kk * g.psP);
-  }
-#pragma unroll
-  for (int j = 0; j < SEG; ++j) {
-    int kk = min(k0 + j, m);
-    int o = kk * inner, op = kk * g.psP;
-    bAp[j] = __ldg(b + nb.Ap + o); qAp[j] = __ldg(q + nq.Ap + op);
-    bBp[j] = __ldg(b + nb.Bp + o); qBp[j] = __ldg(q + nq.Bp + op);
-  }
-  if (t0 == 0) {
-#pragma unroll
-    for (int j = 0; j < SEG; ++j)
-      if (act && k0 + j <= m) agq += __ldg(grad + pb + (k0 + j) * g.psP) * qw[j];
-  }
-#pragma unroll
-  for (int t = 0; t < T; ++t) {
-    float gam = ldexpf(1.0f, -(t0 + t));
-    float x[SEG + 1];
-#pragma unroll
-    for (int j = 0; j <= SEG; ++j) x[j] = fmaf(gam, qw[j], bw[j]);
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      int k = k0 + j;
-      if (!act || k > m) continue;
-      float r = 0.f, phi = 0.f;
-      cell_residual(Ipc, Imc, inner, m, k, x[j], x[j + 1], r, phi);
-      if (k < m) { aD[t] += r * r; aP[t] += phi; }
-      float dPE = x[j + 1] - x[j];
-      float dA = fmaf(gam, qAp[j], bAp[j]) - x[j], dB = fmaf(gam, qBp[j], bBp[j]) - x[j];
-      aS[t] += dPE * dPE + g.wA * dA * dA + g.wB * dB * dB;
-      if (PROX) aR[t] += (x[j] - cw[j]) * (x[j] - cw[j]);
-    }
-  }
-  }   // work items
+  // grid-stride over work items; accumulators carry across items
+  ls_items<TI, SEG, T, PROX, true>(g, Ip, Im, b, q, cpx, grad, t0, blockIdx.x, gridDim.x,
+                                   threadIdx.x, aD, aS, aP, aR, agq);
   constexpr int NV = (PROX ? 4 : 3) * T + 1;
   float v[NV];
   double tot[NV];
@@ -382,23 +207,7 @@ k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, doub
   if (st->stop) return;
   const float gam = (float)st->gamma;
   if (gam == 0.0f) return;
-  // lanes walk consecutive caller-layout nodes (coalesced b); q's pitched index by one division
-  const int T = gridDim.x * blockDim.x;
-  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < g.nf; i0 += 4 * T) {
-    float bv[4], qv[4];
-    int idx[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      int i = min(i0 + u * T, g.nf - 1);
-      int row = (int)fdiv((unsigned)i, g.divfe2);
-      idx[u] = i;
-      bv[u] = b[i];
-      qv[u] = __ldg(q + row * g.P2 + (i - row * g.fe[2]));
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-      if (i0 + u * T < g.nf) b[idx[u]] = fmaf(gam, qv[u], bv[u]);
-  }
+  update_nodes<true>(g, b, q, gam, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta); MEAN: their average
@@ -500,9 +309,15 @@ void set_march(Geo& g, int device) {
   occ((const void*)k_eval<__half, false, false, kEvalU, 2>);
   occ((const void*)k_eval<__half, true, false, kEvalUTrial, 2>);
   if (per_sm == 64) per_sm = kEvalMinBlocks;
-  const int slots = sms * per_sm * (kBlock / 32);
+  set_march_warps(g, sms * per_sm * (kBlock / 32));
+}
+
+void set_march_warps(Geo& g, int warps) {
+  g.divIn = make_fastdiv((unsigned)g.inner);
+  g.divA = make_fastdiv((unsigned)g.nA);
+  g.ntile = ceil_div(g.ncols, 32);
   const int most = ceil_div(g.E, kMinMarch);     // segments of at least kMinMarch nodes
-  int nseg = std::max(1, std::min(slots / g.ntile, most));
+  int nseg = std::max(1, std::min(warps / g.ntile, most));
   g.mseg = ceil_div(g.E, nseg);
   g.nseg = ceil_div(g.E, g.mseg);
 }

@@ -362,7 +362,8 @@ class HyscoBatch:
         """(branches, PCG policy, shared PCG grid blocks) in use; policy 0 / 1: one PCG launch
         shared by all pairs (blocks by field size, >= 1 / >= 2 per pair), 2: each pair's
         persistent PCG in turn, 3 / 4 / 5: waves of pairs whose PCGs share one launch per GN step
-        (vectors packed to 1, 1.25, 1.5 times the on-chip capacity)."""
+        (vectors packed to 1, 1.25, 1.5 times the on-chip capacity), 6 / 7 / 8: the same waves,
+        each wave's whole GN loops in one persistent launch."""
         out = (C.c_int32 * 3)()
         _lib.check(self.lib.hysco_batch_schedule(self._b, out), "hysco_batch_schedule")
         return tuple(out)

@@ -177,10 +177,11 @@ def test_half_precision_images_match_oracle_on_the_same_values(H, orc, dtype):
     check_field(host(g), e["grad"], "grad " + dtype)
 
 
-@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (0, 3), (1, 0)])
+@pytest.mark.parametrize("precond,path", [(0, 1), (0, 2), (0, 3), (0, 4), (1, 0)])
 def test_tiny_solve_matches_oracle(H, orc, precond, path):
     """Tiny case: 32x32x16, OT init, 10 GN-PCG iterations (path 1: separate PCG kernels,
-    path 2: the persistent cooperative PCG kernel, path 3: its one-barrier form)."""
+    path 2: the persistent cooperative PCG kernel, path 3: its one-barrier form, path 4: the
+    whole GN loop in one persistent kernel)."""
     pr = ph.make_pair("tiny")
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
     b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=10, precond=precond, pcg_path=path)
@@ -198,14 +199,14 @@ def test_tiny_solve_matches_oracle(H, orc, precond, path):
 @pytest.mark.parametrize("name", ["small", "7t"])
 def test_both_pcg_paths_match_oracle_on_larger_volumes(H, orc, name):
     """Small (96x96x60, PE axis 1) and 7T-shaped (130x130x85, PE axis 0) pairs, OT init + 4 GN
-    iterations, through the separate PCG kernels and both persistent PCG kernels, against the
-    oracle's own double-precision trajectory."""
+    iterations, through the separate PCG kernels, both persistent PCG kernels and the persistent
+    GN loop, against the oracle's own double-precision trajectory."""
     pr = ph.make_pair(name)
     P = orc.Problem(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
     ref, status, rst = P.solve(pr.Ip, pr.Im, gn_iters=4, contract=False)
     assert status == 0
     h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
-    for path in (1, 2, 3):
+    for path in (1, 2, 3, 4):
         b, st = h.solve(dev(pr.Ip), dev(pr.Im), gn_iters=4, pcg_path=path)
         assert h.last_status() == 0
         gs = host(st)
@@ -278,3 +279,47 @@ def test_infeasible_ot_start_is_halved_like_the_oracle(H, orc, recipe):
     gs = host(st)
     assert np.allclose(gs[:, 0], rst[:, 0], rtol=1e-4), (gs[:, 0], rst[:, 0])
     assert rel(host(b), ref) <= 1e-3
+
+
+def test_persistent_gn_loop_matches_the_separate_kernels(H):
+    """pcg_path 4 (the whole GN loop in one persistent launch) against pcg_path 2 (the same PCG
+    kernel body, every other step its own kernel) on the small pair: the same accepted steps and
+    PCG iteration counts, objective histories within 1e-6 and fields within 1e-5 (only the
+    grouping of J's partial sums differs); a second call, and a graph replay, bit-identical."""
+    pr = ph.make_pair("small")
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    Ip, Im = dev(pr.Ip), dev(pr.Im)
+    b2, s2 = h.solve(Ip, Im, gn_iters=8, pcg_path=2)
+    b2, s2 = host(b2).copy(), host(s2).copy()
+    runs = []
+    for graph in (False, True, True):
+        b4, s4 = h.solve(Ip, Im, gn_iters=8, pcg_path=4, graph=graph)
+        assert h.last_status() == 0
+        runs.append((host(b4).copy(), host(s4).copy()))
+    b4, s4 = runs[0]
+    assert np.array_equal(s4[:, 6], s2[:, 6]) and np.array_equal(s4[:, 7], s2[:, 7])
+    assert np.array_equal(s4[:, 9], s2[:, 9])
+    assert np.allclose(s4[:, 0], s2[:, 0], rtol=1e-6)
+    assert rel(b4, b2) <= 1e-5
+    for bb, ss in runs[1:]:
+        assert np.array_equal(bb, b4) and np.array_equal(ss, s4, equal_nan=True)
+
+
+def test_persistent_gn_loop_stops_on_a_non_finite_objective_like_the_separate_kernels(H):
+    """A NaN image voxel makes J NaN at the first evaluation: both forms stop there with status
+    -4, keep the objective row and fill every statistic after it with NaN, and leave b as the
+    start."""
+    dims, spacing, p = (24, 40, 20), (1.0, 1.0, 1.0), 1
+    Ip, Im, b = case(dims, p, 710)
+    Ipn = Ip.copy()
+    Ipn[3, 5, 7] = np.nan
+    h = H(dims, spacing, p, ALPHA, BETA)
+    out = {}
+    for path in (2, 4):
+        bb, st = h.solve(dev(Ipn), dev(Im), b=dev(b), gn_iters=3, init=False, pcg_path=path)
+        out[path] = (host(bb).copy(), host(st).copy(), h.last_status())
+    for path in (2, 4):
+        bb, st, status = out[path]
+        assert status == -4, path
+        assert np.array_equal(bb, b), path
+        assert np.isnan(st[0, 0]) and np.all(np.isnan(st[0, 4:])) and np.all(np.isnan(st[1:])), path

@@ -95,12 +95,12 @@ def test_oracle_armijo_matches_closed_form(orc, c1, gamma):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 4])
 @pytest.mark.parametrize("c1,gamma", CASES)
 def test_gpu_armijo_matches_closed_form(c1, gamma, path):
     """The same line through hysco_solve: the device-side Armijo decision (gamma = 1 as a full
     trial evaluation, then the halvings) takes the closed-form step, with the separate-kernel and
-    the persistent PCG."""
+    the persistent PCG, and inside the persistent GN loop."""
     import torch
     from paper_2403_10706_b300.hysco import Hysco
     dev = torch.device("cuda", 0)
