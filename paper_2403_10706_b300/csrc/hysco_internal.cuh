@@ -119,6 +119,22 @@ __device__ __forceinline__ T ld_in(const T* p) {
   else return *p;
 }
 
+// Asynchronous 4-byte copies global -> shared (cp.async): the copy lands in shared memory without
+// passing through registers, so the compiler cannot move it next to its use.  pred = false fills
+// the word with zero and reads nothing.  A thread sees its own copies after cp_async_wait<n>
+// (all but its n most recent commit groups complete); other threads after a block barrier too.
+__device__ __forceinline__ void cp_async4(float* smem, const float* gmem, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem),
+               "r"(pred ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ------------------------------------------------------------------------------------------
 // deterministic reductions: per-thread and per-block partial sums in single precision (a warp
 // shuffle tree, then one warp over the block's warp sums); the last block to finish (atomic

@@ -162,72 +162,115 @@ k_zrhs(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* _
     T0[(long long)k * g.ncols + c] = __ldg(b + fb + k * g.inner) + __ldg(u + pb + k * g.psP);
 }
 
-// Batched C_z = A_z B_z (M x N, inner dimension K) over planes z = blockIdx.z, each operand
-// addressed by (plane, row, column) strides; 64 x 64 tiles, 16-deep panels in shared memory, a
-// 4 x 4 block of outputs per thread.  SCALE multiplies entry (i, j) by rho / lambda(i, j),
-// lambda = rho + alpha (wB muB[i] + wA muA[j]) (rho from the device state).
+// Batched C_z = A_z B_z (M x N, inner dimension K) over z = blockIdx.z: A(i, l) at
+// A.p + z A.sz + i A.si + l A.sj, likewise B(l, j); C(i, j) at
+// C + z cz + (i / rp) cp + (i % rp) ci + j cj (rp rows per plane, so that the planes' rows can be
+// one tall operand).  A block computes a kGmM x kGmN tile of C over kGmK-deep panels of A and B
+// in shared memory, double-buffered: the next panel's copies (cp.async, straight to shared memory)
+// are in flight while the current one is multiplied.  Each thread holds an 8 x 8 block of outputs: rows 4 ty + a and
+// kGmM / 2 + 4 ty + a, columns 4 tx + b and kGmN / 2 + 4 tx + b (a, b < 4), so that its operands
+// of a depth step are four 16-byte shared loads that consecutive threads take from consecutive
+// words (no bank conflicts).  SCALE multiplies entry (i, j) by rho / lambda, lambda =
+// rho + alpha (wB muB[i % rp] + wA muA[j]) (rho from the device state).
 struct PlaneOperand {
   const float* p;
   long long sz, si, sj;
 };
-constexpr int kMmTile = 64, kMmDepth = 16;
+constexpr int kGmM = 72, kGmN = 112, kGmK = 16;
+constexpr int kGmTy = kGmM / 8, kGmTx = kGmN / 8, kGmThreads = kGmTy * kGmTx;   // 9 x 14
+constexpr int kGmLdA = (kGmM * kGmK + kGmThreads - 1) / kGmThreads;   // copies per thread
+constexpr int kGmLdB = (kGmK * kGmN + kGmThreads - 1) / kGmThreads;
 
 template <bool SCALE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kGmThreads, 4)
 k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restrict__ C,
-           long long cz, long long ci, long long cj, const float* __restrict__ muB,
-           const float* __restrict__ muA, float alpha, float wB, float wA, const DevState* st) {
+           long long cz, int rp, long long cp, long long ci, long long cj,
+           const float* __restrict__ muB, const float* __restrict__ muA, float alpha, float wB,
+           float wA, const DevState* st) {
   if (st->stop) return;
-  __shared__ __align__(16) float As[kMmDepth][kMmTile + 4];
-  __shared__ __align__(16) float Bs[kMmDepth][kMmTile + 4];
-  const int z = blockIdx.z;
-  const int i0 = blockIdx.y * kMmTile, j0 = blockIdx.x * kMmTile;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  __shared__ __align__(16) float As[2][kGmK][kGmM];
+  __shared__ __align__(16) float Bs[2][kGmK][kGmN];
+  const int z = blockIdx.z, tid = threadIdx.x;
+  const int i0 = blockIdx.y * kGmM, j0 = blockIdx.x * kGmN;
+  const int tx = tid % kGmTx, ty = tid / kGmTx;
   const float* Ap = A.p + z * A.sz;
   const float* Bp = B.p + z * B.sz;
-  float acc[4][4];
+  // panel element e of A (kGmM x kGmK) and of B (kGmK x kGmN): the unit-stride index fastest
+  auto a_pos = [&](int e, int& ri, int& li) {
+    if (A.sj == 1) { li = e % kGmK; ri = e / kGmK; } else { ri = e % kGmM; li = e / kGmM; }
+  };
+  auto b_pos = [&](int e, int& lb, int& jb) {
+    if (B.sj == 1) { jb = e % kGmN; lb = e / kGmN; } else { lb = e % kGmK; jb = e / kGmK; }
+  };
+  // panel at depth l0 into buffer buf, straight to shared memory (cp.async; zeros past the edges)
+  auto fetch = [&](int l0, int buf) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int bb = 0; bb < 4; ++bb) acc[a][bb] = 0.f;
-  for (int l0 = 0; l0 < K; l0 += kMmDepth) {
-    // each thread loads 4 entries of each panel (64 x 16 = 1024 per panel)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = threadIdx.x + 256 * q;
-      const int li = e & (kMmDepth - 1), ri = e >> 4;   // A panel: row ri, depth li
-      const int ia = i0 + ri, la = l0 + li;
-      As[li][ri] = (ia < M && la < K) ? __ldg(Ap + ia * A.si + la * A.sj) : 0.f;
-      const int lb = l0 + (e >> 6), jb = j0 + (e & 63);   // B panel: depth e/64, column e%64
-      Bs[e >> 6][e & 63] = (lb < K && jb < N) ? __ldg(Bp + lb * B.si + jb * B.sj) : 0.f;
+    for (int q = 0; q < kGmLdA; ++q) {
+      const int e = tid + q * kGmThreads;
+      if (e < kGmM * kGmK) {
+        int ri, li;
+        a_pos(e, ri, li);
+        const int ia = i0 + ri, la = l0 + li;
+        const bool in = ia < M && la < K;
+        cp_async4(&As[buf][li][ri], in ? Ap + (int)(ia * A.si + la * A.sj) : Ap, in);
+      }
     }
-    __syncthreads();
-    // thread (ty, tx) owns rows 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3 of the tile: its
-    // operands of each depth step are two 16-byte shared loads
 #pragma unroll
-    for (int l = 0; l < kMmDepth; ++l) {
-      const float4 a4 = *reinterpret_cast<const float4*>(&As[l][4 * ty]);
-      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[l][4 * tx]);
-      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
-#pragma unroll
-      for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int bb = 0; bb < 4; ++bb) acc[a][bb] = fmaf(av[a], bv[bb], acc[a][bb]);
+    for (int q = 0; q < kGmLdB; ++q) {
+      const int e = tid + q * kGmThreads;
+      if (e < kGmK * kGmN) {
+        int lb, jb;
+        b_pos(e, lb, jb);
+        const int lg = l0 + lb, jg = j0 + jb;
+        const bool in = lg < K && jg < N;
+        cp_async4(&Bs[buf][lb][jb], in ? Bp + (int)(lg * B.si + jg * B.sj) : Bp, in);
+      }
     }
+    cp_async_commit();
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+  const int np = (K + kGmK - 1) / kGmK;
+  fetch(0, 0);
+  for (int pnl = 0; pnl < np; ++pnl) {
+    const int cur = pnl & 1;
+    if (pnl + 1 < np) fetch((pnl + 1) * kGmK, cur ^ 1);
+    else cp_async_commit();
+    cp_async_wait<1>();   // this panel's copies (all but the one just issued) have landed
     __syncthreads();
+#pragma unroll
+    for (int l = 0; l < kGmK; ++l) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][l][4 * ty]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][l][kGmM / 2 + 4 * ty]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][l][4 * tx]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][l][kGmN / 2 + 4 * tx]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();   // every thread is done with this buffer before it is refilled
   }
   const float rho = SCALE ? st->admm_rho : 0.f;
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = i0 + 4 * ty + a;
+  for (int a = 0; a < 8; ++a) {
+    const int i = i0 + (a < 4 ? 4 * ty + a : kGmM / 2 + 4 * ty + a - 4);
     if (i >= M) continue;
+    const int ip = i / rp, ir = i - ip * rp;
+    float* Crow = C + z * cz + ip * cp + ir * ci;
+    const float lb = SCALE ? wB * __ldg(muB + ir) : 0.f;
 #pragma unroll
-    for (int bb = 0; bb < 4; ++bb) {
-      const int j = j0 + 4 * tx + bb;
+    for (int b = 0; b < 8; ++b) {
+      const int j = j0 + (b < 4 ? 4 * tx + b : kGmN / 2 + 4 * tx + b - 4);
       if (j >= N) continue;
-      float v = acc[a][bb];
-      if (SCALE) v *= rho / (rho + alpha * (wB * __ldg(muB + i) + wA * __ldg(muA + j)));
-      C[z * cz + i * ci + j * cj] = v;
+      float v = acc[a][b];
+      if (SCALE) v *= rho / (rho + alpha * (lb + wA * __ldg(muA + j)));
+      Crow[j * cj] = v;
     }
   }
 }
@@ -400,23 +443,27 @@ cudaError_t launch_admm_zsolve(const Geo& g, const float* b, const float* u, con
   k_zrhs<<<node_grid(g), kBlock, 0, s>>>(g, b, u, T0, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const dim3 grid(ceil_div(nA, kMmTile), ceil_div(nB, kMmTile), E);
+  // per-plane products (planes z = PE node k) and the products whose planes' rows form one tall
+  // operand (row r = k nB + cB of T, contiguous planes)
+  const dim3 plane_grid(ceil_div(nA, kGmN), ceil_div(nB, kGmM), E);
+  const int rows = E * nB;
+  const dim3 tall_grid(ceil_div(nA, kGmN), ceil_div(rows, kGmM), 1);
   // 1: T1 = Q_B^T T0          (row jB, column cA)
-  k_plane_mm<false><<<grid, 256, 0, s>>>(nB, nA, nB, PlaneOperand{q.QB, 0, 1, nB},
-                                        PlaneOperand{T0, P, nA, 1}, T1, P, nA, 1, nullptr,
-                                        nullptr, 0.f, 0.f, 0.f, st);
+  k_plane_mm<false><<<plane_grid, kGmThreads, 0, s>>>(
+      nB, nA, nB, PlaneOperand{q.QB, 0, 1, nB}, PlaneOperand{T0, P, nA, 1}, T1, P, nB, 0, nA, 1,
+      nullptr, nullptr, 0.f, 0.f, 0.f, st);
   // 2: T0 = (T1 Q_A) .* rho / lambda
-  k_plane_mm<true><<<grid, 256, 0, s>>>(nB, nA, nA, PlaneOperand{T1, P, nA, 1},
-                                       PlaneOperand{q.QA, 0, nA, 1}, T0, P, nA, 1, q.muB, q.muA,
-                                       g.alpha, g.wB, g.wA, st);
+  k_plane_mm<true><<<tall_grid, kGmThreads, 0, s>>>(
+      rows, nA, nA, PlaneOperand{T1, 0, nA, 1}, PlaneOperand{q.QA, 0, nA, 1}, T0, 0, nB, P, nA, 1,
+      q.muB, q.muA, g.alpha, g.wB, g.wA, st);
   // 3: T1 = Q_B T0
-  k_plane_mm<false><<<grid, 256, 0, s>>>(nB, nA, nB, PlaneOperand{q.QB, 0, nB, 1},
-                                        PlaneOperand{T0, P, nA, 1}, T1, P, nA, 1, nullptr,
-                                        nullptr, 0.f, 0.f, 0.f, st);
+  k_plane_mm<false><<<plane_grid, kGmThreads, 0, s>>>(
+      nB, nA, nB, PlaneOperand{q.QB, 0, nB, 1}, PlaneOperand{T0, P, nA, 1}, T1, P, nB, 0, nA, 1,
+      nullptr, nullptr, 0.f, 0.f, 0.f, st);
   // 4: z = T1 Q_A^T, written into the pitched field (plane k, row cB, column cA)
-  k_plane_mm<false><<<grid, 256, 0, s>>>(nB, nA, nA, PlaneOperand{T1, P, nA, 1},
-                                        PlaneOperand{q.QA, 0, 1, nA}, z, g.psP, g.psB, g.psA,
-                                        nullptr, nullptr, 0.f, 0.f, 0.f, st);
+  k_plane_mm<false><<<tall_grid, kGmThreads, 0, s>>>(
+      rows, nA, nA, PlaneOperand{T1, 0, nA, 1}, PlaneOperand{q.QA, 0, 1, nA}, z, 0, nB, g.psP,
+      g.psB, g.psA, nullptr, nullptr, 0.f, 0.f, 0.f, st);
   return cudaGetLastError();
 }
 

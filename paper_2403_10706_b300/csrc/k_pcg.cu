@@ -178,6 +178,9 @@ k_from_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
 //   M = tridiag(vol (e_k - alpha), vol (d_k + alpha (npe_k + nin)), vol (e_k - alpha)), M = L D L^T:
 //   D_0 = dia_0, l_k = off_k / D_k, D_{k+1} = dia_{k+1} - l_k off_k; stored 1 / D_k and l_k.
 constexpr int kColAhead = 16;
+// threads per block of the column kernels: a column per thread and one warp per block, so that
+// the few thousand columns spread over every SM (the sequential recurrences are latency-bound)
+constexpr int kColBlock = 32;
 
 struct ColPos {
   int base;     // pitched offset of node 0
@@ -208,7 +211,7 @@ __device__ __forceinline__ void col_pipeline(int first, int step, int n, Load&& 
   }
 }
 
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kColBlock)
 k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco,
              float* __restrict__ invD, float* __restrict__ lco) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -250,7 +253,7 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
 // apply to r; MODE 1: PCG init (r = sign * grad, x = 0); MODE 2: PCG update (x += alpha p,
 // r -= alpha Hp) first.  MODE 1 / 2 reduce r.r and r.z and take the PCG decisions.
 template <int MODE>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kColBlock)
 k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float* r,
             const float* __restrict__ p, const float* __restrict__ Hp, float* __restrict__ z,
             const float* __restrict__ invD, const float* __restrict__ lco, int first,
@@ -346,7 +349,7 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
 
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
                               float* lco, cudaStream_t s) {
-  k_col_factor<<<ceil_div(g.ncols, kBlock), kBlock, 0, s>>>(g, dco, eco, invD, lco);
+  k_col_factor<<<ceil_div(g.ncols, kColBlock), kColBlock, 0, s>>>(g, dco, eco, invD, lco);
   return cudaGetLastError();
 }
 
@@ -354,9 +357,9 @@ cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x
                              const float* p, const float* Hp, float* z, const float* invD,
                              const float* lco, int first, double rtol, float sign,
                              const Work& w, cudaStream_t s) {
-  const dim3 grid(ceil_div(g.ncols, kBlock));
+  const dim3 grid(ceil_div(g.ncols, kColBlock));
 #define HYSCO_COLSOLVE(M)                                                                       \
-  k_col_solve<M><<<grid, kBlock, 0, s>>>(g, grad, x, r, p, Hp, z, invD, lco, first, rtol, sign, \
+  k_col_solve<M><<<grid, kColBlock, 0, s>>>(g, grad, x, r, p, Hp, z, invD, lco, first, rtol, sign, \
                                          w.partials, w.counter, w.st);
   if (mode == 0) { HYSCO_COLSOLVE(0) }
   else if (mode == 1) { HYSCO_COLSOLVE(1) }
