@@ -70,9 +70,11 @@ def peaks():
 
 
 EVAL_SOURCES = ["paper_2403_10706_b300/csrc/k_eval.cu",
+                "paper_2403_10706_b300/csrc/eval_march.cuh",
                 "paper_2403_10706_b300/csrc/eval_common.cuh",
                 "paper_2403_10706_b300/csrc/hysco_internal.cuh"]
 PCG_SOURCES = ["paper_2403_10706_b300/csrc/k_pcg_persistent.cu",
+               "paper_2403_10706_b300/csrc/pcg_run.cuh",
                "paper_2403_10706_b300/csrc/grid_sync.cuh",
                "paper_2403_10706_b300/csrc/hysco_internal.cuh"]
 
@@ -477,7 +479,26 @@ def batch_bench(dev, stream, flush, reps=2):
         t = sum(a.elapsed_time(b) for a, b in evs) / 1e3
         out[name] = len(pairs) * reps / t
         out[name + "_status_nonzero"] = sum(1 for h in hs if h.last_status() != 0)
+    # two fixed schedules beside the tuned one: waves whose PCGs share a launch per GN step
+    # (policy 4) and waves whose whole GN loops are one persistent launch (policy 7)
+    fixed = {}
+    for label, pol in (("pcg_waves_policy4", 4), ("gn_loop_waves_policy7", 7)):
+        try:
+            batch.set_schedule(2, pol)
+        except RuntimeError:
+            continue
+        run_batch()
+        torch.cuda.synchronize()
+        flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run_batch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fixed[label] = len(pairs) / (e0.elapsed_time(e1) / 1e3)
+    batch.set_schedule(sched[0], sched[1])
     out.update({"unit": UNIT, "speedup": out["batched"] / out["sequential"],
+                "fixed_schedules_2_branches": fixed,
                 "schedule": {"branches": sched[0], "block_share_policy": sched[1],
                              "pcg_grid_blocks": sched[2]},
                 "tune_s": tune_s, "generate_s": gen_s,

@@ -167,22 +167,23 @@ k_zrhs(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* _
 // C + z cz + (i / rp) cp + (i % rp) ci + j cj (rp rows per plane, so that the planes' rows can be
 // one tall operand).  A block computes a kGmM x kGmN tile of C over kGmK-deep panels of A and B
 // in shared memory, double-buffered: the next panel's copies (cp.async, straight to shared memory)
-// are in flight while the current one is multiplied.  Each thread holds an 8 x 8 block of outputs: rows 4 ty + a and
-// kGmM / 2 + 4 ty + a, columns 4 tx + b and kGmN / 2 + 4 tx + b (a, b < 4), so that its operands
-// of a depth step are four 16-byte shared loads that consecutive threads take from consecutive
-// words (no bank conflicts).  SCALE multiplies entry (i, j) by rho / lambda, lambda =
+// are in flight while the current one is multiplied.  Each thread holds a 4 x 8 block of outputs:
+// rows 4 ty + a (a < 4), columns 4 tx + b and kGmN / 2 + 4 tx + b (b < 4), so that its operands of
+// a depth step are three 16-byte shared loads that consecutive threads take from consecutive
+// words (no bank conflicts); 252 threads per 72 x 112 tile keep 18 warps per SM busy on the 3T
+// planes' few hundred tiles.  SCALE multiplies entry (i, j) by rho / lambda, lambda =
 // rho + alpha (wB muB[i % rp] + wA muA[j]) (rho from the device state).
 struct PlaneOperand {
   const float* p;
   long long sz, si, sj;
 };
 constexpr int kGmM = 72, kGmN = 112, kGmK = 16;
-constexpr int kGmTy = kGmM / 8, kGmTx = kGmN / 8, kGmThreads = kGmTy * kGmTx;   // 9 x 14
+constexpr int kGmTy = kGmM / 4, kGmTx = kGmN / 8, kGmThreads = kGmTy * kGmTx;   // 18 x 14
 constexpr int kGmLdA = (kGmM * kGmK + kGmThreads - 1) / kGmThreads;   // copies per thread
 constexpr int kGmLdB = (kGmK * kGmN + kGmThreads - 1) / kGmThreads;
 
 template <bool SCALE>
-__global__ void __launch_bounds__(kGmThreads, 4)
+__global__ void __launch_bounds__(kGmThreads, 3)
 k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restrict__ C,
            long long cz, int rp, long long cp, long long ci, long long cj,
            const float* __restrict__ muB, const float* __restrict__ muA, float alpha, float wB,
@@ -228,9 +229,9 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
     }
     cp_async_commit();
   };
-  float acc[8][8];
+  float acc[4][8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
   const int np = (K + kGmK - 1) / kGmK;
@@ -244,13 +245,12 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
 #pragma unroll
     for (int l = 0; l < kGmK; ++l) {
       const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][l][4 * ty]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][l][kGmM / 2 + 4 * ty]);
       const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][l][4 * tx]);
       const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][l][kGmN / 2 + 4 * tx]);
-      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float av[4] = {a0.x, a0.y, a0.z, a0.w};
       const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
     }
@@ -258,8 +258,8 @@ k_plane_mm(int M, int N, int K, PlaneOperand A, PlaneOperand B, float* __restric
   }
   const float rho = SCALE ? st->admm_rho : 0.f;
 #pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const int i = i0 + (a < 4 ? 4 * ty + a : kGmM / 2 + 4 * ty + a - 4);
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + 4 * ty + a;
     if (i >= M) continue;
     const int ip = i / rp, ir = i - ip * rp;
     float* Crow = C + z * cz + ip * cp + ir * ci;

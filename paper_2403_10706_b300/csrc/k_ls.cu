@@ -196,13 +196,14 @@ template <typename TI>
 __global__ void __launch_bounds__(kBlock)
 k_ls_rows(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
           const float* __restrict__ b, float lambda, float* __restrict__ ws, long long wstride,
-          int* __restrict__ flag) {
+          int* __restrict__ flag, FastDiv ncols_div) {
   constexpr int W = kLsBand;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)g.m * g.ncols) return;
-  const int j = (int)(t / g.ncols), c = (int)(t - (long long)j * g.ncols);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // < m * ncols < 2^31
+  if (t >= g.m * g.ncols) return;
+  const int j = (int)fdiv((unsigned)t, ncols_div), c = t - j * g.ncols;
   const int inner = g.inner, m = g.m;
-  const int ib = col_base(c, inner, g.img_ostride), fb = col_base(c, inner, g.fld_ostride);
+  const int o = (int)fdiv((unsigned)c, g.divIn), ci = c - o * inner;
+  const int ib = o * (int)g.img_ostride + ci, fb = o * (int)g.fld_ostride + ci;
   // b at nodes j .. j + W + 1 (node m past the column's end) and the reciprocal lengths
   // 1 / (e_{u+1} - e_u) of the mapped cells j .. j + W for both directions
   float bw[W + 2], ilp[W + 1], ilm[W + 1];
@@ -237,10 +238,10 @@ k_ls_rows(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
     }
   }
   if (fl) atomicOr(flag + c, fl);
-  const int o = ib + j * inner;
+  const int oj = ib + j * inner;
 #pragma unroll
-  for (int d = 0; d <= W; ++d) ws[d * wstride + o] = N[d];
-  ws[(W + 1) * wstride + o] = r;
+  for (int d = 0; d <= W; ++d) ws[d * wstride + oj] = N[d];
+  ws[(W + 1) * wstride + oj] = r;
 }
 
 constexpr int kLsRing = 16;   // workspace rows a column's thread has in flight (shared ring)
@@ -284,6 +285,7 @@ k_ls_solve(Geo g, float* __restrict__ ws, long long wstride, const int* __restri
     for (int d = 0; d < W; ++d) Lw[t][d] = 0.f;
   }
   for (int u = 0; u < R - 1; ++u) fetch_row(u);
+#pragma unroll 2
   for (int j = 0; j < m; ++j) {
     fetch_row(j + R - 1);
     cp_async_wait<R - 1>();   // row j has landed
@@ -299,7 +301,7 @@ k_ls_solve(Geo g, float* __restrict__ ws, long long wstride, const int* __restri
       dj -= ljk * ljk * Dw[t];
       yj -= ljk * yw[t];
     }
-    const float idj = 1.0f / dj;
+    const float idj = __frcp_rn(dj);   // = 1.0f / dj, correctly rounded
     float Lnew[W];
 #pragma unroll
     for (int d = 0; d < W; ++d) {
@@ -367,7 +369,7 @@ cudaError_t launch_ls_correct(const Geo& g, int dtype, const void* Ip, const voi
   auto run = [&](auto tag) -> cudaError_t {
     using T = decltype(tag);
     k_ls_rows<T><<<grid0, kBlock, 0, s>>>(g, (const T*)Ip, (const T*)Im, b, lambda, band, bstride,
-                                          wide);
+                                          wide, make_fastdiv((unsigned)g.ncols));
     k_ls_solve<<<ceil_div(g.ncols, 32), 32, 0, s>>>(g, band, bstride, wide, out, nbad);
     if (staged) {
       if (cudaError_t ea = cudaFuncSetAttribute(k_ls_correct<T, kLsBandWide, true>,

@@ -171,13 +171,13 @@ k_from_pitched(Geo g, const float* __restrict__ src, float* __restrict__ dst) {
 }
 
 // Per-column block preconditioner (end of Sec. 2.3.1): one thread per PE column marches along it
-// in registers (coalesced row loads across the warp), the loads of the next kColAhead nodes
-// issued before the sequential recurrence of the current ones (two register buffers), so that
-// every thread of the grid does useful work, no shared memory is needed, and the memory latency
-// of a column's march overlaps its arithmetic.
+// (coalesced row accesses across the warp), the values of the next kColRing - 1 nodes already
+// on their way through a per-thread shared-memory ring (cp.async: each thread its own words, so
+// no block barrier), so the sequential recurrence waits on arithmetic, not on memory.
 //   M = tridiag(vol (e_k - alpha), vol (d_k + alpha (npe_k + nin)), vol (e_k - alpha)), M = L D L^T:
 //   D_0 = dia_0, l_k = off_k / D_k, D_{k+1} = dia_{k+1} - l_k off_k; stored 1 / D_k and l_k.
-constexpr int kColAhead = 16;
+constexpr int kColRing = 16;
+constexpr int kColGroup = 4;   // nodes per copy group (one commit and one wait per group)
 // threads per block of the column kernels: a column per thread and one warp per block, so that
 // the few thousand columns spread over every SM (the sequential recurrences are latency-bound)
 constexpr int kColBlock = 32;
@@ -194,58 +194,52 @@ __device__ __forceinline__ ColPos col_pos(const Geo& g, int c) {
   return q;
 }
 
-// Runs body(k0, buf) over blocks of kColAhead steps k0 = first, first + step, ... (n blocks),
-// with load(k0, buf) for block i + 1 issued before body of block i (two buffers).
-template <typename Buf, typename Load, typename Body>
-__device__ __forceinline__ void col_pipeline(int first, int step, int n, Load&& load,
-                                             Body&& body) {
-  Buf A, B;
-  if (n > 0) load(first, A);
-  for (int i = 0; i < n; i += 2) {
-    if (i + 1 < n) load(first + (i + 1) * step, B);
-    body(first + i * step, A);
-    if (i + 1 < n) {
-      if (i + 2 < n) load(first + (i + 2) * step, A);
-      body(first + (i + 1) * step, B);
-    }
-  }
-}
-
 __global__ void __launch_bounds__(kColBlock)
 k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco,
              float* __restrict__ invD, float* __restrict__ lco) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int R = kColRing, NG = kColRing / kColGroup;
+  __shared__ float ring[R][2][kColBlock];
+  const int lane = threadIdx.x, c = blockIdx.x * kColBlock + lane;
   if (c >= g.ncols) return;
   const ColPos cp = col_pos(g, c);
   const int E = g.E, m = g.m, ps = g.psP, fb = cp.base;
+  const float vol = g.vol, alpha = g.alpha;
+  // step k (0 .. E - 2) reads e_k and d_{k+1}; copy group q holds steps kColGroup q .. + 3
+  auto fetch = [&](int q) {
+#pragma unroll
+    for (int u = 0; u < kColGroup; ++u) {
+      const int k = q * kColGroup + u, kk = min(k, E - 2), sl = k % R;
+      cp_async4(&ring[sl][0][lane], eco + fb + kk * ps, true);
+      cp_async4(&ring[sl][1][lane], dco + fb + (kk + 1) * ps, true);
+    }
+    cp_async_commit();
+  };
   // dia_0 (npe = 1: node 0 has one PE neighbour)
-  float D = g.vol * (__ldg(dco + fb) + g.alpha * (1.0f + cp.nin));
-  struct Buf { float ev[kColAhead], dv[kColAhead]; };
-  auto load = [&](int k0, Buf& x) {
+  float D = vol * (__ldg(dco + fb) + alpha * (1.0f + cp.nin));
+  for (int q = 0; q < NG - 1; ++q) fetch(q);
+  for (int q = 0; q * kColGroup < E - 1; ++q) {
+    fetch(q + NG - 1);
+    cp_async_wait<NG - 1>();
+    // no branch inside the group (steps past the column's end are predicated off), so the
+    // compiler can issue the group's shared loads ahead of its recurrence
 #pragma unroll
-    for (int u = 0; u < kColAhead; ++u) {
-      const int kk = min(k0 + u, E - 2);
-      x.ev[u] = __ldg(eco + fb + kk * ps);
-      x.dv[u] = __ldg(dco + fb + (kk + 1) * ps);
-    }
-  };
-  auto body = [&](int k0, const Buf& x) {
-#pragma unroll
-    for (int u = 0; u < kColAhead; ++u) {
-      const int kk = k0 + u;
-      if (kk < E - 1) {
-        const float ok = g.vol * (x.ev[u] - g.alpha);
-        const float iD = 1.0f / D;
-        const float l = ok * iD;
-        invD[fb + kk * ps] = iD;
-        lco[fb + kk * ps] = l;
-        const float npe = (float)(1 + (kk + 1 < m));
-        D = fmaf(-l, ok, g.vol * (x.dv[u] + g.alpha * (npe + cp.nin)));
+    for (int u = 0; u < kColGroup; ++u) {
+      const int k = q * kColGroup + u, sl = k % R;
+      const bool in = k < E - 1;
+      const float ok = vol * (ring[sl][0][lane] - alpha);
+      const float iD = __frcp_rn(D);   // = 1.0f / D, correctly rounded
+      const float l = ok * iD;
+      if (in) {
+        invD[fb + k * ps] = iD;
+        lco[fb + k * ps] = l;
       }
+      const float npe = (float)(1 + (k + 1 < m));
+      const float Dn = fmaf(-l, ok, vol * (ring[sl][1][lane] + alpha * (npe + cp.nin)));
+      D = in ? Dn : D;
     }
-  };
-  col_pipeline<Buf>(0, kColAhead, ceil_div(E - 1, kColAhead), load, body);
-  invD[fb + (E - 1) * ps] = 1.0f / D;
+  }
+  cp_async_wait<0>();
+  invD[fb + (E - 1) * ps] = __frcp_rn(D);
   lco[fb + (E - 1) * ps] = 0.f;
 }
 
@@ -260,77 +254,118 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
             double rtol, float sign, float* partials, unsigned* counter, DevState* st) {
   if (MODE != 0 && st->stop) return;
   if (MODE == 2 && st->pcg_done) return;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  constexpr int R = kColRing, NA = 5, NG = kColRing / kColGroup;
+  __shared__ float ring[R][NA][kColBlock];
+  const int lane = threadIdx.x, c = blockIdx.x * kColBlock + lane;
   float arr = 0.f, arz = 0.f;
   if (c < g.ncols) {
     const int E = g.E, ps = g.psP, fb = col_pos(g, c).base;
     const float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
-    // the residual at pitched offset i (MODE 1 / 2 also update x and r there)
-    auto resid = [&](int i) {
+    // the residual at pitched offset i from its inputs v (MODE 1 / 2 also update x and r there)
+    auto resid = [&](int i, const float* v) {
       float rk;
       if (MODE == 0) {
-        rk = r[i];
+        rk = v[0];
       } else if (MODE == 1) {
-        rk = sign * __ldg(grad + i);
+        rk = sign * v[0];
         x[i] = 0.f;
         r[i] = rk;
       } else {
-        const float pk = __ldg(p + i);
-        x[i] = first ? a * pk : fmaf(a, pk, x[i]);
-        rk = fmaf(-a, __ldg(Hp + i), r[i]);
+        x[i] = first ? a * v[0] : fmaf(a, v[0], v[3]);
+        rk = fmaf(-a, v[1], v[2]);
         r[i] = rk;
       }
       return rk;
     };
-    // forward: y_0 = r_0, y_k = r_k - l_{k-1} y_{k-1}
-    float y = resid(fb);
-    arr += y * y;
-    z[fb] = y;
-    struct Fwd { float rv[kColAhead], lv[kColAhead]; };
-    auto fload = [&](int k0, Fwd& f) {
-#pragma unroll
-      for (int u = 0; u < kColAhead; ++u) {
-        const int kk = min(k0 + u, E - 1);
-        f.lv[u] = __ldg(lco + fb + (kk - 1) * ps);
-        f.rv[u] = k0 + u < E ? resid(fb + kk * ps) : 0.f;
+    // inputs at node i: r (MODE 0); grad (MODE 1); p, Hp, r, x (MODE 2)
+    auto inputs = [&](int i, float* v) {
+      if (MODE == 0) { v[0] = r[i]; }
+      else if (MODE == 1) { v[0] = __ldg(grad + i); }
+      else { v[0] = __ldg(p + i); v[1] = __ldg(Hp + i); v[2] = r[i]; v[3] = first ? 0.f : x[i]; }
+    };
+    auto fetch_inputs = [&](int i, int sl) {
+      if (MODE == 0) {
+        cp_async4(&ring[sl][1][lane], r + i, true);
+      } else if (MODE == 1) {
+        cp_async4(&ring[sl][1][lane], grad + i, true);
+      } else {
+        cp_async4(&ring[sl][1][lane], p + i, true);
+        cp_async4(&ring[sl][2][lane], Hp + i, true);
+        cp_async4(&ring[sl][3][lane], r + i, true);
+        cp_async4(&ring[sl][4][lane], x + i, !first);
       }
     };
-    auto fbody = [&](int k0, const Fwd& f) {
+    // forward: y_0 = r_0, y_k = r_k - l_{k-1} y_{k-1}; step k (1 .. E - 1) reads l_{k-1} and the
+    // inputs at node k
+    float v0[4];
+    inputs(fb, v0);
+    float y = resid(fb, v0);
+    arr += y * y;
+    z[fb] = y;
+    auto ffetch = [&](int q) {   // steps 1 + kColGroup q .. + 3
 #pragma unroll
-      for (int u = 0; u < kColAhead; ++u)
-        if (k0 + u < E) {
-          arr += f.rv[u] * f.rv[u];
-          y = fmaf(-f.lv[u], y, f.rv[u]);
-          z[fb + (k0 + u) * ps] = y;
-        }
+      for (int u = 0; u < kColGroup; ++u) {
+        const int k = 1 + q * kColGroup + u, kk = min(k, E - 1), sl = k % R, i = fb + kk * ps;
+        cp_async4(&ring[sl][0][lane], lco + i - ps, true);
+        fetch_inputs(i, sl);
+      }
+      cp_async_commit();
     };
-    col_pipeline<Fwd>(1, kColAhead, ceil_div(E - 1, kColAhead), fload, fbody);
-    // backward: z_{E-1} = y_{E-1} / D_{E-1}, z_k = y_k / D_k - l_k z_{k+1}
+    for (int q = 0; q < NG - 1; ++q) ffetch(q);
+    for (int q = 0; 1 + q * kColGroup < E; ++q) {
+      ffetch(q + NG - 1);
+      cp_async_wait<NG - 1>();
+#pragma unroll
+      for (int u = 0; u < kColGroup; ++u) {   // predicated past the column's end, no branch
+        const int k = 1 + q * kColGroup + u, sl = k % R, i = fb + k * ps;
+        if (MODE == 0 ? false : k >= E) break;   // MODE 1 / 2 write x and r in resid
+        const bool in = k < E;
+        float v[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) v[w] = ring[sl][1 + w][lane];
+        const float rk = resid(i, v);
+        const float yn = fmaf(-ring[sl][0][lane], y, rk);
+        if (in) {
+          arr += rk * rk;
+          y = yn;
+          z[i] = y;
+        }
+      }
+    }
+    cp_async_wait<0>();
+    __threadfence_block();   // this thread's y (in z) and r stores before its copies read them back
+    // backward: z_{E-1} = y_{E-1} / D_{E-1}, z_k = y_k / D_k - l_k z_{k+1}; step t reads node
+    // k = E - 2 - t: y_k, l_k, 1 / D_k (and r_k)
     float zz = y * __ldg(invD + fb + (E - 1) * ps);
     z[fb + (E - 1) * ps] = zz;
     if (MODE != 0) arz += r[fb + (E - 1) * ps] * zz;
-    constexpr int kB = kColAhead / 2;
-    struct Bwd { float yv[kB], lv[kB], iv[kB], rv[kB]; };
-    auto bload = [&](int k1, Bwd& q) {
+    auto bfetch = [&](int q) {   // steps kColGroup q .. + 3
 #pragma unroll
-      for (int u = 0; u < kB; ++u) {
-        const int kk = max(k1 - u, 0);
-        q.yv[u] = z[fb + kk * ps];
-        q.lv[u] = __ldg(lco + fb + kk * ps);
-        q.iv[u] = __ldg(invD + fb + kk * ps);
-        q.rv[u] = MODE != 0 ? r[fb + kk * ps] : 0.f;
+      for (int u = 0; u < kColGroup; ++u) {
+        const int t = q * kColGroup + u, kk = max(E - 2 - t, 0), sl = t % R, i = fb + kk * ps;
+        cp_async4(&ring[sl][0][lane], z + i, true);
+        cp_async4(&ring[sl][1][lane], lco + i, true);
+        cp_async4(&ring[sl][2][lane], invD + i, true);
+        if (MODE != 0) cp_async4(&ring[sl][3][lane], r + i, true);
       }
+      cp_async_commit();
     };
-    auto bbody = [&](int k1, const Bwd& q) {
+    for (int q = 0; q < NG - 1; ++q) bfetch(q);
+    for (int q = 0; q * kColGroup < E - 1; ++q) {
+      bfetch(q + NG - 1);
+      cp_async_wait<NG - 1>();
 #pragma unroll
-      for (int u = 0; u < kB; ++u)
-        if (k1 - u >= 0) {
-          zz = fmaf(-q.lv[u], zz, q.yv[u] * q.iv[u]);
-          z[fb + (k1 - u) * ps] = zz;
-          if (MODE != 0) arz += q.rv[u] * zz;
+      for (int u = 0; u < kColGroup; ++u) {   // predicated past the column's start, no branch
+        const int t = q * kColGroup + u, sl = t % R, k = E - 2 - t;
+        const float zn = fmaf(-ring[sl][1][lane], zz, ring[sl][0][lane] * ring[sl][2][lane]);
+        if (k >= 0) {
+          zz = zn;
+          z[fb + k * ps] = zz;
+          if (MODE != 0) arz += ring[sl][3][lane] * zz;
         }
-    };
-    col_pipeline<Bwd>(E - 2, -kB, ceil_div(E - 1, kB), bload, bbody);
+      }
+    }
+    cp_async_wait<0>();
   }
   if (MODE == 0) return;
   float v[2] = {arr, arz};
