@@ -323,3 +323,30 @@ def test_persistent_gn_loop_stops_on_a_non_finite_objective_like_the_separate_ke
         assert status == -4, path
         assert np.array_equal(bb, b), path
         assert np.isnan(st[0, 0]) and np.all(np.isnan(st[0, 4:])) and np.all(np.isnan(st[1:])), path
+
+
+@pytest.mark.parametrize("dtype", ["bfloat16", "float16"])
+@pytest.mark.parametrize("dims,spacing,p", [SHAPES[0], SHAPES[1], SHAPES[2]])
+def test_persistent_gn_loop_half_precision_images_every_pe_axis(H, orc, dtype, dims, spacing, p):
+    """pcg_path 4 with bf16 / f16 image storage on each PE axis: the same accepted steps, PCG and
+    line-search counts as pcg_path 2 on the same quantised images, and both within the solve
+    tolerance of the FP64 oracle run on those quantised values."""
+    Ip, Im, b0 = case(dims, p, 720)
+    td = getattr(torch, dtype)
+    Ipq, Imq = dev(Ip, td), dev(Im, td)
+    h = H(dims, spacing, p, ALPHA, BETA, dtype=td)
+    runs = {}
+    for path in (2, 4):
+        bb, st = h.solve(Ipq, Imq, b=dev(b0), gn_iters=5, init=False, pcg_path=path)
+        assert h.last_status() == 0, path
+        runs[path] = (host(bb).copy(), host(st).copy())
+    (b2, s2), (b4, s4) = runs[2], runs[4]
+    assert np.array_equal(s4[:, 6], s2[:, 6]) and np.array_equal(s4[:, 7], s2[:, 7])
+    assert np.array_equal(s4[:, 9], s2[:, 9])
+    assert rel(b4, b2) <= 1e-5
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    ref, status, rst = P.solve(host(Ipq.float()), host(Imq.float()), b=b0.astype(np.float64),
+                               gn_iters=5, init=False, contract=False)
+    assert status == 0
+    assert np.array_equal(s4[:, 6], rst[:, 6])
+    assert rel(b4, ref) <= 1e-3
