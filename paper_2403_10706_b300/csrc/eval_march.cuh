@@ -10,7 +10,8 @@
 namespace hysco {
 
 constexpr int kEvalU = 4;           // nodes whose loads are issued together (evaluation)
-constexpr int kEvalUTrial = 2;      // the same for the trial and the prox variants
+constexpr int kEvalUTrial = 3;      // the same for the gamma = 1 trial (80 registers, no spill)
+constexpr int kEvalUProx = 2;       // and for the prox variants (ADMM b-subproblem)
 
 // per-thread partial sums of one objective evaluation: D, S, P (Eq. 2-4 without their factor
 // vol/2), ||grad||^2, grad^T q (trial) and ||b - c||^2 (prox)

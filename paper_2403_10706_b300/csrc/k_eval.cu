@@ -337,7 +337,7 @@ cudaError_t launch_eval(const Geo& g, int dtype, const void* Ip, const void* Im,
   const int ls_max = 0;
   const double c1 = 0.0;
   if (cpx) {
-    HYSCO_EVAL_LAUNCH(false, true, kEvalUTrial, 2)
+    HYSCO_EVAL_LAUNCH(false, true, kEvalUProx, 2)
   } else if (grad && !grad_p) {
     HYSCO_EVAL_LAUNCH(false, false, kEvalU, 1)
   } else if (!grad && grad_p) {
@@ -358,7 +358,7 @@ cudaError_t launch_eval_trial(const Geo& g, int dtype, const void* Ip, const voi
   double* terms = nullptr;
   const int it = 0;
   if (cpx) {
-    HYSCO_EVAL_LAUNCH(true, true, kEvalUTrial, 2)
+    HYSCO_EVAL_LAUNCH(true, true, kEvalUProx, 2)
   } else {
     HYSCO_EVAL_LAUNCH(true, false, kEvalUTrial, 2)
   }

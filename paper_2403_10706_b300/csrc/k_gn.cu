@@ -42,6 +42,7 @@
 namespace hysco {
 
 constexpr int kGnLsT = 2;   // Armijo halvings per pass (3 sums each fit one barrier's slots)
+constexpr int kGnUTrial = 2;   // nodes per load group of the trial inside the loop (registers)
 
 // grid_allreduce over the group with the totals also in double (hi + lo of the double-float sums)
 template <int K>
@@ -70,7 +71,7 @@ __device__ __forceinline__ EvalAcc gn_eval(const Geo& g, const GnArgs& ga, const
   EvalAcc acc;
   for (int w = rank * warps + (threadIdx.x >> 5); w < items; w += size * warps) {
     if (TRIAL)
-      eval_item<TI, true, false, kEvalUTrial, 6, false>(g, Ip, Im, b, q, nullptr, nullptr,
+      eval_item<TI, true, false, kGnUTrial, 6, false>(g, Ip, Im, b, q, nullptr, nullptr,
                                                          grad_p, dco, eco, invd, 0.f, w,
                                                          threadIdx.x & 31, acc, fout);
     else
