@@ -225,16 +225,17 @@ __device__ __forceinline__ void ls_items(const Geo& g, const TI* __restrict__ Ip
   }   // work items
 }
 
-// b += gam q over the caller-layout nodes gtid, gtid + T, ... (q pitched)
-template <bool RO>
+// b += gam q over the caller-layout nodes gtid, gtid + T, ... (q pitched); UN nodes' loads in
+// flight per thread
+template <bool RO, int UN = 4>
 __device__ __forceinline__ void update_nodes(const Geo& g, float* b, const float* q, float gam,
                                              int gtid, int T) {
   // lanes walk consecutive caller-layout nodes (coalesced b); q's pitched index by one division
-  for (int i0 = gtid; i0 < g.nf; i0 += 4 * T) {
-    float bv[4], qv[4];
-    int idx[4];
+  for (int i0 = gtid; i0 < g.nf; i0 += UN * T) {
+    float bv[UN], qv[UN];
+    int idx[UN];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < UN; ++u) {
       int i = min(i0 + u * T, g.nf - 1);
       int row = (int)fdiv((unsigned)i, g.divfe2);
       idx[u] = i;
@@ -242,7 +243,7 @@ __device__ __forceinline__ void update_nodes(const Geo& g, float* b, const float
       qv[u] = ld_in<RO>(q + row * g.P2 + (i - row * g.fe[2]));
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < UN; ++u)
       if (i0 + u * T < g.nf) b[idx[u]] = fmaf(gam, qv[u], bv[u]);
   }
 }

@@ -116,6 +116,18 @@ __device__ __forceinline__ bool grid_allreduce(float (&v)[K], unsigned* sync, un
   return grid_allreduce_then<K>(v, sync, gen, shf, shd, NoWork{}, first, count, budget, grp);
 }
 
+// grid_allreduce over the group (next generation of gen) with the totals also in double: hi + lo
+// of the double-float sums
+template <int K>
+__device__ __forceinline__ bool group_sum_d(float (&v)[K], double (&tot)[K], unsigned* sync,
+                                            unsigned& gen, float* shf, df32* shd,
+                                            BarrierGroup grp = whole_grid()) {
+  if (!grid_allreduce<K>(v, sync, ++gen, shf, shd, 0, -1, kBarrierSpinCycles, grp)) return false;
+#pragma unroll
+  for (int i = 0; i < K; ++i) tot[i] = (double)shd[i].hi + (double)shd[i].lo;
+  return true;
+}
+
 __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }

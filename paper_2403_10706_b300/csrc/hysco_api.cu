@@ -35,6 +35,7 @@ struct hysco_ctx {
   int onchip_max;     // the plan's on-chip slots before any hysco_set_pcg_onchip
   int fgrid;          // one-barrier persistent PCG grid (0: not available)
   bool gn_ok;         // the persistent GN loop (pcg_path 4) can run with the plan's grid
+  int lsu_grid;       // grid of the halvings-and-update launch (0: separate kernels)
   unsigned* psync;    // their barrier / reduction words
   bool have_lin, have_factor;
   // CUDA graph of the last solve's launch sequence and the arguments it was captured with
@@ -305,9 +306,10 @@ int hysco_create(const int64_t dims[3], const double spacing[3], int pe_dim, dou
   h->onchip_max = h->pplan.onchip;
   h->fgrid = pcg_fused_grid(h->device, pe_dim);
   h->gn_ok = h->pplan.grid > 0 && gn_setup(h->device, h->dtype, h->onchip_max) >= 1;
+  h->lsu_grid = std::min(ls_update_grid(h->device, h->dtype), h->pplan.grid);
   const int sync_grid = h->pplan.grid > h->fgrid ? h->pplan.grid : h->fgrid;
   if (sync_grid > 0 &&
-      cudaMalloc((void**)&h->psync, pcg_sync_words(sync_grid) * sizeof(unsigned)) !=
+      cudaMalloc((void**)&h->psync, 2 * pcg_sync_words(sync_grid) * sizeof(unsigned)) !=
           cudaSuccess) {
     free_all(h);
     delete h;
@@ -596,6 +598,12 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
     // accepted), then the remaining halvings in batches of kLsBatch, J only
     HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, h->dco, h->eco,
                                 h->invd, o->ls_max_iters, o->armijo_c1, w, s));
+    if (mode == kPcgPersistent && h->lsu_grid > 0) {   // halvings and update, one launch
+      HYSCO_TRY(launch_ls_update(g, h->dtype, h->lsu_grid, Ip, Im, b_inout, h->x, it,
+                                 o->ls_max_iters, o->armijo_c1, stats,
+                                 h->psync + pcg_sync_words(h->pplan.grid), h->st, s));
+      continue;
+    }
     for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)
       HYSCO_TRY(launch_linesearch(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, t0,
                                   o->ls_max_iters, o->armijo_c1, w, s));

@@ -411,6 +411,13 @@ cudaError_t launch_linesearch(const Geo& g, int dtype, const void* Ip, const voi
                               const float* cpx = nullptr);
 cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double* stats,
                           const Work& w, cudaStream_t s);
+// the Armijo halvings (when the gamma = 1 trial left them undecided) and the update in one
+// cooperative launch of `grid` kPcgBlock-thread blocks (ls_update_grid: one per SM, 0 when the
+// device cannot run it); sync: pcg_sync_words(grid) zeroed words
+int ls_update_grid(int device, int dtype);
+cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, const void* Im,
+                             float* b, const float* q, int it, int ls_max, double c1,
+                             double* stats, unsigned* sync, DevState* st, cudaStream_t s);
 // Tm == nullptr: Tp receives the corrected image 1/2 (T+ + T-)
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s);
@@ -556,6 +563,7 @@ void set_march_warps(Geo& g, int warps);
 // sync: the problems' sync words, sync_words of them, zeroed first
 cudaError_t launch_gn_wave(const GnWave& w, int dtype, int grid, int onchip_max, unsigned* sync,
                            size_t sync_words, cudaStream_t s);
+// sync: 2 * pcg_sync_words(pl.grid) words, all zeroed first (the second half for launch_ls_update)
 cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,

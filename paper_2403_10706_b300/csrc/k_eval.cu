@@ -18,6 +18,7 @@
 #include <algorithm>
 
 #include "eval_march.cuh"
+#include "grid_sync.cuh"
 
 namespace hysco {
 
@@ -180,34 +181,101 @@ k_linesearch(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im,
   }
 }
 
+// the statistics row of GN iteration `it` (one thread): J, D, S, P, ||grad||, grad^T q, gamma,
+// PCG iterations, relative residual, line-search trials; NaN past a stop
+__device__ __forceinline__ void write_stats_row(const DevState* st, double* stats, int it) {
+  if (!stats) return;
+  const double nan = __longlong_as_double(0x7ff8000000000000LL);
+  const bool stopped_before = st->stop && st->stop_iter < it;
+  const bool stopped_now = st->stop && st->stop_iter == it;
+  double* row = stats + it * 10;
+  if (stopped_before) {
+    for (int i = 0; i < 10; ++i) row[i] = nan;
+  } else {
+    row[0] = st->J; row[1] = st->D; row[2] = st->S; row[3] = st->P;
+    if (stopped_now) {
+      for (int i = 4; i < 10; ++i) row[i] = nan;
+    } else {
+      row[4] = st->gnorm; row[5] = st->gq; row[6] = st->gamma; row[7] = st->pcg_iter;
+      row[8] = st->relres; row[9] = st->ls_trials;
+    }
+  }
+}
+
 // b += gamma q (b in the caller's layout, q pitched); block 0 records the iteration's statistics
 __global__ void __launch_bounds__(kBlock)
 k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, double* stats,
          DevState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    bool stopped_before = st->stop && st->stop_iter < it;
-    bool stopped_now = st->stop && st->stop_iter == it;
-    if (stats) {
-      double* row = stats + it * 10;
-      if (stopped_before) {
-        for (int i = 0; i < 10; ++i) row[i] = nan;
-      } else {
-        row[0] = st->J; row[1] = st->D; row[2] = st->S; row[3] = st->P;
-        if (stopped_now) {
-          for (int i = 4; i < 10; ++i) row[i] = nan;
-        } else {
-          row[4] = st->gnorm; row[5] = st->gq; row[6] = st->gamma; row[7] = st->pcg_iter;
-          row[8] = st->relres; row[9] = st->ls_trials;
-        }
-      }
-    }
+    write_stats_row(st, stats, it);
     st->gn_iter = it + 1;
   }
   if (st->stop) return;
   const float gam = (float)st->gamma;
   if (gam == 0.0f) return;
   update_nodes<true>(g, b, q, gam, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
+// The Armijo halvings and the GN update of one step in one cooperative launch (kPcgBlock threads,
+// one block per SM, all co-resident): when the gamma = 1 trial left the line search undecided,
+// trials gamma_t = 2^-t, t = 1 .. ls_max - 1, kLsPass per pass, each pass's sums reduced by a
+// device-wide barrier so that every block takes the same decision (the first accepted trial in
+// order, exactly as sequential halving); then b += gamma q.  After an accepted gamma = 1 trial it
+// is the update alone, with no barrier.  sync: zeroed words (the step's PCG launch clears them).
+constexpr int kLsPass = 2;   // halvings per pass (3 sums each fit one barrier's slots)
+
+template <typename TI>
+__global__ void __launch_bounds__(kPcgBlock)
+k_ls_update(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restrict__ b,
+            const float* __restrict__ q, int it, int ls_max, double c1, double* stats,
+            unsigned* sync, DevState* st) {
+  __shared__ float shf[32 * kSyncMaxK];
+  __shared__ df32 shd[kSyncMaxK];
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  const int T = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  double gamma = st->gamma;
+  if (!st->stop && !st->ls_done) {
+    const double gq = st->gq, J = st->J, hv = 0.5 * (double)g.vol;
+    const int vper = blockDim.x / kBlock;
+    int trials = st->ls_trials;
+    bool done = !(gq < 0.0);
+    gamma = 0.0;
+    unsigned gen = 0;
+    for (int t0 = 1; !done && t0 < ls_max; t0 += kLsPass) {
+      float aD[kLsPass], aS[kLsPass], aP[kLsPass], aR[kLsPass], agq = 0.f;
+#pragma unroll
+      for (int t = 0; t < kLsPass; ++t) { aD[t] = 0.f; aS[t] = 0.f; aP[t] = 0.f; aR[t] = 0.f; }
+      ls_items<TI, kSeg, kLsPass, false, true>(g, Ip, Im, b, q, nullptr, nullptr, t0,
+                                               blockIdx.x * vper + threadIdx.x / kBlock,
+                                               gridDim.x * vper, threadIdx.x % kBlock, aD, aS,
+                                               aP, aR, agq);
+      float v[3 * kLsPass];
+      double tot[3 * kLsPass];
+#pragma unroll
+      for (int t = 0; t < kLsPass; ++t) {
+        v[3 * t] = aD[t]; v[3 * t + 1] = aS[t]; v[3 * t + 2] = aP[t];
+      }
+      if (!group_sum_d<3 * kLsPass>(v, tot, sync, gen, shf, shd)) {
+        if (threadIdx.x == 0) { st->status = -6; st->stop = 1; }
+        return;
+      }
+      for (int t = 0; t < kLsPass && t0 + t < ls_max; ++t) {
+        const double gm = ldexp(1.0, -(t0 + t));
+        const double Jt = hv * tot[3 * t] + g.alpha_d * hv * tot[3 * t + 1] +
+                          g.beta_d * hv * tot[3 * t + 2];
+        trials = t0 + t + 1;
+        if (Jt <= J + c1 * gm * gq) { done = true; gamma = gm; break; }
+      }
+      if (!done && t0 + kLsPass >= ls_max) done = true;
+    }
+    if (lead) { st->ls_done = 1; st->gamma = gamma; st->ls_trials = trials; }
+  }
+  if (lead) {   // this thread wrote the line search's fields itself
+    write_stats_row(st, stats, it);
+    st->gn_iter = it + 1;
+  }
+  if (st->stop || gamma == 0.0) return;
+  update_nodes<true, 8>(g, b, q, (float)gamma, gtid, T);   // fewer threads: more nodes in flight
 }
 
 // corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta); MEAN: their average
@@ -397,6 +465,35 @@ cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double
   if (blocks > 148 * 8) blocks = 148 * 8;
   k_update<<<blocks, kBlock, 0, s>>>(g, b, q, it, stats, w.st);
   return cudaGetLastError();
+}
+
+int ls_update_grid(int device, int dtype) {
+  int sms = 0, coop = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop)
+    return 0;
+  const void* fn = dtype == 0 ? (const void*)k_ls_update<float>
+                              : (dtype == 1 ? (const void*)k_ls_update<__nv_bfloat16>
+                                            : (const void*)k_ls_update<__half>);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kPcgBlock, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms;   // one block per SM
+}
+
+cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, const void* Im,
+                             float* b, const float* q, int it, int ls_max, double c1,
+                             double* stats, unsigned* sync, DevState* st, cudaStream_t s) {
+  Geo gg = g;
+  float* bb = b;
+  const float* qq = q;
+  void* args[] = {&gg, (void*)&Ip, (void*)&Im, &bb, &qq, &it, &ls_max, &c1, &stats, &sync, &st};
+  const void* fn = dtype == 0 ? (const void*)k_ls_update<float>
+                              : (dtype == 1 ? (const void*)k_ls_update<__nv_bfloat16>
+                                            : (const void*)k_ls_update<__half>);
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kPcgBlock), args, 0, s);
 }
 
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,

@@ -44,17 +44,6 @@ namespace hysco {
 constexpr int kGnLsT = 2;   // Armijo halvings per pass (3 sums each fit one barrier's slots)
 constexpr int kGnUTrial = 2;   // nodes per load group of the trial inside the loop (registers)
 
-// grid_allreduce over the group with the totals also in double (hi + lo of the double-float sums)
-template <int K>
-__device__ __forceinline__ bool group_sum_d(float (&v)[K], double (&tot)[K], unsigned* sync,
-                                            unsigned& gen, float* shf, df32* shd,
-                                            BarrierGroup grp) {
-  if (!grid_allreduce<K>(v, sync, ++gen, shf, shd, 0, -1, kBarrierSpinCycles, grp)) return false;
-#pragma unroll
-  for (int i = 0; i < K; ++i) tot[i] = (double)shd[i].hi + (double)shd[i].lo;
-  return true;
-}
-
 // this thread's share of an evaluation at b (TRIAL: at b + q, writing b + q to fout): the column
 // march's work items rank * warps + warp, stepping by the group's warps
 template <typename TI, bool TRIAL>

@@ -424,7 +424,8 @@ cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* 
                                   float* p1, float* Hp, const float* dco, const float* eco,
                                   const float* invd, unsigned* sync, int max_it, double rtol,
                                   DevState* st, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sync, 0, pcg_sync_words(pl.grid) * sizeof(unsigned), s);
+  // the words of this launch and, after them, as many for the step's halvings-and-update launch
+  cudaError_t e = cudaMemsetAsync(sync, 0, 2 * pcg_sync_words(pl.grid) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol,
             pl.onchip};
