@@ -124,8 +124,9 @@ int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
 }
 
 // PCG for H q = sign * g about the handle's linearisation (Sec. 2.3.1); q is written to x.
+// promote (persistent mode): the launch first promotes a pending gamma = 1 stash
 int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int max_it,
-            double rtol, PcgMode mode, cudaStream_t s) {
+            double rtol, PcgMode mode, cudaStream_t s, int promote = 0) {
   const Geo& geo = h->g;
   Work w = h->work();
   if (mode == kPcgFused) {
@@ -139,7 +140,7 @@ int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int
   if (mode == kPcgPersistent) {
     HYSCO_TRY(launch_pcg_persistent(geo, h->pplan, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
                                     h->dco, h->eco, h->invd, h->psync, max_it, rtol,
-                                    h->st, s));
+                                    h->st, s, promote));
     return HYSCO_OK;
   }
   if (precond == HYSCO_PC_JACOBI) {
@@ -587,21 +588,27 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
                              pcg_sync_words(h->pplan.grid), s));
     return HYSCO_OK;
   }
+  // with the persistent PCG, each step ends in one launch: the halvings (if needed), the update
+  // and the next step's evaluation (unless the accepted gamma = 1 trial made it unnecessary, the
+  // next PCG then promoting the trial's stash)
+  const bool tail = mode == kPcgPersistent && h->lsu_grid > 0;
   for (int it = 0; it < o->gn_iters; ++it) {
-    HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, nullptr, h->grad, h->dco, h->eco, h->invd,
-                          it, w, s));
+    if (!tail || it == 0)
+      HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b_inout, nullptr, h->grad, h->dco, h->eco,
+                            h->invd, it, w, s));
     h->have_factor = false;
     if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
-                         mode, s))
+                         mode, s, tail ? 1 : 0))
       return rc;
     // gamma = 1 as a full evaluation at b + q (its coefficients serve the next GN step when
     // accepted), then the remaining halvings in batches of kLsBatch, J only
     HYSCO_TRY(launch_eval_trial(g, h->dtype, Ip, Im, b_inout, h->x, h->grad, h->dco, h->eco,
                                 h->invd, o->ls_max_iters, o->armijo_c1, w, s));
-    if (mode == kPcgPersistent && h->lsu_grid > 0) {   // halvings and update, one launch
+    if (tail) {
       HYSCO_TRY(launch_ls_update(g, h->dtype, h->lsu_grid, Ip, Im, b_inout, h->x, it,
                                  o->ls_max_iters, o->armijo_c1, stats,
-                                 h->psync + pcg_sync_words(h->pplan.grid), h->st, s));
+                                 h->psync + pcg_sync_words(h->pplan.grid), h->st, s,
+                                 it + 1 < o->gn_iters, h->grad, h->dco, h->eco, h->invd));
       continue;
     }
     for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)

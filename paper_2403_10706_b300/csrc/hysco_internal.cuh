@@ -119,6 +119,18 @@ __device__ __forceinline__ T ld_in(const T* p) {
   else return *p;
 }
 
+// After an accepted gamma = 1 trial the GN coefficients in place are those of the new iterate:
+// its stashed J, terms, gradient norm and status become the current ones and the per-step fields
+// restart (one thread).  Idempotent: a second call copies the same values.
+__device__ __forceinline__ void promote_stash(DevState* st, bool prox) {
+  st->J = st->Jn; st->D = st->Dn; st->S = st->Sn; st->P = st->Pn;
+  if (prox) st->Jacc = st->Jn;
+  st->gnorm = st->gnorm_n;
+  st->status = st->status_n;
+  st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
+  st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
+}
+
 // Asynchronous 4-byte copies global -> shared (cp.async): the copy lands in shared memory without
 // passing through registers, so the compiler cannot move it next to its use.  pred = false fills
 // the word with zero and reads nothing.  A thread sees its own copies after cp_async_wait<n>
@@ -415,9 +427,14 @@ cudaError_t launch_update(const Geo& g, float* b, const float* q, int it, double
 // cooperative launch of `grid` kPcgBlock-thread blocks (ls_update_grid: one per SM, 0 when the
 // device cannot run it); sync: pcg_sync_words(grid) zeroed words
 int ls_update_grid(int device, int dtype);
+// eval_next: also the next GN step's evaluation (grad_p, dco, eco, invd as launch_eval's) unless
+// an accepted gamma = 1 trial already wrote its coefficients; the next launch_pcg_persistent must
+// then promote (its `promote`) and the next launch_eval is not made
 cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, const void* Im,
                              float* b, const float* q, int it, int ls_max, double c1,
-                             double* stats, unsigned* sync, DevState* st, cudaStream_t s);
+                             double* stats, unsigned* sync, DevState* st, cudaStream_t s,
+                             int eval_next = 0, float* grad_p = nullptr, float* dco = nullptr,
+                             float* eco = nullptr, float* invd = nullptr);
 // Tm == nullptr: Tp receives the corrected image 1/2 (T+ + T-)
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s);
@@ -518,6 +535,7 @@ struct PcgArgs {
   int max_it;
   double rtol;
   int onchip;            // slots per thread whose r, p, Hp are in shared memory
+  int promote = 0;       // k_pcg_persistent: first promote a pending stash (promote_stash)
 };
 constexpr int kWaveSlots = 6;   // on-chip slots per thread a wave plans for (221 KB per block)
 // a wave: up to kWaveMax problems, each with its block range and arguments
@@ -568,7 +586,7 @@ cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* 
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,
                                   const float* invd, unsigned* sync, int max_it, double rtol,
-                                  DevState* st, cudaStream_t s);
+                                  DevState* st, cudaStream_t s, int promote = 0);
 // k_pcg_batched.cu: the Jacobi PCG of many pairs in one cooperative launch.  Pair i is worked
 // on by blocks blk0 .. blk0 + nblk - 1 of the grid; its arrays are those of its handle.
 struct BatchPair {

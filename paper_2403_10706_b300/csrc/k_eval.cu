@@ -38,14 +38,7 @@ __device__ __forceinline__ bool eval_skip(int it, DevState* st) {
   if (it >= 0) {
     if (st->stop) return true;
     if (st->coef_fresh) {
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->J = st->Jn; st->D = st->Dn; st->S = st->Sn; st->P = st->Pn;
-        if (PROX) st->Jacc = st->Jn;
-        st->gnorm = st->gnorm_n;
-        st->status = st->status_n;
-        st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
-        st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
-      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) promote_stash(st, PROX);
       return true;
     }
     return false;
@@ -221,26 +214,30 @@ k_update(Geo g, float* __restrict__ b, const float* __restrict__ q, int it, doub
 // trials gamma_t = 2^-t, t = 1 .. ls_max - 1, kLsPass per pass, each pass's sums reduced by a
 // device-wide barrier so that every block takes the same decision (the first accepted trial in
 // order, exactly as sequential halving); then b += gamma q.  After an accepted gamma = 1 trial it
-// is the update alone, with no barrier.  sync: zeroed words (the step's PCG launch clears them).
+// is the update alone, with no barrier.  eval_next: then, unless an accepted gamma = 1 trial left
+// the next iterate's coefficients in place (the next PCG launch then promotes the trial's stash),
+// the next GN step's evaluation at the new b, by the same grid after a barrier (the evaluation's
+// own launch is then not made).  sync: zeroed words (the step's PCG launch clears them).
 constexpr int kLsPass = 2;   // halvings per pass (3 sums each fit one barrier's slots)
 
 template <typename TI>
 __global__ void __launch_bounds__(kPcgBlock)
 k_ls_update(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restrict__ b,
             const float* __restrict__ q, int it, int ls_max, double c1, double* stats,
-            unsigned* sync, DevState* st) {
+            unsigned* sync, DevState* st, int eval_next, float* grad_p, float* dco, float* eco,
+            float* invd) {
   __shared__ float shf[32 * kSyncMaxK];
   __shared__ df32 shd[kSyncMaxK];
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   const int T = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
   double gamma = st->gamma;
+  unsigned gen = 0;
   if (!st->stop && !st->ls_done) {
     const double gq = st->gq, J = st->J, hv = 0.5 * (double)g.vol;
     const int vper = blockDim.x / kBlock;
     int trials = st->ls_trials;
     bool done = !(gq < 0.0);
     gamma = 0.0;
-    unsigned gen = 0;
     for (int t0 = 1; !done && t0 < ls_max; t0 += kLsPass) {
       float aD[kLsPass], aS[kLsPass], aP[kLsPass], aR[kLsPass], agq = 0.f;
 #pragma unroll
@@ -274,8 +271,42 @@ k_ls_update(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* 
     write_stats_row(st, stats, it);
     st->gn_iter = it + 1;
   }
-  if (st->stop || gamma == 0.0) return;
-  update_nodes<true, 8>(g, b, q, (float)gamma, gtid, T);   // fewer threads: more nodes in flight
+  if (st->stop) return;
+  if (gamma != 0.0) update_nodes<true, 8>(g, b, q, (float)gamma, gtid, T);   // 8 in flight
+  if (!eval_next || st->coef_fresh) return;   // the same in every block
+  // the next step's evaluation at the new b (read at other blocks' nodes: after a barrier)
+  {
+    float v[1] = {0.f};
+    double t1[1];
+    if (!group_sum_d<1>(v, t1, sync, gen, shf, shd)) {
+      if (threadIdx.x == 0) { st->status = -6; st->stop = 1; }
+      return;
+    }
+  }
+  EvalAcc acc;
+  const int warps = blockDim.x >> 5, items = g.ntile * g.nseg;
+  for (int w = blockIdx.x * warps + (threadIdx.x >> 5); w < items; w += gridDim.x * warps)
+    eval_item<TI, false, false, kEvalU, 2, false>(g, Ip, Im, b, nullptr, nullptr, nullptr,
+                                                   grad_p, dco, eco, invd, 0.f, w,
+                                                   threadIdx.x & 31, acc);
+  float v[4] = {acc.D, acc.S, acc.P, acc.G};
+  double tot[4];
+  if (!group_sum_d<4>(v, tot, sync, gen, shf, shd)) {
+    if (threadIdx.x == 0) { st->status = -6; st->stop = 1; }
+    return;
+  }
+  if (lead) {   // as the evaluation's own finisher for GN iteration it + 1
+    const double hv = 0.5 * (double)g.vol;
+    const double D = hv * tot[0], S = hv * tot[1], P = hv * tot[2];
+    const double J = D + g.alpha_d * S + g.beta_d * P;
+    st->J = J; st->D = D; st->S = S; st->P = P;
+    st->gnorm = sqrt(tot[3]);
+    st->status = isnan(J) ? -4 : (isinf(J) ? 1 : 0);
+    st->ls_done = 0; st->ls_trials = 0; st->gamma = 0.0; st->gq = 0.0;
+    st->pcg_done = 0; st->pcg_iter = 0; st->relres = 0.0;
+    st->coef_fresh = 0;
+    if (!isfinite(J)) { st->stop = 1; st->stop_iter = it + 1; }
+  }
 }
 
 // corrected images T+ = I+(t+)(1 + delta), T- = I-(t-)(1 - delta); MEAN: their average
@@ -485,11 +516,14 @@ int ls_update_grid(int device, int dtype) {
 
 cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, const void* Im,
                              float* b, const float* q, int it, int ls_max, double c1,
-                             double* stats, unsigned* sync, DevState* st, cudaStream_t s) {
+                             double* stats, unsigned* sync, DevState* st, cudaStream_t s,
+                             int eval_next, float* grad_p, float* dco, float* eco,
+                             float* invd) {
   Geo gg = g;
   float* bb = b;
   const float* qq = q;
-  void* args[] = {&gg, (void*)&Ip, (void*)&Im, &bb, &qq, &it, &ls_max, &c1, &stats, &sync, &st};
+  void* args[] = {&gg,    (void*)&Ip, (void*)&Im, &bb,     &qq,  &it,  &ls_max, &c1,
+                  &stats, &sync,      &st,        &eval_next, &grad_p, &dco, &eco, &invd};
   const void* fn = dtype == 0 ? (const void*)k_ls_update<float>
                               : (dtype == 1 ? (const void*)k_ls_update<__nv_bfloat16>
                                             : (const void*)k_ls_update<__half>);

@@ -45,6 +45,11 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   __shared__ float shf[32 * 2];
   __shared__ df32 shd[32 * 2];
   extern __shared__ float4 slots[];   // [r | p | Hp][onchip][kPcgBlock]
+  // the step's evaluation launch was not made (an accepted gamma = 1 trial left its coefficients
+  // in place): the trial's stash becomes the current state (only the device state's scalars, which
+  // no block of this launch reads but stop)
+  if (a.promote && blockIdx.x == 0 && threadIdx.x == 0 && a.st->coef_fresh && !a.st->stop)
+    promote_stash(a.st, false);
   unsigned gen = 0;
   pcg_run<P>(g, a, whole_grid(), shf, shd, slots, gen);
 }
@@ -423,12 +428,12 @@ cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* 
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,
                                   const float* invd, unsigned* sync, int max_it, double rtol,
-                                  DevState* st, cudaStream_t s) {
+                                  DevState* st, cudaStream_t s, int promote) {
   // the words of this launch and, after them, as many for the step's halvings-and-update launch
   cudaError_t e = cudaMemsetAsync(sync, 0, 2 * pcg_sync_words(pl.grid) * sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol,
-            pl.onchip};
+            pl.onchip, promote};
   Geo gg = g;
   void* args[] = {&gg, &a};
   void* fn = g.p == 0 ? (void*)k_pcg_persistent<0>
