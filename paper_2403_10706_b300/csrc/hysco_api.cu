@@ -124,9 +124,10 @@ int pcg_mode(const hysco_ctx* h, int precond, int path, PcgMode* mode) {
 }
 
 // PCG for H q = sign * g about the handle's linearisation (Sec. 2.3.1); q is written to x.
-// promote (persistent mode): the launch first promotes a pending gamma = 1 stash
+// promote (persistent mode): the launch first promotes a pending gamma = 1 stash and clears the
+// step's tail launch's barrier words; clear: zero the sync words first (see launch_pcg_persistent)
 int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int max_it,
-            double rtol, PcgMode mode, cudaStream_t s, int promote = 0) {
+            double rtol, PcgMode mode, cudaStream_t s, int promote = 0, int clear = 1) {
   const Geo& geo = h->g;
   Work w = h->work();
   if (mode == kPcgFused) {
@@ -140,7 +141,7 @@ int run_pcg(hysco_ctx* h, const float* g, float sign, float* x, int precond, int
   if (mode == kPcgPersistent) {
     HYSCO_TRY(launch_pcg_persistent(geo, h->pplan, g, sign, x, h->r, h->z, h->p0, h->p1, h->Hp,
                                     h->dco, h->eco, h->invd, h->psync, max_it, rtol,
-                                    h->st, s, promote));
+                                    h->st, s, promote, clear));
     return HYSCO_OK;
   }
   if (precond == HYSCO_PC_JACOBI) {
@@ -598,7 +599,7 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
                             h->invd, it, w, s));
     h->have_factor = false;
     if (int rc = run_pcg(h, h->grad, -1.0f, h->x, o->precond, o->pcg_max_iters, o->pcg_rtol,
-                         mode, s, tail ? 1 : 0))
+                         mode, s, tail ? 1 : 0, !tail || it == 0))
       return rc;
     // gamma = 1 as a full evaluation at b + q (its coefficients serve the next GN step when
     // accepted), then the remaining halvings in batches of kLsBatch, J only
@@ -608,7 +609,8 @@ int enqueue_solve(hysco_t h, const void* Ip, const void* Im, float* b_inout, con
       HYSCO_TRY(launch_ls_update(g, h->dtype, h->lsu_grid, Ip, Im, b_inout, h->x, it,
                                  o->ls_max_iters, o->armijo_c1, stats,
                                  h->psync + pcg_sync_words(h->pplan.grid), h->st, s,
-                                 it + 1 < o->gn_iters, h->grad, h->dco, h->eco, h->invd));
+                                 it + 1 < o->gn_iters, h->grad, h->dco, h->eco, h->invd,
+                                 h->psync, (int)pcg_sync_words(h->pplan.grid)));
       continue;
     }
     for (int t0 = 1; t0 < o->ls_max_iters; t0 += kLsBatch)

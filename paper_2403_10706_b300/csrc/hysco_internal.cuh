@@ -434,7 +434,8 @@ cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, 
                              float* b, const float* q, int it, int ls_max, double c1,
                              double* stats, unsigned* sync, DevState* st, cudaStream_t s,
                              int eval_next = 0, float* grad_p = nullptr, float* dco = nullptr,
-                             float* eco = nullptr, float* invd = nullptr);
+                             float* eco = nullptr, float* invd = nullptr,
+                             unsigned* clear = nullptr, int nclear = 0);
 // Tm == nullptr: Tp receives the corrected image 1/2 (T+ + T-)
 cudaError_t launch_correct(const Geo& g, int dtype, const void* Ip, const void* Im,
                            const float* b, float* Tp, float* Tm, cudaStream_t s);
@@ -516,7 +517,7 @@ constexpr int kSyncHeader = 32;   // words before the partial-sum slots (the arr
 constexpr int kSyncMaxK = 8;      // floats per block and slot (widest fused reduction)
 constexpr int kTagWordsPerLaneHost = 16;   // grid_allreduce_unordered's block-range limit / 32
 // counter line, two float slots of kSyncMaxK per block, two slots of one tagged 64-bit word per block
-inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid + 4ull * (size_t)grid; }
+__host__ __device__ inline size_t pcg_sync_words(int grid) { return kSyncHeader + 2ull * kSyncMaxK * (size_t)grid + 4ull * (size_t)grid; }
 // arguments of one problem's persistent PCG
 struct PcgArgs {
   const float* grad;     // right-hand side is rhs_sign * grad
@@ -535,7 +536,9 @@ struct PcgArgs {
   int max_it;
   double rtol;
   int onchip;            // slots per thread whose r, p, Hp are in shared memory
-  int promote = 0;       // k_pcg_persistent: first promote a pending stash (promote_stash)
+  int promote = 0;       // k_pcg_persistent in a solve's step sequence: first promote a pending
+                         // stash (promote_stash), and clear the tail launch's barrier words
+                         // (the pcg_sync_words(grid) after this launch's own)
 };
 constexpr int kWaveSlots = 6;   // on-chip slots per thread a wave plans for (221 KB per block)
 // a wave: up to kWaveMax problems, each with its block range and arguments
@@ -581,12 +584,14 @@ void set_march_warps(Geo& g, int warps);
 // sync: the problems' sync words, sync_words of them, zeroed first
 cudaError_t launch_gn_wave(const GnWave& w, int dtype, int grid, int onchip_max, unsigned* sync,
                            size_t sync_words, cudaStream_t s);
-// sync: 2 * pcg_sync_words(pl.grid) words, all zeroed first (the second half for launch_ls_update)
+// sync: 2 * pcg_sync_words(pl.grid) words (the second half for launch_ls_update), all zeroed
+// first unless clear == 0 (in a solve's step sequence after the first step, where the previous
+// step's tail launch has cleared this launch's words and this launch clears the tail's)
 cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* grad,
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,
                                   const float* invd, unsigned* sync, int max_it, double rtol,
-                                  DevState* st, cudaStream_t s, int promote = 0);
+                                  DevState* st, cudaStream_t s, int promote = 0, int clear = 1);
 // k_pcg_batched.cu: the Jacobi PCG of many pairs in one cooperative launch.  Pair i is worked
 // on by blocks blk0 .. blk0 + nblk - 1 of the grid; its arrays are those of its handle.
 struct BatchPair {

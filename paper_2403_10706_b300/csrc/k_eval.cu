@@ -225,13 +225,15 @@ __global__ void __launch_bounds__(kPcgBlock)
 k_ls_update(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restrict__ b,
             const float* __restrict__ q, int it, int ls_max, double c1, double* stats,
             unsigned* sync, DevState* st, int eval_next, float* grad_p, float* dco, float* eco,
-            float* invd) {
+            float* invd, unsigned* clear, int nclear) {
   __shared__ float shf[32 * kSyncMaxK];
   __shared__ df32 shd[kSyncMaxK];
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   const int T = gridDim.x * blockDim.x, gtid = blockIdx.x * blockDim.x + threadIdx.x;
   double gamma = st->gamma;
   unsigned gen = 0;
+  // the next step's PCG launch's barrier words (not used by this launch)
+  for (int i = gtid; i < nclear; i += T) clear[i] = 0u;
   if (!st->stop && !st->ls_done) {
     const double gq = st->gq, J = st->J, hv = 0.5 * (double)g.vol;
     const int vper = blockDim.x / kBlock;
@@ -518,12 +520,13 @@ cudaError_t launch_ls_update(const Geo& g, int dtype, int grid, const void* Ip, 
                              float* b, const float* q, int it, int ls_max, double c1,
                              double* stats, unsigned* sync, DevState* st, cudaStream_t s,
                              int eval_next, float* grad_p, float* dco, float* eco,
-                             float* invd) {
+                             float* invd, unsigned* clear, int nclear) {
   Geo gg = g;
   float* bb = b;
   const float* qq = q;
-  void* args[] = {&gg,    (void*)&Ip, (void*)&Im, &bb,     &qq,  &it,  &ls_max, &c1,
-                  &stats, &sync,      &st,        &eval_next, &grad_p, &dco, &eco, &invd};
+  void* args[] = {&gg,        (void*)&Ip, (void*)&Im, &bb,  &qq,  &it,  &ls_max, &c1,
+                  &stats,     &sync,      &st,        &eval_next, &grad_p, &dco, &eco, &invd,
+                  &clear,     &nclear};
   const void* fn = dtype == 0 ? (const void*)k_ls_update<float>
                               : (dtype == 1 ? (const void*)k_ls_update<__nv_bfloat16>
                                             : (const void*)k_ls_update<__half>);

@@ -50,6 +50,11 @@ k_pcg_persistent(Geo g, PcgArgs a) {
   // no block of this launch reads but stop)
   if (a.promote && blockIdx.x == 0 && threadIdx.x == 0 && a.st->coef_fresh && !a.st->stop)
     promote_stash(a.st, false);
+  if (a.promote) {   // the tail launch's words, for its use after this launch
+    const int W = (int)pcg_sync_words(gridDim.x);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < W; i += gridDim.x * blockDim.x)
+      a.sync[W + i] = 0u;
+  }
   unsigned gen = 0;
   pcg_run<P>(g, a, whole_grid(), shf, shd, slots, gen);
 }
@@ -428,10 +433,12 @@ cudaError_t launch_pcg_persistent(const Geo& g, const PcgPlan& pl, const float* 
                                   float rhs_sign, float* x, float* r, float* z, float* p0,
                                   float* p1, float* Hp, const float* dco, const float* eco,
                                   const float* invd, unsigned* sync, int max_it, double rtol,
-                                  DevState* st, cudaStream_t s, int promote) {
+                                  DevState* st, cudaStream_t s, int promote, int clear) {
   // the words of this launch and, after them, as many for the step's halvings-and-update launch
-  cudaError_t e = cudaMemsetAsync(sync, 0, 2 * pcg_sync_words(pl.grid) * sizeof(unsigned), s);
-  if (e != cudaSuccess) return e;
+  if (clear) {
+    cudaError_t e = cudaMemsetAsync(sync, 0, 2 * pcg_sync_words(pl.grid) * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+  }
   PcgArgs a{grad, rhs_sign, x, r, z, p0, p1, Hp, dco, eco, invd, sync, st, max_it, rtol,
             pl.onchip, promote};
   Geo gg = g;
