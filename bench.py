@@ -102,9 +102,11 @@ def recorded_traffic(profile, sources):
     text = _current_profile(profile, sources)
     if text is None:
         return None
-    rec = dict(line.split(":", 1) for line in text.splitlines()
-               if line.startswith("dram-bytes-per-launch:"))
-    return int(rec["dram-bytes-per-launch"].strip())
+    # the first record is the summary's own kernel (later sections cover its variants)
+    for line in text.splitlines():
+        if line.startswith("dram-bytes-per-launch:"):
+            return int(line.split(":", 1)[1].strip())
+    return None
 
 
 def recorded_warp_instructions(profile, sources):
@@ -781,7 +783,10 @@ def run_ours(args):
                 "z_update_flop_per_iter": zflop, "status": h.last_status(),
                 "note": "L2 flushed before each run; J at the last iterate of each optimiser"}
     eval_roof = {"bound": "hbm", "achieved": ach_eval, "peak": peak, "unit": "GB/s",
-                 "frac": ach_eval / peak, "kernel": "k_eval<float>",
+                 "frac": ach_eval / peak,
+                 "traffic": recorded_traffic("k_eval_3t.md", EVAL_SOURCES)
+                 if args.workload == "3t" else None,
+                 "kernel": "k_eval<float>",
                  "alg_bytes_per_launch": alg_eval, "launch_ms": eval_ms}
     clk.__exit__(None, None, None)   # sampled over the timed solves, e2e and roofline launches
     # the eval kernel is bound by instruction issue: warp instructions per launch (ncu) over the
