@@ -296,6 +296,16 @@ int hysco_block_pcg(hysco_t h, const void* Ip, const void* Im, const float* b, d
  * real Fourier bases of the in-plane axes.  v, z: field-shaped float32 (device); rho > 0. */
 int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_stream_t stream);
 
+/* The z-update's arithmetic path (Sec. 2.3.2), for testing and tuning: 0 = its four per-plane
+ * basis products on the tensor cores (tcgen05 kind::tf32 with each operand split into a TF32 pair
+ * hi + lo and three products per pair, FP32 accumulation: single-precision accuracy), the default
+ * wherever both in-plane axes have at most 256 nodes; 1 = the same products in FP32 on the CUDA
+ * cores.  hysco_set_zsolve_path returns HYSCO_EINVAL for an unknown path or for path 0 where it
+ * does not apply, and drops the cached ADMM graph when the path changes; hysco_zsolve_path returns
+ * the path in use (or a negative status).  Both allocate the ADMM workspace if needed. */
+int hysco_set_zsolve_path(hysco_t h, int path);
+int hysco_zsolve_path(hysco_t h);
+
 /* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):

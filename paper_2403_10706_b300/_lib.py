@@ -97,6 +97,8 @@ def load():
         "hysco_selftest_barrier": (I, [I, I, C.c_int64, P]),
         "hysco_pcg_plan": (I, [P, C.POINTER(C.c_int32)]),
         "hysco_set_pcg_onchip": (I, [P, I]),
+        "hysco_set_zsolve_path": (I, [P, I]),
+        "hysco_zsolve_path": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

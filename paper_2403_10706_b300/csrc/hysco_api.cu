@@ -49,6 +49,10 @@ struct hysco_ctx {
   // iteration), u, c = z - u and the b of the iteration's start, pitched; the in-plane bases
   float *az[2], *au, *ac, *abprev;
   float *aQA, *aQB, *amuA, *amuB;
+  // the z-update's tensor-core plan (null where it does not apply) and the path in use:
+  // 0 tensor cores (tcgen05, TF32 three-term split), 1 FP32 products on the CUDA cores
+  ZgPlan* zg;
+  int zpath;
   // least-squares correction workspace (allocated at the first hysco_ls_correct call): the
   // normal matrix's band (kLsBandWide image-shaped arrays), its right-hand side, column flags
   float* lsw;
@@ -95,6 +99,7 @@ void free_all(hysco_ctx* h) {
   for (float* b : abufs)
     if (b) cudaFree(b);
   if (h->agexec) cudaGraphExecDestroy(h->agexec);
+  zg_destroy(h->zg);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->st) cudaFree(h->st);
 }
@@ -764,6 +769,10 @@ int admm_setup(hysco_ctx* h) {
   std::vector<float> QA, QB, muA, muB;
   real_fourier_basis(h->g.nA, QA, muA);
   real_fourier_basis(h->g.nB, QB, muB);
+  if (!h->zg) {
+    h->zg = zg_create(h->g, QA, QB);
+    h->zpath = h->zg ? 0 : 1;
+  }
   struct { float** d; const std::vector<float>* v; } up[] = {
       {&h->aQA, &QA}, {&h->aQB, &QB}, {&h->amuA, &muA}, {&h->amuB, &muB}};
   for (auto& u : up) {
@@ -781,6 +790,13 @@ int admm_setup(hysco_ctx* h) {
     *u.d = d;   // set only once uploaded: amuB marks a complete setup
   }
   return HYSCO_OK;
+}
+
+// the z-update by the handle's path (admm_setup has run)
+cudaError_t zsolve(hysco_ctx* h, const float* b, const float* u, float* z, cudaStream_t s) {
+  const AdmmBasis basis{h->aQA, h->aQB, h->amuA, h->amuB};
+  if (h->zpath == 0 && h->zg) return launch_zgemm_zsolve(h->zg, h->g, b, u, basis, z, h->st, s);
+  return launch_admm_zsolve(h->g, b, u, basis, h->tmp, h->q0, z, h->st, s);
 }
 
 int check_admm_opts(const hysco_ctx* h, const hysco_admm_opts* o) {
@@ -816,7 +832,6 @@ int enqueue_admm(hysco_ctx* h, const void* Ip, const void* Im, float* b, const h
   HYSCO_TRY(launch_admm_init(h->st, rho0, stats, o->admm_iters, s));
   HYSCO_TRY(launch_to_pitched(g, b, h->az[0], s));
   HYSCO_TRY(cudaMemsetAsync(h->au, 0, (size_t)g.nfp * sizeof(float), s));
-  const AdmmBasis basis{h->aQA, h->aQB, h->amuA, h->amuB};
   for (int k = 0; k < o->admm_iters; ++k) {
     float* zc = h->az[k & 1];
     float* zn = h->az[(k + 1) & 1];
@@ -836,7 +851,7 @@ int enqueue_admm(hysco_ctx* h, const void* Ip, const void* Im, float* b, const h
     // J(b) for the statistics (a fresh full evaluation unless the run has stopped)
     HYSCO_TRY(launch_eval(g, h->dtype, Ip, Im, b, nullptr, h->grad, h->dco, h->eco, h->invd, -2,
                           w, s));
-    HYSCO_TRY(launch_admm_zsolve(g, b, h->au, basis, h->tmp, h->q0, zn, h->st, s));
+    HYSCO_TRY(zsolve(h, b, h->au, zn, s));
     HYSCO_TRY(launch_admm_post(g, b, zn, zc, h->au, h->abprev, k, o->tol, o->mu, o->tau, stats,
                                w, s));
   }
@@ -916,10 +931,27 @@ int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_str
   if (int rc = reset_state(h, s)) return rc;
   HYSCO_TRY(launch_admm_init(h->st, (float)rho, nullptr, 0, s));
   HYSCO_TRY(cudaMemsetAsync(h->ac, 0, (size_t)g.nfp * sizeof(float), s));   // u = 0
-  const AdmmBasis basis{h->aQA, h->aQB, h->amuA, h->amuB};
-  HYSCO_TRY(launch_admm_zsolve(g, v, h->ac, basis, h->tmp, h->q0, h->az[0], h->st, s));
+  HYSCO_TRY(zsolve(h, v, h->ac, h->az[0], s));
   HYSCO_TRY(launch_from_pitched(g, h->az[0], z, s));
   return HYSCO_OK;
+}
+
+int hysco_set_zsolve_path(hysco_t h, int path) {
+  if (!h || path < 0 || path > 1) return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  if (path == 0 && !h->zg) return HYSCO_EINVAL;
+  if (path != h->zpath && h->agexec) {   // the cached ADMM graph used the other path
+    cudaGraphExecDestroy(h->agexec);
+    h->agexec = nullptr;
+  }
+  h->zpath = path;
+  return HYSCO_OK;
+}
+
+int hysco_zsolve_path(hysco_t h) {
+  if (!h) return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  return h->zpath;
 }
 
 int hysco_admm(hysco_t h, const void* Ip, const void* Im, float* b_inout,

@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace hysco {
 
 // n / d for 0 <= n < 2^31 by multiply-high (Granlund & Montgomery, "Division by invariant
@@ -498,6 +500,14 @@ cudaError_t launch_admm_prep(const Geo& g, const float* b, const float* z, float
 cudaError_t launch_admm_zsolve(const Geo& g, const float* b, const float* u, const AdmmBasis& q,
                                float* T0, float* T1, float* z, const DevState* st,
                                cudaStream_t s);
+// the z-update's four products on the tensor cores (k_zgemm.cu): the plan (null where an in-plane
+// axis exceeds 256 nodes or no tensor-map encoder is available; QA, QB the host bases), its
+// release, and the launches (z pitched)
+struct ZgPlan;
+ZgPlan* zg_create(const Geo& g, const std::vector<float>& QA, const std::vector<float>& QB);
+void zg_destroy(ZgPlan* p);
+cudaError_t launch_zgemm_zsolve(const ZgPlan* p, const Geo& g, const float* b, const float* u,
+                                const AdmmBasis& q, float* z, DevState* st, cudaStream_t s);
 cudaError_t launch_admm_post(const Geo& g, const float* b, const float* z, const float* zprev,
                              float* u, const float* bprev, int it, double tol, double mu,
                              double tau, double* stats, const Work& w, cudaStream_t s);

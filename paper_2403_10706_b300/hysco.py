@@ -259,6 +259,16 @@ class Hysco:
                    "hysco_admm_zsolve")
         return out
 
+    def set_zsolve_path(self, path):
+        """The z-update's arithmetic: 0 tensor cores (TF32 split pairs), 1 FP32 CUDA cores."""
+        _lib.check(self.lib.hysco_set_zsolve_path(self._h, int(path)), "hysco_set_zsolve_path")
+
+    def zsolve_path(self):
+        """The z-update path in use (0 tensor cores, 1 CUDA cores)."""
+        rc = self.lib.hysco_zsolve_path(self._h)
+        _lib.check(min(rc, 0), "hysco_zsolve_path")
+        return rc
+
     def pcg_plan(self):
         """(cooperative grid, on-chip slots per thread, slots per thread, threads per block) of
         the persistent PCG."""

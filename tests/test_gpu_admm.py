@@ -193,19 +193,68 @@ def test_block_pcg_matches_oracle(H, orc, name, p):
     assert abs(int(it.item()) - itref) <= 0.01 * itref, (int(it.item()), itref)
 
 
+@pytest.mark.parametrize("path", [0, 1])
 @pytest.mark.parametrize("dims,spacing,p", [((32, 32, 16), (1.0, 1.0, 1.0), 1),
                                             ((9, 6, 11), (1.1, 1.0, 1.2), 0),
                                             ((5, 4, 17), (0.9, 1.3, 1.0), 2),
-                                            ((1, 7, 6), (1.0, 1.0, 1.0), 1)])
-def test_z_update_matches_the_oracles_fft(H, orc, dims, spacing, p):
-    """The z-update alone (hysco_admm_zsolve, real Fourier bases, single precision) against the
-    oracle's numpy 2D FFT inversion: relative 2e-5 (four transforms of length <= 32)."""
+                                            ((1, 7, 6), (1.0, 1.0, 1.0), 1),
+                                            ((40, 33, 150), (1.0, 1.2, 0.9), 0)])
+def test_z_update_matches_the_oracles_fft(H, orc, dims, spacing, p, path):
+    """The z-update alone (hysco_admm_zsolve, real Fourier bases) against the oracle's numpy 2D
+    FFT inversion, on the tensor cores (path 0: TF32 split pairs, three products each, FP32
+    accumulation) and on the CUDA cores (path 1, FP32): relative 2e-5 (single precision through
+    four transforms; the tensor-core products drop only the lo x lo term, below 2^-21 relative).
+    The shapes cover ragged tiles (rows and contraction lengths not multiples of the tile), a
+    one-node in-plane axis, the PE axis innermost (the other row order of the last product) and
+    in-plane axes of 150 and 40 nodes."""
     P = orc.Problem(dims, spacing, p, ALPHA, BETA)
     rng = np.random.default_rng(901)
     v = rng.standard_normal(P.fdims).astype(np.float32)
     rho = 7.5
     h = H(dims, spacing, p, ALPHA, BETA)
+    h.set_zsolve_path(path)
+    assert h.zsolve_path() == path
     z = h.admm_zsolve(torch.from_numpy(v).cuda(), rho)
     torch.cuda.synchronize()
     zref = P.admm_z_solve(rho * v.astype(np.float64), rho)
     assert rel(z.cpu().numpy(), zref) <= 2e-5, rel(z.cpu().numpy(), zref)
+
+
+@pytest.mark.parametrize("rho", [0.5, 40.0])
+def test_z_update_full_3t_size_on_the_tensor_cores(H, orc, rho):
+    """The 3T plane size (144 x 111 in-plane, 169 PE planes) on the tensor-core path, the default
+    there, against the oracle's FFT inversion, and the two paths against each other."""
+    dims, spacing, p = (144, 168, 111), (1.25, 1.25, 1.25), 1
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    rng = np.random.default_rng(902)
+    v = rng.standard_normal(P.fdims).astype(np.float32)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    assert h.zsolve_path() == 0
+    vd = torch.from_numpy(v).cuda()
+    z0 = h.admm_zsolve(vd, rho).cpu().numpy()
+    h.set_zsolve_path(1)
+    z1 = h.admm_zsolve(vd, rho).cpu().numpy()
+    zref = P.admm_z_solve(rho * v.astype(np.float64), rho)
+    assert rel(z0, zref) <= 2e-5, rel(z0, zref)
+    assert rel(z1, zref) <= 2e-5, rel(z1, zref)
+    assert h.last_status() == 0
+
+
+def test_z_update_path_switch_rejects_unknown_paths_and_rebuilds_the_graph(H):
+    """Path 2 and -1 are rejected; switching paths between two graph-captured ADMM runs gives
+    results that agree to single precision (the cached graph is rebuilt, not replayed)."""
+    pr = ph.make_pair("tiny")
+    h = H(pr.dims, pr.spacing, pr.pe_dim, ALPHA, BETA)
+    for bad in (-1, 2):
+        with pytest.raises(_lib.HyscoError):
+            h.set_zsolve_path(bad)
+    Ip, Im = torch.from_numpy(pr.Ip).cuda(), torch.from_numpy(pr.Im).cuda()
+    outs = []
+    for path in (0, 1, 0):
+        h.set_zsolve_path(path)
+        b, _ = h.admm(Ip, Im, init=1, admm_iters=4)
+        torch.cuda.synchronize()
+        outs.append(b.cpu().numpy().copy())
+    assert np.array_equal(outs[0], outs[2])
+    assert rel(outs[1], outs[0]) <= 1e-4
+    assert not np.array_equal(outs[1], outs[0])
