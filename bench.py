@@ -69,6 +69,16 @@ def peaks():
     return 6400.0, "fallback"
 
 
+def tf32_peak():
+    """Dense TF32 tensor TFLOP/s: the measured bf16 burst figure x the nominal TF32/BF16 ratio
+    (1.1 / 2.25 PFLOP/s), else the fallback bf16 figure x that ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 x 1.1/2.25"
+    return 1800.0 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
+
+
 EVAL_SOURCES = ["paper_2403_10706_b300/csrc/k_eval.cu",
                 "paper_2403_10706_b300/csrc/eval_march.cuh",
                 "paper_2403_10706_b300/csrc/eval_common.cuh",
@@ -765,6 +775,15 @@ def run_ours(args):
         admm_ms = time_launches(lambda: h.admm(Ip, Im, b=ab, init=1, admm_iters=20, tol=0.0,
                                                stats=False), n=5)
         _, ast = h.admm(Ip, Im, b=ab, init=1, admm_iters=20, tol=0.0)
+        # the z-update alone (hysco_admm_zsolve) on both arithmetic paths
+        zv = torch.randn(h.field_dims, device=dev, generator=torch.Generator(device=dev).manual_seed(7))
+        zo = torch.empty_like(zv)
+        z_path = h.zsolve_path()
+        z_ms = {}
+        for zp in ((0, 1) if z_path == 0 else (1,)):
+            h.set_zsolve_path(zp)
+            z_ms[zp] = time_launches(lambda: h.admm_zsolve(zv, 40.0, out=zo), n=20)
+        h.set_zsolve_path(z_path)
     _, gst = h.solve(Ip, Im, gn_iters=gn)
     fe = h.field_dims
     plane = [fe[a] for a in range(3) if a != pr.pe_dim]
@@ -782,6 +801,21 @@ def run_ours(args):
                 "J_gn_solve": float(gst[-1, 0].item()), "rho_final": float(ast[-1, 2].item()),
                 "z_update_flop_per_iter": zflop, "status": h.last_status(),
                 "note": "L2 flushed before each run; J at the last iterate of each optimiser"}
+        tfp, tfsrc = tf32_peak()
+        zu = {"path": "tensor cores (tcgen05 kind::tf32, split pairs)" if z_path == 0
+              else "CUDA cores (FP32)",
+              "ms": z_ms[z_path], "ms_cuda_cores": z_ms[1],
+              "speedup_vs_cuda_cores": z_ms[1] / z_ms[z_path],
+              "note": "hysco_admm_zsolve at 3T (the rhs split, four products, copy out of the "
+                      "pitched field), L2 flushed before each call"}
+        if z_path == 0:
+            # three TF32 products per basis product (hi hi, hi lo, lo hi)
+            zu["tensor_roofline"] = {"bound": "tensor", "achieved": 3 * zflop / (z_ms[0] / 1e3) / 1e12,
+                                     "peak": tfp, "unit": "TFLOP/s",
+                                     "frac": 3 * zflop / (z_ms[0] / 1e3) / 1e12 / tfp,
+                                     "peak_source": tfsrc,
+                                     "flop_per_call": 3 * zflop}
+        admm["z_update"] = zu
     eval_roof = {"bound": "hbm", "achieved": ach_eval, "peak": peak, "unit": "GB/s",
                  "frac": ach_eval / peak,
                  "traffic": recorded_traffic("k_eval_3t.md", EVAL_SOURCES)
