@@ -802,7 +802,7 @@ def run_ours(args):
                 "z_update_flop_per_iter": zflop, "status": h.last_status(),
                 "note": "L2 flushed before each run; J at the last iterate of each optimiser"}
         tfp, tfsrc = tf32_peak()
-        zu = {"path": "tensor cores (tcgen05 kind::tf32, split pairs)" if z_path == 0
+        zu = {"path": "tensor cores (tcgen05 kind::tf32, TF32 split in shared memory)" if z_path == 0
               else "CUDA cores (FP32)",
               "ms": z_ms[z_path], "ms_cuda_cores": z_ms[1],
               "speedup_vs_cuda_cores": z_ms[1] / z_ms[z_path],

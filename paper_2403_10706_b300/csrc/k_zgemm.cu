@@ -7,8 +7,8 @@
 // hi = x rounded to TF32 (10 fraction bits) and lo = x - hi (exact in FP32), and
 //   A B^T ~= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T,
 // the dropped Alo Blo^T being below 2^-21 of |A||B| per term; every product is accumulated in FP32
-// in tensor memory.  The producer of each A operand (k_zrhs, or the previous product's epilogue)
-// writes the split pair; the bases are split once on the host.
+// in tensor memory.  The operands travel in FP32; each stage is split in shared memory after its
+// TMA copy lands, so the pairs never pass through L2 or HBM.
 //
 // Chain (planes k < E, in-plane axes A (n_A, fastest) and B (n_B)); X = b + u:
 //   G1  D(k cB, jA) = sum_cA X(k, cB, cA) Q_A(cA, jA)                 forward, axis A
@@ -31,18 +31,17 @@ namespace hysco {
 
 constexpr int kZgM = 128;          // tile rows (the MMA's M; TMEM lane = row)
 constexpr int kZgKB = 16;          // contraction depth per stage: one 64-byte swizzled row of floats
-constexpr int kZgThreads = 256;    // eight warps: all take the epilogue (warps w and w + 4 share
-                                   // TMEM lanes 32 (w % 4) .., alternate 16-column chunks), one lane
-                                   // each of warps 0 and 1 first drives the TMA copies and the MMAs
+constexpr int kZgThreads = 320;    // warp 0: TMA copies, warp 1: MMAs, warps 2-9: the split of
+                                   // each stage, then the epilogue (two warps per TMEM lane quarter)
+constexpr int kZgConvThreads = 256;
 constexpr int kZgMaxStages = 12;
 constexpr int kZgMaxN = 256;       // the MMA's largest N (one tile spans all output columns)
 constexpr long long kZgSpin = 1LL << 31;   // clock cycles a wait may take before the launch gives up
 
 // where the epilogue puts D(r, j): row r -> (q, x) = (r / n_row, r % n_row), element
-// q sq + x sx + j sj of hi (and lo, for a split pair); SCALE multiplies by scale[j ss + x]
+// q sq + x sx + j sj of out; SCALE multiplies by scale[j ss + x]
 struct ZgEpi {
-  float* hi;
-  float* lo;
+  float* out;
   int n_row;
   long long sq, sx, sj;
   const float* scale;
@@ -168,37 +167,43 @@ __device__ __forceinline__ float zg_tf32(float x) {
   return __uint_as_float(u);
 }
 
-// One 128-row tile of D = A B^T per block (A: M x K, B: N x K, both K-major split pairs behind the
-// tensor maps; N <= BN <= 256, BN a multiple of 16).  Lane 0 of warp 0 copies the stages (16
-// contraction columns of A hi, A lo, B hi, B lo each; rows past M and columns past K read as
-// zeros), lane 0 of warp 1 issues three MMAs per K = 8 slice into one TMEM accumulator of BN
-// columns and frees each stage by a commit; then every thread takes its row of the accumulator
-// (tcgen05.ld, 32 columns per wait) to global memory as ZgEpi says.  A wait that runs out of its
+// One 128-row tile of D = A B^T per block (A: M x K, B: N x K, both K-major FP32 behind the
+// tensor maps; N <= BN <= 256, BN a multiple of 16).  Roles per stage of 16 contraction columns:
+//   lane 0 of warp 0   TMA-copies the FP32 tiles of A (128 rows) and B (BN rows) into the stage's
+//                      hi slots (rows past M and columns past K read as zeros);
+//   warps 2-9          split them in place: hi = x rounded to TF32, lo = x - hi into the lo slots
+//                      (an elementwise map, so the 64-byte swizzle of the copies carries over),
+//                      then fence the writes to the async proxy and arrive on the stage;
+//   lane 0 of warp 1   issues three MMAs per K = 8 slice (hi hi, hi lo, lo hi) into one TMEM
+//                      accumulator of BN columns and frees the stage by a commit.
+// Then warps 2-9 take the accumulator's rows (TMEM lane quarter warp % 4, alternate 16-column
+// chunks, 32 columns per wait) to global memory as ZgEpi says.  A wait that runs out of its
 // budget records HYSCO_ETIMEOUT in the device state and stops the solve; the launch then skips
 // its stores, frees its tensor memory and ends.
-template <bool SPLIT, bool SCALE>
+template <bool SCALE>
 __global__ void __launch_bounds__(kZgThreads, 1)
-k_zgemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-        const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, int M,
+k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M,
         int N, int K, int BN, int stages, ZgEpi ep, DevState* st) {
   if (st->stop) return;
   extern __shared__ unsigned char zg_dyn[];
-  __shared__ __align__(8) unsigned long long bars[2 * kZgMaxStages + 1];
+  __shared__ __align__(8) unsigned long long bars[3 * kZgMaxStages + 1];
   __shared__ uint32_t tmem_slot;
   __shared__ int failed;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t raw = zg_smem(zg_dyn);
   const uint32_t base = (raw + 1023u) & ~1023u;   // tiles start on 1024-byte boundaries
+  unsigned char* const gbase = zg_dyn + (base - raw);
   const uint32_t a_bytes = kZgM * kZgKB * 4, b_bytes = (uint32_t)BN * kZgKB * 4;
-  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  const uint32_t full0 = zg_smem(&bars[0]), empty0 = zg_smem(&bars[kZgMaxStages]),
-                 done = zg_smem(&bars[2 * kZgMaxStages]);
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;   // A hi, A lo, B hi, B lo
+  const uint32_t full0 = zg_smem(&bars[0]), conv0 = zg_smem(&bars[kZgMaxStages]),
+                 empty0 = zg_smem(&bars[2 * kZgMaxStages]), done = zg_smem(&bars[3 * kZgMaxStages]);
   const uint32_t ncols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
   const int nkb = (K + kZgKB - 1) / kZgKB;
   const int row0 = blockIdx.x * kZgM;
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       zg_bar_init(full0 + 8 * s, 1);
+      zg_bar_init(conv0 + 8 * s, kZgConvThreads);
       zg_bar_init(empty0 + 8 * s, 1);
     }
     zg_bar_init(done, 1);
@@ -227,18 +232,16 @@ k_zgemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtenso
         break;
       }
       const uint32_t sa = base + (uint32_t)s * stage_bytes, bar = full0 + 8 * s;
-      zg_bar_expect(bar, stage_bytes);
-      zg_tma_load(sa, &tAh, bar, kb * kZgKB, row0);
-      zg_tma_load(sa + a_bytes, &tAl, bar, kb * kZgKB, row0);
-      zg_tma_load(sa + 2 * a_bytes, &tBh, bar, kb * kZgKB, 0);
-      zg_tma_load(sa + 2 * a_bytes + b_bytes, &tBl, bar, kb * kZgKB, 0);
+      zg_bar_expect(bar, a_bytes + b_bytes);
+      zg_tma_load(sa, &tA, bar, kb * kZgKB, row0);
+      zg_tma_load(sa + 2 * a_bytes, &tB, bar, kb * kZgKB, 0);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: hi hi, hi lo, lo hi per K = 8 slice (the next slice 32 bytes along the rows)
     const uint32_t idesc = zg_idesc(kZgM, BN);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % stages;
-      if (!zg_bar_wait(full0 + 8 * s, (uint32_t)(kb / stages) & 1u)) {
+      if (!zg_bar_wait(conv0 + 8 * s, (uint32_t)(kb / stages) & 1u)) {
         failed = 1;
         break;
       }
@@ -257,58 +260,78 @@ k_zgemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtenso
       zg_commit(empty0 + 8 * s);
     }
     zg_commit(done);
+  } else if (warp >= 2) {
+    // converters: the stage's FP32 copies become TF32 pairs (hi in place, lo beside it)
+    const int ct = threadIdx.x - 64;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % stages;
+      if (!zg_bar_wait(full0 + 8 * s, (uint32_t)(kb / stages) & 1u)) {
+        failed = 1;
+        break;
+      }
+      float4* const ah = reinterpret_cast<float4*>(gbase + (size_t)s * stage_bytes);
+      float4* const bh = reinterpret_cast<float4*>(gbase + (size_t)s * stage_bytes + 2 * a_bytes);
+      const int na4 = (int)(a_bytes / 16), nb4 = (int)(b_bytes / 16);
+      for (int i = ct; i < na4 + nb4; i += kZgConvThreads) {
+        float4* const h = i < na4 ? ah + i : bh + (i - na4);
+        float4* const l = i < na4 ? ah + na4 + i : bh + nb4 + (i - na4);
+        const float4 x = *h;
+        const float4 hv = make_float4(zg_tf32(x.x), zg_tf32(x.y), zg_tf32(x.z), zg_tf32(x.w));
+        *h = hv;
+        *l = make_float4(x.x - hv.x, x.y - hv.y, x.z - hv.z, x.w - hv.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(conv0 + 8 * s) : "memory");
+    }
   }
   __syncwarp();
   const bool ok = zg_bar_wait(done, 0);
   __syncthreads();
   zg_fence_after();
   const bool good = ok && *(volatile int*)&failed == 0;
-  // epilogue: thread = row r of the tile (TMEM lane 32 (warp % 4) + lane); warps 0-3 take the
-  // even 16-column chunks, warps 4-7 the odd ones, two chunks per wait
-  const int quad = warp & 3, grp = warp >> 2;
-  const int r = row0 + quad * 32 + lane;
-  const bool rv = good && r < M;
-  long long rb = 0;
-  int x = 0;
-  if (rv) {
-    const int q = r / ep.n_row;
-    x = r - q * ep.n_row;
-    rb = (long long)q * ep.sq + (long long)x * ep.sx;
-  }
-  const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
-  const int nch = BN / 16;
-  for (int ch = grp; ch < nch; ch += 4) {
-    uint32_t v[32];
-    zg_ld16(tl + (uint32_t)(ch * 16), v);
-    const bool two = ch + 2 < nch;
-    if (two) zg_ld16(tl + (uint32_t)((ch + 2) * 16), v + 16);
-    // the chunk's scale factors, all loads in flight before the first store
-    float sc[32];
-    if (SCALE && rv) {
-#pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        const int j = min((u < 16 ? ch : ch + 2) * 16 + (u & 15), N - 1);
-        sc[u] = __ldg(ep.scale + (long long)j * ep.ss + x);
-      }
-    }
-    zg_ld_wait(v);
+  if (warp >= 2) {
+    // epilogue: thread = row r of the tile (TMEM lane 32 (warp % 4) + lane); warps 2-5 take the
+    // even 16-column chunks, warps 6-9 the odd ones, two chunks per wait
+    const int quad = warp & 3, grp = (warp - 2) >> 2;
+    const int r = row0 + quad * 32 + lane;
+    const bool rv = good && r < M;
+    long long rb = 0;
+    int x = 0;
     if (rv) {
+      const int q = r / ep.n_row;
+      x = r - q * ep.n_row;
+      rb = (long long)q * ep.sq + (long long)x * ep.sx;
+    }
+    const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+    const int nch = BN / 16;
+    __syncwarp();
+    for (int ch = grp; ch < nch; ch += 4) {
+      uint32_t v[32];
+      zg_ld16(tl + (uint32_t)(ch * 16), v);
+      const bool two = ch + 2 < nch;
+      if (two) zg_ld16(tl + (uint32_t)((ch + 2) * 16), v + 16);
+      // the chunk's scale factors, all loads in flight before the first store
+      float sc[32];
+      if (SCALE && rv) {
 #pragma unroll
-      for (int u = 0; u < 32; ++u) {
-        const int j = (u < 16 ? ch : ch + 2) * 16 + (u & 15);
-        if ((u < 16 || two) && j < N) {
-          float val = __uint_as_float(v[u]);
-          if (SCALE) val *= sc[u];
-          const long long o = rb + (long long)j * ep.sj;
-          if (SPLIT) {
-            const float h = zg_tf32(val);
-            ep.hi[o] = h;
-            ep.lo[o] = val - h;
-          } else {
-            ep.hi[o] = val;
+        for (int u = 0; u < 32; ++u) {
+          const int j = min((u < 16 ? ch : ch + 2) * 16 + (u & 15), N - 1);
+          sc[u] = __ldg(ep.scale + (long long)j * ep.ss + x);
+        }
+      }
+      zg_ld_wait(v);
+      if (rv) {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int j = (u < 16 ? ch : ch + 2) * 16 + (u & 15);
+          if ((u < 16 || two) && j < N) {
+            float val = __uint_as_float(v[u]);
+            if (SCALE) val *= sc[u];
+            ep.out[rb + (long long)j * ep.sj] = val;
           }
         }
       }
+      __syncwarp();
     }
   }
   zg_fence_before();
@@ -324,13 +347,13 @@ k_zgemm(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtenso
   }
 }
 
-// X = b + u as the split pair of G1's A operand (row k nB + cB, column cA, row pitch Kp); the
-// blocks of the first node segment also write G2's scale rho / lambda(jB, jA) with lambda =
-// rho + alpha (wB muB[jB] + wA muA[jA]) at S[jB Kp + jA] (rho from the device state)
+// X = b + u as G1's A operand (row k nB + cB, column cA, row pitch Kp); the blocks of the first
+// node segment also write G2's scale rho / lambda(jB, jA) with lambda = rho + alpha (wB muB[jB] +
+// wA muA[jA]) at S[jB Kp + jA] (rho from the device state)
 __global__ void __launch_bounds__(kBlock)
-k_zrhs_split(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* __restrict__ Xh,
-             float* __restrict__ Xl, int Kp, const float* __restrict__ muA,
-             const float* __restrict__ muB, float* __restrict__ S, const DevState* st) {
+k_zrhs_tc(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* __restrict__ X,
+          int Kp, const float* __restrict__ muA, const float* __restrict__ muB,
+          float* __restrict__ S, const DevState* st) {
   if (st->stop) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncols) return;
@@ -338,16 +361,12 @@ k_zrhs_split(Geo g, const float* __restrict__ b, const float* __restrict__ u, fl
   const int cB = c / g.nA, cA = c - cB * g.nA;
   if (blockIdx.y == 0) {
     const float rho = st->admm_rho;
-    S[(long long)cB * Kp + cA] = rho / (rho + g.alpha * (g.wB * __ldg(muB + cB) + g.wA * __ldg(muA + cA)));
+    S[(long long)cB * Kp + cA] =
+        rho / (rho + g.alpha * (g.wB * __ldg(muB + cB) + g.wA * __ldg(muA + cA)));
   }
   const int k0 = blockIdx.y * 8, k1 = min(k0 + 8, g.E);
-  for (int k = k0; k < k1; ++k) {
-    const float v = __ldg(b + fb + k * g.inner) + __ldg(u + pb + k * g.psP);
-    const float h = zg_tf32(v);
-    const long long o = ((long long)k * g.nB + cB) * Kp + cA;
-    Xh[o] = h;
-    Xl[o] = v - h;
-  }
+  for (int k = k0; k < k1; ++k)
+    X[((long long)k * g.nB + cB) * Kp + cA] = __ldg(b + fb + k * g.inner) + __ldg(u + pb + k * g.psP);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -390,10 +409,10 @@ bool zg_map(CUtensorMap* m, const float* p, int K, long long rows, int Kp, int b
 }
 
 struct ZgPlan {
-  CUtensorMap tP[2], tQ[2], tB[4][2];   // A operands (hi, lo) and the four bases (hi, lo)
-  float* P[2] = {nullptr, nullptr};     // X and Y2: E nB rows x KpA (split pair)
-  float* Q[2] = {nullptr, nullptr};     // Y1 and Y3: E nA rows x KpB
-  float* Bm = nullptr;                  // the split bases
+  CUtensorMap tP, tQ, tB[4];           // A operands and the four bases
+  float* P = nullptr;                   // X and Y2: E nB rows x KpA
+  float* Q = nullptr;                   // Y1 and Y3: E nA rows x KpB
+  float* Bm = nullptr;                  // the bases
   float* S = nullptr;                   // G2's scale rho / lambda, nB rows x KpA
   int nA = 0, nB = 0, E = 0, KpA = 0, KpB = 0, BNA = 0, BNB = 0;
   int stA = 0, stB = 0, smA = 0, smB = 0;   // stages and shared memory of G1/G3 and of G2/G4
@@ -401,7 +420,7 @@ struct ZgPlan {
 
 void zg_destroy(ZgPlan* p) {
   if (!p) return;
-  for (float* b : {p->P[0], p->P[1], p->Q[0], p->Q[1], p->Bm, p->S})
+  for (float* b : {p->P, p->Q, p->Bm, p->S})
     if (b) cudaFree(b);
   delete p;
 }
@@ -420,15 +439,6 @@ int zg_stages(int BN, int K, int tiles, int sms) {
 
 int zg_smem_bytes(int BN, int stages) {
   return stages * (2 * kZgM * kZgKB * 4 + 2 * BN * kZgKB * 4) + 1024;
-}
-
-float tf32_round_host(float x) {   // round to nearest, ties away from zero (finite x)
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  u = (u + 0x1000u) & 0xFFFFE000u;
-  float h;
-  std::memcpy(&h, &u, 4);
-  return h;
 }
 
 }  // namespace
@@ -460,57 +470,44 @@ ZgPlan* zg_create(const Geo& g, const std::vector<float>& QA, const std::vector<
   p->smB = zg_smem_bytes(p->BNB, p->stB);
   const size_t np = (size_t)E * nB * p->KpA, nq = (size_t)E * nA * p->KpB;
   const size_t nbA = (size_t)nA * p->KpA, nbB = (size_t)nB * p->KpB;
-  bool ok = true;
-  for (int i = 0; i < 2 && ok; ++i) {
-    ok = cudaMalloc((void**)&p->P[i], np * sizeof(float)) == cudaSuccess &&
-         cudaMalloc((void**)&p->Q[i], nq * sizeof(float)) == cudaSuccess;
-    // pitch padding is never read (the maps stop at K), but keep it defined
-    ok = ok && cudaMemset(p->P[i], 0, np * sizeof(float)) == cudaSuccess &&
-         cudaMemset(p->Q[i], 0, nq * sizeof(float)) == cudaSuccess;
-  }
-  ok = ok && cudaMalloc((void**)&p->Bm, (4 * nbA + 4 * nbB) * sizeof(float)) == cudaSuccess &&
-       cudaMalloc((void**)&p->S, (size_t)nB * p->KpA * sizeof(float)) == cudaSuccess;
+  // pitch padding is never read (the maps stop at K), but keep it defined
+  bool ok = cudaMalloc((void**)&p->P, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&p->Q, nq * sizeof(float)) == cudaSuccess &&
+            cudaMemset(p->P, 0, np * sizeof(float)) == cudaSuccess &&
+            cudaMemset(p->Q, 0, nq * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&p->Bm, (2 * nbA + 2 * nbB) * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&p->S, (size_t)nB * p->KpA * sizeof(float)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     zg_destroy(p);
     return nullptr;
   }
-  // B operands as N x K (K-major): G1 Q_A^T, G2 Q_B^T, G3 Q_A, G4 Q_B; each hi then lo
-  std::vector<float> hb(4 * nbA + 4 * nbB, 0.f);
-  float* Bh[4] = {hb.data(), hb.data() + 2 * nbA, hb.data() + 2 * nbA + 2 * nbB,
-                  hb.data() + 4 * nbA + 2 * nbB};
-  const size_t nb[4] = {nbA, nbB, nbA, nbB};
+  // B operands as N x K (K-major): G1 Q_A^T, G2 Q_B^T, G3 Q_A, G4 Q_B
+  std::vector<float> hb(2 * nbA + 2 * nbB, 0.f);
+  const size_t off[4] = {0, nbA, nbA + nbB, 2 * nbA + nbB};
   for (int t = 0; t < 4; ++t) {
     const int n = (t % 2 == 0) ? nA : nB, Kp = (t % 2 == 0) ? p->KpA : p->KpB;
     const std::vector<float>& Q = (t % 2 == 0) ? QA : QB;
-    for (int row = 0; row < n; ++row)
-      for (int col = 0; col < n; ++col) {
-        // row = output index, col = contraction index
-        const float v = (t < 2) ? Q[(size_t)col * n + row] : Q[(size_t)row * n + col];
-        const float h = tf32_round_host(v);
-        Bh[t][(size_t)row * Kp + col] = h;
-        Bh[t][nb[t] + (size_t)row * Kp + col] = v - h;
-      }
+    for (int row = 0; row < n; ++row)   // row = output index, col = contraction index
+      for (int col = 0; col < n; ++col)
+        hb[off[t] + (size_t)row * Kp + col] =
+            (t < 2) ? Q[(size_t)col * n + row] : Q[(size_t)row * n + col];
   }
   ok = cudaMemcpy(p->Bm, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice) ==
-       cudaSuccess;
-  for (int i = 0; i < 2 && ok; ++i)
-    ok = zg_map(&p->tP[i], p->P[i], nA, (long long)E * nB, p->KpA, kZgM) &&
-         zg_map(&p->tQ[i], p->Q[i], nB, (long long)E * nA, p->KpB, kZgM);
+           cudaSuccess &&
+       zg_map(&p->tP, p->P, nA, (long long)E * nB, p->KpA, kZgM) &&
+       zg_map(&p->tQ, p->Q, nB, (long long)E * nA, p->KpB, kZgM);
   for (int t = 0; t < 4 && ok; ++t) {
     const int n = (t % 2 == 0) ? nA : nB, Kp = (t % 2 == 0) ? p->KpA : p->KpB;
     const int BN = (t % 2 == 0) ? p->BNA : p->BNB;
-    const float* d = p->Bm + (Bh[t] - hb.data());
-    ok = zg_map(&p->tB[t][0], d, n, n, Kp, BN) && zg_map(&p->tB[t][1], d + nb[t], n, n, Kp, BN);
+    ok = zg_map(&p->tB[t], p->Bm + off[t], n, n, Kp, BN);
   }
   if (ok) {
     const int sm = std::max(p->smA, p->smB);
-    ok = cudaFuncSetAttribute(k_zgemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              sm) == cudaSuccess &&
-         cudaFuncSetAttribute(k_zgemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              sm) == cudaSuccess &&
-         cudaFuncSetAttribute(k_zgemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              sm) == cudaSuccess;
+    ok = cudaFuncSetAttribute(k_zgemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
+             cudaSuccess &&
+         cudaFuncSetAttribute(k_zgemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) ==
+             cudaSuccess;
   }
   if (!ok) {
     cudaGetLastError();
@@ -524,28 +521,28 @@ ZgPlan* zg_create(const Geo& g, const std::vector<float>& QA, const std::vector<
 cudaError_t launch_zgemm_zsolve(const ZgPlan* p, const Geo& g, const float* b, const float* u,
                                 const AdmmBasis& q, float* z, DevState* st, cudaStream_t s) {
   const int nA = p->nA, nB = p->nB, E = p->E;
-  k_zrhs_split<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(E, 8)), kBlock, 0, s>>>(
-      g, b, u, p->P[0], p->P[1], p->KpA, q.muA, q.muB, p->S, st);
+  k_zrhs_tc<<<dim3(ceil_div(g.ncols, kBlock), ceil_div(E, 8)), kBlock, 0, s>>>(
+      g, b, u, p->P, p->KpA, q.muA, q.muB, p->S, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int gA = ceil_div(E * nB, kZgM), gB = ceil_div(E * nA, kZgM);
-  const ZgEpi e1{p->Q[0], p->Q[1], nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0};
-  k_zgemm<true, false><<<gA, kZgThreads, p->smA, s>>>(
-      p->tP[0], p->tP[1], p->tB[0][0], p->tB[0][1], E * nB, nA, nA, p->BNA, p->stA, e1, st);
-  const ZgEpi e2{p->P[0], p->P[1], nA, (long long)nB * p->KpA, 1, p->KpA, p->S, p->KpA};
-  k_zgemm<true, true><<<gB, kZgThreads, p->smB, s>>>(
-      p->tQ[0], p->tQ[1], p->tB[1][0], p->tB[1][1], E * nA, nB, nB, p->BNB, p->stB, e2, st);
+  const ZgEpi e1{p->Q, nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0};
+  k_zgemm<false><<<gA, kZgThreads, p->smA, s>>>(p->tP, p->tB[0], E * nB, nA, nA, p->BNA, p->stA,
+                                                e1, st);
+  const ZgEpi e2{p->P, nA, (long long)nB * p->KpA, 1, p->KpA, p->S, p->KpA};
+  k_zgemm<true><<<gB, kZgThreads, p->smB, s>>>(p->tQ, p->tB[1], E * nA, nB, nB, p->BNB, p->stB,
+                                               e2, st);
   // G4's rows: (k, cA) with cA fastest where cA has unit stride in the pitched field, else
   // (cA, k) with k fastest (PE axis innermost); G3 writes its output in that row order
   const bool afast = g.psA == 1 || g.psP != 1;
-  const ZgEpi e3 = afast ? ZgEpi{p->Q[0], p->Q[1], nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0}
-                         : ZgEpi{p->Q[0], p->Q[1], nB, p->KpB, 1, (long long)E * p->KpB, nullptr, 0};
-  k_zgemm<true, false><<<gA, kZgThreads, p->smA, s>>>(
-      p->tP[0], p->tP[1], p->tB[2][0], p->tB[2][1], E * nB, nA, nA, p->BNA, p->stA, e3, st);
-  const ZgEpi e4 = afast ? ZgEpi{z, nullptr, nA, g.psP, g.psA, g.psB, nullptr, 0}
-                         : ZgEpi{z, nullptr, E, g.psA, g.psP, g.psB, nullptr, 0};
-  k_zgemm<false, false><<<gB, kZgThreads, p->smB, s>>>(
-      p->tQ[0], p->tQ[1], p->tB[3][0], p->tB[3][1], nA * E, nB, nB, p->BNB, p->stB, e4, st);
+  const ZgEpi e3 = afast ? ZgEpi{p->Q, nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0}
+                         : ZgEpi{p->Q, nB, p->KpB, 1, (long long)E * p->KpB, nullptr, 0};
+  k_zgemm<false><<<gA, kZgThreads, p->smA, s>>>(p->tP, p->tB[2], E * nB, nA, nA, p->BNA, p->stA,
+                                                e3, st);
+  const ZgEpi e4 = afast ? ZgEpi{z, nA, g.psP, g.psA, g.psB, nullptr, 0}
+                         : ZgEpi{z, E, g.psA, g.psP, g.psB, nullptr, 0};
+  k_zgemm<false><<<gB, kZgThreads, p->smB, s>>>(p->tQ, p->tB[3], nA * E, nB, nB, p->BNB, p->stB,
+                                                e4, st);
   return cudaGetLastError();
 }
 
