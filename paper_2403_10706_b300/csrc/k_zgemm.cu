@@ -184,7 +184,8 @@ template <bool SCALE>
 __global__ void __launch_bounds__(kZgThreads, 1)
 k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M,
         int N, int K, int BN, int stages, ZgEpi ep, DevState* st) {
-  if (st->stop) return;
+  // the next launch of the chain may start its setup now
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ unsigned char zg_dyn[];
   __shared__ __align__(8) unsigned long long bars[3 * kZgMaxStages + 1];
   __shared__ uint32_t tmem_slot;
@@ -221,8 +222,15 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
   __syncthreads();
   zg_fence_after();
   const uint32_t tmem = tmem_slot;
+  // the setup above overlapped the previous launch's tail (programmatic dependent launch); every
+  // global access below waits for that launch to complete.  A stopped solve skips the work (a
+  // block-wide decision, taken after the wait so that every thread sees the same state).
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (threadIdx.x == 0 && st->stop) failed = 2;
+  __syncthreads();
+  const bool run = *(volatile int*)&failed == 0;
 
-  if (warp == 0 && lane == 0) {
+  if (run && warp == 0 && lane == 0) {
     // producer: stage s takes K block kb, kb + stages, ...; a refill waits for the MMAs that read
     // the stage's previous block
     for (int kb = 0; kb < nkb; ++kb) {
@@ -236,7 +244,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
       zg_tma_load(sa, &tA, bar, kb * kZgKB, row0);
       zg_tma_load(sa + 2 * a_bytes, &tB, bar, kb * kZgKB, 0);
     }
-  } else if (warp == 1 && lane == 0) {
+  } else if (run && warp == 1 && lane == 0) {
     // MMA issuer: hi hi, hi lo, lo hi per K = 8 slice (the next slice 32 bytes along the rows)
     const uint32_t idesc = zg_idesc(kZgM, BN);
     for (int kb = 0; kb < nkb; ++kb) {
@@ -260,7 +268,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
       zg_commit(empty0 + 8 * s);
     }
     zg_commit(done);
-  } else if (warp >= 2) {
+  } else if (run && warp >= 2) {
     // converters: the stage's FP32 copies become TF32 pairs (hi in place, lo beside it)
     const int ct = threadIdx.x - 64;
     for (int kb = 0; kb < nkb; ++kb) {
@@ -285,10 +293,11 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     }
   }
   __syncwarp();
-  const bool ok = zg_bar_wait(done, 0);
+  const bool ok = run && zg_bar_wait(done, 0);
   __syncthreads();
   zg_fence_after();
-  const bool good = ok && *(volatile int*)&failed == 0;
+  const int fl = *(volatile int*)&failed;
+  const bool good = ok && fl == 0;
   if (warp >= 2) {
     // epilogue: thread = row r of the tile (TMEM lane 32 (warp % 4) + lane); warps 2-5 take the
     // even 16-column chunks, warps 6-9 the odd ones, two chunks per wait
@@ -341,7 +350,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
                  : "memory");
   }
-  if (!good && threadIdx.x == 0) {
+  if (run && !good && threadIdx.x == 0) {   // a wait ran out of its budget
     st->status = -6;   // HYSCO_ETIMEOUT
     st->stop = 1;
   }
@@ -354,6 +363,7 @@ __global__ void __launch_bounds__(kBlock)
 k_zrhs_tc(Geo g, const float* __restrict__ b, const float* __restrict__ u, float* __restrict__ X,
           int Kp, const float* __restrict__ muA, const float* __restrict__ muB,
           float* __restrict__ S, const DevState* st) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // G1 may start its setup
   if (st->stop) return;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= g.ncols) return;
@@ -517,6 +527,32 @@ ZgPlan* zg_create(const Geo& g, const std::vector<float>& QA, const std::vector<
   return p;
 }
 
+// one product of the chain, launched as a programmatic dependent of the launch before it (its
+// prologue overlaps that launch's tail; its global accesses wait for it to complete)
+template <bool SCALE>
+cudaError_t zg_launch(const ZgPlan* p, const CUtensorMap& tA, const CUtensorMap& tB, int M, int N,
+                      int BN, int stages, int smem, const ZgEpi& ep, DevState* st,
+                      cudaStream_t s) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(ceil_div(M, kZgM));
+  cfg.blockDim = dim3(kZgThreads);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  (void)p;
+  return cudaLaunchKernelEx(&cfg, k_zgemm<SCALE>, tA, tB, M, N, N, BN, stages, ep, st);
+}
+
+#define ZG_TRY(expr)                 \
+  do {                               \
+    cudaError_t e_ = (expr);         \
+    if (e_ != cudaSuccess) return e_; \
+  } while (0)
+
 // z = rho (alpha H_G + rho I)^{-1} (b + u) in the pitched field, by the chain G1-G4
 cudaError_t launch_zgemm_zsolve(const ZgPlan* p, const Geo& g, const float* b, const float* u,
                                 const AdmmBasis& q, float* z, DevState* st, cudaStream_t s) {
@@ -525,25 +561,20 @@ cudaError_t launch_zgemm_zsolve(const ZgPlan* p, const Geo& g, const float* b, c
       g, b, u, p->P, p->KpA, q.muA, q.muB, p->S, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int gA = ceil_div(E * nB, kZgM), gB = ceil_div(E * nA, kZgM);
   const ZgEpi e1{p->Q, nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0};
-  k_zgemm<false><<<gA, kZgThreads, p->smA, s>>>(p->tP, p->tB[0], E * nB, nA, nA, p->BNA, p->stA,
-                                                e1, st);
+  ZG_TRY(zg_launch<false>(p, p->tP, p->tB[0], E * nB, nA, p->BNA, p->stA, p->smA, e1, st, s));
   const ZgEpi e2{p->P, nA, (long long)nB * p->KpA, 1, p->KpA, p->S, p->KpA};
-  k_zgemm<true><<<gB, kZgThreads, p->smB, s>>>(p->tQ, p->tB[1], E * nA, nB, nB, p->BNB, p->stB,
-                                               e2, st);
+  ZG_TRY(zg_launch<true>(p, p->tQ, p->tB[1], E * nA, nB, p->BNB, p->stB, p->smB, e2, st, s));
   // G4's rows: (k, cA) with cA fastest where cA has unit stride in the pitched field, else
   // (cA, k) with k fastest (PE axis innermost); G3 writes its output in that row order
   const bool afast = g.psA == 1 || g.psP != 1;
   const ZgEpi e3 = afast ? ZgEpi{p->Q, nB, (long long)nA * p->KpB, 1, p->KpB, nullptr, 0}
                          : ZgEpi{p->Q, nB, p->KpB, 1, (long long)E * p->KpB, nullptr, 0};
-  k_zgemm<false><<<gA, kZgThreads, p->smA, s>>>(p->tP, p->tB[2], E * nB, nA, nA, p->BNA, p->stA,
-                                                e3, st);
+  ZG_TRY(zg_launch<false>(p, p->tP, p->tB[2], E * nB, nA, p->BNA, p->stA, p->smA, e3, st, s));
   const ZgEpi e4 = afast ? ZgEpi{z, nA, g.psP, g.psA, g.psB, nullptr, 0}
                          : ZgEpi{z, E, g.psA, g.psP, g.psB, nullptr, 0};
-  k_zgemm<false><<<gB, kZgThreads, p->smB, s>>>(p->tQ, p->tB[3], nA * E, nB, nB, p->BNB, p->stB,
-                                                e4, st);
-  return cudaGetLastError();
+  ZG_TRY(zg_launch<false>(p, p->tQ, p->tB[3], nA * E, nB, p->BNB, p->stB, p->smB, e4, st, s));
+  return cudaSuccess;
 }
 
 }  // namespace hysco
