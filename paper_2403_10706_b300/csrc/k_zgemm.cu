@@ -4,10 +4,11 @@
 // 64-byte-swizzled shared memory.
 //
 // Single precision from TF32 products (three-term split): an operand x is held as hi + lo with
-// hi = x rounded to TF32 (10 fraction bits) and lo = x - hi (exact in FP32), and
+// hi = x truncated to TF32 (10 fraction bits) and lo = x - hi (exact in FP32), and
 //   A B^T ~= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T,
-// the dropped Alo Blo^T being below 2^-21 of |A||B| per term; every product is accumulated in FP32
-// in tensor memory.  The operands travel in FP32; each stage is split in shared memory after its
+// the dropped Alo Blo^T and lo's own truncation being below 2^-20 of |A||B| per term; every
+// product is accumulated in FP32 in tensor memory.  The MMA reads an FP32 word as TF32 by dropping
+// its 13 low mantissa bits, so the copied x itself serves as hi and only lo is written.  The operands travel in FP32; each stage is split in shared memory after its
 // TMA copy lands, so the pairs never pass through L2 or HBM.
 //
 // Chain (planes k < E, in-plane axes A (n_A, fastest) and B (n_B)); X = b + u:
@@ -160,19 +161,17 @@ __device__ __forceinline__ void zg_ld_wait(uint32_t (&r)[32]) {
       : "memory");
 }
 
-// x rounded to TF32 (round to nearest, ties away from zero), as an FP32 bit pattern
-__device__ __forceinline__ float zg_tf32(float x) {
-  uint32_t u;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-  return __uint_as_float(u);
+// x truncated to TF32 (its 13 low mantissa bits cleared): the value the MMA reads for x
+__device__ __forceinline__ float zg_tf32_trunc(float x) {
+  return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
 // One 128-row tile of D = A B^T per block (A: M x K, B: N x K, both K-major FP32 behind the
 // tensor maps; N <= BN <= 256, BN a multiple of 16).  Roles per stage of 16 contraction columns:
 //   lane 0 of warp 0   TMA-copies the FP32 tiles of A (128 rows) and B (BN rows) into the stage's
 //                      hi slots (rows past M and columns past K read as zeros);
-//   warps 2-9          split them in place: hi = x rounded to TF32, lo = x - hi into the lo slots
-//                      (an elementwise map, so the 64-byte swizzle of the copies carries over),
+//   warps 2-9          write lo = x - (x truncated to TF32) into the lo slots (the copy is hi;
+//                      an elementwise map, so the 64-byte swizzle of the copies carries over),
 //                      then fence the writes to the async proxy and arrive on the stage;
 //   lane 0 of warp 1   issues three MMAs per K = 8 slice (hi hi, hi lo, lo hi) into one TMEM
 //                      accumulator of BN columns and frees the stage by a commit.
@@ -269,7 +268,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     }
     zg_commit(done);
   } else if (run && warp >= 2) {
-    // converters: the stage's FP32 copies become TF32 pairs (hi in place, lo beside it)
+    // converters: the lo half of each TF32 pair beside the stage's FP32 copy (its hi half)
     const int ct = threadIdx.x - 64;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % stages;
@@ -284,9 +283,8 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
         float4* const h = i < na4 ? ah + i : bh + (i - na4);
         float4* const l = i < na4 ? ah + na4 + i : bh + nb4 + (i - na4);
         const float4 x = *h;
-        const float4 hv = make_float4(zg_tf32(x.x), zg_tf32(x.y), zg_tf32(x.z), zg_tf32(x.w));
-        *h = hv;
-        *l = make_float4(x.x - hv.x, x.y - hv.y, x.z - hv.z, x.w - hv.w);
+        *l = make_float4(x.x - zg_tf32_trunc(x.x), x.y - zg_tf32_trunc(x.y),
+                         x.z - zg_tf32_trunc(x.z), x.w - zg_tf32_trunc(x.w));
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(conv0 + 8 * s) : "memory");
