@@ -240,6 +240,30 @@ def test_z_update_full_3t_size_on_the_tensor_cores(H, orc, rho):
     assert h.last_status() == 0
 
 
+def test_z_update_7t_plane_size_and_the_cuda_core_fallback(H, orc):
+    """The 7T plane (200 x 132 in-plane, PE axis 0: a 208-column tile, five 16-column stages) on
+    the tensor cores against the oracle; an in-plane axis of 300 nodes (past the MMA's largest N)
+    runs on the CUDA cores, where path 0 is refused."""
+    dims, spacing, p = (132, 200, 200), (1.2, 1.0, 1.0), 0
+    P = orc.Problem(dims, spacing, p, ALPHA, BETA)
+    v = np.random.default_rng(903).standard_normal(P.fdims).astype(np.float32)
+    h = H(dims, spacing, p, ALPHA, BETA)
+    assert h.zsolve_path() == 0
+    z = h.admm_zsolve(torch.from_numpy(v).cuda(), 12.0).cpu().numpy()
+    zref = P.admm_z_solve(12.0 * v.astype(np.float64), 12.0)
+    assert rel(z, zref) <= 2e-5, rel(z, zref)
+    dims2 = (300, 6, 5)
+    P2 = orc.Problem(dims2, (1.0, 1.0, 1.0), 1, ALPHA, BETA)
+    v2 = np.random.default_rng(904).standard_normal(P2.fdims).astype(np.float32)
+    h2 = H(dims2, (1.0, 1.0, 1.0), 1, ALPHA, BETA)
+    assert h2.zsolve_path() == 1
+    with pytest.raises(_lib.HyscoError):
+        h2.set_zsolve_path(0)
+    z2 = h2.admm_zsolve(torch.from_numpy(v2).cuda(), 3.0).cpu().numpy()
+    zref2 = P2.admm_z_solve(3.0 * v2.astype(np.float64), 3.0)
+    assert rel(z2, zref2) <= 2e-5, rel(z2, zref2)
+
+
 def test_z_update_path_switch_rejects_unknown_paths_and_rebuilds_the_graph(H):
     """Path 2 and -1 are rejected; switching paths between two graph-captured ADMM runs gives
     results that agree to single precision (the cached graph is rebuilt, not replayed)."""
