@@ -746,7 +746,7 @@ def run_ours(args):
     }
     h.eval(Ip, Im, b_out, grad=g, terms=terms)   # the linearisation the next two calls use
     kernels["hysco_hessvec"] = table_row(time_launches(lambda: h.hessvec(vv, out=hv_out)),
-                                         16 * nfld, "k_to_pitched, k_hv, k_from_pitched")
+                                         16 * nfld, "k_hv_caller")
     kernels["hysco_precond_column"] = table_row(
         time_launches(lambda: h.precond(vv, kind=_lib.PC_COLUMN, out=pc_out)), 16 * nfld,
         "k_to_pitched, k_col_factor, k_col_solve, k_from_pitched")

@@ -397,9 +397,7 @@ int hysco_hessvec(hysco_t h, const float* v, float* Hv, hysco_stream_t stream) {
   if (!h || check_f32(v) || check_f32(Hv)) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
   cudaStream_t s = (cudaStream_t)stream;
-  HYSCO_TRY(launch_to_pitched(h->g, v, h->r, s));
-  HYSCO_TRY(launch_hessvec(h->g, h->r, h->z, h->dco, h->eco, s));
-  HYSCO_TRY(launch_from_pitched(h->g, h->z, Hv, s));
+  HYSCO_TRY(launch_hessvec_caller(h->g, v, Hv, h->dco, h->eco, s));
   return HYSCO_OK;
 }
 

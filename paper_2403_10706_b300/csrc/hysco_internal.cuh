@@ -459,8 +459,9 @@ cudaError_t launch_mixed_image_adjoint(const Geo& g, int dtype, const void* Ip, 
 cudaError_t launch_cells(const Geo& g, const float* b, int* cp, int* cm, cudaStream_t s);
 
 // k_pcg.cu
-cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
-                           const float* eco, cudaStream_t s);
+// Hv = H_J v about the last linearisation, v and Hv in the caller's layout (d, e pitched)
+cudaError_t launch_hessvec_caller(const Geo& g, const float* v, float* Hv, const float* dco,
+                                  const float* eco, cudaStream_t s);
 cudaError_t launch_pcg_init_jacobi(const Geo& g, const float* grad, float sign, float* x, float* r,
                                    float* z, const float* invd, const Work& w, cudaStream_t s);
 cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, const float* dco,

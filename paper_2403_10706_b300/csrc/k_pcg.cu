@@ -15,6 +15,8 @@
 // H p is kept by the recurrence H p = H z + beta H p_old (H is linear, so this is the same vector
 // as applying the stencil to p, up to rounding): the stencil reads only z, and p, Hp are updated
 // in place by their owning thread.
+#include <algorithm>
+
 #include "hysco_internal.cuh"
 
 namespace hysco {
@@ -419,9 +421,37 @@ static void hv_launch(const Geo& g, const float* z, float* p, float* Hp, const f
   else k_hv<2, PCG><<<nb, kBlock, 0, s>>>(g, z, p, Hp, dco, eco, first, pa, ct, st);
 }
 
-cudaError_t launch_hessvec(const Geo& g, const float* v, float* Hv, const float* dco,
-                           const float* eco, cudaStream_t s) {
-  hv_launch<false>(g, v, nullptr, Hv, dco, eco, 0, nullptr, s);
+// Hv = H_J v with v and Hv in the caller's layout and d, e in the pitched one: one node per thread
+// (consecutive threads on consecutive nodes of axis 2), the same arithmetic as hv_core
+template <int P>
+__global__ void __launch_bounds__(kBlock)
+k_hv_caller(Geo g, const float* __restrict__ v, const float* __restrict__ dco,
+            const float* __restrict__ eco, float* __restrict__ Hv) {
+  const int fe0 = g.fe[0], fe1 = g.fe[1], fe2 = g.fe[2], s0 = fe1 * fe2;
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nf; n += gridDim.x * blockDim.x) {
+    const int row = (int)fdiv((unsigned)n, g.divfe2), i2 = n - row * fe2;
+    const int i0 = (int)fdiv((unsigned)row, g.divfe1), i1 = row - i0 * fe1;
+    const int pi = row * g.P2 + i2;
+    const float vk = __ldg(v + n);
+    const float a0m = i0 > 0 ? __ldg(v + n - s0) : vk, a0p = i0 < fe0 - 1 ? __ldg(v + n + s0) : vk;
+    const float a1m = i1 > 0 ? __ldg(v + n - fe2) : vk, a1p = i1 < fe1 - 1 ? __ldg(v + n + fe2) : vk;
+    const float a2m = i2 > 0 ? __ldg(v + n - 1) : vk, a2p = i2 < fe2 - 1 ? __ldg(v + n + 1) : vk;
+    const float lap = g.w[0] * ((vk - a0m) + (vk - a0p)) + g.w[1] * ((vk - a1m) + (vk - a1p)) +
+                      g.w[2] * ((vk - a2m) + (vk - a2p));
+    const int iP = P == 0 ? i0 : (P == 1 ? i1 : i2);
+    const float elo = iP > 0 ? __ldg(eco + pi - g.psP) : 0.f;
+    const float zlo = P == 0 ? a0m : (P == 1 ? a1m : a2m);
+    const float zhi = P == 0 ? a0p : (P == 1 ? a1p : a2p);
+    Hv[n] = g.vol * (elo * zlo + __ldg(dco + pi) * vk + __ldg(eco + pi) * zhi + g.alpha * lap);
+  }
+}
+
+cudaError_t launch_hessvec_caller(const Geo& g, const float* v, float* Hv, const float* dco,
+                                  const float* eco, cudaStream_t s) {
+  const int blocks = std::min(ceil_div(g.nf, kBlock), 148 * 8);
+  if (g.p == 0) k_hv_caller<0><<<blocks, kBlock, 0, s>>>(g, v, dco, eco, Hv);
+  else if (g.p == 1) k_hv_caller<1><<<blocks, kBlock, 0, s>>>(g, v, dco, eco, Hv);
+  else k_hv_caller<2><<<blocks, kBlock, 0, s>>>(g, v, dco, eco, Hv);
   return cudaGetLastError();
 }
 
