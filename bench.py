@@ -749,7 +749,7 @@ def run_ours(args):
                                          16 * nfld, "k_hv_caller")
     kernels["hysco_precond_column"] = table_row(
         time_launches(lambda: h.precond(vv, kind=_lib.PC_COLUMN, out=pc_out)), 16 * nfld,
-        "k_to_pitched, k_col_factor, k_col_solve, k_from_pitched")
+        "k_col_factor, k_col_solve")
     # the paper's 7T acquisition size (200 x 200 x 132, PE axis 0): a field of 5.3 M nodes, twice
     # what the persistent PCG keeps on chip, so half its slots keep r, p, Hp in global memory
     extra = None

@@ -407,18 +407,17 @@ int hysco_precond(hysco_t h, const float* r, float* z, int kind, hysco_stream_t 
   if (kind == HYSCO_PC_COLUMN && h->g.m > 1024) return HYSCO_EINVAL;
   if (!h->have_lin) return HYSCO_ENOTREADY;
   cudaStream_t s = (cudaStream_t)stream;
-  HYSCO_TRY(launch_to_pitched(h->g, r, h->r, s));
+  // both apply in the caller's layout (the factors and 1/diag stay pitched)
   if (kind == HYSCO_PC_JACOBI) {
-    HYSCO_TRY(launch_jacobi_apply(h->g, h->r, h->z, h->invd, s));
+    HYSCO_TRY(launch_jacobi_apply(h->g, r, z, h->invd, s));
   } else {
     if (!h->have_factor) {
       HYSCO_TRY(launch_col_factor(h->g, h->dco, h->eco, h->invD, h->lco, s));
       h->have_factor = true;
     }
-    HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, h->r, nullptr, nullptr, h->z, h->invD,
-                               h->lco, 0, 0.0, 1.0f, h->work(), s));
+    HYSCO_TRY(launch_col_solve(h->g, 0, nullptr, nullptr, const_cast<float*>(r), nullptr,
+                               nullptr, z, h->invD, h->lco, 0, 0.0, 1.0f, h->work(), s));
   }
-  HYSCO_TRY(launch_from_pitched(h->g, h->z, z, s));
   return HYSCO_OK;
 }
 

@@ -469,6 +469,7 @@ cudaError_t launch_pcg_hp(const Geo& g, const float* z, float* p, float* Hp, con
 cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const float* p,
                                      const float* Hp, float* z, const float* invd, int first,
                                      double rtol, const Work& w, cudaStream_t s);
+// z = r / diag, r and z in the caller's layout
 cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s);
 // caller layout <-> pitched layout of a field-shaped array
@@ -476,7 +477,8 @@ cudaError_t launch_to_pitched(const Geo& g, const float* src, float* dst, cudaSt
 cudaError_t launch_from_pitched(const Geo& g, const float* src, float* dst, cudaStream_t s);
 cudaError_t launch_col_factor(const Geo& g, const float* dco, const float* eco, float* invD,
                               float* lco, cudaStream_t s);
-// mode 0 = apply z = M^{-1} r;  1 = PCG init (r = sign * grad, x = 0);  2 = PCG update
+// mode 0 = apply z = M^{-1} r (r, z in the caller's layout);  1 = PCG init (r = sign * grad,
+// x = 0);  2 = PCG update (pitched vectors)
 cudaError_t launch_col_solve(const Geo& g, int mode, const float* grad, float* x, float* r,
                              const float* p, const float* Hp, float* z, const float* invD,
                              const float* lco, int first, double rtol, float sign,

@@ -137,11 +137,14 @@ k_pcg_update_jacobi(Geo g, float* __restrict__ x, float* __restrict__ r,
   if (grid_sum<2>(v, partials, counter, tot)) pcg_finish(st, tot[0], tot[1], rtol);
 }
 
+// z = r / diag with r and z in the caller's layout (1/diag pitched)
 __global__ void __launch_bounds__(kBlock)
-k_jacobi_apply(Geo g, const float* __restrict__ r, float* __restrict__ z,
-               const float* __restrict__ invd) {
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < g.nfp) z[n] = __ldg(r + n) * __ldg(invd + n);
+k_jacobi_caller(Geo g, const float* __restrict__ r, float* __restrict__ z,
+                const float* __restrict__ invd) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= g.nf) return;
+  const int row = (int)fdiv((unsigned)n, g.divfe2);
+  z[n] = __ldg(r + n) * __ldg(invd + row * g.P2 + (n - row * g.fe[2]));
 }
 
 // caller layout <-> pitched layout (padding written as zero)
@@ -246,8 +249,9 @@ k_col_factor(Geo g, const float* __restrict__ dco, const float* __restrict__ eco
 }
 
 // z = M^{-1} r per column (forward L y = r, backward L^T z = D^{-1} y; y kept in z).  MODE 0:
-// apply to r; MODE 1: PCG init (r = sign * grad, x = 0); MODE 2: PCG update (x += alpha p,
-// r -= alpha Hp) first.  MODE 1 / 2 reduce r.r and r.z and take the PCG decisions.
+// apply to r, r and z in the caller's layout (the API call); MODE 1: PCG init (r = sign * grad,
+// x = 0); MODE 2: PCG update (x += alpha p, r -= alpha Hp) first.  MODE 1 / 2 work on pitched
+// vectors, reduce r.r and r.z and take the PCG decisions.  The factors are pitched.
 template <int MODE>
 __global__ void __launch_bounds__(kColBlock)
 k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float* r,
@@ -262,6 +266,9 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
   float arr = 0.f, arz = 0.f;
   if (c < g.ncols) {
     const int E = g.E, ps = g.psP, fb = col_pos(g, c).base;
+    // the vectors' base and PE stride (the factors': fb, ps)
+    const int db = MODE == 0 ? col_base(c, g.inner, g.fld_ostride) : fb;
+    const int ds = MODE == 0 ? g.inner : ps;
     const float a = MODE == 2 ? (float)st->alpha_cg : 0.f;
     // the residual at pitched offset i from its inputs v (MODE 1 / 2 also update x and r there)
     auto resid = [&](int i, const float* v) {
@@ -300,16 +307,16 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
     // forward: y_0 = r_0, y_k = r_k - l_{k-1} y_{k-1}; step k (1 .. E - 1) reads l_{k-1} and the
     // inputs at node k
     float v0[4];
-    inputs(fb, v0);
-    float y = resid(fb, v0);
+    inputs(db, v0);
+    float y = resid(db, v0);
     arr += y * y;
-    z[fb] = y;
+    z[db] = y;
     auto ffetch = [&](int q) {   // steps 1 + kColGroup q .. + 3
 #pragma unroll
       for (int u = 0; u < kColGroup; ++u) {
-        const int k = 1 + q * kColGroup + u, kk = min(k, E - 1), sl = k % R, i = fb + kk * ps;
-        cp_async4(&ring[sl][0][lane], lco + i - ps, true);
-        fetch_inputs(i, sl);
+        const int k = 1 + q * kColGroup + u, kk = min(k, E - 1), sl = k % R;
+        cp_async4(&ring[sl][0][lane], lco + fb + (kk - 1) * ps, true);
+        fetch_inputs(db + kk * ds, sl);
       }
       cp_async_commit();
     };
@@ -319,7 +326,7 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
       cp_async_wait<NG - 1>();
 #pragma unroll
       for (int u = 0; u < kColGroup; ++u) {   // predicated past the column's end, no branch
-        const int k = 1 + q * kColGroup + u, sl = k % R, i = fb + k * ps;
+        const int k = 1 + q * kColGroup + u, sl = k % R, i = db + k * ds;
         if (MODE == 0 ? false : k >= E) break;   // MODE 1 / 2 write x and r in resid
         const bool in = k < E;
         float v[4];
@@ -339,16 +346,17 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
     // backward: z_{E-1} = y_{E-1} / D_{E-1}, z_k = y_k / D_k - l_k z_{k+1}; step t reads node
     // k = E - 2 - t: y_k, l_k, 1 / D_k (and r_k)
     float zz = y * __ldg(invD + fb + (E - 1) * ps);
-    z[fb + (E - 1) * ps] = zz;
-    if (MODE != 0) arz += r[fb + (E - 1) * ps] * zz;
+    z[db + (E - 1) * ds] = zz;
+    if (MODE != 0) arz += r[db + (E - 1) * ds] * zz;
     auto bfetch = [&](int q) {   // steps kColGroup q .. + 3
 #pragma unroll
       for (int u = 0; u < kColGroup; ++u) {
-        const int t = q * kColGroup + u, kk = max(E - 2 - t, 0), sl = t % R, i = fb + kk * ps;
-        cp_async4(&ring[sl][0][lane], z + i, true);
+        const int t = q * kColGroup + u, kk = max(E - 2 - t, 0), sl = t % R;
+        const int i = fb + kk * ps, id = db + kk * ds;
+        cp_async4(&ring[sl][0][lane], z + id, true);
         cp_async4(&ring[sl][1][lane], lco + i, true);
         cp_async4(&ring[sl][2][lane], invD + i, true);
-        if (MODE != 0) cp_async4(&ring[sl][3][lane], r + i, true);
+        if (MODE != 0) cp_async4(&ring[sl][3][lane], r + id, true);
       }
       cp_async_commit();
     };
@@ -362,7 +370,7 @@ k_col_solve(Geo g, const float* __restrict__ grad, float* __restrict__ x, float*
         const float zn = fmaf(-ring[sl][1][lane], zz, ring[sl][0][lane] * ring[sl][2][lane]);
         if (k >= 0) {
           zz = zn;
-          z[fb + k * ps] = zz;
+          z[db + k * ds] = zz;
           if (MODE != 0) arz += ring[sl][3][lane] * zz;
         }
       }
@@ -478,7 +486,7 @@ cudaError_t launch_pcg_update_jacobi(const Geo& g, float* x, float* r, const flo
 
 cudaError_t launch_jacobi_apply(const Geo& g, const float* r, float* z, const float* invd,
                                 cudaStream_t s) {
-  k_jacobi_apply<<<ceil_div(g.nfp, kBlock), kBlock, 0, s>>>(g, r, z, invd);
+  k_jacobi_caller<<<ceil_div(g.nf, kBlock), kBlock, 0, s>>>(g, r, z, invd);
   return cudaGetLastError();
 }
 
