@@ -306,6 +306,14 @@ int hysco_admm_zsolve(hysco_t h, const float* v, double rho, float* z, hysco_str
 int hysco_set_zsolve_path(hysco_t h, int path);
 int hysco_zsolve_path(hysco_t h);
 
+/* Self-test of failure detection in the tensor-core z-update (path 0): one launch of its first
+ * product whose copies are never issued, so that the stage barriers never fill and every wait on
+ * them gives up after `spin_cycles` (1 .. 4e9) clock cycles.  Returns HYSCO_ETIMEOUT when the
+ * launch recorded the timeout (nothing left in flight, its tensor memory freed), HYSCO_OK if it
+ * did not, HYSCO_EINVAL for bad arguments or where path 0 does not apply.  Synchronises `stream`
+ * and clears the handle's device state afterwards; the handle and the context stay usable. */
+int hysco_selftest_zsolve(hysco_t h, int64_t spin_cycles, hysco_stream_t stream);
+
 /* ---- batched solve (many volume pairs of uneven sizes) -------------------------------------
  * A batch groups n distinct handles (same device; any dims, spacings, PE axes and image dtypes)
  * whose solves advance through the Gauss-Newton loop together (Sec. 2.3.1 per pair, unchanged):

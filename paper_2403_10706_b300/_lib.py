@@ -99,6 +99,7 @@ def load():
         "hysco_set_pcg_onchip": (I, [P, I]),
         "hysco_set_zsolve_path": (I, [P, I]),
         "hysco_zsolve_path": (I, [P]),
+        "hysco_selftest_zsolve": (I, [P, C.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

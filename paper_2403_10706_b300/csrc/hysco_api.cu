@@ -945,6 +945,21 @@ int hysco_set_zsolve_path(hysco_t h, int path) {
   return HYSCO_OK;
 }
 
+int hysco_selftest_zsolve(hysco_t h, int64_t spin_cycles, hysco_stream_t stream) {
+  if (!h || spin_cycles < 1 || spin_cycles > 4000000000LL) return HYSCO_EINVAL;
+  if (int rc = admm_setup(h)) return rc;
+  if (!h->zg) return HYSCO_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int rc = reset_state(h, s)) return rc;
+  HYSCO_TRY(zg_selftest(h->zg, h->st, (long long)spin_cycles, s));
+  DevState st;
+  HYSCO_TRY(cudaMemcpyAsync(&st, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  HYSCO_TRY(cudaStreamSynchronize(s));
+  if (int rc = reset_state(h, s)) return rc;
+  HYSCO_TRY(cudaStreamSynchronize(s));
+  return (st.status == HYSCO_ETIMEOUT && st.stop) ? HYSCO_ETIMEOUT : HYSCO_OK;
+}
+
 int hysco_zsolve_path(hysco_t h) {
   if (!h) return HYSCO_EINVAL;
   if (int rc = admm_setup(h)) return rc;

@@ -511,6 +511,9 @@ ZgPlan* zg_create(const Geo& g, const std::vector<float>& QA, const std::vector<
 void zg_destroy(ZgPlan* p);
 cudaError_t launch_zgemm_zsolve(const ZgPlan* p, const Geo& g, const float* b, const float* u,
                                 const AdmmBasis& q, float* z, DevState* st, cudaStream_t s);
+// the failure self-test: a product launch whose stages never fill runs out of a `spin`-cycle wait
+// budget and records HYSCO_ETIMEOUT in st
+cudaError_t zg_selftest(const ZgPlan* p, DevState* st, long long spin, cudaStream_t s);
 cudaError_t launch_admm_post(const Geo& g, const float* b, const float* z, const float* zprev,
                              float* u, const float* bprev, int it, double tol, double mu,
                              double tau, double* stats, const Work& w, cudaStream_t s);

@@ -38,6 +38,7 @@ constexpr int kZgConvThreads = 256;
 constexpr int kZgMaxStages = 12;
 constexpr int kZgMaxN = 256;       // the MMA's largest N (one tile spans all output columns)
 constexpr long long kZgSpin = 1LL << 31;   // clock cycles a wait may take before the launch gives up
+                                           // (about a second)
 
 // where the epilogue puts D(r, j): row r -> (q, x) = (r / n_row, r % n_row), element
 // q sq + x sx + j sj of out; SCALE multiplies by scale[j ss + x]
@@ -74,12 +75,12 @@ __device__ __forceinline__ bool zg_bar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// wait for the phase of the given parity to complete; false once kZgSpin cycles have passed
-__device__ __forceinline__ bool zg_bar_wait(uint32_t bar, uint32_t parity) {
+// wait for the phase of the given parity to complete; false once `spin` clock cycles have passed
+__device__ __forceinline__ bool zg_bar_wait(uint32_t bar, uint32_t parity, long long spin) {
   if (zg_bar_try(bar, parity)) return true;
   const long long t0 = clock64();
   while (!zg_bar_try(bar, parity))
-    if (clock64() - t0 > kZgSpin) return false;
+    if (clock64() - t0 > spin) return false;
   return true;
 }
 
@@ -177,12 +178,14 @@ __device__ __forceinline__ float zg_tf32_trunc(float x) {
 //                      accumulator of BN columns and frees the stage by a commit.
 // Then warps 2-9 take the accumulator's rows (TMEM lane quarter warp % 4, alternate 16-column
 // chunks, 32 columns per wait) to global memory as ZgEpi says.  A wait that runs out of its
-// budget records HYSCO_ETIMEOUT in the device state and stops the solve; the launch then skips
-// its stores, frees its tensor memory and ends.
+// budget (spin clock cycles) records HYSCO_ETIMEOUT in the device state and stops the solve; the
+// launch then skips its stores, frees its tensor memory and ends.  no_copy (the failure self-test
+// only): the producer issues no copies, so the first stage never fills and the waits on it run
+// out — no copy or MMA is then in flight when the launch ends.
 template <bool SCALE>
 __global__ void __launch_bounds__(kZgThreads, 1)
 k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, int M,
-        int N, int K, int BN, int stages, ZgEpi ep, DevState* st) {
+        int N, int K, int BN, int stages, ZgEpi ep, DevState* st, long long spin, int no_copy) {
   // the next launch of the chain may start its setup now
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ unsigned char zg_dyn[];
@@ -229,12 +232,12 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
   __syncthreads();
   const bool run = *(volatile int*)&failed == 0;
 
-  if (run && warp == 0 && lane == 0) {
+  if (run && warp == 0 && lane == 0 && !no_copy) {
     // producer: stage s takes K block kb, kb + stages, ...; a refill waits for the MMAs that read
     // the stage's previous block
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % stages;
-      if (kb >= stages && !zg_bar_wait(empty0 + 8 * s, (uint32_t)(kb / stages - 1) & 1u)) {
+      if (kb >= stages && !zg_bar_wait(empty0 + 8 * s, (uint32_t)(kb / stages - 1) & 1u, spin)) {
         failed = 1;
         break;
       }
@@ -248,7 +251,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     const uint32_t idesc = zg_idesc(kZgM, BN);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % stages;
-      if (!zg_bar_wait(conv0 + 8 * s, (uint32_t)(kb / stages) & 1u)) {
+      if (!zg_bar_wait(conv0 + 8 * s, (uint32_t)(kb / stages) & 1u, spin)) {
         failed = 1;
         break;
       }
@@ -272,7 +275,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     const int ct = threadIdx.x - 64;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % stages;
-      if (!zg_bar_wait(full0 + 8 * s, (uint32_t)(kb / stages) & 1u)) {
+      if (!zg_bar_wait(full0 + 8 * s, (uint32_t)(kb / stages) & 1u, spin)) {
         failed = 1;
         break;
       }
@@ -291,7 +294,7 @@ k_zgemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensor
     }
   }
   __syncwarp();
-  const bool ok = run && zg_bar_wait(done, 0);
+  const bool ok = run && zg_bar_wait(done, 0, spin);
   __syncthreads();
   zg_fence_after();
   const int fl = *(volatile int*)&failed;
@@ -542,7 +545,17 @@ cudaError_t zg_launch(const ZgPlan* p, const CUtensorMap& tA, const CUtensorMap&
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   (void)p;
-  return cudaLaunchKernelEx(&cfg, k_zgemm<SCALE>, tA, tB, M, N, N, BN, stages, ep, st);
+  return cudaLaunchKernelEx(&cfg, k_zgemm<SCALE>, tA, tB, M, N, N, BN, stages, ep, st, kZgSpin, 0);
+}
+
+// The failure self-test: one launch of the first product whose producer issues no copies, with a
+// wait budget of `spin` clock cycles; its converters and its MMA issuer give up on the unfilled
+// stage, and the launch records HYSCO_ETIMEOUT in st and ends (nothing in flight, TMEM freed).
+cudaError_t zg_selftest(const ZgPlan* p, DevState* st, long long spin, cudaStream_t s) {
+  const ZgEpi e{p->Q, p->nB, (long long)p->nA * p->KpB, 1, p->KpB, nullptr, 0};
+  k_zgemm<false><<<ceil_div(p->E * p->nB, kZgM), kZgThreads, p->smA, s>>>(
+      p->tP, p->tB[0], p->E * p->nB, p->nA, p->nA, p->BNA, p->stA, e, st, spin, 1);
+  return cudaGetLastError();
 }
 
 #define ZG_TRY(expr)                 \

@@ -1,6 +1,8 @@
 """Failure detection without a GPU fault: the persistent kernels' device-wide barrier gives up
 after a bounded spin and reports HYSCO_ETIMEOUT; the context stays usable.  The wait is made to
-run out by a block that never arrives (hysco_selftest_barrier), with a ~10 ms budget."""
+run out by a block that never arrives (hysco_selftest_barrier), with a ~10 ms budget.  The same
+for the tensor-core z-update's mbarrier waits: a launch whose copies are never issued
+(hysco_selftest_zsolve) gives up on its unfilled stages."""
 import numpy as np
 import pytest
 
@@ -31,6 +33,23 @@ def test_barrier_completes_when_every_block_arrives(lib):
 @pytest.mark.parametrize("missing", [0, 3, 7])
 def test_barrier_times_out_when_a_block_never_arrives(lib, missing):
     assert lib.hysco_selftest_barrier(8, missing, 20_000_000, stream()) == _lib.ETIMEOUT
+
+
+def test_zsolve_waits_run_out_and_the_handle_recovers(lib, orc):
+    """The tensor-core product launch whose stages never fill records HYSCO_ETIMEOUT (a ~10 ms
+    budget per wait); the same handle's z-update then matches the oracle again."""
+    from paper_2403_10706_b300.hysco import Hysco
+    dims, spacing, p = (32, 40, 24), (1.0, 1.1, 0.9), 1
+    h = Hysco(dims, spacing, p, 300.0, 1e4)
+    assert h.zsolve_path() == 0
+    assert lib.hysco_selftest_zsolve(h._h, 20_000_000, stream()) == _lib.ETIMEOUT
+    assert lib.hysco_selftest_zsolve(h._h, 0, stream()) == _lib.EINVAL
+    P = orc.Problem(dims, spacing, p, 300.0, 1e4)
+    v = np.random.default_rng(905).standard_normal(P.fdims).astype(np.float32)
+    z = h.admm_zsolve(torch.from_numpy(v).cuda(), 5.0).cpu().numpy()
+    zref = P.admm_z_solve(5.0 * v.astype(np.float64), 5.0)
+    assert np.linalg.norm(z - zref) <= 2e-5 * np.linalg.norm(zref)
+    assert h.last_status() == 0
 
 
 def test_context_is_usable_after_a_timeout(lib, orc):
