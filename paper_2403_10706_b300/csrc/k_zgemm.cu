@@ -8,8 +8,10 @@
 //   A B^T ~= Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T,
 // the dropped Alo Blo^T and lo's own truncation being below 2^-20 of |A||B| per term; every
 // product is accumulated in FP32 in tensor memory.  The MMA reads an FP32 word as TF32 by dropping
-// its 13 low mantissa bits, so the copied x itself serves as hi and only lo is written.  The operands travel in FP32; each stage is split in shared memory after its
-// TMA copy lands, so the pairs never pass through L2 or HBM.
+// its 13 low mantissa bits, so the copied x itself serves as hi and only lo is written.  The
+// operands travel in FP32; each stage is split in shared memory after its TMA copy lands, so the
+// pairs never pass through L2 or HBM.  The four launches (and the one before them, which forms
+// X and G2's scale table) are a chain of programmatic dependent launches.
 //
 // Chain (planes k < E, in-plane axes A (n_A, fastest) and B (n_B)); X = b + u:
 //   G1  D(k cB, jA) = sum_cA X(k, cB, cA) Q_A(cA, jA)                 forward, axis A
@@ -23,7 +25,6 @@
 #include <cuda.h>
 
 #include <algorithm>
-#include <cstring>
 #include <vector>
 
 #include "hysco_internal.cuh"
