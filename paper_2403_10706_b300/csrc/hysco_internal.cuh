@@ -638,7 +638,7 @@ cudaError_t launch_ot_shift(const Geo& g, int dtype, const void* Ip, const void*
 int ot_tile_width(int E);
 cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, float* b0,
                       int* kp, int* km, const Work& w, cudaStream_t s);
-cudaError_t launch_blur(const Geo& g, float* in, float* out, cudaStream_t s);   // in: scratch
+cudaError_t launch_blur(const Geo& g, float* in, float* out, cudaStream_t s);   // in unchanged
 // k_ls.cu: least-squares correction; the normal matrix's band lives in kLsBandWide + 1
 // image-layout scratch arrays (band + d * bstride), its right-hand side in rhs; wide: one int per
 // column (the columns the narrow first pass hands to the wide second pass)

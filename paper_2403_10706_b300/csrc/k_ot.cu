@@ -9,8 +9,11 @@
 //     k* = min{j in [0, m-1] : C(j+1) >= r}    (binary search on the other image's CDF)
 //   and C^{-1}(r) = k* + (r - C(k*)) / (C(k*+1) - C(k*)), capped at m.  Then
 //     b0_k = 1/4 [ (C+^{-1}(C-(k)) - k) - (C-^{-1}(C+(k)) - k) ].
-// k_blur_axis: separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
-//   voxel), replicate boundary, one pass per axis.
+// k_blur3: the separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
+//   voxel), replicate boundary, as one launch: a CTA stages a brick of the field with a one-node
+//   halo in shared memory (clamped coordinates, so the halo replicates the boundary) and applies
+//   the passes along axis 0, 1 and 2 in that order, each pass's values rounded to single
+//   precision as three separate passes would round them.
 #include <algorithm>
 #include <cmath>
 
@@ -116,13 +119,21 @@ __device__ __forceinline__ int cdf_bracket(const float* C, int CW, int m, float 
   return lo;
 }
 
+// C^{-1}(r) on the bracket k = k*: k + (r - C(k)) / (C(k+1) - C(k)), capped at m.  The bracket
+// gives C(k) < r <= C(k+1) (C(0) = 0 < r), so the fraction lies in (0, 1]; it is formed with the
+// fast reciprocal (at most 2 ulp of error for a divisor in [2^-126, 2^126]) and saturated to
+// [0, 1], which also covers a divisor below that range
+__device__ __forceinline__ float spline_inverse(const float* C, int CW, int m, float r, int k) {
+  const float c0 = C[k * CW], c1 = C[(k + 1) * CW];
+  const float x = (float)k + __saturatef(__fdividef(r - c0, c1 - c0));
+  return fminf(x, (float)m);
+}
+
 __device__ __forceinline__ float cdf_inverse(const float* C, int CW, int m, float r, int& kstar) {
   if (r <= 0.f) { kstar = 0; return 0.f; }
   int k = cdf_bracket(C, CW, m, r);
   kstar = k;
-  float c0 = C[k * CW], c1 = C[(k + 1) * CW];
-  float x = (float)k + (r - c0) / (c1 - c0);
-  return fminf(x, (float)m);
+  return spline_inverse(C, CW, m, r, k);
 }
 
 // the same lookup with the bracket search started at kstar (a bracket of a smaller or equal r);
@@ -133,9 +144,7 @@ __device__ __forceinline__ float cdf_inverse_from(const float* C, int CW, int m,
   int k = kstar;
   while (k < m - 1 && !(C[(k + 1) * CW] >= r)) ++k;
   kstar = k;
-  float c0 = C[k * CW], c1 = C[(k + 1) * CW];
-  float x = (float)k + (r - c0) / (c1 - c0);
-  return fminf(x, (float)m);
+  return spline_inverse(C, CW, m, r, k);
 }
 
 template <typename TI, bool INDICES>
@@ -151,16 +160,25 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
   bool act = c < g.ncols;
   float s = (float)st->ot_shift;
   int ib = act ? col_base(c, g.inner, g.img_ostride) : 0;
-  // four rows' loads in flight per thread
-#pragma unroll 4
-  for (int k = ty; k < m; k += blockDim.y) {
-    float a = 0.f, b = 0.f;
-    if (act) {
-      a = __fadd_rn(ldf(Ip + ib + k * g.inner), s);
-      b = __fadd_rn(ldf(Im + ib + k * g.inner), s);
+  // eight rows of both images in flight per thread (loads first, then the shifted stores)
+  const int RY = blockDim.y;
+  for (int k0 = ty; k0 < m; k0 += 8 * RY) {
+    float a[8], b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u * RY;
+      const bool in = act && k < m;
+      a[u] = in ? ldf(Ip + ib + k * g.inner) : 0.f;
+      b[u] = in ? ldf(Im + ib + k * g.inner) : 0.f;
     }
-    Cp[(k + 1) * CW + tx] = a;
-    Cm[(k + 1) * CW + tx] = b;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u * RY;
+      if (k < m) {
+        Cp[(k + 1) * CW + tx] = act ? __fadd_rn(a[u], s) : 0.f;
+        Cm[(k + 1) * CW + tx] = act ? __fadd_rn(b[u], s) : 0.f;
+      }
+    }
   }
   __syncthreads();
   // cumulative sums, single precision, left to right: row 0 of threads scans I+, row 1 I-
@@ -224,26 +242,74 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
   }
 }
 
-// one axis of the separable Gaussian: out_k = w1 x_{k-s} + w0 x_k + w1 x_{k+s} along axis AX of
-// the field (caller's layout), replicate boundary; one node per thread
-template <int AX>
+// The 3x3x3 Gaussian in one launch.  CTA (bx, by, bz) owns the brick of BZ x BY x BX nodes at
+// (bz BZ, by BY, bx BX) (axes 0, 1, 2 of the field, caller's layout); it stages the brick and a
+// one-node halo on every side, coordinates clamped into the field (replicate boundary), then
+//   A = pass along axis 0 over the staged brick's BZ planes, all halo rows and columns,
+//   B = pass along axis 1 of A (into the staging buffer), all halo columns,
+//   out = pass along axis 2 of B,
+// each value y = w1 x_- + w0 x + w1 x_+ rounded to single precision, as three one-axis passes
+// through global memory would compute it.  Nodes of the brick outside the field are computed
+// from clamped copies and not stored.
+constexpr int kBlurX = 32, kBlurY = 8, kBlurZ = 4;
+constexpr int kBlurHX = kBlurX + 2, kBlurHY = kBlurY + 2, kBlurHZ = kBlurZ + 2;
+static_assert(kBlurX * kBlurY == kBlock, "one thread per node of a brick plane");
+
 __global__ void __launch_bounds__(kBlock)
-k_blur_axis(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
-  const int T = gridDim.x * blockDim.x;
-  const int s = g.fs[AX], ext = g.fe[AX];
-  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < g.nf; n += T) {
-    int i;
-    if (AX == 0) {
-      i = (int)fdiv((unsigned)n, g.div0);
-    } else if (AX == 1) {
-      const unsigned row = fdiv((unsigned)n, g.divfe2);
-      i = (int)(row - fdiv(row, g.divfe1) * (unsigned)g.fe[1]);
-    } else {
-      i = n - (int)fdiv((unsigned)n, g.divfe2) * g.fe[2];
+k_blur3(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
+  __shared__ float X[kBlurHZ * kBlurHY * kBlurHX];   // staged brick; later B
+  __shared__ float A[kBlurZ * kBlurHY * kBlurHX];
+  const int n0 = g.fe[0], n1 = g.fe[1], n2 = g.fe[2];
+  const int x0 = blockIdx.x * kBlurX, y0 = blockIdx.y * kBlurY, z0 = blockIdx.z * kBlurZ;
+  const int t = threadIdx.x;
+  constexpr int NX = kBlurHZ * kBlurHY * kBlurHX;
+  constexpr int LX = (NX + kBlock - 1) / kBlock;
+  // stage: every load of the thread in flight at once
+  float v[LX];
+#pragma unroll
+  for (int u = 0; u < LX; ++u) {
+    const int e = t + u * kBlock;
+    v[u] = 0.f;
+    if (e < NX) {
+      const int z = e / (kBlurHY * kBlurHX), r = e - z * (kBlurHY * kBlurHX);
+      const int y = r / kBlurHX, x = r - y * kBlurHX;
+      const int i0 = min(max(z0 - 1 + z, 0), n0 - 1);
+      const int i1 = min(max(y0 - 1 + y, 0), n1 - 1);
+      const int i2 = min(max(x0 - 1 + x, 0), n2 - 1);
+      v[u] = __ldg(in + ((long long)i0 * n1 + i1) * n2 + i2);
     }
-    const float xm = __ldg(in + (i > 0 ? n - s : n));
-    const float xp = __ldg(in + (i < ext - 1 ? n + s : n));
-    out[n] = w1 * xm + w0 * __ldg(in + n) + w1 * xp;
+  }
+#pragma unroll
+  for (int u = 0; u < LX; ++u)
+    if (t + u * kBlock < NX) X[t + u * kBlock] = v[u];
+  __syncthreads();
+  // axis 0: A[z][y][x] from planes z, z + 1, z + 2 of the staged brick
+  constexpr int NA = kBlurZ * kBlurHY * kBlurHX, PL = kBlurHY * kBlurHX;
+  for (int e = t; e < NA; e += kBlock) {
+    const float xm = X[e], xc = X[e + PL], xp = X[e + 2 * PL];
+    A[e] = w1 * xm + w0 * xc + w1 * xp;
+  }
+  __syncthreads();
+  // axis 1: B[z][y][x] (y < kBlurY) from rows y, y + 1, y + 2 of A, into X
+  constexpr int NB = kBlurZ * kBlurY * kBlurHX;
+  for (int e = t; e < NB; e += kBlock) {
+    const int z = e / (kBlurY * kBlurHX), r = e - z * (kBlurY * kBlurHX);
+    const int a = z * PL + r;   // A[z][y][x] with r = y * kBlurHX + x
+    const float xm = A[a], xc = A[a + kBlurHX], xp = A[a + 2 * kBlurHX];
+    X[e] = w1 * xm + w0 * xc + w1 * xp;
+  }
+  __syncthreads();
+  // axis 2: thread (tx, ty) writes nodes (z, ty, tx) of the brick, a warp per 32-node row
+  const int tx = t % kBlurX, ty = t / kBlurX;
+  const int i1 = y0 + ty, i2 = x0 + tx;
+  if (i1 >= n1 || i2 >= n2) return;
+#pragma unroll
+  for (int z = 0; z < kBlurZ; ++z) {
+    const int i0 = z0 + z;
+    if (i0 >= n0) break;
+    const int bidx = (z * kBlurY + ty) * kBlurHX + tx;
+    const float xm = X[bidx], xc = X[bidx + 1], xp = X[bidx + 2];
+    out[((long long)i0 * n1 + i1) * n2 + i2] = w1 * xm + w0 * xc + w1 * xp;
   }
 }
 
@@ -291,14 +357,13 @@ cudaError_t launch_ot(const Geo& g, int dtype, const void* Ip, const void* Im, f
              : ot_one<__half, false>(g, Ip, Im, b0, kp, km, w, s);
 }
 
-// three one-axis passes (axis 0, 1, 2): in -> out -> in -> out (in is scratch afterwards)
+// the three passes (axis 0, 1, 2) in one launch: in -> out (in is not modified)
 cudaError_t launch_blur(const Geo& g, float* in, float* out, cudaStream_t s) {
   double e = std::exp(-0.5);   // the sigma = 1 Gaussian at distance 1 voxel
   float w0 = (float)(1.0 / (1.0 + 2.0 * e)), w1 = (float)(e / (1.0 + 2.0 * e));
-  const int blocks = std::min(ceil_div(g.nf, kBlock), 148 * 8);
-  k_blur_axis<0><<<blocks, kBlock, 0, s>>>(g, in, out, w0, w1);
-  k_blur_axis<1><<<blocks, kBlock, 0, s>>>(g, out, in, w0, w1);
-  k_blur_axis<2><<<blocks, kBlock, 0, s>>>(g, in, out, w0, w1);
+  const dim3 grid(ceil_div(g.fe[2], kBlurX), ceil_div(g.fe[1], kBlurY), ceil_div(g.fe[0], kBlurZ));
+  if (grid.y > 65535u || grid.z > 65535u) return cudaErrorInvalidConfiguration;
+  k_blur3<<<grid, kBlock, 0, s>>>(g, in, out, w0, w1);
   return cudaGetLastError();
 }
 
