@@ -253,7 +253,7 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
 // from clamped copies and not stored.
 constexpr int kBlurX = 32, kBlurY = 8, kBlurZ = 4;
 constexpr int kBlurHX = kBlurX + 2, kBlurHY = kBlurY + 2, kBlurHZ = kBlurZ + 2;
-static_assert(kBlurX * kBlurY == kBlock, "one thread per node of a brick plane");
+static_assert(kBlurX * kBlurY == kBlock && kBlurX == 32, "a warp per brick row, a thread per node of a brick plane");
 
 __global__ void __launch_bounds__(kBlock)
 k_blur3(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
@@ -261,27 +261,34 @@ k_blur3(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, 
   __shared__ float A[kBlurZ * kBlurHY * kBlurHX];
   const int n0 = g.fe[0], n1 = g.fe[1], n2 = g.fe[2];
   const int x0 = blockIdx.x * kBlurX, y0 = blockIdx.y * kBlurY, z0 = blockIdx.z * kBlurZ;
-  const int t = threadIdx.x;
-  constexpr int NX = kBlurHZ * kBlurHY * kBlurHX;
-  constexpr int LX = (NX + kBlock - 1) / kBlock;
-  // stage: every load of the thread in flight at once
-  float v[LX];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  constexpr int NR = kBlurHZ * kBlurHY;                        // staged rows of the brick
+  constexpr int RW = (NR + kBlock / 32 - 1) / (kBlock / 32);                 // rows per warp
+  // stage: warp w loads rows w, w + 8, ... (a row: 32 nodes by the lanes, the 2 right-most by
+  // lanes 0 and 1), every load of the thread in flight at once
+  const int cx0 = min(max(x0 - 1 + lane, 0), n2 - 1), cx1 = min(x0 + 31 + lane, n2 - 1);
+  float v[RW], v2[RW];
 #pragma unroll
-  for (int u = 0; u < LX; ++u) {
-    const int e = t + u * kBlock;
+  for (int u = 0; u < RW; ++u) {
+    const int rr = warp + u * (kBlock / 32);
     v[u] = 0.f;
-    if (e < NX) {
-      const int z = e / (kBlurHY * kBlurHX), r = e - z * (kBlurHY * kBlurHX);
-      const int y = r / kBlurHX, x = r - y * kBlurHX;
-      const int i0 = min(max(z0 - 1 + z, 0), n0 - 1);
-      const int i1 = min(max(y0 - 1 + y, 0), n1 - 1);
-      const int i2 = min(max(x0 - 1 + x, 0), n2 - 1);
-      v[u] = __ldg(in + ((long long)i0 * n1 + i1) * n2 + i2);
+    v2[u] = 0.f;
+    if (rr < NR) {
+      const int z = rr / kBlurHY, y = rr - z * kBlurHY;
+      const int i0 = min(max(z0 - 1 + z, 0), n0 - 1), i1 = min(max(y0 - 1 + y, 0), n1 - 1);
+      const float* row = in + ((long long)i0 * n1 + i1) * n2;
+      v[u] = __ldg(row + cx0);
+      if (lane < 2) v2[u] = __ldg(row + cx1);
     }
   }
 #pragma unroll
-  for (int u = 0; u < LX; ++u)
-    if (t + u * kBlock < NX) X[t + u * kBlock] = v[u];
+  for (int u = 0; u < RW; ++u) {
+    const int rr = warp + u * (kBlock / 32);
+    if (rr < NR) {
+      X[rr * kBlurHX + lane] = v[u];
+      if (lane < 2) X[rr * kBlurHX + 32 + lane] = v2[u];
+    }
+  }
   __syncthreads();
   // axis 0: A[z][y][x] from planes z, z + 1, z + 2 of the staged brick
   constexpr int NA = kBlurZ * kBlurHY * kBlurHX, PL = kBlurHY * kBlurHX;
