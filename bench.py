@@ -732,7 +732,7 @@ def run_ours(args):
     # the other hot-path entry points, each timed alone (L2 flushed before every call) with its
     # minimal algorithmic bytes per node (4-byte floats; images 4 B per voxel and image):
     #   hysco_init_ot   read I+, I- (8 per voxel), write b (4 per node)         [shift, OT, blur]
-    #   hysco_hessvec   read v, d, e (12), write Hv (4)                        [to / from pitched]
+    #   hysco_hessvec   read v, d, e (12), write Hv (4)                        [one stencil kernel]
     #   hysco_precond   read r, d, e (12), write z (4): per-column tridiagonal factor and solve
     def table_row(ms, alg, launches):
         return {"launch_ms": ms, "alg_bytes_per_call": alg, "launches": launches,
@@ -742,7 +742,7 @@ def run_ours(args):
     hv_out, pc_out = torch.empty_like(b_out), torch.empty_like(b_out)
     kernels = {
         "hysco_init_ot": table_row(time_launches(lambda: h.init_ot(Ip, Im, out=bt)),
-                                   8 * nimg + 4 * nfld, "k_ot_shift, k_ot, k_blur"),
+                                   8 * nimg + 4 * nfld, "k_ot_shift, k_ot, k_blur3"),
     }
     h.eval(Ip, Im, b_out, grad=g, terms=terms)   # the linearisation the next two calls use
     kernels["hysco_hessvec"] = table_row(time_launches(lambda: h.hessvec(vv, out=hv_out)),
