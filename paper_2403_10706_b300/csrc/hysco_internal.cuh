@@ -250,20 +250,22 @@ __device__ bool grid_sum(float (&v)[K], float* partials, unsigned* counter, doub
   __syncthreads();
   if (!is_last) return false;
   __threadfence();
-  // value i is summed by warp i % nwarps: lane l takes blocks l, l + 32, ... in order (eight
-  // loads in flight, then their sums), then a fixed shuffle tree; double-float throughout
+  // value i is summed by warp i % nwarps: lane l takes blocks l, l + 32, ... in order (sixteen
+  // loads in flight, then their sums: one round trip for up to 512 blocks), then a fixed shuffle
+  // tree; double-float throughout
+  constexpr int NF = 16;
   const int warp = tid >> 5, lane = tid & 31, nwarps = block_threads() >> 5;
   for (int i = warp; i < K; i += nwarps) {
     df32 acc{0.f, 0.f};
-    for (int b0 = lane; b0 < nblk; b0 += 32 * 8) {
-      float x[8];
+    for (int b0 = lane; b0 < nblk; b0 += 32 * NF) {
+      float x[NF];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < NF; ++u) {
         const int b = b0 + 32 * u;
         x[u] = b < nblk ? __ldcg(partials + (long long)b * K + i) : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < NF; ++u)
         if (b0 + 32 * u < nblk) acc = df_add(acc, df32{x[u], 0.f});
     }
 #pragma unroll

@@ -10,10 +10,10 @@
 //   and C^{-1}(r) = k* + (r - C(k*)) / (C(k*+1) - C(k*)), capped at m.  Then
 //     b0_k = 1/4 [ (C+^{-1}(C-(k)) - k) - (C-^{-1}(C+(k)) - k) ].
 // k_blur3: the separable 3-tap weights [e^-1/2, 1, e^-1/2] / (1 + 2 e^-1/2) per axis (sigma = 1
-//   voxel), replicate boundary, as one launch: a CTA stages a brick of the field with a one-node
-//   halo in shared memory (clamped coordinates, so the halo replicates the boundary) and applies
-//   the passes along axis 0, 1 and 2 in that order, each pass's values rounded to single
-//   precision as three separate passes would round them.
+//   voxel), replicate boundary, as one launch: a CTA stages an 8 x 8 x 32 brick of the field with
+//   a one-node halo in shared memory (clamped coordinates, so the halo replicates the boundary)
+//   and applies the passes along axis 0, 1 and 2 in that order, each pass's values rounded to
+//   single precision as three separate passes would round them.
 #include <algorithm>
 #include <cmath>
 
@@ -251,9 +251,10 @@ k_ot(Geo g, const TI* __restrict__ Ip, const TI* __restrict__ Im, float* __restr
 // each value y = w1 x_- + w0 x + w1 x_+ rounded to single precision, as three one-axis passes
 // through global memory would compute it.  Nodes of the brick outside the field are computed
 // from clamped copies and not stored.
-constexpr int kBlurX = 32, kBlurY = 8, kBlurZ = 4;
+constexpr int kBlurX = 32, kBlurY = 8, kBlurZ = 8;
 constexpr int kBlurHX = kBlurX + 2, kBlurHY = kBlurY + 2, kBlurHZ = kBlurZ + 2;
-static_assert(kBlurX * kBlurY == kBlock && kBlurX == 32, "a warp per brick row, a thread per node of a brick plane");
+static_assert(kBlurX * kBlurY == kBlock && kBlurX == 32,
+              "a warp per brick row, a thread per node of a brick plane");
 
 __global__ void __launch_bounds__(kBlock)
 k_blur3(Geo g, const float* __restrict__ in, float* __restrict__ out, float w0, float w1) {
